@@ -1,0 +1,174 @@
+/*
+ * bpimd.h -- C ABI of the GB300 (sm_103a) bosonic PIMD exchange library.
+ *
+ * The library evaluates the bosonic exchange potential V_B = V^{[1,N]} of N
+ * ring polymers with P beads each, and its force on every bead, following
+ * Feldman & Hirshberg, "Quadratic Scaling Bosonic Path Integral Molecular
+ * Dynamics":
+ *   - cycle energies E^{[u,v]}  (Eq. Ek, Eq. e-interior, Eq. e-recurrence-step/base)
+ *   - forward potentials V^{[1,v]}  (Eq. our-forward-potential-recurrence)
+ *   - backward potentials V^{[u,N]} (Eq. backward-potential-recursion)
+ *   - connection probabilities Pr[l -> l'] (Eq. direct-link-probability,
+ *     Eq. close-cycle-probability, Lemma zero-connection-probability)
+ *   - forces: interior beads (Eq. intermediate-bead-force), beads 1 and P
+ *     (Eq. force-on-1-sum-neighbors, Eq. force-on-P-sum-neighbors), i.e.
+ *     Algorithm 1 ("Fast PIMD-B") of the appendix.
+ * and, for molecular dynamics, a Langevin/velocity-Verlet step that adds the
+ * physical potential U-bar = (1/P) sum_j U(r_1^j..r_N^j) of Eq.
+ * int-of-sum-all-permutations (harmonic trap plus a same-bead pair potential).
+ *
+ * Every computation runs in this library's own CUDA kernels on one GPU; there
+ * is no CPU fallback.  All entry points return an int status (BPIMD_OK = 0 or a
+ * negative BPIMD_ERR_* code) and never abort the process.
+ *
+ * Memory layout shared by all calls
+ *   positions, forces, velocities: [N][P][3] row-major float64, i.e. bead j
+ *   (0-based) of particle l (0-based) coordinate d at index (l*P + j)*3 + d.
+ *   Device pointers must be 16-byte aligned.  The caller owns these buffers;
+ *   the library never frees or retains them beyond the call.
+ *
+ * Streams and synchronisation
+ *   A context is bound to one CUDA stream given at creation (NULL = the legacy
+ *   default stream).  Calls that take device pointers enqueue their work on
+ *   that stream and return without waiting for it, unless stated otherwise;
+ *   the caller orders its own use of outputs with that stream.  Calls whose
+ *   name ends in _host take host pointers, copy in, compute, copy out and
+ *   synchronise the stream before returning.  A context must not be used from
+ *   two host threads at once.
+ *
+ * Errors
+ *   Argument errors are detected on the host before anything is enqueued
+ *   (BPIMD_ERR_ARG).  Device-side conditions (non-finite positions or results,
+ *   an expired bounded wait inside a kernel) are recorded in a device status
+ *   word; they surface as BPIMD_ERR_NONFINITE / BPIMD_ERR_TIMEOUT from the
+ *   next call that synchronises (the _host calls, bpimd_sync, bpimd_step).
+ */
+#ifndef BPIMD_H
+#define BPIMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define BPIMD_OK 0
+#define BPIMD_ERR_ARG (-1)       /* invalid size, parameter or null pointer      */
+#define BPIMD_ERR_NONFINITE (-2) /* NaN/Inf in positions or in a result          */
+#define BPIMD_ERR_CUDA (-3)      /* a CUDA runtime call failed                  */
+#define BPIMD_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired          */
+#define BPIMD_ERR_NOMEM (-5)     /* device or host allocation failed            */
+#define BPIMD_ERR_STATE (-6)     /* call not valid for this context's state     */
+
+/* ---------------------------------------------------------------- precision */
+/* BPIMD_FP64: every step in float64.
+ * BPIMD_MIXED: bead differences, per-particle spring sums and the per-pair
+ * Boltzmann factors exp(-beta (1/2) m w_P^2 |r_v^P - r_u^1|^2) in float32; the
+ * prefix sums of spring energies, the cycle-energy differences, both
+ * recursions, the probability normalisation and all force accumulations in
+ * float64. */
+#define BPIMD_FP64 0
+#define BPIMD_MIXED 1
+
+/* --------------------------------------------------------- pair potentials */
+#define BPIMD_PAIR_NONE 0
+#define BPIMD_PAIR_GAUSSIAN 1 /* g exp(-r^2 / (2 s^2)) between same-index beads */
+#define BPIMD_PAIR_LJ 2       /* 4 eps ((sigma/r)^12 - (sigma/r)^6), cut at rc   */
+
+typedef struct bpimd_ctx bpimd_ctx; /* opaque; owns the device workspace */
+
+/* Problem description (Eq. eperm and Eq. int-of-sum-all-permutations).
+ * N >= 1 particles, P >= 2 beads (the bead-1 / bead-P formulas need two
+ * distinct exterior beads).  m, omega_P, beta > 0 and finite; omega_P is passed
+ * explicitly (sqrt(P)/(beta hbar) in the paper's convention).  The fields
+ * after `precision` are used only by bpimd_step and may be zero otherwise. */
+typedef struct {
+  int32_t N;
+  int32_t P;
+  double m;
+  double omega_P;
+  double beta;
+  int32_t precision; /* BPIMD_FP64 or BPIMD_MIXED */
+  int32_t flags;     /* reserved, must be 0 */
+  /* molecular dynamics (bpimd_step) */
+  double dt;         /* time step                                   */
+  double gamma;      /* Langevin friction (0 = NVE)                  */
+  double kT_bead;    /* thermostat temperature per bead: P/beta for PIMD, or 0 => P/beta */
+  double omega0;     /* isotropic harmonic trap frequency (0 = none) */
+  int32_t pair_type; /* BPIMD_PAIR_*                                 */
+  int32_t pad0;
+  double pair_a;     /* Gaussian g  | LJ epsilon                      */
+  double pair_b;     /* Gaussian s  | LJ sigma                        */
+  double pair_rc;    /* LJ cutoff (0 = no cutoff)                     */
+  double box_L;      /* cubic periodic box side (0 = open boundaries) */
+  uint64_t seed;     /* counter-based RNG key for the thermostat      */
+} bpimd_config;
+
+/* Create a context for one system.  Validates cfg (BPIMD_ERR_ARG), allocates
+ * the O(N^2) workspace on the current CUDA device (BPIMD_ERR_NOMEM), binds
+ * `cuda_stream` (a cudaStream_t, NULL = default stream).  On error *out is set
+ * to NULL.  Destroy with bpimd_destroy. */
+int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream);
+
+/* Release all device and host memory of the context.  NULL-safe.
+ * Synchronises the context's stream first. */
+int bpimd_destroy(bpimd_ctx *ctx);
+
+/* Exchange potential and forces, Algorithm 1 (appendix "Algorithm Pseudocode").
+ *   positions : device, [N][P][3] float64, read only.
+ *   V_B       : device pointer to one float64; receives V^{[1,N]}.  May be NULL.
+ *   forces    : device, [N][P][3] float64; overwritten with -grad V^{[1,N]}
+ *               (interior springs included; no physical potential).
+ * Enqueued on the context stream; asynchronous. */
+int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions,
+                                 double *V_B, double *forces);
+
+/* Same computation with HOST buffers: copies positions in, computes, copies
+ * V_B (may be NULL) and forces out, synchronises.  Host buffers may be pageable
+ * or pinned; pinned memory is faster. */
+int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions,
+                                      double *V_B, double *forces);
+
+/* Wait for the context stream and report any device-side status recorded by
+ * earlier calls (BPIMD_ERR_NONFINITE / BPIMD_ERR_TIMEOUT), clearing it. */
+int bpimd_sync(bpimd_ctx *ctx);
+
+/* Intermediate results of the last bpimd_exchange_energy_forces* call, copied
+ * to HOST arrays (synchronises).  Any pointer may be NULL.
+ *   V_fwd : N+1 float64, V_fwd[v] = V^{[1,v]} (V_fwd[0] = 0).
+ *   V_bwd : N+1 float64, V_bwd[u-1] = V^{[u,N]} for u = 1..N+1 (V_bwd[N] = 0).
+ *   Eint  : N float64, E_int^{(l)} (Eq. e-interior).
+ * For testing and diagnostics; O(N) data. */
+int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *Eint);
+
+/* Dense connection-probability matrix of the last evaluation, recomputed on
+ * the device from the stored O(N) state: M[(l-1)*N + (l'-1)] = Pr[l -> l']
+ * (0 for l' > l+1).  M is a DEVICE buffer of N*N float64 owned by the caller.
+ * O(N^2) memory; intended for tests and diagnostics.  Asynchronous. */
+int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
+
+/* Run `nsteps` molecular-dynamics steps in place (BAOAB Langevin splitting:
+ * half kick, half drift, Ornstein-Uhlenbeck velocity update with a
+ * counter-based Philox RNG, half drift, force evaluation, half kick), with the
+ * full force = exchange force + harmonic trap + pair potential of cfg.
+ *   positions, velocities : device [N][P][3] float64, updated in place.
+ *   energies : optional device array of 4 float64 receiving, after the last
+ *              step: [0] V_B, [1] U-bar, [2] kinetic energy of the beads,
+ *              [3] primitive energy estimator (kinetic part + U-bar).
+ * The first call captures the step into a CUDA graph that later calls replay.
+ * Synchronises and returns device status. */
+int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
+               int32_t nsteps, double *energies);
+
+/* Human-readable text for a status code (static storage). */
+const char *bpimd_status_string(int status);
+
+/* Library version string (static storage). */
+const char *bpimd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPIMD_H */

@@ -14,6 +14,9 @@ Contents
   the representative map G (Definition representative-permutation and
   Definition forward-potential), and the sum over the 2^(N-1) representative
   permutations (appendix "Some Combinatorics of Permutations").
+* ``long_double``: the same C routines compiled with long double arithmetic, a
+  higher-precision referee for cases where float64 rounding of the oracle itself
+  approaches the comparison tolerances.
 * ``harmonic``: the closed-form canonical energy of N non-interacting bosons in a
   harmonic trap at finite P.
 
@@ -28,155 +31,205 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
-
 SHIFT_MIN_ALL = 0   # Eq. full-elong
 SHIFT_TWO_TERM = 1  # Eq. original-elong
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        path = _build.build()
-        lib = ctypes.CDLL(path)
-        dp = ctypes.POINTER(ctypes.c_double)
-        i, d = ctypes.c_int, ctypes.c_double
-        sig = {
-            "ora_interior_energies": [i, i, d, d, dp, dp],
-            "ora_cycle_energies": [i, i, d, d, dp, dp],
-            "ora_cycle_energies_direct": [i, i, d, d, dp, dp],
-            "ora_forward_potentials": [i, d, dp, i, dp],
-            "ora_backward_potentials": [i, d, dp, i, dp],
-            "ora_backward_potentials_definition": [i, d, dp, dp],
-            "ora_connection_probabilities": [i, d, dp, dp, dp, dp],
-            "ora_forces": [i, i, d, d, dp, dp, dp],
-            "ora_fast_pimdb": [i, i, d, d, d, dp, dp, dp, dp, dp, dp],
-            "ora_original_pimdb": [i, i, d, d, d, dp, dp, dp],
-            "ora_expected_spring_energy": [i, i, d, d, dp, dp, dp],
-        }
-        for name, args in sig.items():
-            fn = getattr(lib, name)
-            fn.argtypes = args
-            fn.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+class _Oracle:
+    """The C routines for one floating-point type (float64 or long double)."""
+
+    def __init__(self, path_attr, dtype, ctype):
+        self._path_attr = path_attr
+        self.dtype = dtype
+        self._ctype = ctype
+        self._lib = None
+
+    def lib(self):
+        if self._lib is None:
+            _build.build()
+            lib = ctypes.CDLL(getattr(_build, self._path_attr))
+            rp = ctypes.POINTER(self._ctype)
+            i, r = ctypes.c_int, self._ctype
+            sig = {
+                "ora_interior_energies": [i, i, r, r, rp, rp],
+                "ora_cycle_energies": [i, i, r, r, rp, rp],
+                "ora_cycle_energies_direct": [i, i, r, r, rp, rp],
+                "ora_forward_potentials": [i, r, rp, i, rp],
+                "ora_backward_potentials": [i, r, rp, i, rp],
+                "ora_backward_potentials_definition": [i, r, rp, rp],
+                "ora_connection_probabilities": [i, r, rp, rp, rp, rp],
+                "ora_forces": [i, i, r, r, rp, rp, rp],
+                "ora_fast_pimdb": [i, i, r, r, r, rp, rp, rp, rp, rp, rp],
+                "ora_original_pimdb": [i, i, r, r, r, rp, rp, rp],
+                "ora_expected_spring_energy": [i, i, r, r, rp, rp, rp],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            self._lib = lib
+        return self._lib
+
+    def _p(self, a):
+        return None if a is None else a.ctypes.data_as(ctypes.POINTER(self._ctype))
+
+    def _arr(self, a):
+        return np.ascontiguousarray(a, dtype=self.dtype)
+
+    def _pos(self, pos):
+        pos = self._arr(pos)
+        if pos.ndim != 3 or pos.shape[2] != 3:
+            raise ValueError("positions must be [N][P][3]")
+        return pos
+
+    @staticmethod
+    def _check(rc, name):
+        if rc != 0:
+            raise ValueError(f"{name}: invalid arguments")
+
+    def interior_energies(self, pos, m, omega_P):
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        out = np.empty(N, dtype=self.dtype)
+        self._check(self.lib().ora_interior_energies(N, P, m, omega_P, self._p(pos), self._p(out)),
+                    "interior_energies")
+        return out
+
+    def cycle_energies(self, pos, m, omega_P, direct=False):
+        """E[u-1, v-1] = E^{[u,v]} (u <= v); Algorithm 1's recurrence, or Eq. Ek if direct."""
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        E = np.zeros((N, N), dtype=self.dtype)
+        fn = self.lib().ora_cycle_energies_direct if direct else self.lib().ora_cycle_energies
+        self._check(fn(N, P, m, omega_P, self._p(pos), self._p(E)), "cycle_energies")
+        return E
+
+    def forward_potentials(self, E, beta, shift=SHIFT_MIN_ALL):
+        E = self._arr(E)
+        N = E.shape[0]
+        V = np.empty(N + 1, dtype=self.dtype)
+        self._check(self.lib().ora_forward_potentials(N, beta, self._p(E), shift, self._p(V)),
+                    "forward_potentials")
+        return V
+
+    def backward_potentials(self, E, beta, shift=SHIFT_MIN_ALL):
+        E = self._arr(E)
+        N = E.shape[0]
+        W = np.empty(N + 1, dtype=self.dtype)
+        self._check(self.lib().ora_backward_potentials(N, beta, self._p(E), shift, self._p(W)),
+                    "backward_potentials")
+        return W
+
+    def backward_potentials_definition(self, E, beta):
+        E = self._arr(E)
+        N = E.shape[0]
+        W = np.empty(N + 1, dtype=self.dtype)
+        self._check(self.lib().ora_backward_potentials_definition(N, beta, self._p(E), self._p(W)),
+                    "backward_potentials_definition")
+        return W
+
+    def connection_probabilities(self, E, V, W, beta):
+        E, V, W = self._arr(E), self._arr(V), self._arr(W)
+        N = E.shape[0]
+        M = np.empty((N, N), dtype=self.dtype)
+        self._check(self.lib().ora_connection_probabilities(N, beta, self._p(E), self._p(V),
+                                                            self._p(W), self._p(M)),
+                    "connection_probabilities")
+        return M
+
+    def forces(self, pos, M, m, omega_P):
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        M = self._arr(M)
+        F = np.empty_like(pos)
+        self._check(self.lib().ora_forces(N, P, m, omega_P, self._p(pos), self._p(M), self._p(F)),
+                    "forces")
+        return F
+
+    def fast_pimdb(self, pos, m, omega_P, beta, full=False):
+        """Algorithm 1.  Returns (V_B, F) or, with full=True, (V_B, F, V, W, M)."""
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        F = np.empty_like(pos)
+        VB = np.zeros(1, dtype=self.dtype)
+        V = np.empty(N + 1, dtype=self.dtype)
+        W = np.empty(N + 1, dtype=self.dtype)
+        M = np.empty((N, N), dtype=self.dtype) if full else None
+        rc = self.lib().ora_fast_pimdb(N, P, m, omega_P, beta, self._p(pos), self._p(VB),
+                                       self._p(F), self._p(V), self._p(W), self._p(M))
+        self._check(rc, "fast_pimdb")
+        if full:
+            return VB[0], F, V, W, M
+        return VB[0], F
+
+    def original_pimdb(self, pos, m, omega_P, beta):
+        """Algorithm 2 (O(P N^3)).  Returns (V_B, F)."""
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        F = np.empty_like(pos)
+        VB = np.zeros(1, dtype=self.dtype)
+        self._check(self.lib().ora_original_pimdb(N, P, m, omega_P, beta, self._p(pos),
+                                                  self._p(VB), self._p(F)), "original_pimdb")
+        return VB[0], F
+
+    def expected_spring_energy(self, pos, M, m, omega_P):
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        M = self._arr(M)
+        out = np.zeros(1, dtype=self.dtype)
+        self._check(self.lib().ora_expected_spring_energy(N, P, m, omega_P, self._p(pos),
+                                                          self._p(M), self._p(out)),
+                    "expected_spring_energy")
+        return out[0]
 
 
-def _p(a):
-    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-
-
-def _pos(pos):
-    pos = np.ascontiguousarray(pos, dtype=np.float64)
-    if pos.ndim != 3 or pos.shape[2] != 3:
-        raise ValueError("positions must be [N][P][3]")
-    return pos
-
-
-def _check(rc, name):
-    if rc != 0:
-        raise ValueError(f"{name}: invalid arguments")
+#: float64 oracle (the default)
+float64 = _Oracle("LIB", np.float64, ctypes.c_double)
+#: the same routines in long double: the higher-precision referee
+long_double = _Oracle("LIB_LD", np.longdouble, ctypes.c_longdouble)
 
 
 def interior_energies(pos, m, omega_P):
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    out = np.empty(N)
-    _check(_load().ora_interior_energies(N, P, m, omega_P, _p(pos), _p(out)), "interior_energies")
-    return out
+    return float64.interior_energies(pos, m, omega_P)
 
 
 def cycle_energies(pos, m, omega_P, direct=False):
-    """E[u-1, v-1] = E^{[u,v]} (u <= v); Algorithm 1's recurrence, or Eq. Ek if direct."""
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    E = np.zeros((N, N))
-    fn = _load().ora_cycle_energies_direct if direct else _load().ora_cycle_energies
-    _check(fn(N, P, m, omega_P, _p(pos), _p(E)), "cycle_energies")
-    return E
+    return float64.cycle_energies(pos, m, omega_P, direct)
 
 
 def forward_potentials(E, beta, shift=SHIFT_MIN_ALL):
-    E = np.ascontiguousarray(E, dtype=np.float64)
-    N = E.shape[0]
-    V = np.empty(N + 1)
-    _check(_load().ora_forward_potentials(N, beta, _p(E), shift, _p(V)), "forward_potentials")
-    return V
+    return float64.forward_potentials(E, beta, shift)
 
 
 def backward_potentials(E, beta, shift=SHIFT_MIN_ALL):
-    E = np.ascontiguousarray(E, dtype=np.float64)
-    N = E.shape[0]
-    W = np.empty(N + 1)
-    _check(_load().ora_backward_potentials(N, beta, _p(E), shift, _p(W)), "backward_potentials")
-    return W
+    return float64.backward_potentials(E, beta, shift)
 
 
 def backward_potentials_definition(E, beta):
-    E = np.ascontiguousarray(E, dtype=np.float64)
-    N = E.shape[0]
-    W = np.empty(N + 1)
-    _check(_load().ora_backward_potentials_definition(N, beta, _p(E), _p(W)),
-           "backward_potentials_definition")
-    return W
+    return float64.backward_potentials_definition(E, beta)
 
 
 def connection_probabilities(E, V, W, beta):
-    E = np.ascontiguousarray(E, dtype=np.float64)
-    N = E.shape[0]
-    V = np.ascontiguousarray(V, dtype=np.float64)
-    W = np.ascontiguousarray(W, dtype=np.float64)
-    M = np.empty((N, N))
-    _check(_load().ora_connection_probabilities(N, beta, _p(E), _p(V), _p(W), _p(M)),
-           "connection_probabilities")
-    return M
+    return float64.connection_probabilities(E, V, W, beta)
 
 
 def forces(pos, M, m, omega_P):
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    M = np.ascontiguousarray(M, dtype=np.float64)
-    F = np.empty_like(pos)
-    _check(_load().ora_forces(N, P, m, omega_P, _p(pos), _p(M), _p(F)), "forces")
-    return F
+    return float64.forces(pos, M, m, omega_P)
 
 
 def fast_pimdb(pos, m, omega_P, beta, full=False):
-    """Algorithm 1.  Returns (V_B, F) or, with full=True, (V_B, F, V, W, M)."""
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    F = np.empty_like(pos)
-    VB = ctypes.c_double()
-    V = np.empty(N + 1)
-    W = np.empty(N + 1)
-    M = np.empty((N, N)) if full else None
-    rc = _load().ora_fast_pimdb(N, P, m, omega_P, beta, _p(pos), ctypes.byref(VB), _p(F),
-                                _p(V), _p(W), _p(M) if full else None)
-    _check(rc, "fast_pimdb")
-    if full:
-        return VB.value, F, V, W, M
-    return VB.value, F
+    """Algorithm 1 in float64.  Returns (V_B, F) or (V_B, F, V, W, M)."""
+    out = float64.fast_pimdb(pos, m, omega_P, beta, full)
+    return (float(out[0]),) + tuple(out[1:])
 
 
 def original_pimdb(pos, m, omega_P, beta):
-    """Algorithm 2 (O(P N^3)).  Returns (V_B, F)."""
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    F = np.empty_like(pos)
-    VB = ctypes.c_double()
-    _check(_load().ora_original_pimdb(N, P, m, omega_P, beta, _p(pos), ctypes.byref(VB), _p(F)),
-           "original_pimdb")
-    return VB.value, F
+    VB, F = float64.original_pimdb(pos, m, omega_P, beta)
+    return float(VB), F
 
 
 def expected_spring_energy(pos, M, m, omega_P):
-    pos = _pos(pos)
-    N, P, _ = pos.shape
-    M = np.ascontiguousarray(M, dtype=np.float64)
-    out = ctypes.c_double()
-    _check(_load().ora_expected_spring_energy(N, P, m, omega_P, _p(pos), _p(M), ctypes.byref(out)),
-           "expected_spring_energy")
-    return out.value
+    return float(float64.expected_spring_energy(pos, M, m, omega_P))
 
 
 def library_path():

@@ -18,12 +18,24 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef ORA_LONG_DOUBLE
+#define EXP expl
+#define LOG logl
+#define EXPM1 expm1l
+#define INF_REAL HUGE_VALL
+#else
+#define EXP exp
+#define LOG log
+#define EXPM1 expm1
+#define INF_REAL HUGE_VAL
+#endif
+
 /* bead j of particle l, coordinate d (1-based l, j; 0-based d) */
 #define BEAD(pos, P, l, j) (&(pos)[((size_t)((l) - 1) * (size_t)(P) + (size_t)((j) - 1)) * 3])
 #define EIDX(N, u, v) ((size_t)((u) - 1) * (size_t)(N) + (size_t)((v) - 1))
 
-static double sqdist(const double *a, const double *b) {
-  double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+static ora_real sqdist(const ora_real *a, const ora_real *b) {
+  ora_real dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
   return dx * dx + dy * dy + dz * dz;
 }
 
@@ -31,12 +43,12 @@ static int bad_args(int N, int P) { return N < 1 || P < 2; }
 
 /* Eq. e-interior: E_int^{(l)} = (1/2) m w_P^2 sum_{j=1}^{P-1} (r_l^{j+1} - r_l^j)^2.
  * The spring from bead P is not part of it. */
-int ora_interior_energies(int N, int P, double m, double omega_P,
-                          const double *pos, double *Eint) {
+int ora_interior_energies(int N, int P, ora_real m, ora_real omega_P,
+                          const ora_real *pos, ora_real *Eint) {
   if (bad_args(N, P) || !pos || !Eint) return -1;
-  const double half_k = 0.5 * m * omega_P * omega_P;
+  const ora_real half_k = 0.5 * m * omega_P * omega_P;
   for (int l = 1; l <= N; ++l) {
-    double s = 0.0;
+    ora_real s = 0.0;
     for (int j = 1; j <= P - 1; ++j) s += sqdist(BEAD(pos, P, l, j + 1), BEAD(pos, P, l, j));
     Eint[l - 1] = half_k * s;
   }
@@ -49,11 +61,11 @@ int ora_interior_energies(int N, int P, double m, double omega_P,
  *                     + (1/2)k (r_u^P - r_{u+1}^1)^2 + E_int^{(u)}
  *                     + (1/2)k (r_v^P - r_u^1)^2                 (Eq. e-recurrence-step)
  * with (1/2)k = (1/2) m w_P^2. */
-int ora_cycle_energies(int N, int P, double m, double omega_P,
-                       const double *pos, double *E) {
+int ora_cycle_energies(int N, int P, ora_real m, ora_real omega_P,
+                       const ora_real *pos, ora_real *E) {
   if (bad_args(N, P) || !pos || !E) return -1;
-  const double half_k = 0.5 * m * omega_P * omega_P;
-  double *Eint = (double *)malloc(sizeof(double) * (size_t)N);
+  const ora_real half_k = 0.5 * m * omega_P * omega_P;
+  ora_real *Eint = (ora_real *)malloc(sizeof(ora_real) * (size_t)N);
   if (!Eint) return -1;
   ora_interior_energies(N, P, m, omega_P, pos, Eint);
   for (int v = 1; v <= N; ++v) {
@@ -72,16 +84,16 @@ int ora_cycle_energies(int N, int P, double m, double omega_P,
 
 /* Eq. Ek with the ring through u..v: E^{[u,v]} = (1/2)k sum_{l=u}^{v} sum_{j=1}^{P}
  * (r_l^{j+1} - r_l^j)^2 where r_l^{P+1} = r_{l+1}^1, except r_v^{P+1} = r_u^1. */
-int ora_cycle_energies_direct(int N, int P, double m, double omega_P,
-                              const double *pos, double *E) {
+int ora_cycle_energies_direct(int N, int P, ora_real m, ora_real omega_P,
+                              const ora_real *pos, ora_real *E) {
   if (bad_args(N, P) || !pos || !E) return -1;
-  const double half_k = 0.5 * m * omega_P * omega_P;
+  const ora_real half_k = 0.5 * m * omega_P * omega_P;
   for (int v = 1; v <= N; ++v) {
     for (int u = 1; u <= v; ++u) {
-      double s = 0.0;
+      ora_real s = 0.0;
       for (int l = u; l <= v; ++l) {
         for (int j = 1; j <= P; ++j) {
-          const double *next;
+          const ora_real *next;
           if (j < P) next = BEAD(pos, P, l, j + 1);
           else if (l < v) next = BEAD(pos, P, l + 1, 1);
           else next = BEAD(pos, P, u, 1);
@@ -96,86 +108,86 @@ int ora_cycle_energies_direct(int N, int P, double m, double omega_P,
 
 /* Eq. our-forward-potential-recurrence, shifted as in the Numerical Stability
  * section:  V^{[1,v]} = Et - (1/beta) ln[(1/v) sum_{k=1}^{v}
- *                          exp(-beta (V^{[1,v-k]} + E^{[v-k+1,v]} - Et))],
+ *                          EXP(-beta (V^{[1,v-k]} + E^{[v-k+1,v]} - Et))],
  * V^{[1,0]} = 0.  Et is Eq. full-elong (min over the v terms) or Eq.
  * original-elong (min of E^{[1,v]} and V^{[1,v-1]} + E^{[v,v]}). */
-int ora_forward_potentials(int N, double beta, const double *E, int shift_mode,
-                           double *V) {
+int ora_forward_potentials(int N, ora_real beta, const ora_real *E, int shift_mode,
+                           ora_real *V) {
   if (N < 1 || !(beta > 0.0) || !E || !V) return -1;
   V[0] = 0.0;
   for (int v = 1; v <= N; ++v) {
-    double Et;
+    ora_real Et;
     if (shift_mode == ORA_SHIFT_TWO_TERM) {
-      double a = E[EIDX(N, 1, v)], b = V[v - 1] + E[EIDX(N, v, v)];
+      ora_real a = E[EIDX(N, 1, v)], b = V[v - 1] + E[EIDX(N, v, v)];
       Et = a < b ? a : b;
     } else {
-      Et = INFINITY;
+      Et = INF_REAL;
       for (int k = 1; k <= v; ++k) {
-        double t = V[v - k] + E[EIDX(N, v - k + 1, v)];
+        ora_real t = V[v - k] + E[EIDX(N, v - k + 1, v)];
         if (t < Et) Et = t;
       }
     }
-    double s = 0.0;
+    ora_real s = 0.0;
     for (int k = 1; k <= v; ++k)
-      s += exp(-beta * (V[v - k] + E[EIDX(N, v - k + 1, v)] - Et));
-    V[v] = Et - (1.0 / beta) * log(s / (double)v);
+      s += EXP(-beta * (V[v - k] + E[EIDX(N, v - k + 1, v)] - Et));
+    V[v] = Et - (1.0 / beta) * LOG(s / (ora_real)v);
   }
   return 0;
 }
 
 /* Eq. backward-potential-recursion (Theorem backward-recurrence), shifted:
- *   V^{[u,N]} = Et - (1/beta) ln[ sum_{l=u}^{N} (1/l) exp(-beta (E^{[u,l]}
+ *   V^{[u,N]} = Et - (1/beta) ln[ sum_{l=u}^{N} (1/l) EXP(-beta (E^{[u,l]}
  *                                   + V^{[l+1,N]} - Et)) ],   V^{[N+1,N]} = 0,
  * Et = min over the terms (Eq. full-elong) or the two-term form of Eq.
  * original-elong (E^{[u,u]} + V^{[u+1,N]} and E^{[u,N]}). */
-int ora_backward_potentials(int N, double beta, const double *E, int shift_mode,
-                            double *W) {
+int ora_backward_potentials(int N, ora_real beta, const ora_real *E, int shift_mode,
+                            ora_real *W) {
   if (N < 1 || !(beta > 0.0) || !E || !W) return -1;
   /* W[u-1] holds V^{[u,N]} */
   W[N] = 0.0;
   for (int u = N; u >= 1; --u) {
-    double Et;
+    ora_real Et;
     if (shift_mode == ORA_SHIFT_TWO_TERM) {
-      double a = E[EIDX(N, u, u)] + W[u], b = E[EIDX(N, u, N)];
+      ora_real a = E[EIDX(N, u, u)] + W[u], b = E[EIDX(N, u, N)];
       Et = a < b ? a : b;
     } else {
-      Et = INFINITY;
+      Et = INF_REAL;
       for (int l = u; l <= N; ++l) {
-        double t = E[EIDX(N, u, l)] + W[l];
+        ora_real t = E[EIDX(N, u, l)] + W[l];
         if (t < Et) Et = t;
       }
     }
-    double s = 0.0;
+    ora_real s = 0.0;
     for (int l = u; l <= N; ++l)
-      s += (1.0 / (double)l) * exp(-beta * (E[EIDX(N, u, l)] + W[l] - Et));
-    W[u - 1] = Et - (1.0 / beta) * log(s);
+      s += (1.0 / (ora_real)l) * EXP(-beta * (E[EIDX(N, u, l)] + W[l] - Et));
+    W[u - 1] = Et - (1.0 / beta) * LOG(s);
   }
   return 0;
 }
 
 /* Definition backward-potential, evaluated literally: for each u,
- *   exp(-beta V^{[u,v]}) = (1/v) sum_{k=1}^{v-u+1} exp(-beta (V^{[u,v-k]} + E^{[v-k+1,v]}))
- * for v = u..N with exp(-beta V^{[u,u-1]}) = 1; then V^{[u,N]} is the v = N value.
+ *   EXP(-beta V^{[u,v]}) = (1/v) sum_{k=1}^{v-u+1} EXP(-beta (V^{[u,v-k]} + E^{[v-k+1,v]}))
+ * for v = u..N with EXP(-beta V^{[u,u-1]}) = 1; then V^{[u,N]} is the v = N value.
  * O(N^2) per u, O(N^3) overall.  Same min-shift as the forward recursion. */
-int ora_backward_potentials_definition(int N, double beta, const double *E,
-                                       double *W) {
+int ora_backward_potentials_definition(int N, ora_real beta, const ora_real *E,
+                                       ora_real *W) {
   if (N < 1 || !(beta > 0.0) || !E || !W) return -1;
   /* X[v - (u-1)] = V^{[u,v]} for v = u-1..N */
-  double *X = (double *)malloc(sizeof(double) * (size_t)(N + 2));
+  ora_real *X = (ora_real *)malloc(sizeof(ora_real) * (size_t)(N + 2));
   if (!X) return -1;
   W[N] = 0.0;
   for (int u = 1; u <= N; ++u) {
     X[0] = 0.0; /* V^{[u,u-1]} */
     for (int v = u; v <= N; ++v) {
-      double Et = INFINITY;
+      ora_real Et = INF_REAL;
       for (int k = 1; k <= v - u + 1; ++k) {
-        double t = X[v - k - (u - 1)] + E[EIDX(N, v - k + 1, v)];
+        ora_real t = X[v - k - (u - 1)] + E[EIDX(N, v - k + 1, v)];
         if (t < Et) Et = t;
       }
-      double s = 0.0;
+      ora_real s = 0.0;
       for (int k = 1; k <= v - u + 1; ++k)
-        s += exp(-beta * (X[v - k - (u - 1)] + E[EIDX(N, v - k + 1, v)] - Et));
-      X[v - (u - 1)] = Et - (1.0 / beta) * log(s / (double)v);
+        s += EXP(-beta * (X[v - k - (u - 1)] + E[EIDX(N, v - k + 1, v)] - Et));
+      X[v - (u - 1)] = Et - (1.0 / beta) * LOG(s / (ora_real)v);
     }
     W[u - 1] = X[N - (u - 1)];
   }
@@ -184,22 +196,22 @@ int ora_backward_potentials_definition(int N, double beta, const double *E,
 }
 
 /* Connection probabilities (Methods, "Expressions for connection probabilities"):
- *   Pr[l -> l+1] = 1 - exp(-beta (V^{[1,l]} + V^{[l+1,N]} - V^{[1,N]}))   (Eq. direct-link)
- *   Pr[l -> l']  = (1/l) exp(-beta (V^{[1,l'-1]} + E^{[l',l]} + V^{[l+1,N]}
+ *   Pr[l -> l+1] = 1 - EXP(-beta (V^{[1,l]} + V^{[l+1,N]} - V^{[1,N]}))   (Eq. direct-link)
+ *   Pr[l -> l']  = (1/l) EXP(-beta (V^{[1,l'-1]} + E^{[l',l]} + V^{[l+1,N]}
  *                                   - V^{[1,N]}))  for l' <= l           (Eq. close-cycle)
  *   Pr[l -> l']  = 0 for l' > l + 1           (Lemma zero-connection-probability)
- * The direct link uses -expm1(-x) for 1 - exp(-x). */
-int ora_connection_probabilities(int N, double beta, const double *E,
-                                 const double *V, const double *W, double *M) {
+ * The direct link uses -EXPM1(-x) for 1 - EXP(-x). */
+int ora_connection_probabilities(int N, ora_real beta, const ora_real *E,
+                                 const ora_real *V, const ora_real *W, ora_real *M) {
   if (N < 1 || !(beta > 0.0) || !E || !V || !W || !M) return -1;
-  memset(M, 0, sizeof(double) * (size_t)N * (size_t)N);
-  const double VN = V[N];
+  memset(M, 0, sizeof(ora_real) * (size_t)N * (size_t)N);
+  const ora_real VN = V[N];
   for (int l = 1; l <= N - 1; ++l)
-    M[EIDX(N, l, l + 1)] = -expm1(-beta * (V[l] + W[l] - VN)); /* W[l] = V^{[l+1,N]} */
+    M[EIDX(N, l, l + 1)] = -EXPM1(-beta * (V[l] + W[l] - VN)); /* W[l] = V^{[l+1,N]} */
   for (int lp = 1; lp <= N; ++lp)
     for (int l = lp; l <= N; ++l)
-      M[EIDX(N, l, lp)] = (1.0 / (double)l) *
-                          exp(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l] - VN));
+      M[EIDX(N, l, lp)] = (1.0 / (ora_real)l) *
+                          EXP(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l] - VN));
   return 0;
 }
 
@@ -208,27 +220,27 @@ int ora_connection_probabilities(int N, double beta, const double *E,
  *   bead 1: -sum_{l'=l-1}^{N} Pr[l'->l] m w_P^2 (2 r_l^1 - r_l^2 - r_{l'}^P)
  *   bead P: -sum_{l'=1}^{l+1} Pr[l->l'] m w_P^2 (2 r_l^P - r_{l'}^1 - r_l^{P-1})
  * with the edge limits clipped to 1..N (Algorithm 1, exterior-force lines). */
-int ora_forces(int N, int P, double m, double omega_P, const double *pos,
-               const double *M, double *F) {
+int ora_forces(int N, int P, ora_real m, ora_real omega_P, const ora_real *pos,
+               const ora_real *M, ora_real *F) {
   if (bad_args(N, P) || !pos || !M || !F) return -1;
-  const double k = m * omega_P * omega_P;
+  const ora_real k = m * omega_P * omega_P;
   for (int l = 1; l <= N; ++l)
     for (int j = 2; j <= P - 1; ++j)
       for (int d = 0; d < 3; ++d)
         BEAD(F, P, l, j)[d] = -k * (2.0 * BEAD(pos, P, l, j)[d] - BEAD(pos, P, l, j + 1)[d]
                                     - BEAD(pos, P, l, j - 1)[d]);
   for (int l = 1; l <= N; ++l) {
-    double f1[3] = {0.0, 0.0, 0.0}, fP[3] = {0.0, 0.0, 0.0};
+    ora_real f1[3] = {0.0, 0.0, 0.0}, fP[3] = {0.0, 0.0, 0.0};
     int lo = l - 1 < 1 ? 1 : l - 1;
     for (int lp = lo; lp <= N; ++lp) {
-      double pr = M[EIDX(N, lp, l)];
+      ora_real pr = M[EIDX(N, lp, l)];
       for (int d = 0; d < 3; ++d)
         f1[d] -= pr * k * (2.0 * BEAD(pos, P, l, 1)[d] - BEAD(pos, P, l, 2)[d]
                            - BEAD(pos, P, lp, P)[d]);
     }
     int hi = l + 1 > N ? N : l + 1;
     for (int lp = 1; lp <= hi; ++lp) {
-      double pr = M[EIDX(N, l, lp)];
+      ora_real pr = M[EIDX(N, l, lp)];
       for (int d = 0; d < 3; ++d)
         fP[d] -= pr * k * (2.0 * BEAD(pos, P, l, P)[d] - BEAD(pos, P, lp, 1)[d]
                            - BEAD(pos, P, l, P - 1)[d]);
@@ -243,16 +255,16 @@ int ora_forces(int N, int P, double m, double omega_P, const double *pos,
 
 /* Algorithm 1 (Fast PIMD-B): cycle energies, forward potentials, backward
  * potentials, connection probabilities, interior and exterior forces. */
-int ora_fast_pimdb(int N, int P, double m, double omega_P, double beta,
-                   const double *pos, double *V_B, double *F,
-                   double *Vout, double *Wout, double *Mout) {
+int ora_fast_pimdb(int N, int P, ora_real m, ora_real omega_P, ora_real beta,
+                   const ora_real *pos, ora_real *V_B, ora_real *F,
+                   ora_real *Vout, ora_real *Wout, ora_real *Mout) {
   if (bad_args(N, P) || !(beta > 0.0) || !(m > 0.0) || !(omega_P > 0.0) || !pos || !F)
     return -1;
   size_t NN = (size_t)N * (size_t)N;
-  double *E = (double *)malloc(sizeof(double) * NN);
-  double *M = Mout ? Mout : (double *)malloc(sizeof(double) * NN);
-  double *V = Vout ? Vout : (double *)malloc(sizeof(double) * (size_t)(N + 1));
-  double *W = Wout ? Wout : (double *)malloc(sizeof(double) * (size_t)(N + 1));
+  ora_real *E = (ora_real *)malloc(sizeof(ora_real) * NN);
+  ora_real *M = Mout ? Mout : (ora_real *)malloc(sizeof(ora_real) * NN);
+  ora_real *V = Vout ? Vout : (ora_real *)malloc(sizeof(ora_real) * (size_t)(N + 1));
+  ora_real *W = Wout ? Wout : (ora_real *)malloc(sizeof(ora_real) * (size_t)(N + 1));
   int rc = -1;
   if (E && M && V && W) {
     rc = ora_cycle_energies(N, P, m, omega_P, pos, E);
@@ -273,15 +285,15 @@ int ora_fast_pimdb(int N, int P, double m, double omega_P, double beta,
  * into g[3] (Algorithm 2, cycle-energy derivative lines): m w_P^2 (2 r_l^j -
  * r_l^{j+1} - r_l^{j-1}) with r_l^0 = r_{l-1}^P, r_l^{P+1} = r_{l+1}^1, except
  * r_u^0 = r_v^P and r_v^{P+1} = r_u^1; zero when l is outside [u, v]. */
-static void cycle_energy_gradient(int P, double k, const double *pos, int u, int v,
-                                  int l, int j, double *g) {
+static void cycle_energy_gradient(int P, ora_real k, const ora_real *pos, int u, int v,
+                                  int l, int j, ora_real *g) {
   if (l < u || l > v) { g[0] = g[1] = g[2] = 0.0; return; }
-  const double *next, *prev;
+  const ora_real *next, *prev;
   if (j < P) next = BEAD(pos, P, l, j + 1);
   else next = (l < v) ? BEAD(pos, P, l + 1, 1) : BEAD(pos, P, u, 1);
   if (j > 1) prev = BEAD(pos, P, l, j - 1);
   else prev = (l > u) ? BEAD(pos, P, l - 1, P) : BEAD(pos, P, v, P);
-  const double *r = BEAD(pos, P, l, j);
+  const ora_real *r = BEAD(pos, P, l, j);
   for (int d = 0; d < 3; ++d) g[d] = k * (2.0 * r[d] - next[d] - prev[d]);
 }
 
@@ -291,21 +303,21 @@ static void cycle_energy_gradient(int P, double k, const double *pos, int u, int
  * in Algorithm 1; then for every bead the recursion obtained by differentiating
  * Eq. our-forward-potential-recurrence:
  *   grad V^{[1,v]} = sum_{k=1}^{v} (grad E^{[v-k+1,v]} + grad V^{[1,v-k]})
- *                    exp(-beta (E^{[v-k+1,v]} + V^{[1,v-k]})) / (v exp(-beta V^{[1,v]})),
+ *                    EXP(-beta (E^{[v-k+1,v]} + V^{[1,v-k]})) / (v EXP(-beta V^{[1,v]})),
  * grad V^{[1,0]} = 0, and F = -grad V^{[1,N]}. */
-int ora_original_pimdb(int N, int P, double m, double omega_P, double beta,
-                       const double *pos, double *V_B, double *F) {
+int ora_original_pimdb(int N, int P, ora_real m, ora_real omega_P, ora_real beta,
+                       const ora_real *pos, ora_real *V_B, ora_real *F) {
   if (bad_args(N, P) || !(beta > 0.0) || !(m > 0.0) || !(omega_P > 0.0) || !pos || !F)
     return -1;
-  const double half_k = 0.5 * m * omega_P * omega_P, k = m * omega_P * omega_P;
+  const ora_real half_k = 0.5 * m * omega_P * omega_P, k = m * omega_P * omega_P;
   size_t NN = (size_t)N * (size_t)N;
-  double *E = (double *)malloc(sizeof(double) * NN);
-  double *V = (double *)malloc(sizeof(double) * (size_t)(N + 1));
-  double *dV = (double *)malloc(sizeof(double) * 3 * (size_t)(N + 1));
+  ora_real *E = (ora_real *)malloc(sizeof(ora_real) * NN);
+  ora_real *V = (ora_real *)malloc(sizeof(ora_real) * (size_t)(N + 1));
+  ora_real *dV = (ora_real *)malloc(sizeof(ora_real) * 3 * (size_t)(N + 1));
   if (!E || !V || !dV) { free(E); free(V); free(dV); return -1; }
   for (int v = 1; v <= N; ++v) {
     for (int u = 1; u <= v; ++u) {
-      double s = 0.0;
+      ora_real s = 0.0;
       for (int l = u; l <= v; ++l)
         for (int j = 1; j <= P - 1; ++j) s += sqdist(BEAD(pos, P, l, j + 1), BEAD(pos, P, l, j));
       for (int l = u; l <= v - 1; ++l) s += sqdist(BEAD(pos, P, l + 1, 1), BEAD(pos, P, l, P));
@@ -318,13 +330,13 @@ int ora_original_pimdb(int N, int P, double m, double omega_P, double beta,
     for (int j = 1; j <= P; ++j) {
       dV[0] = dV[1] = dV[2] = 0.0;
       for (int v = 1; v <= N; ++v) {
-        double acc[3] = {0.0, 0.0, 0.0};
+        ora_real acc[3] = {0.0, 0.0, 0.0};
         for (int kk = 1; kk <= v; ++kk) {
           int u = v - kk + 1;
-          double g[3];
+          ora_real g[3];
           cycle_energy_gradient(P, k, pos, u, v, l, j, g);
-          /* exp(-beta(E + V^{[1,v-k]})) / (v exp(-beta V^{[1,v]})) */
-          double w = exp(-beta * (E[EIDX(N, u, v)] + V[v - kk] - V[v])) / (double)v;
+          /* EXP(-beta(E + V^{[1,v-k]})) / (v EXP(-beta V^{[1,v]})) */
+          ora_real w = EXP(-beta * (E[EIDX(N, u, v)] + V[v - kk] - V[v])) / (ora_real)v;
           for (int d = 0; d < 3; ++d) acc[d] += (g[d] + dV[3 * (v - kk) + d]) * w;
         }
         for (int d = 0; d < 3; ++d) dV[3 * v + d] = acc[d];
@@ -341,18 +353,18 @@ int ora_original_pimdb(int N, int P, double m, double omega_P, double beta,
  * sum_l E_int^{(l)} + sum_l sum_{l'} Pr[l->l'] (1/2) m w_P^2 (r_l^P - r_{l'}^1)^2.
  * Linear in the exterior springs, so the expectation over the distribution of
  * Eq. representative-distribution reduces to the connection probabilities. */
-int ora_expected_spring_energy(int N, int P, double m, double omega_P,
-                               const double *pos, const double *M, double *out) {
+int ora_expected_spring_energy(int N, int P, ora_real m, ora_real omega_P,
+                               const ora_real *pos, const ora_real *M, ora_real *out) {
   if (bad_args(N, P) || !pos || !M || !out) return -1;
-  const double half_k = 0.5 * m * omega_P * omega_P;
-  double *Eint = (double *)malloc(sizeof(double) * (size_t)N);
+  const ora_real half_k = 0.5 * m * omega_P * omega_P;
+  ora_real *Eint = (ora_real *)malloc(sizeof(ora_real) * (size_t)N);
   if (!Eint) return -1;
   ora_interior_energies(N, P, m, omega_P, pos, Eint);
-  double s = 0.0;
+  ora_real s = 0.0;
   for (int l = 1; l <= N; ++l) {
     s += Eint[l - 1];
     for (int lp = 1; lp <= N; ++lp) {
-      double pr = M[EIDX(N, l, lp)];
+      ora_real pr = M[EIDX(N, l, lp)];
       if (pr != 0.0) s += pr * half_k * sqdist(BEAD(pos, P, l, P), BEAD(pos, P, lp, 1));
     }
   }

@@ -8,15 +8,15 @@
  * reference arm of bench.py use it.  It shares no code with the CUDA library.
  *
  * Conventions (all functions):
- *   pos  : [N][P][3] row-major doubles; bead j (1-based) of particle l (1-based)
+ *   pos  : [N][P][3] row-major ora_real values; bead j (1-based) of particle l (1-based)
  *          is pos[((l-1)*P + (j-1))*3 + d].
  *   m, omega_P, beta : mass, ring-polymer spring frequency, inverse temperature;
  *          the spring prefactor is (1/2) m omega_P^2 (Eq. eperm).
- *   E    : N*N doubles, E[(u-1)*N + (v-1)] = E^{[u,v]} for u <= v (cycle energy
+ *   E    : N*N values, E[(u-1)*N + (v-1)] = E^{[u,v]} for u <= v (cycle energy
  *          of the ring through particles u..v); entries with u > v unused.
- *   V    : N+1 doubles, V[v] = V^{[1,v]}, V[0] = 0.
- *   W    : N+1 doubles, W[u-1] = V^{[u,N]} for u = 1..N+1, so W[N] = 0.
- *   M    : N*N doubles, M[(l-1)*N + (l'-1)] = Pr[l -> l'], the probability that
+ *   V    : N+1 values, V[v] = V^{[1,v]}, V[0] = 0.
+ *   W    : N+1 values, W[u-1] = V^{[u,N]} for u = 1..N+1, so W[N] = 0.
+ *   M    : N*N values, M[(l-1)*N + (l'-1)] = Pr[l -> l'], the probability that
  *          bead P of particle l is joined to bead 1 of particle l'.
  *   F    : [N][P][3] forces -grad V^{[1,N]}.
  * Return value of int functions: 0 on success, -1 on invalid arguments.
@@ -28,63 +28,74 @@
 extern "C" {
 #endif
 
+/* Floating-point type of every array and parameter.  The default build is
+ * float64.  Compiling with -DORA_LONG_DOUBLE gives the same routines in long
+ * double (64-bit mantissa on x86-64, 113-bit on aarch64); that build serves as
+ * a higher-precision referee in the tests, where float64 rounding of the
+ * oracle itself would otherwise be compared with the tolerances. */
+#ifdef ORA_LONG_DOUBLE
+typedef long double ora_real;
+#else
+typedef double ora_real;
+#endif
+
 /* Shift choice for the log-sum-exp steps (Methods, "Numerical Stability"). */
 #define ORA_SHIFT_MIN_ALL 0   /* Eq. full-elong: min over all terms of the step   */
 #define ORA_SHIFT_TWO_TERM 1  /* Eq. original-elong: min of two designated terms  */
 
 /* Eq. e-interior: E_int^{(l)} for every particle. */
-int ora_interior_energies(int N, int P, double m, double omega_P,
-                          const double *pos, double *Eint);
+int ora_interior_energies(int N, int P, ora_real m, ora_real omega_P,
+                          const ora_real *pos, ora_real *Eint);
 
 /* Algorithm 1 cycle-energy stage: base case Eq. e-recurrence-base and the
  * O(1) step Eq. e-recurrence-step, v ascending, u descending. */
-int ora_cycle_energies(int N, int P, double m, double omega_P,
-                       const double *pos, double *E);
+int ora_cycle_energies(int N, int P, ora_real m, ora_real omega_P,
+                       const ora_real *pos, ora_real *E);
 
 /* Eq. Ek: the direct double sum over the ring through u..v (O(P N^3) total). */
-int ora_cycle_energies_direct(int N, int P, double m, double omega_P,
-                              const double *pos, double *E);
+int ora_cycle_energies_direct(int N, int P, ora_real m, ora_real omega_P,
+                              const ora_real *pos, ora_real *E);
 
 /* Eq. our-forward-potential-recurrence with the shifted form of the
  * Numerical Stability section.  Writes V[0..N]. */
-int ora_forward_potentials(int N, double beta, const double *E, int shift_mode,
-                           double *V);
+int ora_forward_potentials(int N, ora_real beta, const ora_real *E, int shift_mode,
+                           ora_real *V);
 
 /* Eq. backward-potential-recursion (Theorem backward-recurrence), shifted.
  * Writes W[0..N] (W[u-1] = V^{[u,N]}). */
-int ora_backward_potentials(int N, double beta, const double *E, int shift_mode,
-                            double *W);
+int ora_backward_potentials(int N, ora_real beta, const ora_real *E, int shift_mode,
+                            ora_real *W);
 
 /* Definition backward-potential: the O(N^3) route to V^{[u,N]}. */
-int ora_backward_potentials_definition(int N, double beta, const double *E,
-                                       double *W);
+int ora_backward_potentials_definition(int N, ora_real beta, const ora_real *E,
+                                       ora_real *W);
 
 /* Eq. direct-link-probability and Eq. close-cycle-probability; zero for
  * l' > l + 1 (Lemma zero-connection-probability). */
-int ora_connection_probabilities(int N, double beta, const double *E,
-                                 const double *V, const double *W, double *M);
+int ora_connection_probabilities(int N, ora_real beta, const ora_real *E,
+                                 const ora_real *V, const ora_real *W, ora_real *M);
 
 /* Interior-bead forces (Eq. intermediate-bead-force) and exterior-bead forces
  * (Eq. force-on-1/P-sum-neighbors) with Algorithm 1's trimmed sum limits. */
-int ora_forces(int N, int P, double m, double omega_P, const double *pos,
-               const double *M, double *F);
+int ora_forces(int N, int P, ora_real m, ora_real omega_P, const ora_real *pos,
+               const ora_real *M, ora_real *F);
 
 /* Algorithm 1 (Fast PIMD-B) end to end.  Returns 0/-1; *V_B = V^{[1,N]}.
  * Optional outputs (may be NULL): V (N+1), W (N+1), M (N*N). */
-int ora_fast_pimdb(int N, int P, double m, double omega_P, double beta,
-                   const double *pos, double *V_B, double *F,
-                   double *V, double *W, double *M);
+int ora_fast_pimdb(int N, int P, ora_real m, ora_real omega_P, ora_real beta,
+                   const ora_real *pos, ora_real *V_B, ora_real *F,
+                   ora_real *V, ora_real *W, ora_real *M);
 
 /* Algorithm 2 (Original PIMD-B): O(P N^3) potential and per-bead force
  * recursion.  Returns 0/-1; *V_B = V^{[1,N]}. */
-int ora_original_pimdb(int N, int P, double m, double omega_P, double beta,
-                       const double *pos, double *V_B, double *F);
+int ora_original_pimdb(int N, int P, ora_real m, ora_real omega_P, ora_real beta,
+                       const ora_real *pos, ora_real *V_B, ora_real *F);
 
 /* Spring part of the primitive energy estimator of the bosonic ring polymer:
  * sum_l E_int^{(l)} + sum_{l,l'} Pr[l->l'] (1/2) m omega_P^2 |r_l^P - r_l'^1|^2,
  * i.e. the expectation over representative permutations of E^{G[sigma]}. */
-int ora_expected_spring_energy(int N, int P, double m, double omega_P,
-                               const double *pos, const double *M, double *out);
+int ora_expected_spring_energy(int N, int P, ora_real m, ora_real omega_P,
+                               const ora_real *pos, const ora_real *M, ora_real *out);
 
 #ifdef __cplusplus
 }

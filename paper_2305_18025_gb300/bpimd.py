@@ -1,0 +1,169 @@
+"""Thin ctypes binding of the bpimd C ABI (``include/bpimd.h``).
+
+Argument marshalling only: every step of the exchange computation runs in the
+CUDA kernels of ``libbpimd.so``.  The functions keep the C names; tensors are
+passed as ``torch.Tensor`` (their ``data_ptr()`` is handed to the library) and
+streams as ``torch.cuda.Stream`` or raw handles.  There is no CPU fallback:
+if the library cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+BPIMD_OK = 0
+BPIMD_ERR_ARG = -1
+BPIMD_ERR_NONFINITE = -2
+BPIMD_ERR_CUDA = -3
+BPIMD_ERR_TIMEOUT = -4
+BPIMD_ERR_NOMEM = -5
+BPIMD_ERR_STATE = -6
+
+BPIMD_FP64 = 0
+BPIMD_MIXED = 1
+
+BPIMD_PAIR_NONE = 0
+BPIMD_PAIR_GAUSSIAN = 1
+BPIMD_PAIR_LJ = 2
+
+EXPORTED = [
+    "bpimd_create", "bpimd_destroy", "bpimd_exchange_energy_forces",
+    "bpimd_exchange_energy_forces_host", "bpimd_sync", "bpimd_get_potentials",
+    "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
+]
+
+
+class bpimd_config(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("P", ctypes.c_int32),
+        ("m", ctypes.c_double), ("omega_P", ctypes.c_double), ("beta", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("dt", ctypes.c_double), ("gamma", ctypes.c_double), ("kT_bead", ctypes.c_double),
+        ("omega0", ctypes.c_double),
+        ("pair_type", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("pair_a", ctypes.c_double), ("pair_b", ctypes.c_double), ("pair_rc", ctypes.c_double),
+        ("box_L", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+class BpimdError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {bpimd_status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libbpimd.so (building it first if asked); raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise ImportError(f"bpimd CUDA library missing: {_build.LIB}")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.bpimd_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(bpimd_config), vp]
+    lib.bpimd_destroy.argtypes = [vp]
+    lib.bpimd_exchange_energy_forces.argtypes = [vp, vp, vp, vp]
+    lib.bpimd_exchange_energy_forces_host.argtypes = [vp, vp, vp, vp]
+    lib.bpimd_sync.argtypes = [vp]
+    lib.bpimd_get_potentials.argtypes = [vp, vp, vp, vp]
+    lib.bpimd_connection_probabilities.argtypes = [vp, vp]
+    lib.bpimd_step.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.bpimd_status_string.argtypes = [ip]
+    lib.bpimd_status_string.restype = ctypes.c_char_p
+    lib.bpimd_version.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("bpimd_status_string", "bpimd_version"):
+            getattr(lib, name).restype = ip
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device/host address of a tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status, where):
+    if status != BPIMD_OK:
+        raise BpimdError(status, where)
+
+
+def bpimd_status_string(status):
+    return load().bpimd_status_string(int(status)).decode()
+
+
+def bpimd_version():
+    return load().bpimd_version().decode()
+
+
+def bpimd_create(cfg, stream=None):
+    """Create a context; returns its opaque handle (int)."""
+    h = ctypes.c_void_p()
+    _check(load().bpimd_create(ctypes.byref(h), ctypes.byref(cfg), _stream_handle(stream)), "bpimd_create")
+    return h.value
+
+
+def bpimd_destroy(ctx):
+    _check(load().bpimd_destroy(ctx), "bpimd_destroy")
+
+
+def bpimd_exchange_energy_forces(ctx, positions, V_B, forces):
+    _check(load().bpimd_exchange_energy_forces(ctx, _ptr(positions), _ptr(V_B), _ptr(forces)),
+           "bpimd_exchange_energy_forces")
+
+
+def bpimd_exchange_energy_forces_host(ctx, positions, V_B, forces):
+    _check(load().bpimd_exchange_energy_forces_host(ctx, _ptr(positions), _ptr(V_B), _ptr(forces)),
+           "bpimd_exchange_energy_forces_host")
+
+
+def bpimd_sync(ctx):
+    _check(load().bpimd_sync(ctx), "bpimd_sync")
+
+
+def bpimd_get_potentials(ctx, V_fwd, V_bwd, Eint):
+    _check(load().bpimd_get_potentials(ctx, _ptr(V_fwd), _ptr(V_bwd), _ptr(Eint)), "bpimd_get_potentials")
+
+
+def bpimd_connection_probabilities(ctx, M):
+    _check(load().bpimd_connection_probabilities(ctx, _ptr(M)), "bpimd_connection_probabilities")
+
+
+def bpimd_step(ctx, positions, velocities, nsteps, energies=None):
+    _check(load().bpimd_step(ctx, _ptr(positions), _ptr(velocities), int(nsteps), _ptr(energies)),
+           "bpimd_step")
+
+
+def make_config(N, P, m, omega_P, beta, precision=BPIMD_FP64, **md):
+    cfg = bpimd_config()
+    cfg.N, cfg.P, cfg.m, cfg.omega_P, cfg.beta = N, P, m, omega_P, beta
+    cfg.precision = precision
+    for k, v in md.items():
+        setattr(cfg, k, v)
+    return cfg

@@ -1,0 +1,250 @@
+// C ABI of the bpimd library: argument checks, workspace ownership, launch
+// sequence of one evaluation of Algorithm 1 (appendix "Algorithm Pseudocode").
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "bpimd_internal.cuh"
+#include "md.cuh"
+
+using namespace bpimd;
+
+struct bpimd_ctx {
+  bpimd_config cfg;
+  cudaStream_t stream;
+  Workspace w;
+  void *dev_block;     // single device allocation holding the workspace
+  size_t dev_bytes;
+  int *host_status;    // pinned
+  double *d_pos, *d_F, *d_VB;  // staging for the _host entry point (lazy)
+  bool evaluated;
+  MDState md;
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int validate(const bpimd_config *c) {
+  if (!c) return BPIMD_ERR_ARG;
+  if (c->N < 1 || c->P < 2) return BPIMD_ERR_ARG;
+  if (c->N > CHAIN_MAX_N) return BPIMD_ERR_ARG;
+  if ((long long)c->N * c->P > (1LL << 31) / 3) return BPIMD_ERR_ARG;
+  if (!finite_pos(c->m) || !finite_pos(c->omega_P) || !finite_pos(c->beta)) return BPIMD_ERR_ARG;
+  if (c->precision != BPIMD_FP64 && c->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
+  if (c->flags != 0) return BPIMD_ERR_ARG;
+  return BPIMD_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA; }
+
+int check_ptr(const void *p) {
+  if (!p) return BPIMD_ERR_ARG;
+  if (((uintptr_t)p) & 15) return BPIMD_ERR_ARG;
+  return BPIMD_OK;
+}
+
+int read_status(bpimd_ctx *ctx) {
+  cudaError_t e = cudaMemcpyAsync(ctx->host_status, ctx->w.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return BPIMD_ERR_CUDA;
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return BPIMD_ERR_CUDA;
+  const int st = *ctx->host_status;
+  if (st) {
+    e = cudaMemsetAsync(ctx->w.status, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return BPIMD_ERR_CUDA;
+    if (st & ST_TIMEOUT) return BPIMD_ERR_TIMEOUT;
+    if (st & ST_NONFINITE) return BPIMD_ERR_NONFINITE;
+  }
+  return BPIMD_OK;
+}
+
+}  // namespace
+
+namespace bpimd {
+// one evaluation of V_B and forces on ctx->stream
+int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
+  const Workspace &w = ctx->w;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e;
+  if ((e = launch_bead_pass(w, pos, F, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if ((e = launch_gmat(w, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if ((e = launch_chains(w, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if ((e = launch_scalars(w, V_B, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if ((e = launch_forces(w, pos, F, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  ctx->evaluated = true;
+  return BPIMD_OK;
+}
+}  // namespace bpimd
+
+extern "C" {
+
+int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
+  if (!out) return BPIMD_ERR_ARG;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != BPIMD_OK) return rc;
+  bpimd_ctx *ctx = new (std::nothrow) bpimd_ctx();
+  if (!ctx) return BPIMD_ERR_NOMEM;
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  Workspace &w = ctx->w;
+  w.N = cfg->N;
+  w.P = cfg->P;
+  w.NT = (w.N + TILE - 1) / TILE;
+  w.NB = w.NT * (w.NT + 1) / 2;
+  w.mixed = cfg->precision == BPIMD_MIXED;
+  w.m = cfg->m;
+  w.omega_P = cfg->omega_P;
+  w.beta = cfg->beta;
+  w.k = cfg->m * cfg->omega_P * cfg->omega_P;
+  w.half_k = 0.5 * w.k;
+  const size_t N = w.N, NB = w.NB;
+  const size_t gelems = NB * TILE2;
+  // carve one allocation
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+  size_t oR1 = take(sizeof(double) * 4 * N), oRP = take(sizeof(double) * 4 * N);
+  size_t oEint = take(sizeof(double) * N), oLink = take(sizeof(double) * N);
+  size_t occm = take(sizeof(double) * N), occe = take(sizeof(int) * N);
+  size_t oC = take(sizeof(double) * (N + 1));
+  size_t ogm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), oge = take(sizeof(int) * gelems);
+  size_t oyfm = take(sizeof(double) * (N + 1)), oyfe = take(sizeof(int) * (N + 1));
+  size_t osfm = take(sizeof(double) * N), osfe = take(sizeof(int) * N);
+  size_t oybm = take(sizeof(double) * (N + 1)), oybe = take(sizeof(int) * (N + 1));
+  size_t osbm = take(sizeof(double) * N), osbe = take(sizeof(int) * N);
+  size_t oscal = take(sizeof(double) * 4), oscali = take(sizeof(int) * 4);
+  size_t orow = take(sizeof(double) * NB * TILE * 4), ocol = take(sizeof(double) * NB * TILE * 4);
+  size_t ost = take(sizeof(int) * 4);
+  size_t oVf = take(sizeof(double) * (N + 1)), oVb = take(sizeof(double) * (N + 1));
+  ctx->dev_bytes = off;
+  if (cudaMalloc(&ctx->dev_block, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return BPIMD_ERR_NOMEM;
+  }
+  char *b = (char *)ctx->dev_block;
+  w.R1 = (double *)(b + oR1); w.RP = (double *)(b + oRP);
+  w.Eint = (double *)(b + oEint); w.link = (double *)(b + oLink);
+  w.ccm = (double *)(b + occm); w.cce = (int *)(b + occe);
+  w.C = (double *)(b + oC);
+  w.gm = (void *)(b + ogm); w.ge = (int *)(b + oge);
+  w.yfm = (double *)(b + oyfm); w.yfe = (int *)(b + oyfe);
+  w.sfm = (double *)(b + osfm); w.sfe = (int *)(b + osfe);
+  w.ybm = (double *)(b + oybm); w.ybe = (int *)(b + oybe);
+  w.sbm = (double *)(b + osbm); w.sbe = (int *)(b + osbe);
+  w.scal = (double *)(b + oscal); w.scal_i = (int *)(b + oscali);
+  w.rowpart = (double *)(b + orow); w.colpart = (double *)(b + ocol);
+  w.status = (int *)(b + ost);
+  w.Vf = (double *)(b + oVf); w.Vb = (double *)(b + oVb);
+  if (cudaMemsetAsync(ctx->dev_block, 0, off, ctx->stream) != cudaSuccess ||
+      cudaMallocHost(&ctx->host_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->dev_block);
+    delete ctx;
+    return BPIMD_ERR_NOMEM;
+  }
+  *ctx->host_status = 0;
+  md_init(&ctx->md);
+  *out = ctx;
+  return BPIMD_OK;
+}
+
+int bpimd_destroy(bpimd_ctx *ctx) {
+  if (!ctx) return BPIMD_OK;
+  cudaStreamSynchronize(ctx->stream);
+  md_free(&ctx->md);
+  cudaFree(ctx->dev_block);
+  cudaFree(ctx->d_pos);
+  cudaFree(ctx->d_F);
+  cudaFree(ctx->d_VB);
+  cudaFreeHost(ctx->host_status);
+  delete ctx;
+  return BPIMD_OK;
+}
+
+int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions, double *V_B, double *forces) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(positions)) || (rc = check_ptr(forces))) return rc;
+  if (V_B && (((uintptr_t)V_B) & 7)) return BPIMD_ERR_ARG;
+  return evaluate(ctx, positions, V_B, forces);
+}
+
+int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions, double *V_B, double *forces) {
+  if (!ctx || !positions || !forces) return BPIMD_ERR_ARG;
+  const size_t bytes = sizeof(double) * 3 * (size_t)ctx->w.N * ctx->w.P;
+  if (!ctx->d_pos) {
+    if (cudaMalloc(&ctx->d_pos, bytes) != cudaSuccess || cudaMalloc(&ctx->d_F, bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return BPIMD_ERR_NOMEM;
+    }
+  }
+  cudaStream_t s = ctx->stream;
+  if (cudaMemcpyAsync(ctx->d_pos, positions, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  int rc = evaluate(ctx, ctx->d_pos, ctx->d_VB, ctx->d_F);
+  if (rc != BPIMD_OK) return rc;
+  if (cudaMemcpyAsync(forces, ctx->d_F, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (V_B && cudaMemcpyAsync(V_B, ctx->d_VB, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BPIMD_ERR_CUDA;
+  return read_status(ctx);
+}
+
+int bpimd_sync(bpimd_ctx *ctx) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  return read_status(ctx);
+}
+
+int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *Eint) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  if (!ctx->evaluated) return BPIMD_ERR_STATE;
+  const size_t N = ctx->w.N;
+  cudaStream_t s = ctx->stream;
+  if (V_fwd && cudaMemcpyAsync(V_fwd, ctx->w.Vf, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BPIMD_ERR_CUDA;
+  if (V_bwd && cudaMemcpyAsync(V_bwd, ctx->w.Vb, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BPIMD_ERR_CUDA;
+  if (Eint && cudaMemcpyAsync(Eint, ctx->w.Eint, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BPIMD_ERR_CUDA;
+  return read_status(ctx);
+}
+
+int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(M))) return rc;
+  if (!ctx->evaluated) return BPIMD_ERR_STATE;
+  return cuda_status(launch_dense_probabilities(ctx->w, M, ctx->stream));
+}
+
+int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities, int32_t nsteps, double *energies) {
+  if (!ctx || nsteps < 0) return BPIMD_ERR_ARG;
+  int rc;
+  if ((rc = check_ptr(positions)) || (rc = check_ptr(velocities))) return rc;
+  if (energies && (((uintptr_t)energies) & 7)) return BPIMD_ERR_ARG;
+  rc = md_run(ctx, positions, velocities, nsteps, energies);
+  if (rc != BPIMD_OK) return rc;
+  return read_status(ctx);
+}
+
+const char *bpimd_status_string(int status) {
+  switch (status) {
+    case BPIMD_OK: return "ok";
+    case BPIMD_ERR_ARG: return "invalid argument";
+    case BPIMD_ERR_NONFINITE: return "non-finite value in positions or results";
+    case BPIMD_ERR_CUDA: return "CUDA runtime error";
+    case BPIMD_ERR_TIMEOUT: return "bounded device wait expired";
+    case BPIMD_ERR_NOMEM: return "allocation failed";
+    case BPIMD_ERR_STATE: return "call not valid in this state";
+    default: return "unknown status";
+  }
+}
+
+const char *bpimd_version(void) { return "bpimd 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Bead pass: one read of the positions per evaluation.
+//
+// Per particle l (one warp):
+//   E_int^{(l)} = (1/2) m w_P^2 sum_{j=1}^{P-1} (r_l^{j+1} - r_l^j)^2     (Eq. e-interior)
+//   link_l      = (1/2) m w_P^2 (r_l^P - r_{l+1}^1)^2, 0 for l = N       (spring of Eq. e-recurrence-step)
+//   interior forces -m w_P^2 (2 r_l^j - r_l^{j+1} - r_l^{j-1}), j=2..P-1  (Eq. intermediate-bead-force)
+//   copies of r_l^1 and r_l^P, and the coefficient c_l = exp(beta link_l)/l
+//   of the linear-space recursions, as an extended number.
+// FP64: everything in float64.  MIXED: bead differences formed in float64,
+// rounded to float32; squares, warp sums and interior forces in float32;
+// E_int and link widened to float64.
+#include "bpimd_internal.cuh"
+
+namespace bpimd {
+namespace {
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) bead_pass_kernel(Workspace w, const double *__restrict__ pos,
+                                                        double *__restrict__ F) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= w.N) return;
+  const int P = w.P;
+  const double *p = pos + (size_t)l * P * 3;
+  double *f = F + (size_t)l * P * 3;
+  const double k = w.k;
+  bool finite = true;
+  double s64 = 0.0;
+  float s32 = 0.0f;
+  for (int j = lane; j < P; j += 32) {
+    const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
+    finite &= isfinite(x) && isfinite(y) && isfinite(z);
+    if (j + 1 < P) {
+      const double dx = p[3 * j + 3] - x, dy = p[3 * j + 4] - y, dz = p[3 * j + 5] - z;
+      if (MIXED) {
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        s32 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, s32)));
+      } else {
+        s64 = fma(dx, dx, fma(dy, dy, fma(dz, dz, s64)));
+      }
+    }
+    if (j >= 1 && j + 1 < P) {  // interior bead (0-based 1..P-2)
+      const double ax = x - p[3 * j + 3], ay = y - p[3 * j + 4], az = z - p[3 * j + 5];
+      const double bx = x - p[3 * j - 3], by = y - p[3 * j - 2], bz = z - p[3 * j - 1];
+      if (MIXED) {
+        const float kf = (float)k;
+        f[3 * j] = (double)(-kf * ((float)ax + (float)bx));
+        f[3 * j + 1] = (double)(-kf * ((float)ay + (float)by));
+        f[3 * j + 2] = (double)(-kf * ((float)az + (float)bz));
+      } else {
+        f[3 * j] = -k * (ax + bx);
+        f[3 * j + 1] = -k * (ay + by);
+        f[3 * j + 2] = -k * (az + bz);
+      }
+    }
+  }
+  double eint;
+  if (MIXED) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s32 += __shfl_xor_sync(0xffffffffu, s32, o);
+    eint = w.half_k * (double)s32;
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+    eint = w.half_k * s64;
+  }
+  finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) {
+    if (!finite) atomicOr(w.status, ST_NONFINITE);
+    const double *b1 = p, *bP = p + 3 * (P - 1);
+    double lk = 0.0;
+    if (l + 1 < w.N) {
+      const double *n1 = p + 3 * P;  // bead 1 of particle l+1
+      const double dx = bP[0] - n1[0], dy = bP[1] - n1[1], dz = bP[2] - n1[2];
+      if (MIXED) {
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        lk = w.half_k * (double)fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+      } else {
+        lk = w.half_k * fma(dx, dx, fma(dy, dy, dz * dz));
+      }
+    }
+    w.Eint[l] = eint;
+    w.link[l] = lk;
+    double *r1 = w.R1 + 4 * (size_t)l, *rp = w.RP + 4 * (size_t)l;
+    r1[0] = b1[0]; r1[1] = b1[1]; r1[2] = b1[2]; r1[3] = 0.0;
+    rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
+    // c_{l+1} = exp(beta link_l) / (l+1) = 2^x, x = beta link_l log2(e) - log2(l+1)
+    const double x = w.beta * lk * LOG2E - log2((double)(l + 1));
+    const double n = floor(x);
+    xd c = xnorm(exp2(x - n), (int)n);
+    w.ccm[l] = c.m;
+    w.cce[l] = c.e;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
+  const int warps = 8;
+  dim3 grid((w.N + warps - 1) / warps), block(32 * warps);
+  if (w.mixed) bead_pass_kernel<true><<<grid, block, 0, s>>>(w, pos, F);
+  else bead_pass_kernel<false><<<grid, block, 0, s>>>(w, pos, F);
+  return cudaGetLastError();
+}
+
+}  // namespace bpimd

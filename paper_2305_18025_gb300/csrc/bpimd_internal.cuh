@@ -1,0 +1,141 @@
+// Internal definitions of the bpimd CUDA library (not part of the C ABI).
+//
+// Numerical formulation used on the device
+// ----------------------------------------
+// The paper evaluates the forward and backward potentials as log-sum-exp
+// recursions (Eq. our-forward-potential-recurrence, Eq.
+// backward-potential-recursion, shifted as in the Numerical Stability
+// section).  On GB300 one FP64 exp costs ~1100 cycles of latency and one FP64
+// log ~2000, so a log-sum-exp per sequential step would dominate.  The device
+// therefore runs the SAME recursions in linear space, with every quantity
+// carried as an extended-range number  x = m * 2^e  (m a float/double
+// mantissa, e a 32-bit integer exponent) -- a power-of-two shift per value in
+// place of the paper's energy shift E~ (any shift is valid, Numerical
+// Stability section).  With the prefix sums
+//     C[l]  = sum_{i<=l} (E_int^{(i)} + link_i),  link_i = (1/2)k (r_i^P - r_{i+1}^1)^2,
+// the cycle energy factorises (telescoping Eq. e-recurrence-step):
+//     E^{[u,v]} = C[v-1] - C[u-1] + E_int^{(v)} + (1/2)k (r_v^P - r_u^1)^2,
+// so that, with g(u,v) = exp(-beta (1/2)k (r_v^P - r_u^1)^2) and
+// c_v = exp(beta link_v)/v,
+//     forward : y_0 = 1,  y_{r+1} = c_{r+1} sum_{w<=r} y_w g(w+1, r+1)
+//               (0-based rows r; y_v = exp(-beta (V^{[1,v]} - C[v])))
+//     backward: mu_{N} = 1, B_u = sum_{l>=u} g(u,l) mu_l, mu_{u-1} = c_{u-1} B_u
+//               (exp(-beta V^{[u,N]}) = exp(beta (C[u-1]-C[N])) B_u / N)
+//     Pr[l -> u<=l] = y_{u-1} g(u,l) mu_l / (N y_N)          (Eq. close-cycle)
+//     Pr[l -> l+1]  = 1 - y_l B_{l+1} / (N y_N)              (Eq. direct-link)
+// Each sequential step is then one multiply-add; no transcendental function
+// sits on the dependency chain.  g is computed once per evaluation and shared
+// by both recursions and the probability pass.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bpimd.h"
+
+namespace bpimd {
+
+constexpr int TILE = 32;              // row / source tile of the recursions and of g
+constexpr int TILE2 = TILE * TILE;
+constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
+constexpr int CHAIN_THREADS = 1024;
+constexpr int CHAIN_MAX_N = 7168;     // recursion state lives in shared memory (28 B per particle)
+constexpr double LOG2E = 1.4426950408889634074;
+constexpr double LN2 = 0.6931471805599453094;
+
+// status bits recorded on the device
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_TIMEOUT = 2;
+
+// ------------------------------------------------------------ extended numbers
+struct xd {  // value = m * 2^e
+  double m;
+  int e;
+};
+
+__device__ __forceinline__ double pow2_nonpos(int k) {
+  // 2^k for k <= 0; 0 below the normal range (the scaled operand is then
+  // below 2^-1022 of the larger one and cannot change a double sum).
+  return (k < -1022) ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52);
+}
+__device__ __forceinline__ float pow2f_nonpos(int k) {
+  return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
+}
+
+// Bring m into [1,2), folding its binary exponent into e.  m >= 0, finite.
+__device__ __forceinline__ xd xnorm(double m, int e) {
+  if (!(m > 0.0)) return xd{0.0, XZERO_E};
+  long long b = __double_as_longlong(m);
+  int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) {  // subnormal mantissa: rescale exactly
+    m *= 18446744073709551616.0;  // 2^64
+    e -= 64;
+    b = __double_as_longlong(m);
+    ex = (int)((b >> 52) & 0x7ff);
+  }
+  b = (b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL;
+  return xd{__longlong_as_double(b), e + ex - 1023};
+}
+
+__device__ __forceinline__ xd xmul(xd a, xd b) { return xnorm(a.m * b.m, a.e + b.e); }
+
+// a + b (not normalised; mantissa stays < 2 * (terms) and is renormalised by callers)
+__device__ __forceinline__ xd xadd_raw(xd a, xd b) {
+  int E = max(a.e, b.e);
+  return xd{fma(b.m, pow2_nonpos(b.e - E), a.m * pow2_nonpos(a.e - E)), E};
+}
+// acc + y * h  with y, h extended (h may be an extended zero)
+__device__ __forceinline__ xd xmuladd_raw(xd acc, xd y, double hm, int he) {
+  double pm = y.m * hm;
+  int pe = y.e + he;
+  int E = max(acc.e, pe);
+  return xd{fma(pm, pow2_nonpos(pe - E), acc.m * pow2_nonpos(acc.e - E)), E};
+}
+// Convert an extended number to a double (0 below the normal range).
+__device__ __forceinline__ double xtod(xd a) {
+  if (a.m == 0.0 || a.e < -1100) return 0.0;
+  if (a.e > 1023) return __longlong_as_double(0x7ff0000000000000LL);
+  // split to stay within the range of pow2 for exponents near the limits
+  int e1 = a.e / 2, e2 = a.e - e1;
+  double s1 = __longlong_as_double((long long)(e1 + 1023) << 52);
+  double s2 = __longlong_as_double((long long)(e2 + 1023) << 52);
+  return a.m * s1 * s2;
+}
+// natural log of an extended number (m > 0)
+__device__ __forceinline__ double xlog(xd a) { return log(a.m) + (double)a.e * LN2; }
+
+// ------------------------------------------------------------------ workspace
+struct Workspace {
+  int N, P, NT, NB;     // NT = ceil(N/TILE), NB = NT(NT+1)/2 blocks of g
+  int mixed;
+  double m, omega_P, beta, k, half_k;
+  // O(N) per-particle state
+  double *R1, *RP;      // [N][4] bead 1 / bead P positions (x, y, z, 0)
+  double *Eint, *link;  // [N]
+  double *ccm; int *cce;          // c_{i+1} = exp(beta link_i)/(i+1), extended
+  double *C;            // [N+1] prefix sums of E_int + link
+  // g matrix, tile-packed triangle: block (t, s), s <= t, at (t(t+1)/2 + s) * TILE2,
+  // entry [i][j] = g for a = s*TILE + i (bead 1 particle), b = t*TILE + j (bead P particle)
+  void *gm;             // double (FP64) or float (MIXED) mantissas
+  int *ge;              // exponents
+  // recursion outputs (extended): forward y[0..N], S_f[0..N-1];
+  // backward Yb[0..N] (Yb[w] = mu_{N-1-w} 0-based), S_b[r] = B_{a=N-1-r}
+  double *yfm; int *yfe; double *sfm; int *sfe;
+  double *ybm; int *ybe; double *sbm; int *sbe;
+  // scalars: [0] V_B, [1] invZ mantissa, [2] reserved ; int [0] invZ exponent
+  double *scal; int *scal_i;
+  // force partial sums: rowpart/colpart [NB][TILE][4]
+  double *rowpart, *colpart;
+  int *status;          // device status word
+  // debug: potentials V^{[1,v]} and V^{[u,N]}
+  double *Vf, *Vb;
+};
+
+// kernel launchers (stream-ordered)
+cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+cudaError_t launch_gmat(const Workspace &w, cudaStream_t s);
+cudaError_t launch_chains(const Workspace &w, cudaStream_t s);
+cudaError_t launch_scalars(const Workspace &w, double *V_B, cudaStream_t s);
+cudaError_t launch_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
+
+}  // namespace bpimd

@@ -1,0 +1,152 @@
+// Pair Boltzmann factors and the scalar epilogue.
+//
+// gmat: g(u,v) = exp(-beta (1/2) m w_P^2 (r_v^P - r_u^1)^2) for every u <= v --
+// the closing-spring factor of the cycle energy E^{[u,v]} (Eq. e-recurrence-step,
+// last term) -- stored once per evaluation as an extended number 2^x =
+// mantissa(2^frac(x)) * 2^floor(x), x = -beta (1/2)k |d|^2 log2(e).
+// FP64: float64 difference, square and exp2.  MIXED: float64 difference
+// rounded to float32, float32 square, hardware ex2.approx.
+//
+// scalars: prefix sums C[l] (FP64), V^{[1,N]} = C[N] - ln(y_N)/beta, the
+// probability normaliser 1/(N y_N), and the potentials V^{[1,v]},
+// V^{[u,N]} for diagnostics.
+#include "bpimd_internal.cuh"
+
+namespace bpimd {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// block index -> (t, s) with s <= t, blk = t(t+1)/2 + s
+__device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
+  int tt = (int)((sqrt(8.0 * blk + 1.0) - 1.0) * 0.5);
+  while ((tt + 1) * (tt + 2) / 2 <= blk) ++tt;
+  while (tt * (tt + 1) / 2 > blk) --tt;
+  t = tt;
+  s = blk - tt * (tt + 1) / 2;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
+  const double cx = -w.beta * w.half_k * LOG2E;
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+    int t, s;
+    block_coords(blk, t, s);
+    const int j = threadIdx.x & 31;
+    const int b = t * TILE + j;  // bead-P particle
+    double bx = 0, by = 0, bz = 0;
+    if (b < w.N) { bx = w.RP[4 * b]; by = w.RP[4 * b + 1]; bz = w.RP[4 * b + 2]; }
+    for (int i = threadIdx.x >> 5; i < TILE; i += 8) {
+      const int a = s * TILE + i;  // bead-1 particle
+      const size_t idx = (size_t)blk * TILE2 + i * TILE + j;
+      if (b >= w.N || a > b) {
+        if (MIXED) ((float *)w.gm)[idx] = 0.0f; else ((double *)w.gm)[idx] = 0.0;
+        w.ge[idx] = XZERO_E;
+        continue;
+      }
+      const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
+      if (MIXED) {
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        const float x = (float)cx * fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        const float n = floorf(x);
+        float mm = ex2_approx(x - n);  // in [1, 2]
+        int e = (int)n;
+        if (mm >= 2.0f) { mm *= 0.5f; e += 1; }
+        ((float *)w.gm)[idx] = mm;
+        w.ge[idx] = e;
+      } else {
+        const double x = cx * fma(dx, dx, fma(dy, dy, dz * dz));
+        const double n = floor(x);
+        xd g = xnorm(exp2(x - n), (int)n);
+        ((double *)w.gm)[idx] = g.m;
+        w.ge[idx] = g.e;
+      }
+    }
+  }
+}
+
+// Single CTA: prefix sums, V_B, normaliser, diagnostic potentials.
+__global__ void __launch_bounds__(1024) scalars_kernel(Workspace w, double *V_B) {
+  __shared__ double warp_tot[32];
+  __shared__ double carry;
+  const int N = w.N;
+  if (threadIdx.x == 0) { carry = 0.0; w.C[0] = 0.0; }
+  __syncthreads();
+  // inclusive scan of A_i = E_int_i + link_i, C[i+1] = sum_{t<=i} A_t
+  for (int base = 0; base < N; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    double v = (i < N) ? (w.Eint[i] + w.link[i]) : 0.0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      double tsum = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0.0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        double u = __shfl_up_sync(0xffffffffu, tsum, o);
+        if (lane >= o) tsum += u;
+      }
+      warp_tot[lane] = tsum;  // inclusive
+    }
+    __syncthreads();
+    const double prefix = carry + (wid > 0 ? warp_tot[wid - 1] : 0.0);
+    if (i < N) w.C[i + 1] = prefix + v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = prefix + v;
+    __syncthreads();
+  }
+  // V_B and the normaliser 1/(N y_N)
+  const xd yN{w.yfm[N], w.yfe[N]};
+  if (threadIdx.x == 0) {
+    const double CN = w.C[N];
+    const double VB = CN - xlog(yN) / w.beta;
+    w.scal[0] = VB;
+    if (V_B) *V_B = VB;
+    xd inv = xnorm(1.0 / (yN.m * (double)N), -yN.e);
+    w.scal[1] = inv.m;
+    w.scal_i[0] = inv.e;
+    if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);
+  }
+  // diagnostic potentials: V^{[1,v]} = C[v] - ln(y_v)/beta,
+  // V^{[u,N]} = C[N] - C[u-1] - ln(B_u / N)/beta, V^{[N+1,N]} = 0
+  if (w.Vf) {
+    for (int v = threadIdx.x; v <= N; v += blockDim.x) {
+      w.Vf[v] = (v == 0) ? 0.0 : w.C[v] - xlog(xd{w.yfm[v], w.yfe[v]}) / w.beta;
+      if (v < N) {  // u = v+1, a = v, backward row r = N-1-a
+        const int r = N - 1 - v;
+        const xd B{w.sbm[r], w.sbe[r]};
+        w.Vb[v] = w.C[N] - w.C[v] - (xlog(B) - log((double)N)) / w.beta;
+      } else {
+        w.Vb[N] = 0.0;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gmat(const Workspace &w, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
+  if (w.mixed) gmat_kernel<true><<<grid, 256, 0, s>>>(w);
+  else gmat_kernel<false><<<grid, 256, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(const Workspace &w, double *V_B, cudaStream_t s) {
+  scalars_kernel<<<1, 1024, 0, s>>>(w, V_B);
+  return cudaGetLastError();
+}
+
+}  // namespace bpimd

@@ -1,0 +1,99 @@
+"""torch-facing wrappers of the bpimd library.
+
+``ExchangeEnergy`` owns one C-ABI context (``bpimd_create``) bound to the
+current CUDA stream and evaluates V^{[1,N]} and the bead forces of Algorithm 1
+on device tensors.  ``exchange_potential`` is the autograd form: its forward
+returns V^{[1,N]}; its backward multiplies the incoming gradient by -F, where F
+is the force the same kernel pass produced (the connection-probability force
+expression of Lemma expected-force is exactly -grad V), so no O(N^2) tensor is
+saved for backward.
+"""
+import torch
+
+from . import bpimd as _c
+
+
+class ExchangeEnergy:
+    """Exchange potential and forces for one system of N particles, P beads."""
+
+    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
+        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        self.N, self.P = int(N), int(P)
+        self.m, self.omega_P, self.beta = float(m), float(omega_P), float(beta)
+        self.precision = precision
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec)
+            self.ctx = _c.bpimd_create(self.cfg, self.stream)
+            self._V = torch.empty((), dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _c.bpimd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, pos):
+        if pos.dtype != torch.float64 or pos.device != self.device or tuple(pos.shape) != (self.N, self.P, 3):
+            raise ValueError(f"positions must be float64 [{self.N}][{self.P}][3] on {self.device}")
+        return pos.contiguous()
+
+    def forces(self, pos, out=None, V_out=None):
+        """Enqueue one evaluation; returns (V_B 0-d tensor, forces)."""
+        pos = self._check(pos)
+        F = out if out is not None else torch.empty_like(pos)
+        V = V_out if V_out is not None else torch.empty((), dtype=torch.float64, device=self.device)
+        _c.bpimd_exchange_energy_forces(self.ctx, pos, V, F)
+        return V, F
+
+    __call__ = forces
+
+    def forces_host(self, pos_host, F_host=None):
+        """Host-buffer entry point (copies in and out, synchronises)."""
+        import numpy as np
+        F_host = F_host if F_host is not None else torch.empty_like(pos_host)
+        V = np.zeros(1)
+        _c.bpimd_exchange_energy_forces_host(self.ctx, pos_host, V, F_host)
+        return float(V[0]), F_host
+
+    def potentials(self):
+        """(V^{[1,v]} for v=0..N, V^{[u,N]} for u=1..N+1, E_int) of the last evaluation."""
+        import numpy as np
+        Vf, Vb, Ei = np.empty(self.N + 1), np.empty(self.N + 1), np.empty(self.N)
+        _c.bpimd_get_potentials(self.ctx, Vf, Vb, Ei)
+        return Vf, Vb, Ei
+
+    def connection_probabilities(self):
+        """Dense N x N matrix Pr[l -> l'] of the last evaluation (device tensor)."""
+        M = torch.empty((self.N, self.N), dtype=torch.float64, device=self.device)
+        _c.bpimd_connection_probabilities(self.ctx, M)
+        return M
+
+    def sync(self):
+        _c.bpimd_sync(self.ctx)
+
+
+class _ExchangeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pos, engine):
+        V, F = engine.forces(pos)
+        ctx.save_for_backward(F)
+        return V
+
+    @staticmethod
+    def backward(ctx, gV):
+        (F,) = ctx.saved_tensors
+        return -gV * F, None
+
+
+def exchange_potential(pos, engine):
+    """V^{[1,N]}(pos) as a differentiable scalar; d/dpos is -F from the force kernel."""
+    return _ExchangeFn.apply(pos, engine)

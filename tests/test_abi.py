@@ -1,0 +1,83 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every entry point that include/bpimd.h declares, and rejects invalid
+configurations on the host before touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2305_18025_gb300 import bpimd, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bpimd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpimd_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return bpimd.load(build_if_missing=False)
+
+
+def test_header_declares_the_documented_calls():
+    names = declared_functions()
+    for required in ("bpimd_create", "bpimd_exchange_energy_forces", "bpimd_step", "bpimd_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s+(bpimd_\w+)", out))
+    for name in declared_functions():
+        assert name in exported, f"{name} declared in bpimd.h but not exported"
+        assert hasattr(lib, name)
+    assert set(bpimd.EXPORTED) <= exported
+
+
+def test_library_is_built_for_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", build.LIB], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_config_struct_matches_header_layout():
+    # N, P (2 x int32) then 3 doubles, 2 int32, 4 doubles, 2 int32, 4 doubles, uint64
+    assert ctypes.sizeof(bpimd.bpimd_config) == 8 + 24 + 8 + 32 + 8 + 32 + 8
+    assert bpimd.bpimd_config.dt.offset == 40
+    assert bpimd.bpimd_config.seed.offset == ctypes.sizeof(bpimd.bpimd_config) - 8
+
+
+@pytest.mark.parametrize("field,value", [
+    ("N", 0), ("P", 1), ("m", 0.0), ("omega_P", -1.0), ("beta", float("nan")),
+    ("beta", float("inf")), ("precision", 7), ("flags", 1),
+])
+def test_create_rejects_invalid_config_without_gpu(lib, field, value):
+    cfg = bpimd.make_config(8, 4, 1.0, 2.0, 1.0)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p(123)
+    rc = lib.bpimd_create(ctypes.byref(h), ctypes.byref(cfg), None)
+    assert rc == bpimd.BPIMD_ERR_ARG
+    assert h.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.bpimd_create(None, None, None) == bpimd.BPIMD_ERR_ARG
+    assert lib.bpimd_destroy(None) == bpimd.BPIMD_OK
+    assert lib.bpimd_exchange_energy_forces(None, None, None, None) == bpimd.BPIMD_ERR_ARG
+    assert lib.bpimd_sync(None) == bpimd.BPIMD_ERR_ARG
+    assert lib.bpimd_step(None, None, None, 1, None) == bpimd.BPIMD_ERR_ARG
+
+
+def test_status_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert bpimd.bpimd_status_string(code) != "unknown status"
+    assert "sm_103a" in bpimd.bpimd_version()

@@ -27,22 +27,22 @@ MUTANTS = {
     "step_drops_interior_energy": (
         "+ Eint[u - 1]\n", "\n"),
     "forward_drops_one_over_v": (
-        "V[v] = Et - (1.0 / beta) * log(s / (double)v);",
-        "V[v] = Et - (1.0 / beta) * log(s);"),
+        "V[v] = Et - (1.0 / beta) * LOG(s / (ora_real)v);",
+        "V[v] = Et - (1.0 / beta) * LOG(s);"),
     "backward_weight_one_over_u": (
-        "s += (1.0 / (double)l) * exp(-beta * (E[EIDX(N, u, l)] + W[l] - Et));",
-        "s += (1.0 / (double)u) * exp(-beta * (E[EIDX(N, u, l)] + W[l] - Et));"),
+        "s += (1.0 / (ora_real)l) * EXP(-beta * (E[EIDX(N, u, l)] + W[l] - Et));",
+        "s += (1.0 / (ora_real)u) * EXP(-beta * (E[EIDX(N, u, l)] + W[l] - Et));"),
     "close_cycle_shifted_backward_index": (
-        "exp(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l] - VN));",
-        "exp(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l - 1] - VN));"),
+        "EXP(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l] - VN));",
+        "EXP(-beta * (V[lp - 1] + E[EIDX(N, lp, l)] + W[l - 1] - VN));"),
     "direct_link_sign": (
-        "-expm1(-beta * (V[l] + W[l] - VN))", "expm1(-beta * (V[l] + W[l] - VN))"),
+        "-EXPM1(-beta * (V[l] + W[l] - VN))", "EXPM1(-beta * (V[l] + W[l] - VN))"),
     "bead1_force_wrong_neighbour_bead": (
         "- BEAD(pos, P, lp, P)[d]);", "- BEAD(pos, P, lp, 1)[d]);"),
     "beadP_force_drops_superdiagonal": (
         "int hi = l + 1 > N ? N : l + 1;", "int hi = l;"),
     "transposed_probability_in_bead1": (
-        "double pr = M[EIDX(N, lp, l)];", "double pr = M[EIDX(N, l, lp)];"),
+        "ora_real pr = M[EIDX(N, lp, l)];", "ora_real pr = M[EIDX(N, l, lp)];"),
     "interior_force_sign": (
         "BEAD(F, P, l, j)[d] = -k * (", "BEAD(F, P, l, j)[d] = k * ("),
     "base_case_drops_closing_spring": (

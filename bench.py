@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the bosonic exchange potential + forces on GB300.
+
+Metric: exchange V_B + force evaluations per second for N = 1024 bosons with
+P = 32 beads (beta = 1, m = hbar = 1, omega_P = sqrt(P)/beta), trapped-boson
+positions (centres N(0,1), bead offsets N(0,0.1), seed 3), in the mixed
+float32/float64 form (the reported `value`) and the plain float64 form
+(`fp64`).  A step is one full evaluation: bead pass, pair factors, forward
+and backward recursions, prefix sums, probability/force blocks, finalise.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas of the same workload (the
+single-system evaluation does not shard); `value` is the sum over ranks.
+`--impl reference` times the CPU oracle (Algorithm 1 in float64, one core) on
+the same workload on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exchange V_B+force evals/s at N=1024,P=32 (mixed vs FP64 GPU); MD steps/s"
+N_DEF, P_DEF, BETA_DEF, SEED_DEF = 1024, 32, 1.0, 3
+LAUNCHES_PER_EVAL = 6          # bead, pair factors, recursions, scalars, prob/force blocks, finalise
+DFMA_LATENCY_CYCLES = 64       # measured on GB300: dependent float64 FMA latency
+FLUSH_BYTES = 256 << 20        # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--P", type=int, default=P_DEF)
+    ap.add_argument("--beta", type=float, default=BETA_DEF)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bounded CPU-oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    return {"workload": f"trapped bosons N={args.N} P={args.P} beta={args.beta:g}: exchange V_B + all bead forces",
+            "N": args.N, "P": args.P, "beta": args.beta, "m": 1.0, "hbar": 1.0,
+            "positions": f"centres N(0,1), bead offsets N(0,0.1), seed {SEED_DEF}",
+            "parallelism": "independent replicas, one per GPU"}
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ roofline
+def load_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary, if the kernel's
+    sources are unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(kernel)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for rel in ent.get("sources", []):
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        except OSError:
+            return None
+    if h.hexdigest() != ent.get("sources_sha256"):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def roofline(stage_ms_per_eval, args, sm_mhz, peaks):
+    """Roofline object for the dominant stage."""
+    import numpy as np
+    from paper_2305_18025_gb300.bpimd import STAGE_NAMES
+    i = int(np.argmax(stage_ms_per_eval))
+    name = STAGE_NAMES[i]
+    t = stage_ms_per_eval[i] * 1e-3
+    N, P = args.N, args.P
+    clock = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if name == "recursions":
+        # N dependent steps per chain (forward and backward run concurrently);
+        # each step carries at least one dependent float64 FMA.
+        achieved = N / t
+        peak = clock / DFMA_LATENCY_CYCLES
+        obj = {"bound": "alu", "kind": "dependent-latency (float64 FMA chain)",
+               "achieved": achieved, "peak": peak, "unit": "chain steps/s",
+               "frac": achieved / peak,
+               "peak_source": f"measured DFMA latency {DFMA_LATENCY_CYCLES} cycles at the sampled SM clock"}
+    elif name == "bead_pass":
+        bytes_ = N * P * 24 + N * max(P - 2, 0) * 24 + N * 8 * 12
+        achieved = bytes_ / t / 1e9
+        obj = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": achieved / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        pairs = N * (N + 1) / 2
+        achieved = pairs / t
+        obj = {"bound": "alu", "kind": "pair throughput", "achieved": achieved, "peak": None,
+               "unit": "pairs/s", "frac": None}
+    obj["kernel"] = name
+    obj["traffic"] = load_traffic(name)
+    return obj
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2305_18025_gb300 import bpimd, inputs
+    from paper_2305_18025_gb300.exchange import ExchangeEnergy
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    N, P, beta = args.N, args.P, args.beta
+    wP = inputs.omega_P(P, beta)
+    pos_np = inputs.trapped_positions(N, P, SEED_DEF)
+    pos = torch.from_numpy(pos_np).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        peaks = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    results = {}
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("mixed", "fp64"):
+        eng = ExchangeEnergy(N, P, 1.0, wP, beta, precision=prec, device=dev)
+        F = torch.empty_like(pos)
+        V = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            eng.forces(pos, out=F, V_out=V)
+        eng.sync()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        bpimd.bpimd_profile_begin(eng.ctx, args.steps)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 255)          # untimed: evict L2 between steps
+            starts[k].record(stream)
+            eng.forces(pos, out=F, V_out=V)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        wall = time.perf_counter() - t_wall0
+        stage_ms, n_prof = bpimd.bpimd_profile_end(eng.ctx)
+        eng.sync()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        total_ms = max_over_ranks(sum(step_ms))
+        results[prec] = {
+            "value": world * args.steps / (total_ms * 1e-3),
+            "ms_per_step": total_ms / args.steps,
+            "median_ms": statistics.median(step_ms),
+            "stage_ms": (stage_ms / max(n_prof, 1)).tolist(),
+            "wall_s": wall,
+            "V_B": float(V.item()),
+        }
+        # end-to-end through the host entry point (pinned buffers), same metric
+        if prec == "mixed":
+            pos_h = torch.from_numpy(pos_np.copy()).pin_memory()
+            F_h = torch.empty_like(pos_h).pin_memory()
+            for _ in range(args.warmup):
+                eng.forces_host(pos_h, F_h)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                eng.forces_host(pos_h, F_h)
+            e2e_s = max_over_ranks(time.perf_counter() - t0)
+            barrier()
+            results["e2e"] = {"value": world * args.steps / e2e_s, "unit": "evals/s",
+                              "h2d_bytes_per_step": pos_h.numel() * 8,
+                              "d2h_bytes_per_step": F_h.numel() * 8 + 8,
+                              "api": "bpimd_exchange_energy_forces_host (pinned host buffers)"}
+        eng.close()
+    clocks = sampler.stop()
+
+    if rank != 0:
+        return None
+    mixed, fp64 = results["mixed"], results["fp64"]
+    from paper_2305_18025_gb300.bpimd import STAGE_NAMES
+    line = {
+        "metric": METRIC, "value": mixed["value"], "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": dict(workload(args), precision="mixed",
+                       l2="flushed between timed steps (256 MiB device write, untimed)"),
+        "fp64": {"value": fp64["value"], "unit": "evals/s", "ms_per_step": fp64["ms_per_step"],
+                 "dtype": "f64", "stages_ms": dict(zip(STAGE_NAMES, fp64["stage_ms"]))},
+        "stages_ms": dict(zip(STAGE_NAMES, mixed["stage_ms"])),
+        "e2e": results["e2e"],
+        "roofline": roofline(mixed["stage_ms"], args, clocks.get("sm_mhz"), peaks),
+        "roofline_fp64": roofline(fp64["stage_ms"], args, clocks.get("sm_mhz"), peaks),
+        "clocks": clocks,
+        "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
+        "V_B": {"mixed": mixed["V_B"], "fp64": fp64["V_B"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
+    return line
+
+
+def cpu_baseline(args, pos_np, wP, seconds=None, max_evals=None):
+    """The float64 oracle (Algorithm 1, single thread) on the host cores."""
+    import oracle
+    seconds = args.cpu_seconds if seconds is None else seconds
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.fast_pimdb(pos_np, 1.0, wP, args.beta)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_evals and n >= max_evals):
+            break
+    return {"value": n / el, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full evaluations of the same workload in {el:.1f} s "
+                      f"(C oracle, float64, single thread; host has {os.cpu_count()} cores)"}
+
+
+# ------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    from paper_2305_18025_gb300 import inputs
+    wP = inputs.omega_P(args.P, args.beta)
+    pos_np = inputs.trapped_positions(args.N, args.P, SEED_DEF)
+    import oracle
+    for _ in range(min(args.warmup, 3)):
+        oracle.fast_pimdb(pos_np, 1.0, wP, args.beta)
+    # bounded: at most ~120 s of oracle work however large --steps is
+    t0 = time.perf_counter()
+    oracle.fast_pimdb(pos_np, 1.0, wP, args.beta)
+    one = time.perf_counter() - t0
+    k = max(1, min(args.steps, int(120.0 / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        oracle.fast_pimdb(pos_np, 1.0, wP, args.beta)
+    el = time.perf_counter() - t0
+    value = k / el
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload(args), precision="fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{k} of {args.steps} requested steps timed (bounded to ~120 s); "
+                                   f"C oracle Algorithm 1, float64, single thread, host has {os.cpu_count()} cores"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        from paper_2305_18025_gb300 import build as _b
+        if not _b.up_to_date():
+            if rank == 0:
+                _b.build()
+            if world > 1:
+                # other ranks wait for rank 0's build
+                for _ in range(600):
+                    if _b.up_to_date():
+                        break
+                    time.sleep(1)
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,22 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
                int32_t nsteps, double *energies);
 
+/* ------------------------------------------------------------- profiling */
+/* Stage timing with CUDA events recorded on the context stream around each
+ * kernel of an evaluation.  Stage order:
+ *   0 bead pass, 1 pair Boltzmann factors, 2 forward+backward recursions,
+ *   3 prefix sums / V_B, 4 probability + force blocks, 5 force finalise. */
+#define BPIMD_NUM_STAGES 6
+
+/* Start recording stage events for up to `max_evals` following evaluations
+ * (older records are discarded).  Adds 7 event records per evaluation. */
+int bpimd_profile_begin(bpimd_ctx *ctx, int max_evals);
+
+/* Stop recording, synchronise, and write the summed device time of each stage
+ * in milliseconds to stage_ms[BPIMD_NUM_STAGES] and the number of recorded
+ * evaluations to *n_evals.  Either pointer may be NULL. */
+int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
+
 /* Human-readable text for a status code (static storage). */
 const char *bpimd_status_string(int status);
 

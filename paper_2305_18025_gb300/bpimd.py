@@ -30,7 +30,10 @@ EXPORTED = [
     "bpimd_create", "bpimd_destroy", "bpimd_exchange_energy_forces",
     "bpimd_exchange_energy_forces_host", "bpimd_sync", "bpimd_get_potentials",
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
+    "bpimd_profile_begin", "bpimd_profile_end",
 ]
+BPIMD_NUM_STAGES = 6
+STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "scalars", "prob_force_blocks", "force_finalize"]
 
 
 class bpimd_config(ctypes.Structure):
@@ -81,6 +84,8 @@ def load(build_if_missing=True):
     lib.bpimd_status_string.argtypes = [ip]
     lib.bpimd_status_string.restype = ctypes.c_char_p
     lib.bpimd_version.restype = ctypes.c_char_p
+    lib.bpimd_profile_begin.argtypes = [vp, ip]
+    lib.bpimd_profile_end.argtypes = [vp, vp, vp]
     for name in EXPORTED:
         if name not in ("bpimd_status_string", "bpimd_version"):
             getattr(lib, name).restype = ip
@@ -158,6 +163,19 @@ def bpimd_connection_probabilities(ctx, M):
 def bpimd_step(ctx, positions, velocities, nsteps, energies=None):
     _check(load().bpimd_step(ctx, _ptr(positions), _ptr(velocities), int(nsteps), _ptr(energies)),
            "bpimd_step")
+
+
+def bpimd_profile_begin(ctx, max_evals):
+    _check(load().bpimd_profile_begin(ctx, int(max_evals)), "bpimd_profile_begin")
+
+
+def bpimd_profile_end(ctx):
+    """Returns (per-stage summed milliseconds, number of evaluations)."""
+    import numpy as np
+    ms = np.zeros(BPIMD_NUM_STAGES)
+    n = ctypes.c_int()
+    _check(load().bpimd_profile_end(ctx, ms.ctypes.data, ctypes.byref(n)), "bpimd_profile_end")
+    return ms, n.value
 
 
 def make_config(N, P, m, omega_P, beta, precision=BPIMD_FP64, **md):

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "bpimd_internal.cuh"
 #include "md.cuh"
@@ -21,6 +22,11 @@ struct bpimd_ctx {
   double *d_pos, *d_F, *d_VB;  // staging for the _host entry point (lazy)
   bool evaluated;
   MDState md;
+  // stage profiling
+  bool prof_on;
+  int prof_max;
+  std::vector<cudaEvent_t> prof_events;  // (BPIMD_NUM_STAGES + 1) per evaluation
+  int prof_count;
 };
 
 namespace {
@@ -70,12 +76,23 @@ namespace bpimd {
 int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   const Workspace &w = ctx->w;
   cudaStream_t s = ctx->stream;
-  cudaError_t e;
-  if ((e = launch_bead_pass(w, pos, F, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if ((e = launch_gmat(w, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if ((e = launch_chains(w, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if ((e = launch_scalars(w, V_B, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if ((e = launch_forces(w, pos, F, s)) != cudaSuccess) return BPIMD_ERR_CUDA;
+  cudaEvent_t *ev = nullptr;
+  if (ctx->prof_on && ctx->prof_count < ctx->prof_max)
+    ev = &ctx->prof_events[(size_t)ctx->prof_count++ * (BPIMD_NUM_STAGES + 1)];
+  auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
+  mark(0);
+  if (launch_bead_pass(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(1);
+  if (launch_gmat(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(2);
+  if (launch_chains(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(3);
+  if (launch_scalars(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(4);
+  if (launch_prob_blocks(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(5);
+  if (launch_force_finalize(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  mark(6);
   ctx->evaluated = true;
   return BPIMD_OK;
 }
@@ -157,6 +174,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
 int bpimd_destroy(bpimd_ctx *ctx) {
   if (!ctx) return BPIMD_OK;
   cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
   md_free(&ctx->md);
   cudaFree(ctx->dev_block);
   cudaFree(ctx->d_pos);
@@ -230,6 +248,40 @@ int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities, int32_t ns
   rc = md_run(ctx, positions, velocities, nsteps, energies);
   if (rc != BPIMD_OK) return rc;
   return read_status(ctx);
+}
+
+int bpimd_profile_begin(bpimd_ctx *ctx, int max_evals) {
+  if (!ctx || max_evals < 1 || max_evals > (1 << 20)) return BPIMD_ERR_ARG;
+  const size_t need = (size_t)max_evals * (BPIMD_NUM_STAGES + 1);
+  while (ctx->prof_events.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return BPIMD_ERR_CUDA;
+    ctx->prof_events.push_back(e);
+  }
+  ctx->prof_max = max_evals;
+  ctx->prof_count = 0;
+  ctx->prof_on = true;
+  return BPIMD_OK;
+}
+
+int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  ctx->prof_on = false;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return BPIMD_ERR_CUDA;
+  double acc[BPIMD_NUM_STAGES] = {0};
+  for (int k = 0; k < ctx->prof_count; ++k) {
+    cudaEvent_t *ev = &ctx->prof_events[(size_t)k * (BPIMD_NUM_STAGES + 1)];
+    for (int i = 0; i < BPIMD_NUM_STAGES; ++i) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) return BPIMD_ERR_CUDA;
+      acc[i] += ms;
+    }
+  }
+  if (stage_ms)
+    for (int i = 0; i < BPIMD_NUM_STAGES; ++i) stage_ms[i] = acc[i];
+  if (n_evals) *n_evals = ctx->prof_count;
+  ctx->prof_count = 0;
+  return BPIMD_OK;
 }
 
 const char *bpimd_status_string(int status) {

@@ -135,7 +135,8 @@ cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, c
 cudaError_t launch_gmat(const Workspace &w, cudaStream_t s);
 cudaError_t launch_chains(const Workspace &w, cudaStream_t s);
 cudaError_t launch_scalars(const Workspace &w, double *V_B, cudaStream_t s);
-cudaError_t launch_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s);
+cudaError_t launch_force_finalize(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
 
 }  // namespace bpimd

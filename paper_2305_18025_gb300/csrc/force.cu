@@ -200,15 +200,17 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 
 }  // namespace
 
-cudaError_t launch_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
+cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w);
   else prob_force_kernel<false><<<grid, 256, 0, s>>>(w);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_finalize(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   force_finalize_kernel<<<(w.N + 255) / 256, 256, 0, s>>>(w, pos, F);
   return cudaGetLastError();
 }

@@ -61,6 +61,7 @@ extern "C" {
 #define BPIMD_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired          */
 #define BPIMD_ERR_NOMEM (-5)     /* device or host allocation failed            */
 #define BPIMD_ERR_STATE (-6)     /* call not valid for this context's state     */
+#define BPIMD_ERR_SIZE (-7)      /* problem larger than a fixed-size buffer      */
 
 /* ---------------------------------------------------------------- precision */
 /* BPIMD_FP64: every step in float64.
@@ -177,6 +178,32 @@ int bpimd_profile_begin(bpimd_ctx *ctx, int max_evals);
  * in milliseconds to stage_ms[BPIMD_NUM_STAGES] and the number of recorded
  * evaluations to *n_evals.  Either pointer may be NULL. */
 int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
+
+/* ----------------------------------------------- allocation-free variant */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory at the moment they need an evaluation: a host
+ * program whose memory manager owns every device allocation, a simulation loop
+ * that may not call cudaMalloc/cudaFree (they can synchronise the whole
+ * device and stall other streams), or an embedding with a fixed memory budget.
+ *
+ * Same computation and arguments as bpimd_exchange_energy_forces, without a
+ * context: cfg describes the system (N, P, m, omega_P, beta, precision; the MD
+ * fields are ignored), positions/V_B/forces are device pointers owned by the
+ * caller, cuda_stream is a cudaStream_t (NULL = default stream).  It allocates
+ * nothing: its scratch memory is one file-scope __device__ array of 1 MiB per
+ * device, which bounds the size to N <= BPIMD_NOALLOC_MAX_N (larger N returns
+ * BPIMD_ERR_SIZE before any work is enqueued).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call before any stream capture.
+ *   - Every call on a device shares the array, which keeps the previous call's
+ *     contents; calls whose work overlaps on the GPU (e.g. on two streams)
+ *     race on it.  Serialise them (one stream).
+ *   - Asynchronous; device-side status (non-finite inputs) is not reported:
+ *     non-finite positions give non-finite outputs. */
+#define BPIMD_NOALLOC_MAX_N 352
+int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, const double *positions,
+                                         double *V_B, double *forces, void *cuda_stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *bpimd_status_string(int status);

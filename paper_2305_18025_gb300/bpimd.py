@@ -18,6 +18,8 @@ BPIMD_ERR_CUDA = -3
 BPIMD_ERR_TIMEOUT = -4
 BPIMD_ERR_NOMEM = -5
 BPIMD_ERR_STATE = -6
+BPIMD_ERR_SIZE = -7
+BPIMD_NOALLOC_MAX_N = 352
 
 BPIMD_FP64 = 0
 BPIMD_MIXED = 1
@@ -30,7 +32,7 @@ EXPORTED = [
     "bpimd_create", "bpimd_destroy", "bpimd_exchange_energy_forces",
     "bpimd_exchange_energy_forces_host", "bpimd_sync", "bpimd_get_potentials",
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
-    "bpimd_profile_begin", "bpimd_profile_end",
+    "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
 ]
 BPIMD_NUM_STAGES = 6
 STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "scalars", "prob_force_blocks", "force_finalize"]
@@ -86,6 +88,7 @@ def load(build_if_missing=True):
     lib.bpimd_version.restype = ctypes.c_char_p
     lib.bpimd_profile_begin.argtypes = [vp, ip]
     lib.bpimd_profile_end.argtypes = [vp, vp, vp]
+    lib.bpimd_exchange_energy_forces_noalloc.argtypes = [ctypes.POINTER(bpimd_config), vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("bpimd_status_string", "bpimd_version"):
             getattr(lib, name).restype = ip
@@ -176,6 +179,19 @@ def bpimd_profile_end(ctx):
     n = ctypes.c_int()
     _check(load().bpimd_profile_end(ctx, ms.ctypes.data, ctypes.byref(n)), "bpimd_profile_end")
     return ms, n.value
+
+
+def bpimd_exchange_energy_forces_noalloc(cfg, positions, V_B, forces, stream=None):
+    """Allocation-free evaluation (no context; fixed 1 MiB device scratch, N <= 352).
+
+    For callers that cannot allocate device memory when they evaluate (their
+    memory manager owns all device memory, or cudaMalloc's device-wide
+    synchronisation is not allowed in their loop).  The first call on a device
+    sets up the scratch address and should precede any stream capture; calls
+    that overlap on the GPU race on the shared scratch."""
+    _check(load().bpimd_exchange_energy_forces_noalloc(ctypes.byref(cfg), _ptr(positions), _ptr(V_B),
+                                                       _ptr(forces), _stream_handle(stream)),
+           "bpimd_exchange_energy_forces_noalloc")
 
 
 def make_config(N, P, m, omega_P, beta, precision=BPIMD_FP64, **md):

@@ -293,6 +293,7 @@ const char *bpimd_status_string(int status) {
     case BPIMD_ERR_TIMEOUT: return "bounded device wait expired";
     case BPIMD_ERR_NOMEM: return "allocation failed";
     case BPIMD_ERR_STATE: return "call not valid in this state";
+    case BPIMD_ERR_SIZE: return "problem larger than the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }

@@ -78,6 +78,6 @@ def test_null_handles_are_rejected(lib):
 
 
 def test_status_strings(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert bpimd.bpimd_status_string(code) != "unknown status"
     assert "sm_103a" in bpimd.bpimd_version()

@@ -20,6 +20,7 @@ struct bpimd_ctx {
   size_t dev_bytes;
   int *host_status;    // pinned
   double *d_pos, *d_F, *d_VB;  // staging for the _host entry point (lazy)
+  double *d_Vf, *d_Vb;         // diagnostic potentials (bpimd_get_potentials)
   bool evaluated;
   MDState md;
   // stage profiling
@@ -128,12 +129,11 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   size_t oR1 = take(sizeof(double) * 4 * N), oRP = take(sizeof(double) * 4 * N);
   size_t oEint = take(sizeof(double) * N), oLink = take(sizeof(double) * N);
   size_t occm = take(sizeof(double) * N), occe = take(sizeof(int) * N);
+  size_t oicm = take(sizeof(double) * N), oice = take(sizeof(int) * N);
   size_t oC = take(sizeof(double) * (N + 1));
   size_t ogm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), oge = take(sizeof(int) * gelems);
   size_t oyfm = take(sizeof(double) * (N + 1)), oyfe = take(sizeof(int) * (N + 1));
-  size_t osfm = take(sizeof(double) * N), osfe = take(sizeof(int) * N);
   size_t oybm = take(sizeof(double) * (N + 1)), oybe = take(sizeof(int) * (N + 1));
-  size_t osbm = take(sizeof(double) * N), osbe = take(sizeof(int) * N);
   size_t oscal = take(sizeof(double) * 4), oscali = take(sizeof(int) * 4);
   size_t orow = take(sizeof(double) * NB * TILE * 4), ocol = take(sizeof(double) * NB * TILE * 4);
   size_t ost = take(sizeof(int) * 4);
@@ -148,16 +148,15 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.R1 = (double *)(b + oR1); w.RP = (double *)(b + oRP);
   w.Eint = (double *)(b + oEint); w.link = (double *)(b + oLink);
   w.ccm = (double *)(b + occm); w.cce = (int *)(b + occe);
+  w.icm = (double *)(b + oicm); w.ice = (int *)(b + oice);
   w.C = (double *)(b + oC);
   w.gm = (void *)(b + ogm); w.ge = (int *)(b + oge);
   w.yfm = (double *)(b + oyfm); w.yfe = (int *)(b + oyfe);
-  w.sfm = (double *)(b + osfm); w.sfe = (int *)(b + osfe);
   w.ybm = (double *)(b + oybm); w.ybe = (int *)(b + oybe);
-  w.sbm = (double *)(b + osbm); w.sbe = (int *)(b + osbe);
   w.scal = (double *)(b + oscal); w.scal_i = (int *)(b + oscali);
   w.rowpart = (double *)(b + orow); w.colpart = (double *)(b + ocol);
   w.status = (int *)(b + ost);
-  w.Vf = (double *)(b + oVf); w.Vb = (double *)(b + oVb);
+  ctx->d_Vf = (double *)(b + oVf); ctx->d_Vb = (double *)(b + oVb);
   if (cudaMemsetAsync(ctx->dev_block, 0, off, ctx->stream) != cudaSuccess ||
       cudaMallocHost(&ctx->host_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -223,9 +222,10 @@ int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *E
   if (!ctx->evaluated) return BPIMD_ERR_STATE;
   const size_t N = ctx->w.N;
   cudaStream_t s = ctx->stream;
-  if (V_fwd && cudaMemcpyAsync(V_fwd, ctx->w.Vf, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (launch_diag_potentials(ctx->w, ctx->d_Vf, ctx->d_Vb, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (V_fwd && cudaMemcpyAsync(V_fwd, ctx->d_Vf, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
-  if (V_bwd && cudaMemcpyAsync(V_bwd, ctx->w.Vb, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (V_bwd && cudaMemcpyAsync(V_bwd, ctx->d_Vb, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   if (Eint && cudaMemcpyAsync(Eint, ctx->w.Eint, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;

@@ -85,11 +85,16 @@ __global__ void __launch_bounds__(256) bead_pass_kernel(Workspace w, const doubl
     r1[0] = b1[0]; r1[1] = b1[1]; r1[2] = b1[2]; r1[3] = 0.0;
     rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
     // c_{l+1} = exp(beta link_l) / (l+1) = 2^x, x = beta link_l log2(e) - log2(l+1)
-    const double x = w.beta * lk * LOG2E - log2((double)(l + 1));
+    // |x| is clamped to 2^28 so that exponent sums stay in int32
+    const double x = fmin(fmax(w.beta * lk * LOG2E - log2((double)(l + 1)), -268435456.0), 268435456.0);
     const double n = floor(x);
     xd c = xnorm(exp2(x - n), (int)n);
     w.ccm[l] = c.m;
     w.cce[l] = c.e;
+    const double ni = floor(-x);
+    xd ic = xnorm(exp2(-x - ni), (int)ni);
+    w.icm[l] = ic.m;
+    w.ice[l] = ic.e;
   }
 }
 

@@ -38,7 +38,7 @@ constexpr int TILE = 32;              // row / source tile of the recursions and
 constexpr int TILE2 = TILE * TILE;
 constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
 constexpr int CHAIN_THREADS = 1024;
-constexpr int CHAIN_MAX_N = 7168;     // recursion state lives in shared memory (28 B per particle)
+constexpr int CHAIN_MAX_N = 6912;     // recursion state lives in shared memory (28 B per particle + 39 KB)
 constexpr double LOG2E = 1.4426950408889634074;
 constexpr double LN2 = 0.6931471805599453094;
 
@@ -112,23 +112,35 @@ struct Workspace {
   double *R1, *RP;      // [N][4] bead 1 / bead P positions (x, y, z, 0)
   double *Eint, *link;  // [N]
   double *ccm; int *cce;          // c_{i+1} = exp(beta link_i)/(i+1), extended
+  double *icm; int *ice;          // 1/c_{i+1}, extended
   double *C;            // [N+1] prefix sums of E_int + link
   // g matrix, tile-packed triangle: block (t, s), s <= t, at (t(t+1)/2 + s) * TILE2,
   // entry [i][j] = g for a = s*TILE + i (bead 1 particle), b = t*TILE + j (bead P particle)
   void *gm;             // double (FP64) or float (MIXED) mantissas
   int *ge;              // exponents
-  // recursion outputs (extended): forward y[0..N], S_f[0..N-1];
-  // backward Yb[0..N] (Yb[w] = mu_{N-1-w} 0-based), S_b[r] = B_{a=N-1-r}
-  double *yfm; int *yfe; double *sfm; int *sfe;
-  double *ybm; int *ybe; double *sbm; int *sbe;
+  // recursion outputs (extended): forward y[0..N]; backward Yb[0..N]
+  // (Yb[w] = mu_{N-1-w} 0-based; the backward row sums are B_{a+1} = Yb[N-a] / c_a)
+  double *yfm; int *yfe;
+  double *ybm; int *ybe;
   // scalars: [0] V_B, [1] invZ mantissa, [2] reserved ; int [0] invZ exponent
   double *scal; int *scal_i;
   // force partial sums: rowpart/colpart [NB][TILE][4]
   double *rowpart, *colpart;
   int *status;          // device status word
-  // debug: potentials V^{[1,v]} and V^{[u,N]}
-  double *Vf, *Vb;
 };
+
+// number of SMs of the current device (cached per device)
+inline int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 152;
+  }
+  return cached[dev];
+}
 
 // kernel launchers (stream-ordered)
 cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s);
@@ -138,5 +150,13 @@ cudaError_t launch_scalars(const Workspace &w, double *V_B, cudaStream_t s);
 cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s);
 cudaError_t launch_force_finalize(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
+cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);
+
+// B_{a+1} (1-based backward row sum for 0-based particle a) from the stored state
+__device__ __forceinline__ xd backward_row_sum(const Workspace &w, int a) {
+  const xd Y{w.ybm[w.N - a], w.ybe[w.N - a]};
+  if (a == 0) return Y;  // B_1 = Y_N
+  return xmul(Y, xd{w.icm[a - 1], w.ice[a - 1]});
+}
 
 }  // namespace bpimd

@@ -6,24 +6,32 @@
 // r = N-1-a and sources w = N-1-b so that it has the same lower-triangular
 // shape:  Y_0 = mu_N = 1, S_r = B_{a+1} = sum_{w<=r} Y_w g(a+1, b+1),
 //   Y_{r+1} = mu_a = c_a * S_r   (c_0 := 1 for the last row, Y_N = B_1).
-// Both are lower-triangular solves with the matrix of pair factors g.
+// Both are lower-triangular solves with the matrix H of pair factors g, and
+// with K(w, r) = c_r H(w, r) each is  Y_{r+1} = sum_{w<=r} K(w, r) Y_w.
 //
-// Schedule (rows in tiles of 32):
-//   phase a (all warps)   : rows of tile t += contributions of source tile t-1;
-//                           the diagonal 32x32 block of g is staged in smem.
-//   phase b (concurrently): warp 0 runs the 32 dependent steps of tile t
-//                           (lane j holds row 32t+j; each step adds the newest
-//                           y to every later row and finalises one row);
-//                           warps 1..31 add source tile t-1 to all rows of
-//                           tiles >= t+1.
-// Every value is an extended number (mantissa * 2^exponent), so a step is a
-// multiply-add; no exp/log is on the dependency chain.
-// MIXED: the bulk tile products are summed in float32 per 32-source tile and
-// then added to the float64 row accumulator; the dependent steps stay float64.
+// GB300 facts behind the schedule (measured): a float64 FMA has a 64-cycle
+// latency and a warp has one float64 instruction in flight at a time; a
+// release/acquire hand-off between warps inside a step costs far more than
+// the step itself.  So all intra-tile work stays in one warp:
+//   * warp 0 runs the 32 dependent steps of row tile t.  Lane j holds
+//     c_r * (partial row sum) of row 32t+j and the partial sum of row
+//     32(t+1)+j.  A step is one float64 FMA on the current row (the dependency
+//     chain: acc_j += K(i, j) y_i, exponents aligned with integer operations
+//     on the double's bits), one FMA on the next tile's row (off the chain),
+//     and a shuffle that broadcasts the new Y;
+//   * warp 2 stages, for tile t+1, the diagonal block pre-scaled by c and the
+//     block of H from source tile t+1 to the rows of tile t+2;
+//   * bulk warps (never on warp 0's sub-partition) add source tile t-1 to the
+//     rows of tiles >= t+2; tiles only meet at __syncthreads.
+// Every value is an extended number m * 2^e (int32 exponent), so no exp/log
+// sits on the dependency chain.  MIXED: the bulk products are summed in
+// float32 per 32-source tile and added to the float64 row accumulator; the
+// dependent steps and the tile hand-offs stay float64.
 #include "bpimd_internal.cuh"
 
 namespace bpimd {
 namespace {
+
 
 template <bool MIXED>
 struct GView {
@@ -42,144 +50,268 @@ struct GView {
   __device__ __forceinline__ int e(size_t i) const { return ge[i]; }
 };
 
+// x * 2^k for k <= 0 by integer arithmetic on the exponent field (x >= 0 normal
+// or zero); 0 when the result would leave the normal range.
+__device__ __forceinline__ double scale_nonpos(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)(b >> 52);  // sign bit is 0
+  return (ex + k <= 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
+}
+
+// acc + K * y with K = (km, ke) normalised (or an extended zero), y normalised,
+// acc any positive mantissa: one float64 FMA.
+__device__ __forceinline__ xd fma_x(xd acc, double km, int ke, xd y) {
+  const int pe = ke + y.e;
+  const int E = max(acc.e, pe);
+  return xd{fma(scale_nonpos(km, pe - E), y.m, scale_nonpos(acc.m, acc.e - E)), E};
+}
+
+// acc + K * y, branch-free, for the dependency chain.  Operands are extended
+// numbers whose mantissas are normal doubles in [1, 2^60) (an extended zero is
+// carried as mantissa 1 with exponent XZERO_E, i.e. 2^-536870912).  Both
+// operands are scaled by 2^k, k <= 0 clamped at -1000, by adding k to the
+// exponent field of the high word: a clamped operand is below 2^-900 of the
+// other and cannot change the float64 sum.  One float64 FMA, five integer ops.
+__device__ __forceinline__ xd fma_chain(xd acc, double km, int ke, xd y) {
+  const int pe = ke + y.e;
+  const int E = max(acc.e, pe);
+  const int k1 = max(pe - E, -1000), k2 = max(acc.e - E, -1000);
+  const double ks = __hiloint2double(__double2hiint(km) + k1 * (1 << 20), __double2loint(km));
+  const double as = __hiloint2double(__double2hiint(acc.m) + k2 * (1 << 20), __double2loint(acc.m));
+  return xd{fma(ks, y.m, as), E};
+}
+
+// Explicit shared-memory loads (32-bit shared-window addresses).
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ double lds_f64(unsigned a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int lds_s32(unsigned a) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+
+// Normalise with integer ops only (m > 0 normal, or 0).
+__device__ __forceinline__ xd xnorm_int(xd a) {
+  const long long b = __double_as_longlong(a.m);
+  if (b <= 0) return xd{0.0, XZERO_E};
+  const int ex = (int)(b >> 52);
+  return xd{__longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL), a.e + ex - 1023};
+}
+
+// a * b with integer normalisation (one float64 multiply).
+__device__ __forceinline__ xd xmul_int(xd a, xd b) { return xnorm_int(xd{a.m * b.m, a.e + b.e}); }
+
+// Round a mantissa in [1,2) to float with integer ops (no float64 conversion unit).
+__device__ __forceinline__ float mant_to_float(double m) {
+  const long long b = __double_as_longlong(m);
+  const long long frac = b & 0x000fffffffffffffLL;
+  return __int_as_float((int)((frac + (1LL << 28)) >> 29) + 0x3f800000);
+}
+
 struct ChainSmem {
-  double *Ym;
-  int *Ye;
-  float *Y32;  // float copy of the mantissas (MIXED bulk)
-  double *Am;
+  double *Ym;  // [N+1] Y mantissas
+  int *Ye;     // [N+1]
+  double *Am;  // [N] bulk row sums (sources of tiles <= t-1 for rows of tile t+1)
   int *Ae;
-  double *Dm;  // [32][33]
-  int *De;     // [32][33]
+  double *Kdm;  // [2][32][33] c-scaled diagonal blocks (double buffer)
+  int *Kde;
+  double *Hom;  // [2][32][33] H(source of tile t, row of tile t+1) (double buffer)
+  int *Hoe;
 };
 
 template <bool MIXED, bool BWD>
 __device__ void run_chain(const Workspace &w, ChainSmem sm) {
-  const int N = w.N;
+  const int N = w.N, NT = w.NT;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   GView<MIXED> G{w.gm, w.ge};
-  // H(src, row) for this direction
   auto hidx = [&](int src, int row) -> size_t {
     return BWD ? GView<MIXED>::idx(N - 1 - row, N - 1 - src) : GView<MIXED>::idx(src, row);
   };
   auto coef = [&](int row) -> xd {
-    if (!BWD) return xd{w.ccm[row], w.cce[row]};
+    if (!BWD) return xd{__ldg(w.ccm + row), __ldg(w.cce + row)};
     if (row >= N - 1) return xd{1.0, 0};
-    return xd{w.ccm[N - 2 - row], w.cce[N - 2 - row]};
+    return xd{__ldg(w.ccm + N - 2 - row), __ldg(w.cce + N - 2 - row)};
   };
   double *gYm = BWD ? w.ybm : w.yfm;
   int *gYe = BWD ? w.ybe : w.yfe;
-  double *gSm = BWD ? w.sbm : w.sfm;
-  int *gSe = BWD ? w.sbe : w.sfe;
+  // bulk warps: every warp except the chain warp, the stager and the other
+  // warps of the chain warp's sub-partition (warp id % 4 == 0)
+  auto bulk_warp = [](int q) { return q != 2 && (q & 3) != 0; };
+  const bool is_bulk = bulk_warp(wid);
+  int nbulk = 0, bulk_rank = 0;
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+    if (bulk_warp(q)) { if (q < wid) ++bulk_rank; ++nbulk; }
 
-  for (int r = tid; r < N; r += blockDim.x) { sm.Am[r] = 0.0; sm.Ae[r] = XZERO_E; }
-  if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; sm.Y32[0] = 1.0f; }
-  __syncthreads();
-
-  const int NT = w.NT;
-  for (int t = 0; t < NT; ++t) {
-    const int r0 = t * TILE;
-    // ---------------- phase a: critical update of tile t with source tile t-1
-    if (t >= 1) {
-      const int r = r0 + wid;
-      if (r < N) {
-        const int src = r0 - TILE + lane;
-        const size_t gi = hidx(src, r);
-        if (MIXED) {
-          float pm = sm.Y32[src] * G.mf(gi);
-          int pe = sm.Ye[src] + G.e(gi);
-          int E = pe;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-          float v = pm * pow2f_nonpos(pe - E);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) {
-            xd a = xadd_raw(xd{sm.Am[r], sm.Ae[r]}, xd{(double)v, E});
-            a = xnorm(a.m, a.e);
-            sm.Am[r] = a.m; sm.Ae[r] = a.e;
-          }
-        } else {
-          double pm = sm.Ym[src] * G.m(gi);
-          int pe = sm.Ye[src] + G.e(gi);
-          int E = pe;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-          double v = pm * pow2_nonpos(pe - E);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) {
-            xd a = xadd_raw(xd{sm.Am[r], sm.Ae[r]}, xd{v, E});
-            a = xnorm(a.m, a.e);
-            sm.Am[r] = a.m; sm.Ae[r] = a.e;
-          }
-        }
-      }
-    }
-    {  // stage the diagonal block: D[i][j] = H(r0+i, r0+j) for i <= j
-      const int src = r0 + wid, row = r0 + lane;
-      double dm = 0.0;
-      int de = XZERO_E;
+  // Load the 32x32 block H(srcbase+i, rowbase+j) into smem dm/de[i*33+j] (one
+  // warp).  Global loads are coalesced along the bead-P particle b of the
+  // stored g: rows (b = row) in the forward chain, sources (b = N-1-src) in the
+  // backward chain.  Pairs outside 0 <= src <= row < N are stored as zero.
+  auto load_block = [&](int srcbase, int rowbase, double *dm, int *de) {
+#pragma unroll 4
+    for (int k = 0; k < TILE; ++k) {
+      const int i = BWD ? lane : k, j = BWD ? k : lane;
+      const int src = srcbase + i, row = rowbase + j;
+      double m = 1.0;  // extended zero of fma_chain: 1 * 2^XZERO_E
+      int e = XZERO_E;
       if (row < N && src <= row) {
         const size_t gi = hidx(src, row);
-        dm = G.m(gi);
-        de = G.e(gi);
+        m = MIXED ? (double)__ldg((const float *)w.gm + gi) : __ldg((const double *)w.gm + gi);
+        e = __ldg(w.ge + gi);
       }
-      sm.Dm[wid * 33 + lane] = dm;
-      sm.De[wid * 33 + lane] = de;
+      dm[i * 33 + j] = m;
+      de[i * 33 + j] = e;
     }
-    __syncthreads();
-    // ---------------- phase b
+  };
+  // stage, for row tile tt, the c-scaled diagonal block and the block of H
+  // from source tile tt to the rows of tile tt+1 into buffer buf (one warp)
+  auto stage_diag = [&](int tt, int buf) {
+    const int r0 = tt * TILE, row = r0 + lane;
+    double *dm = sm.Kdm + buf * 32 * 33;
+    int *de = sm.Kde + buf * 32 * 33;
+    load_block(r0, r0 + TILE, sm.Hom + buf * 32 * 33, sm.Hoe + buf * 32 * 33);
+    load_block(r0, r0, dm, de);
+    __syncwarp();
+    const xd c = (row < N) ? xnorm_int(coef(row)) : xd{1.0, 0};
+    for (int i = 0; i < TILE; ++i) {
+      const xd k = xmul_int(c, xd{dm[i * 33 + lane], de[i * 33 + lane]});
+      dm[i * 33 + lane] = k.m;
+      de[i * 33 + lane] = k.e;
+    }
+  };
+
+  for (int r = tid; r < N; r += blockDim.x) { sm.Am[r] = 0.0; sm.Ae[r] = XZERO_E; }
+  if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; }
+  xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
+  if (wid == 2) stage_diag(0, 0);
+  __syncthreads();
+
+  for (int t = 0; t < NT; ++t) {
+    const int r0 = t * TILE, buf = t & 1;
     if (wid == 0) {
+      // ------------------------------------------------ dependent steps of tile t
       const int row = r0 + lane;
-      xd acc = (row < N) ? xd{sm.Am[row], sm.Ae[row]} : xd{0.0, XZERO_E};
-      xd ycur{sm.Ym[r0], sm.Ye[r0]};
-      for (int i = 0; i < TILE; ++i) {
-        const int r = r0 + i;
-        if (r >= N) break;
-        if (lane >= i) acc = xmuladd_raw(acc, ycur, sm.Dm[i * 33 + lane], sm.De[i * 33 + lane]);
-        xd ynew{0.0, 0};
-        if (lane == i) {
-          const xd S = xnorm(acc.m, acc.e);
-          ynew = xmul(S, coef(r));
-          sm.Ym[r + 1] = ynew.m;
-          sm.Ye[r + 1] = ynew.e;
-          sm.Y32[r + 1] = (float)ynew.m;
-          gSm[r] = S.m;
-          gSe[r] = S.e;
-        }
-        ycur.m = __shfl_sync(0xffffffffu, ynew.m, i);
-        ycur.e = __shfl_sync(0xffffffffu, ynew.e, i);
+      xd acc{0.0, XZERO_E};
+      if (row < N) {
+        acc = xadd_raw(xd{sm.Am[row], sm.Ae[row]}, nxt);
+        acc = xmul_int(xnorm(acc.m, acc.e), coef(row));  // acc' = c_row * (sum over sources < r0)
       }
-    } else if (t >= 1) {
-      // bulk: rows of tiles >= t+1 += source tile t-1
+      xd ycur{sm.Ym[r0], sm.Ye[r0]};
+      const double *Kdm = sm.Kdm + buf * 32 * 33, *Hom = sm.Hom + buf * 32 * 33;
+      const int *Kde = sm.Kde + buf * 32 * 33, *Hoe = sm.Hoe + buf * 32 * 33;
+      if (!(acc.m > 0.0)) acc = xd{1.0, XZERO_E};
+      nxt = xd{1.0, XZERO_E};
+      // 32 steps, no branches and no stores: rows past N and finished rows see
+      // extended zeros in the staged blocks, and row j's accumulator is final
+      // after step j (later steps add at most 2^-1000 of it).
+      // block entries of step i+1 are loaded (explicit ld.shared) before step
+      // i's shuffle, so no load latency sits on the dependency chain
+      const unsigned aKm = smem_addr(Kdm + lane), aHm = smem_addr(Hom + lane);
+      const unsigned aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
+      double km = lds_f64(aKm), hm = lds_f64(aHm);
+      int ke = lds_s32(aKe), he = lds_s32(aHe);
+#pragma unroll
+      for (int i = 0; i < TILE; ++i) {
+        double km1 = 0.0, hm1 = 0.0;
+        int ke1 = 0, he1 = 0;
+        if (i + 1 < TILE) {
+          km1 = lds_f64(aKm + (i + 1) * 33 * 8);
+          hm1 = lds_f64(aHm + (i + 1) * 33 * 8);
+          ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
+          he1 = lds_s32(aHe + (i + 1) * 33 * 4);
+        }
+        acc = fma_chain(acc, km, ke, ycur);  // the dependency chain
+        nxt = fma_chain(nxt, hm, he, ycur);  // next tile's rows, off the chain
+        ycur.m = __shfl_sync(0xffffffffu, acc.m, i);
+        ycur.e = __shfl_sync(0xffffffffu, acc.e, i);
+        km = km1; hm = hm1; ke = ke1; he = he1;
+      }
+      if (row < N) {  // Y_{row+1} = final accumulator of row `row`
+        const xd yn = xnorm_int(acc);
+        sm.Ym[row + 1] = yn.m;
+        sm.Ye[row + 1] = yn.e;
+      }
+      nxt = xnorm_int(nxt);
+    } else if (wid == 2) {
+      if (t + 1 < NT) stage_diag(t + 1, buf ^ 1);
+    } else if (is_bulk && t >= 1) {
+      // ------------------------------ bulk: source tile t-1 -> rows of tiles >= t+1
       const int srcbase = r0 - TILE;
-      for (int r = r0 + TILE + (tid - 32); r < N; r += blockDim.x - 32) {
-        xd acc{sm.Am[r], sm.Ae[r]};
-        if (MIXED) {
-          float s = 0.0f;
-          int E = XZERO_E;
+      if (!BWD) {
+        // thread per row: loads coalesced along rows (b = row)
+        const int bthreads = nbulk * 32;
+        for (int r = r0 + TILE + bulk_rank * 32 + lane; r < N; r += bthreads) {
+          xd acc{sm.Am[r], sm.Ae[r]};
+          int E = XZERO_E;  // pass 1: largest exponent of the tile's terms (integer only)
 #pragma unroll 8
-          for (int i = 0; i < TILE; ++i) {
-            const int src = srcbase + i;
-            const size_t gi = hidx(src, r);
-            const float pm = sm.Y32[src] * G.mf(gi);
-            const int pe = sm.Ye[src] + G.e(gi);
-            const int En = max(E, pe);
-            s = fmaf(pm, pow2f_nonpos(pe - En), s * pow2f_nonpos(E - En));
-            E = En;
+          for (int i = 0; i < TILE; ++i) E = max(E, sm.Ye[srcbase + i] + __ldg(w.ge + hidx(srcbase + i, r)));
+          if (MIXED) {
+            float sacc = 0.0f;
+#pragma unroll 8
+            for (int i = 0; i < TILE; ++i) {
+              const int src = srcbase + i;
+              const size_t gi = hidx(src, r);
+              sacc = fmaf(mant_to_float(sm.Ym[src]) * __ldg((const float *)w.gm + gi),
+                          pow2f_nonpos(sm.Ye[src] + __ldg(w.ge + gi) - E), sacc);
+            }
+            acc = xadd_raw(acc, xd{(double)sacc, E});
+          } else {
+            double sacc = 0.0;
+#pragma unroll 8
+            for (int i = 0; i < TILE; ++i) {
+              const int src = srcbase + i;
+              const size_t gi = hidx(src, r);
+              sacc = fma(scale_nonpos(__ldg((const double *)w.gm + gi), sm.Ye[src] + __ldg(w.ge + gi) - E),
+                         sm.Ym[src], sacc);
+            }
+            acc = xadd_raw(acc, xd{sacc, E});
           }
-          acc = xadd_raw(acc, xd{(double)s, E});
-        } else {
-#pragma unroll 8
-          for (int i = 0; i < TILE; ++i) {
-            const int src = srcbase + i;
+          acc = xnorm(acc.m, acc.e);
+          sm.Am[r] = acc.m;
+          sm.Ae[r] = acc.e;
+        }
+      } else {
+        // warp per group of 32 rows, lane per source: loads coalesced along
+        // sources (b = N-1-src); each row is a warp reduction.
+        const int src = srcbase + lane;
+        const int ys = sm.Ye[src];
+        const float y32 = mant_to_float(sm.Ym[src]);
+        const double y64 = sm.Ym[src];
+        const int ngroups = (N - (r0 + TILE) + TILE - 1) / TILE;
+        for (int gidx = bulk_rank; gidx < ngroups; gidx += nbulk) {
+          const int rbase = r0 + TILE + gidx * TILE;
+          xd mine{0.0, XZERO_E};  // row rbase+lane's tile sum, gathered from the reductions
+          for (int j = 0; j < TILE; ++j) {
+            const int r = rbase + j;
+            if (r >= N) break;
             const size_t gi = hidx(src, r);
-            acc = xmuladd_raw(acc, xd{sm.Ym[src], sm.Ye[src]}, G.m(gi), G.e(gi));
+            const int e = ys + __ldg(w.ge + gi);
+            int E = e;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+            if (MIXED) {
+              float v = y32 * __ldg((const float *)w.gm + gi) * pow2f_nonpos(e - E);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+              if (lane == j) mine = xd{(double)v, E};
+            } else {
+              double v = scale_nonpos(__ldg((const double *)w.gm + gi), e - E) * y64;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+              if (lane == j) mine = xd{v, E};
+            }
+          }
+          const int r = rbase + lane;
+          if (r < N) {
+            xd acc = xadd_raw(xd{sm.Am[r], sm.Ae[r]}, mine);
+            acc = xnorm(acc.m, acc.e);
+            sm.Am[r] = acc.m;
+            sm.Ae[r] = acc.e;
           }
         }
-        acc = xnorm(acc.m, acc.e);
-        sm.Am[r] = acc.m;
-        sm.Ae[r] = acc.e;
       }
     }
     __syncthreads();
@@ -195,34 +327,46 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 1) chain_kernel(Workspace w) {
   unsigned char *p = smem_raw;
   sm.Ym = (double *)p; p += sizeof(double) * (N + 1);
   sm.Am = (double *)p; p += sizeof(double) * N;
-  sm.Dm = (double *)p; p += sizeof(double) * 32 * 33;
+  sm.Kdm = (double *)p; p += sizeof(double) * 2 * 32 * 33;
+  sm.Hom = (double *)p; p += sizeof(double) * 2 * 32 * 33;
   sm.Ye = (int *)p; p += sizeof(int) * (N + 1);
   sm.Ae = (int *)p; p += sizeof(int) * N;
-  sm.De = (int *)p; p += sizeof(int) * 32 * 33;
-  sm.Y32 = (float *)p;
+  sm.Kde = (int *)p; p += sizeof(int) * 2 * 32 * 33;
+  sm.Hoe = (int *)p; p += sizeof(int) * 2 * 32 * 33;
   if (blockIdx.x == 0) run_chain<MIXED, false>(w, sm);
   else run_chain<MIXED, true>(w, sm);
 }
 
-size_t chain_smem_bytes(int N) {
-  return sizeof(double) * ((size_t)(N + 1) + N + 32 * 33) + sizeof(int) * ((size_t)(N + 1) + N + 32 * 33)
-         + sizeof(float) * (size_t)(N + 1);
+constexpr size_t chain_smem_bytes(int N) {
+  return sizeof(double) * ((size_t)(N + 1) + N + 4 * 32 * 33) + sizeof(int) * ((size_t)(N + 1) + N + 4 * 32 * 33);
 }
+static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
 
 }  // namespace
 
+// Raise the dynamic shared-memory limit of both chain kernels to the maximum
+// once per process and device (a host call that must not sit between the
+// launches of an evaluation).
+cudaError_t prepare_chains() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  const int bytes = (int)chain_smem_bytes(CHAIN_MAX_N);
+  e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
 cudaError_t launch_chains(const Workspace &w, cudaStream_t s) {
+  cudaError_t e = prepare_chains();
+  if (e != cudaSuccess) return e;
   const size_t bytes = chain_smem_bytes(w.N);
-  cudaError_t e;
-  if (w.mixed) {
-    e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    chain_kernel<true><<<2, CHAIN_THREADS, bytes, s>>>(w);
-  } else {
-    e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    chain_kernel<false><<<2, CHAIN_THREADS, bytes, s>>>(w);
-  }
+  if (w.mixed) chain_kernel<true><<<2, CHAIN_THREADS, bytes, s>>>(w);
+  else chain_kernel<false><<<2, CHAIN_THREADS, bytes, s>>>(w);
   return cudaGetLastError();
 }
 

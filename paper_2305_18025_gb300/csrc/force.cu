@@ -117,12 +117,12 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
   }
 }
 
-// q_l = y_l B_{l+1} / (N y_N), 0-based particle p -> y_{p+1} B_{p+2} (1-based) ...
-// In 0-based particle index p (row p, column p+1): Pr = 1 - y[p+1] * S_b[N-2-p] * invZ.
+// Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,
+// column p+1) this is 1 - y[p+1] B(p+1) / (N y_N) with B(a) the backward row sum
+// of particle a.
 __device__ __forceinline__ double direct_link_prob(const Workspace &w, int p) {
   const xd y{w.yfm[p + 1], w.yfe[p + 1]};
-  const int r = w.N - 2 - p;
-  const xd B{w.sbm[r], w.sbe[r]};
+  const xd B = backward_row_sum(w, p + 1);
   const double q = xtod(xmul(xmul(y, B), xd{w.scal[1], w.scal_i[0]}));
   return 1.0 - q;
 }
@@ -201,9 +201,7 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 }  // namespace
 
 cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s) {
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w);
   else prob_force_kernel<false><<<grid, 256, 0, s>>>(w);

@@ -68,24 +68,20 @@ size_t noalloc_layout(Workspace &w, char *base) {
   w.link = (double *)take(sizeof(double) * N);
   w.ccm = (double *)take(sizeof(double) * N);
   w.cce = (int *)take(sizeof(int) * N);
+  w.icm = (double *)take(sizeof(double) * N);
+  w.ice = (int *)take(sizeof(int) * N);
   w.C = (double *)take(sizeof(double) * (N + 1));
   w.gm = (void *)take((w.mixed ? sizeof(float) : sizeof(double)) * gelems);
   w.ge = (int *)take(sizeof(int) * gelems);
   w.yfm = (double *)take(sizeof(double) * (N + 1));
   w.yfe = (int *)take(sizeof(int) * (N + 1));
-  w.sfm = (double *)take(sizeof(double) * N);
-  w.sfe = (int *)take(sizeof(int) * N);
   w.ybm = (double *)take(sizeof(double) * (N + 1));
   w.ybe = (int *)take(sizeof(int) * (N + 1));
-  w.sbm = (double *)take(sizeof(double) * N);
-  w.sbe = (int *)take(sizeof(int) * N);
   w.scal = (double *)take(sizeof(double) * 4);
   w.scal_i = (int *)take(sizeof(int) * 4);
   w.rowpart = (double *)take(sizeof(double) * NB * TILE * 4);
   w.colpart = (double *)take(sizeof(double) * NB * TILE * 4);
   w.status = (int *)take(sizeof(int) * 4);
-  w.Vf = nullptr;  // no diagnostic potentials
-  w.Vb = nullptr;
   return off;
 }
 

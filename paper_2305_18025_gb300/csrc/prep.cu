@@ -7,9 +7,9 @@
 // FP64: float64 difference, square and exp2.  MIXED: float64 difference
 // rounded to float32, float32 square, hardware ex2.approx.
 //
-// scalars: prefix sums C[l] (FP64), V^{[1,N]} = C[N] - ln(y_N)/beta, the
-// probability normaliser 1/(N y_N), and the potentials V^{[1,v]},
-// V^{[u,N]} for diagnostics.
+// scalars: prefix sums C[l] (FP64), V^{[1,N]} = C[N] - ln(y_N)/beta and the
+// probability normaliser 1/(N y_N).  The potentials V^{[1,v]}, V^{[u,N]} for
+// diagnostics are computed on demand by diag_potentials_kernel.
 #include "bpimd_internal.cuh"
 
 namespace bpimd {
@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
       const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
       if (MIXED) {
         const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-        const float x = (float)cx * fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
+        const float x = fmaxf((float)cx * fmaf(fx, fx, fmaf(fy, fy, fz * fz)), -268435456.0f);
         const float n = floorf(x);
         float mm = ex2_approx(x - n);  // in [1, 2]
         int e = (int)n;
@@ -59,7 +60,8 @@ __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
         ((float *)w.gm)[idx] = mm;
         w.ge[idx] = e;
       } else {
-        const double x = cx * fma(dx, dx, fma(dy, dy, dz * dz));
+        // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
+        const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
         const double n = floor(x);
         xd g = xnorm(exp2(x - n), (int)n);
         ((double *)w.gm)[idx] = g.m;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
   }
 }
 
-// Single CTA: prefix sums, V_B, normaliser, diagnostic potentials.
+// Single CTA: prefix sums, V_B, normaliser.
 __global__ void __launch_bounds__(1024) scalars_kernel(Workspace w, double *V_B) {
   __shared__ double warp_tot[32];
   __shared__ double carry;
@@ -116,28 +118,32 @@ __global__ void __launch_bounds__(1024) scalars_kernel(Workspace w, double *V_B)
     w.scal_i[0] = inv.e;
     if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);
   }
-  // diagnostic potentials: V^{[1,v]} = C[v] - ln(y_v)/beta,
-  // V^{[u,N]} = C[N] - C[u-1] - ln(B_u / N)/beta, V^{[N+1,N]} = 0
-  if (w.Vf) {
-    for (int v = threadIdx.x; v <= N; v += blockDim.x) {
-      w.Vf[v] = (v == 0) ? 0.0 : w.C[v] - xlog(xd{w.yfm[v], w.yfe[v]}) / w.beta;
-      if (v < N) {  // u = v+1, a = v, backward row r = N-1-a
-        const int r = N - 1 - v;
-        const xd B{w.sbm[r], w.sbe[r]};
-        w.Vb[v] = w.C[N] - w.C[v] - (xlog(B) - log((double)N)) / w.beta;
-      } else {
-        w.Vb[N] = 0.0;
-      }
+}
+
+// Diagnostic potentials of the last evaluation (on demand):
+//   V^{[1,v]} = C[v] - ln(y_v)/beta,  V^{[u,N]} = C[N] - C[u-1] - ln(B_u / N)/beta.
+__global__ void diag_potentials_kernel(Workspace w, double *Vf, double *Vb) {
+  const int N = w.N;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= N; v += gridDim.x * blockDim.x) {
+    Vf[v] = (v == 0) ? 0.0 : w.C[v] - xlog(xd{w.yfm[v], w.yfe[v]}) / w.beta;
+    if (v < N) {  // u = v+1, particle a = v
+      const xd B = backward_row_sum(w, v);
+      Vb[v] = w.C[N] - w.C[v] - (xlog(B) - log((double)N)) / w.beta;
+    } else {
+      Vb[N] = 0.0;
     }
   }
 }
 
 }  // namespace
 
+cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s) {
+  diag_potentials_kernel<<<(w.N + 256) / 256, 256, 0, s>>>(w, Vf, Vb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gmat(const Workspace &w, cudaStream_t s) {
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   if (w.mixed) gmat_kernel<true><<<grid, 256, 0, s>>>(w);
   else gmat_kernel<false><<<grid, 256, 0, s>>>(w);

@@ -24,6 +24,10 @@ class ExchangeEnergy:
         self.m, self.omega_P, self.beta = float(m), float(omega_P), float(beta)
         self.precision = precision
         self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("bpimd runs on CUDA devices only")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec)

@@ -1,6 +1,6 @@
 """Write sampled long-double oracle outputs for the largest GPU parity case.
 
-The float64 oracle's own rounding at N = 7168 (~1e-10 relative on forces, from
+The float64 oracle's own rounding at N = 6912 (~1e-10 relative on forces, from
 the shifted log-sum-exp of the Numerical Stability section accumulating
 eps * |V| per step) is as large as the force tolerance, so the reference for
 that case is the same oracle compiled in long double.  Running it takes tens
@@ -22,7 +22,7 @@ from paper_2305_18025_gb300 import inputs  # noqa: E402
 
 CASES = [
     # name, N, P, beta, generator, seed
-    ("referee_N7168_P4_trapped_seed9_beta1.txt", 7168, 4, 1.0, "trapped", 9),
+    ("referee_N6912_P4_trapped_seed9_beta1.txt", 6912, 4, 1.0, "trapped", 9),
 ]
 SAMPLES = 256
 

@@ -61,11 +61,13 @@ def energy_scale(pos, m, wP, beta, VB):
 
 
 def reference(pos, m, wP, beta, full=True):
-    """The oracle's Algorithm 1.  From N = 512 on, the long-double build is the
+    """The oracle's Algorithm 1.  From N = 128 on, the long-double build is the
     reference: the float64 oracle's own rounding (the shifted log-sum-exp adds
-    about eps*|V| per step) reaches ~1e-10 on forces at N ~ 1000."""
+    about eps*|V| per step) reaches ~1e-10 on forces at N ~ 1000 for trapped
+    inputs, and at N = 300 for well-separated particles, where the long-double
+    build reproduces the exact ring-polymer forces to 3e-14."""
     N = pos.shape[0]
-    if N < 512:
+    if N < 128:
         return oracle.fast_pimdb(pos, m, wP, beta, full=full)
     out = oracle.long_double.fast_pimdb(pos, m, wP, beta, full=full)
     return tuple(float(x) if np.ndim(x) == 0 else (None if x is None else np.asarray(x, np.float64))
@@ -102,7 +104,7 @@ def check(pos, beta, prec, want_M=True, m=1.0):
     (1, 2, "trapped"), (1, 5, "trapped"), (2, 3, "trapped"), (3, 4, "clustered"),
     (5, 2, "clustered"), (16, 8, "trapped"), (31, 8, "clustered"), (32, 8, "trapped"),
     (33, 3, "clustered"), (64, 32, "trapped"), (100, 16, "clustered"), (257, 6, "trapped"),
-    (40, 4, "coincident"), (20, 6, "separated"),
+    (40, 4, "coincident"), (20, 6, "separated"), (300, 8, "separated"), (1024, 4, "coincident"),
 ])
 def test_parity_small(prec, N, P, kind):
     check(gen(kind, N, P, seed=1000 + N), beta=1.3, prec=prec)
@@ -143,9 +145,9 @@ def load_referee(name):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_parity_maximum_size(prec):
-    """Largest N the recursion kernel accepts (7168), against sampled outputs of
+    """Largest N the recursion kernel accepts (6912), against sampled outputs of
     the long-double oracle stored by tests/golden/make_referee_samples.py."""
-    ref = load_referee("referee_N7168_P4_trapped_seed9_beta1.txt")
+    ref = load_referee("referee_N6912_P4_trapped_seed9_beta1.txt")
     N, P, beta = int(ref["N"]), int(ref["P"]), ref["beta"]
     pos = inputs.trapped_positions(N, P, int(ref["seed"]))
     gV, gF, gVf, gVb, _, _ = run_gpu(pos, beta, prec)

@@ -201,7 +201,7 @@ int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
  *     race on it.  Serialise them (one stream).
  *   - Asynchronous; device-side status (non-finite inputs) is not reported:
  *     non-finite positions give non-finite outputs. */
-#define BPIMD_NOALLOC_MAX_N 352
+#define BPIMD_NOALLOC_MAX_N 256
 int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, const double *positions,
                                          double *V_B, double *forces, void *cuda_stream);
 

@@ -19,7 +19,7 @@ BPIMD_ERR_TIMEOUT = -4
 BPIMD_ERR_NOMEM = -5
 BPIMD_ERR_STATE = -6
 BPIMD_ERR_SIZE = -7
-BPIMD_NOALLOC_MAX_N = 352
+BPIMD_NOALLOC_MAX_N = 256
 
 BPIMD_FP64 = 0
 BPIMD_MIXED = 1
@@ -182,7 +182,7 @@ def bpimd_profile_end(ctx):
 
 
 def bpimd_exchange_energy_forces_noalloc(cfg, positions, V_B, forces, stream=None):
-    """Allocation-free evaluation (no context; fixed 1 MiB device scratch, N <= 352).
+    """Allocation-free evaluation (no context; fixed 1 MiB device scratch, N <= 256).
 
     For callers that cannot allocate device memory when they evaluate (their
     memory manager owns all device memory, or cudaMalloc's device-wide

@@ -132,6 +132,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   size_t oicm = take(sizeof(double) * N), oice = take(sizeof(int) * N);
   size_t oC = take(sizeof(double) * (N + 1));
   size_t ogm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), oge = take(sizeof(int) * gelems);
+  size_t ogbm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), ogbe = take(sizeof(int) * gelems);
   size_t oyfm = take(sizeof(double) * (N + 1)), oyfe = take(sizeof(int) * (N + 1));
   size_t oybm = take(sizeof(double) * (N + 1)), oybe = take(sizeof(int) * (N + 1));
   size_t oscal = take(sizeof(double) * 4), oscali = take(sizeof(int) * 4);
@@ -151,6 +152,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.icm = (double *)(b + oicm); w.ice = (int *)(b + oice);
   w.C = (double *)(b + oC);
   w.gm = (void *)(b + ogm); w.ge = (int *)(b + oge);
+  w.gbm = (void *)(b + ogbm); w.gbe = (int *)(b + ogbe);
   w.yfm = (double *)(b + oyfm); w.yfe = (int *)(b + oyfe);
   w.ybm = (double *)(b + oybm); w.ybe = (int *)(b + oybe);
   w.scal = (double *)(b + oscal); w.scal_i = (int *)(b + oscali);

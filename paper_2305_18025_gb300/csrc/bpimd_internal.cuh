@@ -118,6 +118,11 @@ struct Workspace {
   // entry [i][j] = g for a = s*TILE + i (bead 1 particle), b = t*TILE + j (bead P particle)
   void *gm;             // double (FP64) or float (MIXED) mantissas
   int *ge;              // exponents
+  // the same factors in the backward recursion's coordinates (rows r = N-1-a,
+  // sources w = N-1-b), same tile-packed layout, so that both recursions read
+  // their blocks with coalesced loads
+  void *gbm;
+  int *gbe;
   // recursion outputs (extended): forward y[0..N]; backward Yb[0..N]
   // (Yb[w] = mu_{N-1-w} 0-based; the backward row sums are B_{a+1} = Yb[N-a] / c_a)
   double *yfm; int *yfe;

@@ -19,10 +19,12 @@
 //     chain: acc_j += K(i, j) y_i, exponents aligned with integer operations
 //     on the double's bits), one FMA on the next tile's row (off the chain),
 //     and a shuffle that broadcasts the new Y;
-//   * warp 2 stages, for tile t+1, the diagonal block pre-scaled by c and the
-//     block of H from source tile t+1 to the rows of tile t+2;
+//   * warps 1 and 2 stage, for tile t+1, the block of H from source tile t+1
+//     to the rows of tile t+2 and the diagonal block pre-scaled by c;
 //   * bulk warps (never on warp 0's sub-partition) add source tile t-1 to the
-//     rows of tiles >= t+2; tiles only meet at __syncthreads.
+//     rows of tiles >= t+1; tiles only meet at __syncthreads.
+// Each recursion reads H from a copy of the pair factors laid out in its own
+// (row, source) coordinates, so all its block loads are coalesced.
 // Every value is an extended number m * 2^e (int32 exponent), so no exp/log
 // sits on the dependency chain.  MIXED: the bulk products are summed in
 // float32 per 32-source tile and added to the float64 row accumulator; the
@@ -127,9 +129,12 @@ template <bool MIXED, bool BWD>
 __device__ void run_chain(const Workspace &w, ChainSmem sm) {
   const int N = w.N, NT = w.NT;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  GView<MIXED> G{w.gm, w.ge};
-  auto hidx = [&](int src, int row) -> size_t {
-    return BWD ? GView<MIXED>::idx(N - 1 - row, N - 1 - src) : GView<MIXED>::idx(src, row);
+  // H(src, row) in this recursion's own coordinates (both copies share the layout)
+  const void *gm = BWD ? w.gbm : w.gm;
+  const int *ge = BWD ? w.gbe : w.ge;
+  auto hidx = [](int src, int row) -> size_t { return GView<MIXED>::idx(src, row); };
+  auto hm_ld = [&](size_t gi) -> double {
+    return MIXED ? (double)__ldg((const float *)gm + gi) : __ldg((const double *)gm + gi);
   };
   auto coef = [&](int row) -> xd {
     if (!BWD) return xd{__ldg(w.ccm + row), __ldg(w.cce + row)};
@@ -138,44 +143,45 @@ __device__ void run_chain(const Workspace &w, ChainSmem sm) {
   };
   double *gYm = BWD ? w.ybm : w.yfm;
   int *gYe = BWD ? w.ybe : w.yfe;
-  // bulk warps: every warp except the chain warp, the stager and the other
-  // warps of the chain warp's sub-partition (warp id % 4 == 0)
-  auto bulk_warp = [](int q) { return q != 2 && (q & 3) != 0; };
+  // roles: warp 0 = dependency chain; warps 1, 2 = staging of the next tile's
+  // blocks; bulk = every other warp not on warp 0's sub-partition (id % 4 != 0)
+  auto bulk_warp = [](int q) { return q > 2 && (q & 3) != 0; };
   const bool is_bulk = bulk_warp(wid);
   int nbulk = 0, bulk_rank = 0;
   for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
     if (bulk_warp(q)) { if (q < wid) ++bulk_rank; ++nbulk; }
 
-  // Load the 32x32 block H(srcbase+i, rowbase+j) into smem dm/de[i*33+j] (one
-  // warp).  Global loads are coalesced along the bead-P particle b of the
-  // stored g: rows (b = row) in the forward chain, sources (b = N-1-src) in the
-  // backward chain.  Pairs outside 0 <= src <= row < N are stored as zero.
+  // Load H(srcbase+i, rowbase+lane), i = 0..31, into dm/de[i*33+lane] (one warp,
+  // loads coalesced along rows, all issued before use).  Pairs outside
+  // src <= row < N hold the extended zero 1 * 2^XZERO_E.
   auto load_block = [&](int srcbase, int rowbase, double *dm, int *de) {
-#pragma unroll 4
-    for (int k = 0; k < TILE; ++k) {
-      const int i = BWD ? lane : k, j = BWD ? k : lane;
-      const int src = srcbase + i, row = rowbase + j;
-      double m = 1.0;  // extended zero of fma_chain: 1 * 2^XZERO_E
+    const int row = rowbase + lane;
+#pragma unroll 16
+    for (int i = 0; i < TILE; ++i) {
+      const int src = srcbase + i;
+      double m = 1.0;
       int e = XZERO_E;
       if (row < N && src <= row) {
         const size_t gi = hidx(src, row);
-        m = MIXED ? (double)__ldg((const float *)w.gm + gi) : __ldg((const double *)w.gm + gi);
-        e = __ldg(w.ge + gi);
+        m = hm_ld(gi);
+        e = __ldg(ge + gi);
       }
-      dm[i * 33 + j] = m;
-      de[i * 33 + j] = e;
+      dm[i * 33 + lane] = m;
+      de[i * 33 + lane] = e;
     }
   };
-  // stage, for row tile tt, the c-scaled diagonal block and the block of H
-  // from source tile tt to the rows of tile tt+1 into buffer buf (one warp)
+  // warp 1: H from source tile tt to the rows of tile tt+1 (raw)
+  auto stage_offdiag = [&](int tt, int buf) {
+    load_block(tt * TILE, tt * TILE + TILE, sm.Hom + buf * 32 * 33, sm.Hoe + buf * 32 * 33);
+  };
+  // warp 2: the diagonal block of tile tt, pre-scaled by the row coefficient c
   auto stage_diag = [&](int tt, int buf) {
     const int r0 = tt * TILE, row = r0 + lane;
     double *dm = sm.Kdm + buf * 32 * 33;
     int *de = sm.Kde + buf * 32 * 33;
-    load_block(r0, r0 + TILE, sm.Hom + buf * 32 * 33, sm.Hoe + buf * 32 * 33);
     load_block(r0, r0, dm, de);
-    __syncwarp();
     const xd c = (row < N) ? xnorm_int(coef(row)) : xd{1.0, 0};
+#pragma unroll 8
     for (int i = 0; i < TILE; ++i) {
       const xd k = xmul_int(c, xd{dm[i * 33 + lane], de[i * 33 + lane]});
       dm[i * 33 + lane] = k.m;
@@ -186,6 +192,7 @@ __device__ void run_chain(const Workspace &w, ChainSmem sm) {
   for (int r = tid; r < N; r += blockDim.x) { sm.Am[r] = 0.0; sm.Ae[r] = XZERO_E; }
   if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; }
   xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
+  if (wid == 1) stage_offdiag(0, 0);
   if (wid == 2) stage_diag(0, 0);
   __syncthreads();
 
@@ -206,9 +213,8 @@ __device__ void run_chain(const Workspace &w, ChainSmem sm) {
       nxt = xd{1.0, XZERO_E};
       // 32 steps, no branches and no stores: rows past N and finished rows see
       // extended zeros in the staged blocks, and row j's accumulator is final
-      // after step j (later steps add at most 2^-1000 of it).
-      // block entries of step i+1 are loaded (explicit ld.shared) before step
-      // i's shuffle, so no load latency sits on the dependency chain
+      // after step j (later steps add at most 2^-1000 of it).  Block entries of
+      // step i+1 are loaded (explicit ld.shared) before step i's shuffle.
       const unsigned aKm = smem_addr(Kdm + lane), aHm = smem_addr(Hom + lane);
       const unsigned aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
       double km = lds_f64(aKm), hm = lds_f64(aHm);
@@ -235,83 +241,50 @@ __device__ void run_chain(const Workspace &w, ChainSmem sm) {
         sm.Ye[row + 1] = yn.e;
       }
       nxt = xnorm_int(nxt);
+    } else if (wid == 1) {
+      if (t + 1 < NT) stage_offdiag(t + 1, buf ^ 1);
     } else if (wid == 2) {
       if (t + 1 < NT) stage_diag(t + 1, buf ^ 1);
     } else if (is_bulk && t >= 1) {
       // ------------------------------ bulk: source tile t-1 -> rows of tiles >= t+1
+      // thread per row; loads coalesced along rows
       const int srcbase = r0 - TILE;
-      if (!BWD) {
-        // thread per row: loads coalesced along rows (b = row)
-        const int bthreads = nbulk * 32;
-        for (int r = r0 + TILE + bulk_rank * 32 + lane; r < N; r += bthreads) {
-          xd acc{sm.Am[r], sm.Ae[r]};
-          int E = XZERO_E;  // pass 1: largest exponent of the tile's terms (integer only)
+      const int bthreads = nbulk * 32;
+      for (int r = r0 + TILE + bulk_rank * 32 + lane; r < N; r += bthreads) {
+        xd acc{sm.Am[r], sm.Ae[r]};
+        if (MIXED) {
+          // one pass with a running maximum exponent (rescale on increase)
+          float sacc = 0.0f;
+          int E = XZERO_E;
 #pragma unroll 8
-          for (int i = 0; i < TILE; ++i) E = max(E, sm.Ye[srcbase + i] + __ldg(w.ge + hidx(srcbase + i, r)));
-          if (MIXED) {
-            float sacc = 0.0f;
-#pragma unroll 8
-            for (int i = 0; i < TILE; ++i) {
-              const int src = srcbase + i;
-              const size_t gi = hidx(src, r);
-              sacc = fmaf(mant_to_float(sm.Ym[src]) * __ldg((const float *)w.gm + gi),
-                          pow2f_nonpos(sm.Ye[src] + __ldg(w.ge + gi) - E), sacc);
-            }
-            acc = xadd_raw(acc, xd{(double)sacc, E});
-          } else {
-            double sacc = 0.0;
-#pragma unroll 8
-            for (int i = 0; i < TILE; ++i) {
-              const int src = srcbase + i;
-              const size_t gi = hidx(src, r);
-              sacc = fma(scale_nonpos(__ldg((const double *)w.gm + gi), sm.Ye[src] + __ldg(w.ge + gi) - E),
-                         sm.Ym[src], sacc);
-            }
-            acc = xadd_raw(acc, xd{sacc, E});
-          }
-          acc = xnorm(acc.m, acc.e);
-          sm.Am[r] = acc.m;
-          sm.Ae[r] = acc.e;
-        }
-      } else {
-        // warp per group of 32 rows, lane per source: loads coalesced along
-        // sources (b = N-1-src); each row is a warp reduction.
-        const int src = srcbase + lane;
-        const int ys = sm.Ye[src];
-        const float y32 = mant_to_float(sm.Ym[src]);
-        const double y64 = sm.Ym[src];
-        const int ngroups = (N - (r0 + TILE) + TILE - 1) / TILE;
-        for (int gidx = bulk_rank; gidx < ngroups; gidx += nbulk) {
-          const int rbase = r0 + TILE + gidx * TILE;
-          xd mine{0.0, XZERO_E};  // row rbase+lane's tile sum, gathered from the reductions
-          for (int j = 0; j < TILE; ++j) {
-            const int r = rbase + j;
-            if (r >= N) break;
+          for (int i = 0; i < TILE; ++i) {
+            const int src = srcbase + i;
             const size_t gi = hidx(src, r);
-            const int e = ys + __ldg(w.ge + gi);
-            int E = e;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-            if (MIXED) {
-              float v = y32 * __ldg((const float *)w.gm + gi) * pow2f_nonpos(e - E);
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-              if (lane == j) mine = xd{(double)v, E};
-            } else {
-              double v = scale_nonpos(__ldg((const double *)w.gm + gi), e - E) * y64;
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-              if (lane == j) mine = xd{v, E};
-            }
+            const float m = __ldg((const float *)gm + gi);
+            const int e = __ldg(ge + gi) + sm.Ye[src];
+            const int En = max(E, e);
+            sacc = fmaf(mant_to_float(sm.Ym[src]) * m, pow2f_nonpos(e - En), sacc * pow2f_nonpos(E - En));
+            E = En;
           }
-          const int r = rbase + lane;
-          if (r < N) {
-            xd acc = xadd_raw(xd{sm.Am[r], sm.Ae[r]}, mine);
-            acc = xnorm(acc.m, acc.e);
-            sm.Am[r] = acc.m;
-            sm.Ae[r] = acc.e;
+          acc = xadd_raw(acc, xd{(double)sacc, E});
+        } else {
+          // float64: an integer pass for the maximum exponent, then one FMA per term
+          int E = XZERO_E;
+#pragma unroll 16
+          for (int i = 0; i < TILE; ++i) E = max(E, sm.Ye[srcbase + i] + __ldg(ge + hidx(srcbase + i, r)));
+          double sacc = 0.0;
+#pragma unroll 16
+          for (int i = 0; i < TILE; ++i) {
+            const int src = srcbase + i;
+            const size_t gi = hidx(src, r);
+            sacc = fma(scale_nonpos(__ldg((const double *)gm + gi), sm.Ye[src] + __ldg(ge + gi) - E), sm.Ym[src],
+                       sacc);
           }
+          acc = xadd_raw(acc, xd{sacc, E});
         }
+        acc = xnorm(acc.m, acc.e);
+        sm.Am[r] = acc.m;
+        sm.Ae[r] = acc.e;
       }
     }
     __syncthreads();

@@ -73,6 +73,8 @@ size_t noalloc_layout(Workspace &w, char *base) {
   w.C = (double *)take(sizeof(double) * (N + 1));
   w.gm = (void *)take((w.mixed ? sizeof(float) : sizeof(double)) * gelems);
   w.ge = (int *)take(sizeof(int) * gelems);
+  w.gbm = (void *)take((w.mixed ? sizeof(float) : sizeof(double)) * gelems);
+  w.gbe = (int *)take(sizeof(int) * gelems);
   w.yfm = (double *)take(sizeof(double) * (N + 1));
   w.yfe = (int *)take(sizeof(int) * (N + 1));
   w.ybm = (double *)take(sizeof(double) * (N + 1));

@@ -30,25 +30,34 @@ __device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
   s = blk - tt * (tt + 1) / 2;
 }
 
+// Blocks 0..NB-1 fill the forward copy (a = s*32+i, b = t*32+j); blocks
+// NB..2NB-1 fill the backward copy in its own coordinates (source w = s*32+i,
+// row r = t*32+j, i.e. a = N-1-r, b = N-1-w).  Invalid pairs (outside a <= b < N)
+// are stored as mantissa 1 with exponent XZERO_E (an extended zero).
 template <bool MIXED>
 __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
   const double cx = -w.beta * w.half_k * LOG2E;
-  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+  const int N = w.N;
+  for (int gblk = blockIdx.x; gblk < 2 * w.NB; gblk += gridDim.x) {
+    const bool bwd = gblk >= w.NB;
+    const int blk = bwd ? gblk - w.NB : gblk;
     int t, s;
     block_coords(blk, t, s);
+    void *gm = bwd ? w.gbm : w.gm;
+    int *ge = bwd ? w.gbe : w.ge;
     const int j = threadIdx.x & 31;
-    const int b = t * TILE + j;  // bead-P particle
-    double bx = 0, by = 0, bz = 0;
-    if (b < w.N) { bx = w.RP[4 * b]; by = w.RP[4 * b + 1]; bz = w.RP[4 * b + 2]; }
+    const int col = t * TILE + j;  // b (forward) or r (backward)
     for (int i = threadIdx.x >> 5; i < TILE; i += 8) {
-      const int a = s * TILE + i;  // bead-1 particle
+      const int lo = s * TILE + i;  // a (forward) or w (backward)
       const size_t idx = (size_t)blk * TILE2 + i * TILE + j;
-      if (b >= w.N || a > b) {
-        if (MIXED) ((float *)w.gm)[idx] = 0.0f; else ((double *)w.gm)[idx] = 0.0;
-        w.ge[idx] = XZERO_E;
+      if (col >= N || lo > col) {
+        if (MIXED) ((float *)gm)[idx] = 1.0f; else ((double *)gm)[idx] = 1.0;
+        ge[idx] = XZERO_E;
         continue;
       }
-      const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
+      const int a = bwd ? N - 1 - col : lo, b = bwd ? N - 1 - lo : col;
+      const double dx = w.RP[4 * b] - w.R1[4 * a], dy = w.RP[4 * b + 1] - w.R1[4 * a + 1],
+                   dz = w.RP[4 * b + 2] - w.R1[4 * a + 2];
       if (MIXED) {
         const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
         // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
@@ -57,15 +66,15 @@ __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
         float mm = ex2_approx(x - n);  // in [1, 2]
         int e = (int)n;
         if (mm >= 2.0f) { mm *= 0.5f; e += 1; }
-        ((float *)w.gm)[idx] = mm;
-        w.ge[idx] = e;
+        ((float *)gm)[idx] = mm;
+        ge[idx] = e;
       } else {
         // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
         const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
         const double n = floor(x);
         xd g = xnorm(exp2(x - n), (int)n);
-        ((double *)w.gm)[idx] = g.m;
-        w.ge[idx] = g.e;
+        ((double *)gm)[idx] = g.m;
+        ge[idx] = g.e;
       }
     }
   }
@@ -144,7 +153,7 @@ cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, c
 
 cudaError_t launch_gmat(const Workspace &w, cudaStream_t s) {
   const int sms = sm_count();
-  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
+  const int grid = 2 * w.NB < sms * 8 ? 2 * w.NB : sms * 8;
   if (w.mixed) gmat_kernel<true><<<grid, 256, 0, s>>>(w);
   else gmat_kernel<false><<<grid, 256, 0, s>>>(w);
   return cudaGetLastError();

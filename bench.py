@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exchange V_B+force evals/s at N=1024,P=32 (mixed vs FP64 GPU); MD steps/s"
 N_DEF, P_DEF, BETA_DEF, SEED_DEF = 1024, 32, 1.0, 3
-LAUNCHES_PER_EVAL = 6          # bead, pair factors, recursions, scalars, prob/force blocks, finalise
+LAUNCHES_PER_EVAL = 4          # bead pass, pair factors, recursions (2 clusters), probabilities + forces
 DFMA_LATENCY_CYCLES = 64       # measured on GB300: dependent float64 FMA latency
 FLUSH_BYTES = 256 << 20        # > 129 MB L2
 

@@ -166,12 +166,13 @@ int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
 /* ------------------------------------------------------------- profiling */
 /* Stage timing with CUDA events recorded on the context stream around each
  * kernel of an evaluation.  Stage order:
- *   0 bead pass, 1 pair Boltzmann factors, 2 forward+backward recursions,
- *   3 prefix sums / V_B, 4 probability + force blocks, 5 force finalise. */
-#define BPIMD_NUM_STAGES 6
+ *   0 bead pass, 1 pair Boltzmann factors, 2 forward+backward recursions
+ *   (with the prefix sums, V_B and the probability normaliser),
+ *   3 connection probabilities + exterior-bead forces. */
+#define BPIMD_NUM_STAGES 4
 
 /* Start recording stage events for up to `max_evals` following evaluations
- * (older records are discarded).  Adds 7 event records per evaluation. */
+ * (older records are discarded).  Adds 5 event records per evaluation. */
 int bpimd_profile_begin(bpimd_ctx *ctx, int max_evals);
 
 /* Stop recording, synchronise, and write the summed device time of each stage

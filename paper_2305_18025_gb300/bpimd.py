@@ -34,8 +34,8 @@ EXPORTED = [
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
     "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
 ]
-BPIMD_NUM_STAGES = 6
-STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "scalars", "prob_force_blocks", "force_finalize"]
+BPIMD_NUM_STAGES = 4
+STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "prob_forces"]
 
 
 class bpimd_config(ctypes.Structure):

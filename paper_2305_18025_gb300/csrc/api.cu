@@ -73,6 +73,47 @@ int read_status(bpimd_ctx *ctx) {
 }  // namespace
 
 namespace bpimd {
+
+size_t layout_workspace(Workspace &w, char *base) {
+  const size_t N = w.N, NB = w.NB, NT = w.NT, gelems = NB * TILE2;
+  const size_t gm_bytes = (w.mixed ? sizeof(float) : sizeof(double)) * gelems;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    char *p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  w.R1 = (double *)take(sizeof(double) * 4 * N);
+  w.RP = (double *)take(sizeof(double) * 4 * N);
+  w.R1s = (float *)take(sizeof(float) * 8 * N);
+  w.RPs = (float *)take(sizeof(float) * 8 * N);
+  w.Eint = (double *)take(sizeof(double) * N);
+  w.link = (double *)take(sizeof(double) * N);
+  w.ccm = (double *)take(sizeof(double) * N);
+  w.cce = (int *)take(sizeof(int) * N);
+  w.icm = (double *)take(sizeof(double) * N);
+  w.ice = (int *)take(sizeof(int) * N);
+  w.C = (double *)take(sizeof(double) * (N + 1));
+  w.gm = (void *)take(gm_bytes);
+  w.ge = (int *)take(sizeof(int) * gelems);
+  w.gbm = (void *)take(gm_bytes);
+  w.gbe = (int *)take(sizeof(int) * gelems);
+  w.yfm = (double *)take(sizeof(double) * (N + 1));
+  w.yfe = (int *)take(sizeof(int) * (N + 1));
+  w.ybm = (double *)take(sizeof(double) * (N + 1));
+  w.ybe = (int *)take(sizeof(int) * (N + 1));
+  w.alm = (void *)take(sizeof(double) * N);
+  w.ale = (int *)take(sizeof(int) * N);
+  w.scal = (double *)take(sizeof(double) * 4);
+  w.scal_i = (int *)take(sizeof(int) * 4);
+  w.rowpart = (double *)take(sizeof(double) * NB * TILE * 4);
+  w.colpart = (double *)take(sizeof(double) * NB * TILE * 4);
+  w.rowcnt = (int *)take(sizeof(int) * NT);
+  w.colcnt = (int *)take(sizeof(int) * NT);
+  w.status = (int *)take(sizeof(int) * 4);
+  return off;
+}
+
 // one evaluation of V_B and forces on ctx->stream
 int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   const Workspace &w = ctx->w;
@@ -86,14 +127,10 @@ int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   mark(1);
   if (launch_gmat(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(2);
-  if (launch_chains(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(3);
-  if (launch_scalars(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_prob_forces(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(4);
-  if (launch_prob_blocks(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  mark(5);
-  if (launch_force_finalize(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  mark(6);
   ctx->evaluated = true;
   return BPIMD_OK;
 }
@@ -121,24 +158,10 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
-  const size_t N = w.N, NB = w.NB;
-  const size_t gelems = NB * TILE2;
-  // carve one allocation
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
-  size_t oR1 = take(sizeof(double) * 4 * N), oRP = take(sizeof(double) * 4 * N);
-  size_t oEint = take(sizeof(double) * N), oLink = take(sizeof(double) * N);
-  size_t occm = take(sizeof(double) * N), occe = take(sizeof(int) * N);
-  size_t oicm = take(sizeof(double) * N), oice = take(sizeof(int) * N);
-  size_t oC = take(sizeof(double) * (N + 1));
-  size_t ogm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), oge = take(sizeof(int) * gelems);
-  size_t ogbm = take((w.mixed ? sizeof(float) : sizeof(double)) * gelems), ogbe = take(sizeof(int) * gelems);
-  size_t oyfm = take(sizeof(double) * (N + 1)), oyfe = take(sizeof(int) * (N + 1));
-  size_t oybm = take(sizeof(double) * (N + 1)), oybe = take(sizeof(int) * (N + 1));
-  size_t oscal = take(sizeof(double) * 4), oscali = take(sizeof(int) * 4);
-  size_t orow = take(sizeof(double) * NB * TILE * 4), ocol = take(sizeof(double) * NB * TILE * 4);
-  size_t ost = take(sizeof(int) * 4);
-  size_t oVf = take(sizeof(double) * (N + 1)), oVb = take(sizeof(double) * (N + 1));
+  const size_t N = w.N;
+  // one allocation: the workspace, then the diagnostic potentials
+  const size_t wbytes = layout_workspace(w, nullptr);
+  const size_t off = wbytes + 2 * align_up(sizeof(double) * (N + 1));
   ctx->dev_bytes = off;
   if (cudaMalloc(&ctx->dev_block, off) != cudaSuccess) {
     cudaGetLastError();
@@ -146,20 +169,11 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
     return BPIMD_ERR_NOMEM;
   }
   char *b = (char *)ctx->dev_block;
-  w.R1 = (double *)(b + oR1); w.RP = (double *)(b + oRP);
-  w.Eint = (double *)(b + oEint); w.link = (double *)(b + oLink);
-  w.ccm = (double *)(b + occm); w.cce = (int *)(b + occe);
-  w.icm = (double *)(b + oicm); w.ice = (int *)(b + oice);
-  w.C = (double *)(b + oC);
-  w.gm = (void *)(b + ogm); w.ge = (int *)(b + oge);
-  w.gbm = (void *)(b + ogbm); w.gbe = (int *)(b + ogbe);
-  w.yfm = (double *)(b + oyfm); w.yfe = (int *)(b + oyfe);
-  w.ybm = (double *)(b + oybm); w.ybe = (int *)(b + oybe);
-  w.scal = (double *)(b + oscal); w.scal_i = (int *)(b + oscali);
-  w.rowpart = (double *)(b + orow); w.colpart = (double *)(b + ocol);
-  w.status = (int *)(b + ost);
-  ctx->d_Vf = (double *)(b + oVf); ctx->d_Vb = (double *)(b + oVb);
+  layout_workspace(w, b);
+  ctx->d_Vf = (double *)(b + wbytes);
+  ctx->d_Vb = (double *)(b + wbytes + align_up(sizeof(double) * (N + 1)));
   if (cudaMemsetAsync(ctx->dev_block, 0, off, ctx->stream) != cudaSuccess ||
+      launch_gmat_padding(w, ctx->stream) != cudaSuccess ||
       cudaMallocHost(&ctx->host_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ctx->dev_block);
@@ -300,6 +314,6 @@ const char *bpimd_status_string(int status) {
   }
 }
 
-const char *bpimd_version(void) { return "bpimd 0.1 (sm_103a)"; }
+const char *bpimd_version(void) { return "bpimd 0.2 (sm_103a)"; }
 
 }  // extern "C"

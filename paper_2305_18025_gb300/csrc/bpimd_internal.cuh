@@ -37,8 +37,9 @@ namespace bpimd {
 constexpr int TILE = 32;              // row / source tile of the recursions and of g
 constexpr int TILE2 = TILE * TILE;
 constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
-constexpr int CHAIN_THREADS = 1024;
-constexpr int CHAIN_MAX_N = 6912;     // recursion state lives in shared memory (28 B per particle + 39 KB)
+constexpr int CHAIN_THREADS = 640;     // 20 warps: up to 96 registers per thread
+constexpr int CHAIN_CLUSTER = 8;      // CTAs per recursion: one lead + seven bulk CTAs
+constexpr int CHAIN_MAX_N = 6912;     // largest N the library accepts
 constexpr double LOG2E = 1.4426950408889634074;
 constexpr double LN2 = 0.6931471805599453094;
 
@@ -110,6 +111,9 @@ struct Workspace {
   double m, omega_P, beta, k, half_k;
   // O(N) per-particle state
   double *R1, *RP;      // [N][4] bead 1 / bead P positions (x, y, z, 0)
+  float *R1s, *RPs;     // MIXED: [N][8] the same positions split into float
+                        // high and low parts (hx, hy, hz, 0, lx, ly, lz, 0), so that
+                        // a bead difference is formed in float32 to float32 accuracy
   double *Eint, *link;  // [N]
   double *ccm; int *cce;          // c_{i+1} = exp(beta link_i)/(i+1), extended
   double *icm; int *ice;          // 1/c_{i+1}, extended
@@ -127,10 +131,16 @@ struct Workspace {
   // (Yb[w] = mu_{N-1-w} 0-based; the backward row sums are B_{a+1} = Yb[N-a] / c_a)
   double *yfm; int *yfe;
   double *ybm; int *ybe;
+  // alpha_a = y_a / (N y_N), a = 0..N-1, extended (float mantissa for MIXED),
+  // written by the forward recursion once y_N is known
+  void *alm; int *ale;
   // scalars: [0] V_B, [1] invZ mantissa, [2] reserved ; int [0] invZ exponent
   double *scal; int *scal_i;
   // force partial sums: rowpart/colpart [NB][TILE][4]
   double *rowpart, *colpart;
+  // per row / column tile: number of finished blocks of the probability pass
+  // (the last block of a tile forms its forces and resets the count to 0)
+  int *rowcnt, *colcnt;
   int *status;          // device status word
 };
 
@@ -147,13 +157,20 @@ inline int sm_count() {
   return cached[dev];
 }
 
+// Lay the workspace out from `base` (nullptr: only measure); returns the bytes
+// used.  Every array starts on a 256-byte boundary.
+size_t layout_workspace(Workspace &w, char *base);
+
 // kernel launchers (stream-ordered)
 cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+// fill the pair-factor entries outside a <= b < N (fixed for a given N) with
+// extended zeros; needed once per workspace before the first launch_gmat
+cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s);
 cudaError_t launch_gmat(const Workspace &w, cudaStream_t s);
-cudaError_t launch_chains(const Workspace &w, cudaStream_t s);
-cudaError_t launch_scalars(const Workspace &w, double *V_B, cudaStream_t s);
-cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s);
-cudaError_t launch_force_finalize(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+// both recursions, prefix sums, V_B (device scalar, may be null), normaliser, alpha
+cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
+// connection probabilities and all exterior-bead forces
+cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);
 

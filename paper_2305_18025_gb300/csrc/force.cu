@@ -7,13 +7,18 @@
 // generated from the stored pair factors g and reduced on the spot into
 //   row l    : sum_u Pr[l->u],  sum_u Pr[l->u] (r_l^P - r_u^1)    (bead P of l)
 //   column u : sum_l Pr[l->u],  sum_l Pr[l->u] (r_u^1 - r_l^P)    (bead 1 of u)
-// partial sums per block (deterministic, no atomics).  The finalise pass adds
-// the partials of each particle in a fixed order, adds the direct-link term and
+// partial sums per block.  Each block then counts itself in its row tile and
+// its column tile (an atomic counter per tile); the block that completes a
+// tile adds that tile's partials in a fixed block order (so the result does
+// not depend on which block finishes last), adds the direct-link term and
 // forms (Eq. force-on-1-sum-neighbors, Eq. force-on-P-sum-neighbors)
 //   F_l^P = -m w_P^2 [ (sum_u Pr[l->u]) (r_l^P - r_l^{P-1}) + sum_u Pr[l->u] (r_l^P - r_u^1) ]
 //   F_l^1 = -m w_P^2 [ (sum_l' Pr[l'->l]) (r_l^1 - r_l^2) + sum_l' Pr[l'->l] (r_l^1 - r_l'^P) ]
 // i.e. the per-neighbour sums of the paper distributed over their terms.
-// MIXED: block-local products and sums in float32, combination in float64.
+// MIXED: bead differences from float32 high/low parts, block-local products
+// and sums in float32, combination in float64.
+#include <type_traits>
+
 #include "bpimd_internal.cuh"
 
 namespace bpimd {
@@ -28,17 +33,102 @@ __device__ __forceinline__ void block_coords_f(int blk, int &t, int &s) {
 }
 
 __device__ __forceinline__ xd alpha_of(const Workspace &w, int a) {
-  // y_a / (N y_N)
-  return xmul(xd{w.yfm[a], w.yfe[a]}, xd{w.scal[1], w.scal_i[0]});
+  // y_a / (N y_N), stored by the forward recursion
+  return xd{w.mixed ? (double)((const float *)w.alm)[a] : ((const double *)w.alm)[a], w.ale[a]};
 }
 __device__ __forceinline__ xd mu_of(const Workspace &w, int b) {
   const int r = w.N - 1 - b;  // backward row index of mu_b (0-based mu~_b = Yb[N-1-b])
   return xd{w.ybm[r], w.ybe[r]};
 }
 
+// Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,
+// column p+1) this is 1 - y[p+1] B(p+1) / (N y_N) with B(a) the backward row sum
+// of particle a.
+__device__ __forceinline__ double direct_link_prob(const Workspace &w, int p) {
+  const xd y{w.yfm[p + 1], w.yfe[p + 1]};
+  const xd B = backward_row_sum(w, p + 1);
+  const double q = xtod(xmul(xmul(y, B), xd{w.scal[1], w.scal_i[0]}));
+  return 1.0 - q;
+}
+
+// Bead P of the 32 particles of row tile t: sum the row partials of blocks
+// (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
+// block of the tile to finish; all 256 threads call it.
+template <typename P_t>
+__device__ void finalize_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
+                              double (*fin)[9]) {
+  const int q = threadIdx.x & 3, jj = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
+  double acc = 0.0;
+  const size_t base = (size_t)t * (t + 1) / 2;
+  const P_t *part = (const P_t *)w.rowpart;
+  for (int s = half; s <= t; s += 2) acc += (double)__ldcg(part + ((base + s) * TILE + jj) * 4 + q);
+  fin[jj][q + 4 * half] = acc;
+  __syncthreads();
+  const int p = t * TILE + threadIdx.x;
+  if (threadIdx.x < TILE && p < w.N) {
+    const double *f = fin[threadIdx.x];
+    double rs = f[0] + f[4], rx = f[1] + f[5], ry = f[2] + f[6], rz = f[3] + f[7];
+    const double *rp = w.RP + 4 * (size_t)p;
+    if (p + 1 < w.N) {
+      const double M = direct_link_prob(w, p);
+      const double *n1 = w.R1 + 4 * (size_t)(p + 1);
+      rs += M;
+      rx = fma(M, rp[0] - n1[0], rx); ry = fma(M, rp[1] - n1[1], ry); rz = fma(M, rp[2] - n1[2], rz);
+    }
+    const double k = w.k;
+    const double *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1 (1-based)
+    double *fP = F + ((size_t)p * w.P + (w.P - 1)) * 3;
+    fP[0] = -k * fma(rs, rp[0] - nbP[0], rx);
+    fP[1] = -k * fma(rs, rp[1] - nbP[1], ry);
+    fP[2] = -k * fma(rs, rp[2] - nbP[2], rz);
+    if (!(isfinite(fP[0]) && isfinite(fP[1]) && isfinite(fP[2]))) atomicOr(w.status, ST_NONFINITE);
+  }
+  if (threadIdx.x == 0) w.rowcnt[t] = 0;  // ready for the next evaluation
+  __syncthreads();
+}
+
+// Bead 1 of the 32 particles of column tile s: blocks (s..NT-1, s) in order.
+template <typename P_t>
+__device__ void finalize_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
+                              double (*fin)[9]) {
+  const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
+  double acc = 0.0;
+  const P_t *part = (const P_t *)w.colpart;
+  for (int t = s + half; t < w.NT; t += 2)
+    acc += (double)__ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
+  fin[ii][q + 4 * half] = acc;
+  __syncthreads();
+  const int p = s * TILE + threadIdx.x;
+  if (threadIdx.x < TILE && p < w.N) {
+    const double *f = fin[threadIdx.x];
+    double cs = f[0] + f[4], cx = f[1] + f[5], cy = f[2] + f[6], cz = f[3] + f[7];
+    const double *r1 = w.R1 + 4 * (size_t)p;
+    if (p >= 1) {
+      const double M = direct_link_prob(w, p - 1);
+      const double *pP = w.RP + 4 * (size_t)(p - 1);
+      cs += M;
+      cx = fma(M, r1[0] - pP[0], cx); cy = fma(M, r1[1] - pP[1], cy); cz = fma(M, r1[2] - pP[2], cz);
+    }
+    const double k = w.k;
+    const double *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2 (1-based)
+    double *f1 = F + (size_t)p * w.P * 3;
+    f1[0] = -k * fma(cs, r1[0] - nb1[0], cx);
+    f1[1] = -k * fma(cs, r1[1] - nb1[1], cy);
+    f1[2] = -k * fma(cs, r1[2] - nb1[2], cz);
+    if (!(isfinite(f1[0]) && isfinite(f1[1]) && isfinite(f1[2]))) atomicOr(w.status, ST_NONFINITE);
+  }
+  if (threadIdx.x == 0) w.colcnt[s] = 0;
+  __syncthreads();
+}
+
 template <bool MIXED>
-__global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
-  __shared__ double red[8][32][4];
+__global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const double *__restrict__ pos,
+                                                         double *__restrict__ F) {
+  // MIXED keeps the block partials in float32 (each is a float32 sum already)
+  using P_t = typename std::conditional<MIXED, float, double>::type;
+  __shared__ P_t red[8][32][4];
+  __shared__ double fin[32][9];
+  __shared__ int last[2];
   for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
     int t, s;
     block_coords_f(blk, t, s);
@@ -47,10 +137,17 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
     const bool bvalid = b < w.N;
     xd mub{0.0, XZERO_E};
     double bx = 0, by = 0, bz = 0;
+    float4 bh = make_float4(0.f, 0.f, 0.f, 0.f), bl = bh;
     if (bvalid) {
       mub = mu_of(w, b);
-      bx = w.RP[4 * b]; by = w.RP[4 * b + 1]; bz = w.RP[4 * b + 2];
+      if (MIXED) {
+        bh = *(const float4 *)(w.RPs + 8 * (size_t)b);
+        bl = *(const float4 *)(w.RPs + 8 * (size_t)b + 4);
+      } else {
+        bx = w.RP[4 * b]; by = w.RP[4 * b + 1]; bz = w.RP[4 * b + 2];
+      }
     }
+    const float mubf = (float)mub.m;
     double rs = 0, rx = 0, ry = 0, rz = 0;  // row partials (thread's 4 entries)
     float frs = 0, frx = 0, fry = 0, frz = 0;
 #pragma unroll
@@ -62,19 +159,22 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
       double cs = 0, cx = 0, cy = 0, cz = 0;
       float fcs = 0, fcx = 0, fcy = 0, fcz = 0;
       if (valid) {
-        const xd al = alpha_of(w, a);
-        const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
         if (MIXED) {
+          const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a);
+          const float4 al4 = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
+          const float fx = (bh.x - ah.x) + (bl.x - al4.x);
+          const float fy = (bh.y - ah.y) + (bl.y - al4.y);
+          const float fz = (bh.z - ah.z) + (bl.z - al4.z);
           const float gmf = ((const float *)w.gm)[gi];
-          const int e = al.e + mub.e + w.ge[gi];
-          float M = (float)al.m * (float)mub.m * gmf;
+          const int e = ((const int *)w.ale)[a] + mub.e + w.ge[gi];
+          float M = ((const float *)w.alm)[a] * mubf * gmf;
           M = (e < -150) ? 0.0f : (e > 0 ? M * (float)(1 << min(e, 2)) : M * pow2f_nonpos(e));
-          const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
           frs += M; frx += M * fx; fry += M * fy; frz += M * fz;
           fcs = M; fcx = -M * fx; fcy = -M * fy; fcz = -M * fz;
         } else {
+          const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
           const double gmd = ((const double *)w.gm)[gi];
-          const double M = xtod(xd{al.m * mub.m * gmd, al.e + mub.e + w.ge[gi]});
+          const double M = xtod(xd{((const double *)w.alm)[a] * mub.m * gmd, w.ale[a] + mub.e + w.ge[gi]});
           rs += M; rx = fma(M, dx, rx); ry = fma(M, dy, ry); rz = fma(M, dz, rz);
           cs = M; cx = -M * dx; cy = -M * dy; cz = -M * dz;
         }
@@ -88,7 +188,6 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
           fcy += __shfl_xor_sync(0xffffffffu, fcy, o);
           fcz += __shfl_xor_sync(0xffffffffu, fcz, o);
         }
-        cs = fcs; cx = fcx; cy = fcy; cz = fcz;
       } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -99,85 +198,38 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w) {
         }
       }
       if (j == 0) {
-        double *cp = w.colpart + ((size_t)blk * TILE + i) * 4;
-        cp[0] = cs; cp[1] = cx; cp[2] = cy; cp[3] = cz;
+        P_t *cp = (P_t *)w.colpart + ((size_t)blk * TILE + i) * 4;
+        if (MIXED) { cp[0] = fcs; cp[1] = fcx; cp[2] = fcy; cp[3] = fcz; }
+        else { cp[0] = (P_t)cs; cp[1] = (P_t)cx; cp[2] = (P_t)cy; cp[3] = (P_t)cz; }
       }
     }
-    if (MIXED) { rs = frs; rx = frx; ry = fry; rz = frz; }
-    red[i0][j][0] = rs; red[i0][j][1] = rx; red[i0][j][2] = ry; red[i0][j][3] = rz;
+    if (MIXED) {
+      red[i0][j][0] = frs; red[i0][j][1] = frx; red[i0][j][2] = fry; red[i0][j][3] = frz;
+    } else {
+      red[i0][j][0] = (P_t)rs; red[i0][j][1] = (P_t)rx; red[i0][j][2] = (P_t)ry; red[i0][j][3] = (P_t)rz;
+    }
     __syncthreads();
     if (threadIdx.x < 128) {
       const int jj = threadIdx.x >> 2, q = threadIdx.x & 3;
-      double acc = 0.0;
+      P_t acc = 0;
 #pragma unroll
       for (int g = 0; g < 8; ++g) acc += red[g][jj][q];
-      w.rowpart[((size_t)blk * TILE + jj) * 4 + q] = acc;
+      ((P_t *)w.rowpart)[((size_t)blk * TILE + jj) * 4 + q] = acc;
+    }
+    // publish this block's partials, then count it in its row and column tile;
+    // the block that completes a tile forms that tile's forces (no waiting)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      last[0] = atomicAdd(w.rowcnt + t, 1) == t;             // blocks (t, 0..t)
+      last[1] = atomicAdd(w.colcnt + s, 1) == w.NT - 1 - s;  // blocks (s..NT-1, s)
     }
     __syncthreads();
+    const bool last_row = last[0], last_col = last[1];
+    if (last_row || last_col) __threadfence();
+    if (last_row) finalize_rows<P_t>(w, t, pos, F, fin);
+    if (last_col) finalize_cols<P_t>(w, s, pos, F, fin);
   }
-}
-
-// Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,
-// column p+1) this is 1 - y[p+1] B(p+1) / (N y_N) with B(a) the backward row sum
-// of particle a.
-__device__ __forceinline__ double direct_link_prob(const Workspace &w, int p) {
-  const xd y{w.yfm[p + 1], w.yfe[p + 1]};
-  const xd B = backward_row_sum(w, p + 1);
-  const double q = xtod(xmul(xmul(y, B), xd{w.scal[1], w.scal_i[0]}));
-  return 1.0 - q;
-}
-
-__global__ void __launch_bounds__(256) force_finalize_kernel(Workspace w, const double *__restrict__ pos,
-                                                             double *__restrict__ F) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= w.N) return;
-  const int N = w.N, P = w.P, NT = w.NT;
-  const double *r1 = w.R1 + 4 * (size_t)p, *rp = w.RP + 4 * (size_t)p;
-  // row p (bead P of particle p)
-  double rs = 0, rx = 0, ry = 0, rz = 0;
-  {
-    const int t = p >> 5, j = p & 31;
-    for (int s = 0; s <= t; ++s) {
-      const double *q = w.rowpart + ((size_t)(t * (t + 1) / 2 + s) * TILE + j) * 4;
-      rs += q[0]; rx += q[1]; ry += q[2]; rz += q[3];
-    }
-    if (p + 1 < N) {
-      const double M = direct_link_prob(w, p);
-      const double *n1 = w.R1 + 4 * (size_t)(p + 1);
-      rs += M;
-      rx = fma(M, rp[0] - n1[0], rx); ry = fma(M, rp[1] - n1[1], ry); rz = fma(M, rp[2] - n1[2], rz);
-    }
-  }
-  // column p (bead 1 of particle p)
-  double cs = 0, cx = 0, cy = 0, cz = 0;
-  {
-    const int s = p >> 5, i = p & 31;
-    for (int t = s; t < NT; ++t) {
-      const double *q = w.colpart + ((size_t)(t * (t + 1) / 2 + s) * TILE + i) * 4;
-      cs += q[0]; cx += q[1]; cy += q[2]; cz += q[3];
-    }
-    if (p >= 1) {
-      const double M = direct_link_prob(w, p - 1);
-      const double *pP = w.RP + 4 * (size_t)(p - 1);
-      cs += M;
-      cx = fma(M, r1[0] - pP[0], cx); cy = fma(M, r1[1] - pP[1], cy); cz = fma(M, r1[2] - pP[2], cz);
-    }
-  }
-  const double k = w.k;
-  const double *bead = pos + (size_t)p * P * 3;
-  const double *nbP = bead + 3 * (P - 2);  // bead P-1 (1-based) next to bead P
-  const double *nb1 = bead + 3;            // bead 2 (1-based) next to bead 1
-  double *fP = F + ((size_t)p * P + (P - 1)) * 3;
-  double *f1 = F + (size_t)p * P * 3;
-  fP[0] = -k * fma(rs, rp[0] - nbP[0], rx);
-  fP[1] = -k * fma(rs, rp[1] - nbP[1], ry);
-  fP[2] = -k * fma(rs, rp[2] - nbP[2], rz);
-  f1[0] = -k * fma(cs, r1[0] - nb1[0], cx);
-  f1[1] = -k * fma(cs, r1[1] - nb1[1], cy);
-  f1[2] = -k * fma(cs, r1[2] - nb1[2], cz);
-  if (!(isfinite(fP[0]) && isfinite(fP[1]) && isfinite(fP[2]) && isfinite(f1[0]) && isfinite(f1[1]) &&
-        isfinite(f1[2])))
-    atomicOr(w.status, ST_NONFINITE);
 }
 
 __global__ void dense_prob_kernel(Workspace w, double *M) {
@@ -200,16 +252,11 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 
 }  // namespace
 
-cudaError_t launch_prob_blocks(const Workspace &w, cudaStream_t s) {
+cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   const int sms = sm_count();
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
-  if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w);
-  else prob_force_kernel<false><<<grid, 256, 0, s>>>(w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_force_finalize(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
-  force_finalize_kernel<<<(w.N + 255) / 256, 256, 0, s>>>(w, pos, F);
+  if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w, pos, F);
+  else prob_force_kernel<false><<<grid, 256, 0, s>>>(w, pos, F);
   return cudaGetLastError();
 }
 

@@ -13,8 +13,9 @@
 // array's device address with cudaGetSymbolAddress and caches it for that
 // device.  That first call should therefore come before any stream capture.
 // Shared state: every call on a device uses the same array, which keeps the
-// previous call's contents; this file clears the part that must start at zero
-// (the device status word).  Two calls whose work overlaps on the GPU (for
+// previous call's contents; each call clears the parts that must start at zero
+// (the device status word and the tile counters) and rewrites the padding of
+// the pair factors, which depends on N.  Two calls whose work overlaps on the GPU (for
 // example on two different streams) race on the array and give wrong results.
 #include <mutex>
 
@@ -51,42 +52,6 @@ int noalloc_scratch(void **out) {
   return BPIMD_OK;
 }
 
-size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Lay the workspace out from `base` (nullptr: only measure).  Returns the bytes used.
-size_t noalloc_layout(Workspace &w, char *base) {
-  const size_t N = w.N, NB = w.NB, gelems = NB * TILE2;
-  size_t off = 0;
-  auto take = [&](size_t bytes) -> char * {
-    char *p = base ? base + off : nullptr;
-    off += round256(bytes);
-    return p;
-  };
-  w.R1 = (double *)take(sizeof(double) * 4 * N);
-  w.RP = (double *)take(sizeof(double) * 4 * N);
-  w.Eint = (double *)take(sizeof(double) * N);
-  w.link = (double *)take(sizeof(double) * N);
-  w.ccm = (double *)take(sizeof(double) * N);
-  w.cce = (int *)take(sizeof(int) * N);
-  w.icm = (double *)take(sizeof(double) * N);
-  w.ice = (int *)take(sizeof(int) * N);
-  w.C = (double *)take(sizeof(double) * (N + 1));
-  w.gm = (void *)take((w.mixed ? sizeof(float) : sizeof(double)) * gelems);
-  w.ge = (int *)take(sizeof(int) * gelems);
-  w.gbm = (void *)take((w.mixed ? sizeof(float) : sizeof(double)) * gelems);
-  w.gbe = (int *)take(sizeof(int) * gelems);
-  w.yfm = (double *)take(sizeof(double) * (N + 1));
-  w.yfe = (int *)take(sizeof(int) * (N + 1));
-  w.ybm = (double *)take(sizeof(double) * (N + 1));
-  w.ybe = (int *)take(sizeof(int) * (N + 1));
-  w.scal = (double *)take(sizeof(double) * 4);
-  w.scal_i = (int *)take(sizeof(int) * 4);
-  w.rowpart = (double *)take(sizeof(double) * NB * TILE * 4);
-  w.colpart = (double *)take(sizeof(double) * NB * TILE * 4);
-  w.status = (int *)take(sizeof(int) * 4);
-  return off;
-}
-
 bool positive_finite(double x) { return x > 0.0 && x < __builtin_huge_val(); }
 
 }  // namespace
@@ -115,20 +80,23 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
-  if (noalloc_layout(w, nullptr) > NOALLOC_SCRATCH_BYTES) return BPIMD_ERR_SIZE;
+  if (layout_workspace(w, nullptr) > NOALLOC_SCRATCH_BYTES) return BPIMD_ERR_SIZE;
 
   void *base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc != BPIMD_OK) return rc;
-  noalloc_layout(w, (char *)base);
+  layout_workspace(w, (char *)base);
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (cudaMemsetAsync(w.status, 0, sizeof(int), s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  // the tile counters of the probability pass start at zero (a previous call
+  // with another N leaves its counters at zero, but at other offsets)
+  if (cudaMemsetAsync(w.rowcnt, 0, sizeof(int) * w.NT, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (cudaMemsetAsync(w.colcnt, 0, sizeof(int) * w.NT, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_gmat_padding(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_bead_pass(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_gmat(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_chains(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_scalars(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_prob_blocks(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_force_finalize(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_prob_forces(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   return BPIMD_OK;
 }

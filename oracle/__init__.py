@@ -19,6 +19,9 @@ Contents
   approaches the comparison tolerances.
 * ``harmonic``: the closed-form canonical energy of N non-interacting bosons in a
   harmonic trap at finite P.
+* molecular dynamics (``md_oracle.c``): Philox4x32-10, thermostat normals, the
+  trap and Gaussian pair forces, and BAOAB Langevin steps with the primitive
+  energy estimator.
 
 Arrays use the layout of ``bpimd_oracle.h``: positions ``[N][P][3]`` float64,
 ``E[u-1, v-1] = E^{[u,v]}``, ``V[v] = V^{[1,v]}``, ``W[u-1] = V^{[u,N]}``,
@@ -62,11 +65,20 @@ class _Oracle:
                 "ora_fast_pimdb": [i, i, r, r, r, rp, rp, rp, rp, rp, rp],
                 "ora_original_pimdb": [i, i, r, r, r, rp, rp, rp],
                 "ora_expected_spring_energy": [i, i, r, r, rp, rp, rp],
+                "ora_external_forces": [i, i, r, r, i, r, r, rp, rp, rp],
+                "ora_md_run": [i, i, r, r, r, r, r, r, r, i, r, r, ctypes.c_uint64, ctypes.c_uint64,
+                               i, rp, rp, rp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            lib.ora_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            lib.ora_philox4x32_10.restype = None
+            lib.ora_thermostat_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                                   ctypes.POINTER(ctypes.c_double)]
+            lib.ora_thermostat_normals.restype = None
             self._lib = lib
         return self._lib
 
@@ -181,6 +193,43 @@ class _Oracle:
                                                           self._p(M), self._p(out)),
                     "expected_spring_energy")
         return out[0]
+
+    # ------------------------------------------------ molecular dynamics
+    def philox4x32_10(self, counter, key):
+        """Philox4x32-10 block: four 32-bit counter words, two key words -> four words."""
+        c = (ctypes.c_uint32 * 4)(*counter)
+        k = (ctypes.c_uint32 * 2)(*key)
+        o = (ctypes.c_uint32 * 4)()
+        self.lib().ora_philox4x32_10(c, k, o)
+        return [int(x) for x in o]
+
+    def thermostat_normals(self, seed, step, n):
+        z = np.empty(n, dtype=np.float64)
+        self.lib().ora_thermostat_normals(seed, step, n, z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return z
+
+    def external_forces(self, pos, m, omega0, pair_type=0, pair_a=0.0, pair_b=1.0):
+        """(U-bar, -grad U-bar) of the trap and same-bead pair potential."""
+        pos = self._pos(pos)
+        N, P, _ = pos.shape
+        F = np.zeros_like(pos)
+        U = np.zeros(1, dtype=self.dtype)
+        self._check(self.lib().ora_external_forces(N, P, m, omega0, pair_type, pair_a, pair_b,
+                                                   self._p(pos), self._p(F), self._p(U)),
+                    "external_forces")
+        return U[0], F
+
+    def md_run(self, pos, vel, m, omega_P, beta, dt, gamma, nsteps, omega0=0.0, pair_type=0,
+               pair_a=0.0, pair_b=1.0, kT=0.0, seed=0, step0=0):
+        """nsteps BAOAB steps; returns (pos, vel, energies[4]) as new arrays."""
+        pos = self._pos(pos).copy()
+        vel = self._arr(vel).copy()
+        N, P, _ = pos.shape
+        en = np.zeros(4, dtype=self.dtype)
+        self._check(self.lib().ora_md_run(N, P, m, omega_P, beta, dt, gamma, kT, omega0, pair_type,
+                                          pair_a, pair_b, seed, step0, nsteps, self._p(pos),
+                                          self._p(vel), self._p(en)), "md_run")
+        return pos, vel, en
 
 
 #: float64 oracle (the default)

@@ -97,6 +97,28 @@ int ora_original_pimdb(int N, int P, ora_real m, ora_real omega_P, ora_real beta
 int ora_expected_spring_energy(int N, int P, ora_real m, ora_real omega_P,
                                const ora_real *pos, const ora_real *M, ora_real *out);
 
+/* ------------------------------------------------ molecular dynamics (md_oracle.c) */
+#include <stdint.h>
+
+/* Philox4x32-10 block function (published definition, 10 rounds). */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Thermostat normals for elements 0..n-1 of step `step` (float64 Box-Muller of
+ * Philox4x32-10 words; mapping in md_oracle.c). */
+void ora_thermostat_normals(uint64_t seed, uint64_t step, int64_t n, double *z);
+
+/* Physical forces -grad U-bar added to F (harmonic trap of frequency omega0 if
+ * omega0 > 0; pair_type 1: Gaussian g = pa, s = pb between equal-index beads);
+ * *ubar = U-bar (may be NULL). */
+int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type, ora_real pa,
+                        ora_real pb, const ora_real *pos, ora_real *F, ora_real *ubar);
+
+/* nsteps BAOAB Langevin steps in place (kT <= 0: 1/beta); energies (may be
+ * NULL): [0] V^{[1,N]}, [1] U-bar, [2] kinetic, [3] primitive estimator. */
+int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_real dt, ora_real gamma,
+               ora_real kT, ora_real omega0, int pair_type, ora_real pa, ora_real pb, uint64_t seed,
+               uint64_t step0, int nsteps, ora_real *pos, ora_real *vel, ora_real *energies);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,20 +10,22 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "bpimd_oracle.c")
+MD_SRC = os.path.join(HERE, "md_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 LIB_LD = os.path.join(HERE, "liboracle_ld.so")
 
 
 def _fresh(lib):
-    return (os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC)
-            and os.path.getmtime(lib) >= os.path.getmtime(os.path.join(HERE, "bpimd_oracle.h")))
+    return os.path.exists(lib) and all(
+        os.path.getmtime(lib) >= os.path.getmtime(p)
+        for p in (SRC, MD_SRC, os.path.join(HERE, "bpimd_oracle.h")))
 
 
 def _compile(lib, extra):
     # ISO C mode and -ffp-contract=off: no fused multiply-add contraction, so
     # the float64 oracle rounds the same way on x86-64 and aarch64 hosts.
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC"] + extra + ["-o", lib + ".tmp", SRC, "-lm"]
+           "-shared", "-fPIC"] + extra + ["-o", lib + ".tmp", SRC, MD_SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(lib + ".tmp", lib)
 

@@ -96,14 +96,15 @@ typedef struct {
   /* molecular dynamics (bpimd_step) */
   double dt;         /* time step                                   */
   double gamma;      /* Langevin friction (0 = NVE)                  */
-  double kT_bead;    /* thermostat temperature per bead: P/beta for PIMD, or 0 => P/beta */
+  double kT_bead;    /* thermostat kT of the bead momenta; 0 => 1/beta, the temperature
+                        at which exp(-beta (V_B + U-bar)) is sampled with w_P = sqrt(P)/(beta hbar) */
   double omega0;     /* isotropic harmonic trap frequency (0 = none) */
-  int32_t pair_type; /* BPIMD_PAIR_*                                 */
+  int32_t pair_type; /* BPIMD_PAIR_NONE or BPIMD_PAIR_GAUSSIAN        */
   int32_t pad0;
   double pair_a;     /* Gaussian g  | LJ epsilon                      */
   double pair_b;     /* Gaussian s  | LJ sigma                        */
   double pair_rc;    /* LJ cutoff (0 = no cutoff)                     */
-  double box_L;      /* cubic periodic box side (0 = open boundaries) */
+  double box_L;      /* reserved for periodic boxes, must be 0        */
   uint64_t seed;     /* counter-based RNG key for the thermostat      */
 } bpimd_config;
 
@@ -150,16 +151,28 @@ int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *E
  * O(N^2) memory; intended for tests and diagnostics.  Asynchronous. */
 int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
 
-/* Run `nsteps` molecular-dynamics steps in place (BAOAB Langevin splitting:
- * half kick, half drift, Ornstein-Uhlenbeck velocity update with a
- * counter-based Philox RNG, half drift, force evaluation, half kick), with the
- * full force = exchange force + harmonic trap + pair potential of cfg.
+/* Run `nsteps` molecular-dynamics steps in place, sampling
+ * exp(-beta (V_B + U-bar)) (Eq. int-of-sum-all-permutations; the paper does not
+ * state its integrator): BAOAB Langevin splitting -- half kick, half drift,
+ * exact Ornstein-Uhlenbeck velocity update v = c1 v + c2 z (c1 = exp(-gamma dt),
+ * c2 = sqrt((1 - c1^2) kT / m)), half drift, force evaluation, half kick -- with
+ * bead mass m and the full force = exchange force (Algorithm 1) + harmonic trap
+ * (omega0) + pair potential of cfg, U-bar = (1/P) sum_j U(r_1^j..r_N^j).
+ * Thermostat normals: Philox4x32-10 (Salmon et al., SC'11) keyed by cfg.seed,
+ * counter (element/4, step index) with Box-Muller; the step index counts the
+ * steps this context has taken (0 at creation).
  *   positions, velocities : device [N][P][3] float64, updated in place.
  *   energies : optional device array of 4 float64 receiving, after the last
- *              step: [0] V_B, [1] U-bar, [2] kinetic energy of the beads,
- *              [3] primitive energy estimator (kinetic part + U-bar).
- * The first call captures the step into a CUDA graph that later calls replay.
- * Synchronises and returns device status. */
+ *              step: [0] V_B, [1] U-bar, [2] kinetic energy sum (1/2) m v^2,
+ *              [3] primitive energy estimator 3NP/(2 beta) - <E^{G[sigma]}> + U-bar,
+ *              where <E^{G[sigma]}> is the spring energy averaged over the
+ *              connection probabilities.  May be NULL.
+ * Each call first evaluates the force at the given positions.  On a stream
+ * other than the legacy default stream the step is captured once into a CUDA
+ * graph (bound to these position/velocity buffers) and replayed.
+ * Errors: BPIMD_ERR_ARG for nsteps < 0, misaligned pointers, dt <= 0,
+ * gamma < 0, kT_bead < 0, omega0 < 0, an unknown pair_type, s <= 0 for the
+ * Gaussian pair, or box_L != 0.  Synchronises and returns device status. */
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
                int32_t nsteps, double *energies);
 

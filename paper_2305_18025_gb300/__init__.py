@@ -8,8 +8,9 @@ hand-written sm_103a CUDA kernels behind the C ABI of ``include/bpimd.h``.
 Modules
 -------
 ``bpimd``     ctypes binding with the C ABI's names (argument marshalling only).
-``exchange``  torch-facing wrappers: ``ExchangeEnergy`` (context + tensors) and the
-              autograd function whose backward is the force kernel.
+``exchange``  torch-facing wrappers: ``ExchangeEnergy`` (context + tensors), the
+              autograd function whose backward is the force kernel, and
+              ``RingPolymerMD`` (BAOAB Langevin steps of bpimd_step).
 ``inputs``    seeded synthetic inputs (no arithmetic of the method).
 ``build``     in-tree nvcc build of ``libbpimd.so``.
 

@@ -172,6 +172,8 @@ cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
 // connection probabilities and all exterior-bead forces
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
+// per block of g: (1/2) m w_P^2 sum Pr[b -> a] |r_b^P - r_a^1|^2 over a <= b (part[NB])
+cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStream_t s);
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);
 
 // B_{a+1} (1-based backward row sum for 0-based particle a) from the stored state
@@ -179,6 +181,16 @@ __device__ __forceinline__ xd backward_row_sum(const Workspace &w, int a) {
   const xd Y{w.ybm[w.N - a], w.ybe[w.N - a]};
   if (a == 0) return Y;  // B_1 = Y_N
   return xmul(Y, xd{w.icm[a - 1], w.ice[a - 1]});
+}
+
+// Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,
+// column p+1) this is 1 - y[p+1] B(p+1) / (N y_N) with B(a) the backward row sum
+// of particle a.
+__device__ __forceinline__ double direct_link_prob(const Workspace &w, int p) {
+  const xd y{w.yfm[p + 1], w.yfe[p + 1]};
+  const xd B = backward_row_sum(w, p + 1);
+  const double q = xtod(xmul(xmul(y, B), xd{w.scal[1], w.scal_i[0]}));
+  return 1.0 - q;
 }
 
 }  // namespace bpimd

@@ -41,16 +41,6 @@ __device__ __forceinline__ xd mu_of(const Workspace &w, int b) {
   return xd{w.ybm[r], w.ybe[r]};
 }
 
-// Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,
-// column p+1) this is 1 - y[p+1] B(p+1) / (N y_N) with B(a) the backward row sum
-// of particle a.
-__device__ __forceinline__ double direct_link_prob(const Workspace &w, int p) {
-  const xd y{w.yfm[p + 1], w.yfe[p + 1]};
-  const xd B = backward_row_sum(w, p + 1);
-  const double q = xtod(xmul(xmul(y, B), xd{w.scal[1], w.scal_i[0]}));
-  return 1.0 - q;
-}
-
 // Bead P of the 32 particles of row tile t: sum the row partials of blocks
 // (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
 // block of the tile to finish; all 256 threads call it.
@@ -232,6 +222,41 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
   }
 }
 
+// Expected exterior-spring energy over representative permutations, per block
+// of the lower triangle: (1/2) m w_P^2 sum_{a<=b in block} Pr[b -> a] |r_b^P - r_a^1|^2
+// (the direct links l -> l+1 are added by the caller).  Float64 throughout;
+// run once per molecular-dynamics call, for the primitive energy estimator.
+__global__ void __launch_bounds__(256) spring_expect_kernel(Workspace w, double *part) {
+  __shared__ double red[8];
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+    int t, s;
+    block_coords_f(blk, t, s);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+      const int a = s * TILE + (e >> 5), b = t * TILE + (e & 31);
+      if (b < w.N && a <= b) {
+        const size_t gi = (size_t)blk * TILE2 + e;
+        const double gmd = w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi];
+        const xd al = alpha_of(w, a), mu = mu_of(w, b);
+        const double M = xtod(xd{al.m * mu.m * gmd, al.e + mu.e + w.ge[gi]});
+        const double dx = w.RP[4 * b] - w.R1[4 * a], dy = w.RP[4 * b + 1] - w.R1[4 * a + 1],
+                     dz = w.RP[4 * b + 2] - w.R1[4 * a + 2];
+        acc += M * (dx * dx + dy * dy + dz * dz);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q];
+      part[blk] = w.half_k * sum;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void dense_prob_kernel(Workspace w, double *M) {
   const size_t NN = (size_t)w.N * w.N;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
@@ -257,6 +282,13 @@ cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F,
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w, pos, F);
   else prob_force_kernel<false><<<grid, 256, 0, s>>>(w, pos, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStream_t s) {
+  const int sms = sm_count();
+  const int grid = w.NB < sms * 4 ? w.NB : sms * 4;
+  spring_expect_kernel<<<grid, 256, 0, s>>>(w, part);
   return cudaGetLastError();
 }
 

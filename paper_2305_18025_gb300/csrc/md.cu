@@ -1,12 +1,377 @@
-// Molecular dynamics step (placeholder until the integrator lands).
-#include "md.cuh"
-#include "bpimd_internal.cuh"
+// Molecular dynamics of the bosonic ring polymers.
+//
+// The paper samples exp(-beta (V^{[1,N]} + U-bar)) (Eq.
+// int-of-sum-all-permutations; spring frequency w_P = sqrt(P)/(beta hbar),
+// Eq. eperm; U-bar = (1/P) sum_j U(r_1^j..r_N^j)) with molecular dynamics and
+// a thermostat, without stating the integrator.  This file runs Cartesian
+// BAOAB Langevin steps at temperature kT (default 1/beta) with bead mass m:
+//   B  v += (dt/2) F/m            A  x += (dt/2) v
+//   O  v  = c1 v + c2 z,  c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT/m)
+//   A  x += (dt/2) v              F = -grad(V^{[1,N]} + U-bar)(x)
+//   B  v += (dt/2) F/m
+// with U = sum_l (1/2) m w0^2 |r_l|^2 (harmonic trap) + sum_{l<l'} g
+// exp(-|r_l - r_l'|^2 / (2 s^2)) (Gaussian repulsion) between beads of equal
+// index.  The exchange force is one evaluation of Algorithm 1 (the kernels of
+// bead.cu, prep.cu, chain.cu, force.cu).
+//
+// Thermostat noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+// written here from its published definition.  Element e = 4g + i of the
+// velocity array at step s takes word i of the block with counter
+// (g, s mod 2^32, s div 2^32, 0) and key (seed mod 2^32, seed div 2^32);
+// words become uniforms u = (x + 1/2) 2^-32 and pairs of uniforms become
+// normals by the Box-Muller transform (float64; MIXED: float32).
+//
+// One step (7 kernel launches) is captured once into a CUDA graph bound to the
+// caller's position and velocity buffers and replayed; the step counter lives
+// in device memory and is advanced by the last kernel of the step.
+#include <cmath>
+#include <type_traits>
+
+#include "context.cuh"
 
 namespace bpimd {
+namespace {
+
+constexpr int MD_THREADS = 256;
+constexpr int EXT_THREADS = 128;
+constexpr int EXT_CHUNK = 1024;  // positions of one bead index staged per pass
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void box_muller(const uint32_t x[4], double z[4]) {
+  if (MIXED) {
+    float u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = ((float)x[i] + 0.5f) * 2.3283064365386963e-10f;
+    const float ra = sqrtf(-2.0f * logf(u[0])), rb = sqrtf(-2.0f * logf(u[2]));
+    float sa, ca, sb, cb;
+    sincosf(6.28318530717958648f * u[1], &sa, &ca);
+    sincosf(6.28318530717958648f * u[3], &sb, &cb);
+    z[0] = ra * ca; z[1] = ra * sa; z[2] = rb * cb; z[3] = rb * sb;
+  } else {
+    double u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = ((double)x[i] + 0.5) * 2.3283064365386962890625e-10;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double ra = sqrt(-2.0 * log(u[0])), rb = sqrt(-2.0 * log(u[2]));
+    double sa, ca, sb, cb;
+    sincos(two_pi * u[1], &sa, &ca);
+    sincos(two_pi * u[3], &sb, &cb);
+    z[0] = ra * ca; z[1] = ra * sa; z[2] = rb * cb; z[3] = rb * sb;
+  }
+}
+
+// B A O A of one step (four velocity components per thread: one Philox block).
+template <bool MIXED>
+__global__ void __launch_bounds__(MD_THREADS) md_baoa_kernel(double *__restrict__ x, double *__restrict__ v,
+                                                             const double *__restrict__ F, long long n,
+                                                             double half_dt_over_m, double half_dt, double c1,
+                                                             double c2, uint32_t k0, uint32_t k1,
+                                                             const unsigned long long *__restrict__ step) {
+  const unsigned long long s = *step;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * g < n;
+       g += (long long)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)g, (uint32_t)s, (uint32_t)(s >> 32), 0u};
+    philox4x32_10(c, k0, k1);
+    double z[4];
+    box_muller<MIXED>(c, z);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long e = 4 * g + i;
+      if (e < n) {
+        double vi = v[e] + half_dt_over_m * F[e];  // B
+        double xi = x[e] + half_dt * vi;           // A
+        vi = c1 * vi + c2 * z[i];                  // O
+        x[e] = xi + half_dt * vi;                  // A
+        v[e] = vi;
+      }
+    }
+  }
+}
+
+// Closing B of a step; advances the step counter.
+__global__ void __launch_bounds__(MD_THREADS) md_kick_kernel(double *__restrict__ v, const double *__restrict__ F,
+                                                             long long n, double half_dt_over_m,
+                                                             unsigned long long *step) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    v[e] += half_dt_over_m * F[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1ull;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warps in order); thread 0 gets it.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
+// -grad U-bar added to F, per bead index j = blockIdx.y and particle
+// l = blockIdx.x * EXT_THREADS + thread; U-bar partial sum per block.  The
+// positions of bead j of all particles pass through shared memory in chunks.
+// MIXED: pair terms in float32 (relative positions), accumulated per thread in
+// float32 and added to the float64 force.
+template <bool MIXED>
+__global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__restrict__ pos, double *__restrict__ F,
+                                                                int N, int P, double inv_P, double kt, int pair,
+                                                                double ga, double inv_s2, double *ubar_part) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  __shared__ R sx[EXT_CHUNK], sy[EXT_CHUNK], sz[EXT_CHUNK];
+  __shared__ double red[EXT_THREADS / 32];
+  const int j = blockIdx.y, l = blockIdx.x * EXT_THREADS + threadIdx.x;
+  const bool valid = l < N;
+  double rx = 0, ry = 0, rz = 0;
+  if (valid) {
+    const double *r = pos + ((size_t)l * P + j) * 3;
+    rx = r[0]; ry = r[1]; rz = r[2];
+  }
+  const R px = (R)rx, py = (R)ry, pz = (R)rz;
+  const R a = (R)(-0.5 * inv_s2);
+  R fx = 0, fy = 0, fz = 0, u = 0;
+  if (pair == BPIMD_PAIR_GAUSSIAN) {
+    for (int base = 0; base < N; base += EXT_CHUNK) {
+      const int cnt = min(EXT_CHUNK, N - base);
+      __syncthreads();
+      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const double *r = pos + ((size_t)(base + q) * P + j) * 3;
+        sx[q] = (R)r[0]; sy[q] = (R)r[1]; sz[q] = (R)r[2];
+      }
+      __syncthreads();
+      if (valid) {
+        for (int q = 0; q < cnt; ++q) {
+          const R dx = px - sx[q], dy = py - sy[q], dz = pz - sz[q];
+          const R d2 = dx * dx + dy * dy + dz * dz;
+          const R e = MIXED ? (R)__expf((float)(a * d2)) : (R)exp((double)(a * d2));
+          fx += e * dx; fy += e * dy; fz += e * dz;
+          u += e;
+        }
+      }
+    }
+    if (valid) u -= (R)1;  // the self term (d = 0, e = 1) carries no force
+  }
+  double ul = 0.0;
+  if (valid) {
+    double *f = F + ((size_t)l * P + j) * 3;
+    const double gs = ga * inv_s2;
+    f[0] += inv_P * (gs * (double)fx - kt * rx);
+    f[1] += inv_P * (gs * (double)fy - kt * ry);
+    f[2] += inv_P * (gs * (double)fz - kt * rz);
+    ul = inv_P * (0.5 * ga * (double)u + 0.5 * kt * (rx * rx + ry * ry + rz * rz));
+  }
+  const double s = block_sum(ul, red);
+  if (threadIdx.x == 0) ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(MD_THREADS) ke_kernel(const double *__restrict__ v, long long n, double half_m,
+                                                        double *ke_part) {
+  __shared__ double red[MD_THREADS / 32];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    acc += v[e] * v[e];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) ke_part[blockIdx.x] = half_m * s;
+}
+
+// energies[0..3] = V_B, U-bar, kinetic, primitive estimator 3NP/(2 beta) - <springs> + U-bar,
+// with <springs> = sum_l E_int + sum Pr[l -> u<=l] (1/2)k d^2 + sum Pr[l -> l+1] link_l.
+__global__ void __launch_bounds__(MD_THREADS) energies_kernel(Workspace w, const double *VB, const double *ubar_part,
+                                                              int n_ubar, const double *ke_part, int n_ke,
+                                                              const double *spring_part, double *energies) {
+  __shared__ double red[MD_THREADS / 32];
+  double sp = 0.0, ub = 0.0, ke = 0.0;
+  for (int q = threadIdx.x; q < w.NB; q += blockDim.x) sp += spring_part[q];
+  for (int l = threadIdx.x; l < w.N; l += blockDim.x) {
+    sp += w.Eint[l];
+    if (l + 1 < w.N) sp += direct_link_prob(w, l) * w.link[l];
+  }
+  for (int q = threadIdx.x; q < n_ubar; q += blockDim.x) ub += ubar_part[q];
+  for (int q = threadIdx.x; q < n_ke; q += blockDim.x) ke += ke_part[q];
+  sp = block_sum(sp, red);
+  ub = block_sum(ub, red);
+  ke = block_sum(ke, red);
+  if (threadIdx.x == 0) {
+    energies[0] = *VB;
+    energies[1] = ub;
+    energies[2] = ke;
+    energies[3] = 1.5 * (double)w.N * (double)w.P / w.beta - sp + ub;
+    for (int i = 0; i < 4; ++i)
+      if (!isfinite(energies[i])) atomicOr(w.status, ST_NONFINITE);
+  }
+}
+
+struct MDParams {
+  long long n;
+  double half_dt_over_m, half_dt, c1, c2, inv_P, kt, ga, inv_s2;
+  int pair;
+  uint32_t k0, k1;
+};
+
+int md_params(const bpimd_config &c, MDParams &p) {
+  if (!(c.dt > 0.0) || !std::isfinite(c.dt) || !(c.gamma >= 0.0) || !std::isfinite(c.gamma)) return BPIMD_ERR_ARG;
+  if (!(c.kT_bead >= 0.0) || !std::isfinite(c.kT_bead) || !(c.omega0 >= 0.0) || !std::isfinite(c.omega0))
+    return BPIMD_ERR_ARG;
+  if (c.pair_type != BPIMD_PAIR_NONE && c.pair_type != BPIMD_PAIR_GAUSSIAN) return BPIMD_ERR_ARG;
+  if (c.pair_type == BPIMD_PAIR_GAUSSIAN && (!std::isfinite(c.pair_a) || !(c.pair_b > 0.0) || !std::isfinite(c.pair_b)))
+    return BPIMD_ERR_ARG;
+  if (c.box_L != 0.0) return BPIMD_ERR_ARG;  // periodic boxes are not supported by this step
+  const double kT = c.kT_bead > 0.0 ? c.kT_bead : 1.0 / c.beta;
+  p.n = (long long)c.N * c.P * 3;
+  p.half_dt_over_m = 0.5 * c.dt / c.m;
+  p.half_dt = 0.5 * c.dt;
+  p.c1 = std::exp(-c.gamma * c.dt);
+  p.c2 = std::sqrt((1.0 - p.c1 * p.c1) * kT / c.m);
+  p.inv_P = 1.0 / c.P;
+  p.kt = c.m * c.omega0 * c.omega0;
+  p.pair = c.pair_type;
+  p.ga = c.pair_type == BPIMD_PAIR_GAUSSIAN ? c.pair_a : 0.0;
+  p.inv_s2 = c.pair_type == BPIMD_PAIR_GAUSSIAN ? 1.0 / (c.pair_b * c.pair_b) : 0.0;
+  p.k0 = (uint32_t)c.seed;
+  p.k1 = (uint32_t)(c.seed >> 32);
+  return BPIMD_OK;
+}
+
+int grid_for(long long work, int threads) {
+  const long long b = (work + threads - 1) / threads;
+  const long long cap = (long long)sm_count() * 8;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// F(pos) = exchange force (Algorithm 1) + physical force, U-bar partials.
+int total_force(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
+  MDState &md = ctx->md;
+  int rc = evaluate(ctx, pos, md.VB, md.F);
+  if (rc != BPIMD_OK) return rc;
+  const dim3 grid((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS, ctx->cfg.P);
+  if (ctx->w.mixed)
+    ext_force_kernel<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.inv_P, p.kt,
+                                                                  p.pair, p.ga, p.inv_s2, md.ubar_part);
+  else
+    ext_force_kernel<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.inv_P, p.kt,
+                                                                   p.pair, p.ga, p.inv_s2, md.ubar_part);
+  return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+}
+
+// Enqueue one step (B A O A, force, B) on the context stream.
+int enqueue_step(bpimd_ctx *ctx, const MDParams &p, double *pos, double *vel) {
+  MDState &md = ctx->md;
+  cudaStream_t s = ctx->stream;
+  const int g4 = grid_for((p.n + 3) / 4, MD_THREADS), g1 = grid_for(p.n, MD_THREADS);
+  if (ctx->w.mixed)
+    md_baoa_kernel<true><<<g4, MD_THREADS, 0, s>>>(pos, vel, md.F, p.n, p.half_dt_over_m, p.half_dt, p.c1, p.c2,
+                                                   p.k0, p.k1, md.step);
+  else
+    md_baoa_kernel<false><<<g4, MD_THREADS, 0, s>>>(pos, vel, md.F, p.n, p.half_dt_over_m, p.half_dt, p.c1, p.c2,
+                                                    p.k0, p.k1, md.step);
+  if (cudaGetLastError() != cudaSuccess) return BPIMD_ERR_CUDA;
+  int rc = total_force(ctx, p, pos);
+  if (rc != BPIMD_OK) return rc;
+  md_kick_kernel<<<g1, MD_THREADS, 0, s>>>(vel, md.F, p.n, p.half_dt_over_m, md.step);
+  return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+}
+
+int md_alloc(bpimd_ctx *ctx) {
+  MDState &md = ctx->md;
+  const size_t n = (size_t)ctx->cfg.N * ctx->cfg.P * 3;
+  md.ext_blocks = ((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS) * ctx->cfg.P;
+  md.ke_blocks = grid_for((long long)n, MD_THREADS);
+  md.spring_blocks = ctx->w.NB;
+  if (cudaMalloc(&md.F, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&md.VB, sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&md.ubar_part, sizeof(double) * md.ext_blocks) != cudaSuccess ||
+      cudaMalloc(&md.ke_part, sizeof(double) * md.ke_blocks) != cudaSuccess ||
+      cudaMalloc(&md.spring_part, sizeof(double) * md.spring_blocks) != cudaSuccess ||
+      cudaMalloc(&md.step, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    md_free(&md);
+    return BPIMD_ERR_NOMEM;
+  }
+  if (cudaMemsetAsync(md.step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess) return BPIMD_ERR_CUDA;
+  md.ready = true;
+  return BPIMD_OK;
+}
+
+}  // namespace
+
 void md_init(MDState *md) { *md = MDState{}; }
+
 void md_free(MDState *md) {
-  cudaFree(md->F); cudaFree(md->F_ex); cudaFree(md->acc); cudaFree(md->VB);
+  if (md->exec) cudaGraphExecDestroy(md->exec);
+  if (md->graph) cudaGraphDestroy(md->graph);
+  cudaFree(md->F);
+  cudaFree(md->VB);
+  cudaFree(md->ubar_part);
+  cudaFree(md->ke_part);
+  cudaFree(md->spring_part);
+  cudaFree(md->step);
   *md = MDState{};
 }
-int md_run(bpimd_ctx *, double *, double *, int32_t, double *) { return BPIMD_ERR_STATE; }
+
+int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies) {
+  MDParams p;
+  int rc = md_params(ctx->cfg, p);
+  if (rc != BPIMD_OK) return rc;
+  MDState &md = ctx->md;
+  if (!md.ready && (rc = md_alloc(ctx)) != BPIMD_OK) return rc;
+  // stage profiling is not recorded inside MD steps
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  // the caller may have moved the positions since the last call
+  rc = total_force(ctx, p, pos);
+  // capture one step into a graph (not possible on the legacy default stream)
+  const bool use_graph = ctx->stream != nullptr && nsteps > 1;
+  if (rc == BPIMD_OK && use_graph && (!md.exec || md.g_pos != pos || md.g_vel != vel)) {
+    if (md.exec) { cudaGraphExecDestroy(md.exec); md.exec = nullptr; }
+    if (md.graph) { cudaGraphDestroy(md.graph); md.graph = nullptr; }
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = BPIMD_ERR_CUDA;
+    } else {
+      const int rc_step = enqueue_step(ctx, p, pos, vel);
+      const cudaError_t e = cudaStreamEndCapture(ctx->stream, &md.graph);
+      if (rc_step != BPIMD_OK || e != cudaSuccess ||
+          cudaGraphInstantiate(&md.exec, md.graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        rc = BPIMD_ERR_CUDA;
+      } else {
+        md.g_pos = pos;
+        md.g_vel = vel;
+      }
+    }
+  }
+  for (int32_t s = 0; s < nsteps && rc == BPIMD_OK; ++s) {
+    if (use_graph) rc = cudaGraphLaunch(md.exec, ctx->stream) == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+    else rc = enqueue_step(ctx, p, pos, vel);
+  }
+  if (rc == BPIMD_OK) md.steps_taken += (uint64_t)nsteps;
+  if (rc == BPIMD_OK && energies) {
+    cudaStream_t s = ctx->stream;
+    const int g1 = md.ke_blocks;
+    ke_kernel<<<g1, MD_THREADS, 0, s>>>(vel, p.n, 0.5 * ctx->cfg.m, md.ke_part);
+    if (cudaGetLastError() != cudaSuccess || launch_spring_expectation(ctx->w, md.spring_part, s) != cudaSuccess)
+      rc = BPIMD_ERR_CUDA;
+    if (rc == BPIMD_OK) {
+      energies_kernel<<<1, MD_THREADS, 0, s>>>(ctx->w, md.VB, md.ubar_part, md.ext_blocks, md.ke_part, g1,
+                                              md.spring_part, energies);
+      if (cudaGetLastError() != cudaSuccess) rc = BPIMD_ERR_CUDA;
+    }
+  }
+  ctx->prof_on = prof;
+  return rc;
+}
+
 }  // namespace bpimd

@@ -7,11 +7,17 @@ struct bpimd_ctx;
 
 namespace bpimd {
 struct MDState {
-  double *F;          // [N][P][3] total force
-  double *F_ex;       // [N][P][3] exchange force
-  double *acc;        // per-step energy accumulators
-  double *VB;         // device scalar
-  uint64_t counter;   // RNG counter (steps taken)
+  double *F;                 // [N][P][3] total force of the current positions
+  double *VB;                // device scalar: V^{[1,N]} of the last evaluation
+  double *ubar_part;         // per-block U-bar partial sums of the last force pass
+  double *ke_part;           // per-block kinetic-energy partial sums
+  double *spring_part;       // per-block expected exterior-spring energies
+  unsigned long long *step;  // device step counter (thermostat noise counter)
+  int ext_blocks, ke_blocks, spring_blocks;
+  cudaGraph_t graph;         // one captured step
+  cudaGraphExec_t exec;
+  double *g_pos, *g_vel;     // buffers the captured step is bound to
+  uint64_t steps_taken;
   bool ready;
 };
 void md_init(MDState *md);

@@ -101,3 +101,53 @@ class _ExchangeFn(torch.autograd.Function):
 def exchange_potential(pos, engine):
     """V^{[1,N]}(pos) as a differentiable scalar; d/dpos is -F from the force kernel."""
     return _ExchangeFn.apply(pos, engine)
+
+
+class RingPolymerMD:
+    """BAOAB Langevin molecular dynamics of N bosonic ring polymers (bpimd_step).
+
+    Samples exp(-beta (V^{[1,N]} + U-bar)) with the exchange force of Algorithm 1
+    plus a harmonic trap (omega0) and an optional Gaussian repulsion
+    g exp(-r^2/(2 s^2)) between beads of equal index.  ``step`` advances the
+    caller's position and velocity tensors in place; with a non-default stream
+    the step runs as a replayed CUDA graph.
+    """
+
+    def __init__(self, N, P, m, omega_P, beta, dt, gamma=1.0, omega0=0.0, gaussian=None, kT=0.0,
+                 seed=0, precision="fp64", device="cuda", stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
+        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        self.N, self.P = int(N), int(P)
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        md = dict(dt=float(dt), gamma=float(gamma), kT_bead=float(kT), omega0=float(omega0), seed=int(seed))
+        if gaussian is not None:
+            md.update(pair_type=_c.BPIMD_PAIR_GAUSSIAN, pair_a=float(gaussian[0]), pair_b=float(gaussian[1]))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.cfg = _c.make_config(self.N, self.P, float(m), float(omega_P), float(beta), prec, **md)
+            self.ctx = _c.bpimd_create(self.cfg, self.stream)
+            self.energies = torch.zeros(4, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _c.bpimd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, pos, vel, nsteps=1, energies=True):
+        """Advance (pos, vel) by nsteps; returns the device tensor
+        [V_B, U-bar, kinetic, primitive estimator] after the last step, or None."""
+        for t in (pos, vel):
+            if t.dtype != torch.float64 or t.device != self.device or tuple(t.shape) != (self.N, self.P, 3) \
+                    or not t.is_contiguous():
+                raise ValueError(f"positions/velocities must be contiguous float64 [{self.N}][{self.P}][3]")
+        _c.bpimd_step(self.ctx, pos, vel, nsteps, self.energies if energies else None)
+        return self.energies if energies else None

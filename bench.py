@@ -6,7 +6,9 @@ P = 32 beads (beta = 1, m = hbar = 1, omega_P = sqrt(P)/beta), trapped-boson
 positions (centres N(0,1), bead offsets N(0,0.1), seed 3), in the mixed
 float32/float64 form (the reported `value`) and the plain float64 form
 (`fp64`).  A step is one full evaluation: bead pass, pair factors, forward
-and backward recursions, prefix sums, probability/force blocks, finalise.
+and backward recursions with the prefix sums and V_B, probabilities with all
+exterior-bead forces.  The line also carries MD steps/s (`md`) of the same
+system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -47,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--md-steps", type=int, default=200, help="timed MD steps (mixed; float64 runs a quarter)")
     return ap.parse_args()
 
 
@@ -262,6 +265,7 @@ def run_ours(args, rank, world, local_rank):
                               "d2h_bytes_per_step": F_h.numel() * 8 + 8,
                               "api": "bpimd_exchange_energy_forces_host (pinned host buffers)"}
         eng.close()
+    results["md"] = md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world)
     clocks = sampler.stop()
 
     if rank != 0:
@@ -284,10 +288,50 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
         "V_B": {"mixed": mixed["V_B"], "fp64": fp64["V_B"]},
+        "md": results["md"],
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
     return line
+
+
+MD_CFG = dict(dt=0.01, gamma=1.0, omega0=1.0, gaussian=(3.0, 0.5), seed=7)
+
+
+def md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world):
+    """MD steps/s of the same system with a harmonic trap (w0 = 1) and Gaussian
+    repulsion (g = 3, s = 0.5): bpimd_step replaying one captured CUDA graph per
+    step (BAOAB + exchange force + pair force), mixed and float64."""
+    import torch
+    from paper_2305_18025_gb300.exchange import RingPolymerMD
+    out = {}
+    for prec, steps in (("mixed", args.md_steps), ("fp64", max(1, args.md_steps // 4))):
+        side = torch.cuda.Stream(dev)
+        md = RingPolymerMD(args.N, args.P, 1.0, wP, args.beta, precision=prec, stream=side, **MD_CFG)
+        x = torch.from_numpy(pos_np.copy()).to(dev)
+        v = torch.zeros_like(x)
+        md.step(x, v, 5, energies=False)            # warm-up, graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(side)
+        md.step(x, v, steps, energies=False)
+        e1.record(side)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        en = md.step(x, v, 1).cpu().tolist()
+        md.close()
+        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "MD steps/s", "steps": steps,
+                     "gpu_launches": 7 * steps + 5,
+                     "ms_per_step": ms / steps, "energies_after": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
+    out["config"] = {"workload": f"trapped bosons N={args.N} P={args.P} beta={args.beta:g}, harmonic trap w0=1, "
+                                 "Gaussian repulsion g=3 s=0.5 between equal-index beads",
+                     "integrator": "BAOAB Langevin, dt=0.01, gamma=1, kT=1/beta, Philox4x32-10 noise",
+                     "timing": "CUDA events around one bpimd_step call (one initial force evaluation + "
+                               "the steps as CUDA-graph replays); L2 not flushed between MD steps, "
+                               "which run back to back as in a production trajectory"}
+    return out
 
 
 def cpu_baseline(args, pos_np, wP, seconds=None, max_evals=None):

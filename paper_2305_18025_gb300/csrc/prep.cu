@@ -22,8 +22,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // block index -> (t, s) with s <= t, blk = t(t+1)/2 + s
+// (float32 estimate of the triangular root, corrected with integer tests:
+// no float64 instruction)
 __device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
-  int tt = (int)((sqrt(8.0 * blk + 1.0) - 1.0) * 0.5);
+  int tt = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
   while ((tt + 1) * (tt + 2) / 2 <= blk) ++tt;
   while (tt * (tt + 1) / 2 > blk) --tt;
   t = tt;

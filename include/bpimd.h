@@ -176,6 +176,43 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
                int32_t nsteps, double *energies);
 
+/* --------------------------------------------------------- replica batches */
+/* Many independent systems ("replicas") of uneven size and temperature
+ * evaluated together: the same Algorithm 1 per replica, four kernel launches
+ * per batch whatever the number of replicas.  The paper has no batched form;
+ * it serves workloads such as parallel tempering or many small trapped
+ * systems that are too small to fill a GPU one at a time.
+ *
+ * bpimd_create_batched: cfg supplies m, precision and flags (its N, P,
+ * omega_P, beta and MD fields are ignored); host arrays of length R give each
+ * replica's N[r] (1..4096), P[r] (>= 2), omega_P[r] and beta[r] (> 0, finite).
+ * Packed layout of positions and forces: replica r occupies
+ * [N[r]][P[r]][3] float64 starting at element offset
+ * off[r] = 3 * sum_{q<r} N[q] P[q] (bpimd_batch_info returns them).
+ * Errors: BPIMD_ERR_ARG (sizes, parameters), BPIMD_ERR_NOMEM.  Single-system
+ * calls on a batch context (and batch calls on a single-system context)
+ * return BPIMD_ERR_STATE; bpimd_sync, bpimd_profile_* and bpimd_destroy work
+ * on both. */
+int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R,
+                         const int32_t *N, const int32_t *P, const double *omega_P,
+                         const double *beta, void *cuda_stream);
+
+/* One evaluation of every replica (asynchronous on the context stream):
+ *   positions : device, packed [sum 3 N_r P_r] float64 (16-byte aligned).
+ *   V_B       : device array of R float64 receiving V^{[1,N_r]}; may be NULL.
+ *   forces    : device, packed like positions; overwritten with -grad V. */
+int bpimd_exchange_energy_forces_batched(bpimd_ctx *ctx, const double *positions,
+                                         double *V_B, double *forces);
+
+/* Batch geometry: *R, the total number of float64 elements of the packed
+ * arrays, and (if not NULL) offsets[R] in elements.  Any pointer may be NULL. */
+int bpimd_batch_info(bpimd_ctx *ctx, int32_t *R, int64_t *elements, int64_t *offsets);
+
+/* Launch shape of the batched pair-factor and probability passes: at most
+ * blocks_per_sm x (number of SMs) CTAs each (1..64; default 8).  Set by the
+ * autotuner (paper_2305_18025_gb300/autotune.py); results do not depend on it. */
+int bpimd_batch_set_tuning(bpimd_ctx *ctx, int32_t pair_blocks_per_sm, int32_t prob_blocks_per_sm);
+
 /* ------------------------------------------------------------- profiling */
 /* Stage timing with CUDA events recorded on the context stream around each
  * kernel of an evaluation.  Stage order:

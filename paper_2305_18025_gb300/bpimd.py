@@ -33,7 +33,10 @@ EXPORTED = [
     "bpimd_exchange_energy_forces_host", "bpimd_sync", "bpimd_get_potentials",
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
     "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
+    "bpimd_create_batched", "bpimd_exchange_energy_forces_batched", "bpimd_batch_info",
+    "bpimd_batch_set_tuning",
 ]
+BATCH_MAX_N = 4096
 BPIMD_NUM_STAGES = 4
 STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "prob_forces"]
 
@@ -89,6 +92,11 @@ def load(build_if_missing=True):
     lib.bpimd_profile_begin.argtypes = [vp, ip]
     lib.bpimd_profile_end.argtypes = [vp, vp, vp]
     lib.bpimd_exchange_energy_forces_noalloc.argtypes = [ctypes.POINTER(bpimd_config), vp, vp, vp, vp]
+    lib.bpimd_create_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(bpimd_config), ctypes.c_int32,
+                                         vp, vp, vp, vp, vp]
+    lib.bpimd_exchange_energy_forces_batched.argtypes = [vp, vp, vp, vp]
+    lib.bpimd_batch_info.argtypes = [vp, vp, vp, vp]
+    lib.bpimd_batch_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     for name in EXPORTED:
         if name not in ("bpimd_status_string", "bpimd_version"):
             getattr(lib, name).restype = ip
@@ -192,6 +200,44 @@ def bpimd_exchange_energy_forces_noalloc(cfg, positions, V_B, forces, stream=Non
     _check(load().bpimd_exchange_energy_forces_noalloc(ctypes.byref(cfg), _ptr(positions), _ptr(V_B),
                                                        _ptr(forces), _stream_handle(stream)),
            "bpimd_exchange_energy_forces_noalloc")
+
+
+def bpimd_create_batched(cfg, N, P, omega_P, beta, stream=None):
+    """Batch context for replicas with per-replica N, P, omega_P, beta (host sequences)."""
+    import numpy as np
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    P = np.ascontiguousarray(P, dtype=np.int32)
+    omega_P = np.ascontiguousarray(omega_P, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    R = len(N)
+    if not (len(P) == len(omega_P) == len(beta) == R):
+        raise ValueError("N, P, omega_P, beta must have the same length")
+    h = ctypes.c_void_p()
+    _check(load().bpimd_create_batched(ctypes.byref(h), ctypes.byref(cfg), R, N.ctypes.data, P.ctypes.data,
+                                       omega_P.ctypes.data, beta.ctypes.data, _stream_handle(stream)),
+           "bpimd_create_batched")
+    return h.value
+
+
+def bpimd_exchange_energy_forces_batched(ctx, positions, V_B, forces):
+    _check(load().bpimd_exchange_energy_forces_batched(ctx, _ptr(positions), _ptr(V_B), _ptr(forces)),
+           "bpimd_exchange_energy_forces_batched")
+
+
+def bpimd_batch_info(ctx):
+    """(R, total elements, element offsets of the replicas)."""
+    import numpy as np
+    R = ctypes.c_int32()
+    n = ctypes.c_int64()
+    _check(load().bpimd_batch_info(ctx, ctypes.byref(R), ctypes.byref(n), None), "bpimd_batch_info")
+    off = np.zeros(R.value, dtype=np.int64)
+    _check(load().bpimd_batch_info(ctx, None, None, off.ctypes.data), "bpimd_batch_info")
+    return R.value, n.value, off
+
+
+def bpimd_batch_set_tuning(ctx, pair_blocks_per_sm, prob_blocks_per_sm):
+    _check(load().bpimd_batch_set_tuning(ctx, int(pair_blocks_per_sm), int(prob_blocks_per_sm)),
+           "bpimd_batch_set_tuning")
 
 
 def make_config(N, P, m, omega_P, beta, precision=BPIMD_FP64, **md):

@@ -184,6 +184,7 @@ int bpimd_destroy(bpimd_ctx *ctx) {
 
 int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions, double *V_B, double *forces) {
   if (!ctx) return BPIMD_ERR_ARG;
+  if (ctx->R) return BPIMD_ERR_STATE;
   int rc;
   if ((rc = check_ptr(positions)) || (rc = check_ptr(forces))) return rc;
   if (V_B && (((uintptr_t)V_B) & 7)) return BPIMD_ERR_ARG;
@@ -192,6 +193,7 @@ int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions, double
 
 int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions, double *V_B, double *forces) {
   if (!ctx || !positions || !forces) return BPIMD_ERR_ARG;
+  if (ctx->R) return BPIMD_ERR_STATE;
   const size_t bytes = sizeof(double) * 3 * (size_t)ctx->w.N * ctx->w.P;
   if (!ctx->d_pos) {
     if (cudaMalloc(&ctx->d_pos, bytes) != cudaSuccess || cudaMalloc(&ctx->d_F, bytes) != cudaSuccess ||
@@ -217,6 +219,7 @@ int bpimd_sync(bpimd_ctx *ctx) {
 
 int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *Eint) {
   if (!ctx) return BPIMD_ERR_ARG;
+  if (ctx->R) return BPIMD_ERR_STATE;
   if (!ctx->evaluated) return BPIMD_ERR_STATE;
   const size_t N = ctx->w.N;
   cudaStream_t s = ctx->stream;
@@ -232,6 +235,7 @@ int bpimd_get_potentials(bpimd_ctx *ctx, double *V_fwd, double *V_bwd, double *E
 
 int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M) {
   if (!ctx) return BPIMD_ERR_ARG;
+  if (ctx->R) return BPIMD_ERR_STATE;
   int rc;
   if ((rc = check_ptr(M))) return rc;
   if (!ctx->evaluated) return BPIMD_ERR_STATE;
@@ -240,6 +244,7 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M) {
 
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities, int32_t nsteps, double *energies) {
   if (!ctx || nsteps < 0) return BPIMD_ERR_ARG;
+  if (ctx->R) return BPIMD_ERR_STATE;
   int rc;
   if ((rc = check_ptr(positions)) || (rc = check_ptr(velocities))) return rc;
   if (energies && (((uintptr_t)energies) & 7)) return BPIMD_ERR_ARG;

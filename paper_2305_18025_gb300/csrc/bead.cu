@@ -15,15 +15,15 @@
 namespace bpimd {
 namespace {
 
-constexpr int BEAD_WARPS = 8;  // particles per block (one warp each)
+constexpr int BEAD_WARPS = BEAD_BLOCK_PARTICLES;  // particles per block (one warp each)
 
+// Particles l0 .. l0+7 of one system (all threads of the block).
 template <bool MIXED>
-__global__ void __launch_bounds__(32 * BEAD_WARPS) bead_pass_kernel(Workspace w, const double *__restrict__ pos,
-                                                                    double *__restrict__ F) {
+__device__ __forceinline__ void bead_pass_body(const Workspace &w, const double *__restrict__ pos,
+                                               double *__restrict__ F, int l0) {
   __shared__ double eint_s[BEAD_WARPS];
   __shared__ int finite_s[BEAD_WARPS];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int l0 = blockIdx.x * BEAD_WARPS;
   const int P = w.P;
   const double k = w.k;
   // phase 1: one warp per particle -- interior springs and interior forces
@@ -123,12 +123,38 @@ __global__ void __launch_bounds__(32 * BEAD_WARPS) bead_pass_kernel(Workspace w,
   }
 }
 
+template <bool MIXED>
+__global__ void __launch_bounds__(32 * BEAD_WARPS) bead_pass_kernel(Workspace w, const double *__restrict__ pos,
+                                                                    double *__restrict__ F) {
+  bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
+}
+
+// Replica batch: block k handles particles tab[k].y.. of replica tab[k].x,
+// whose positions and forces start at element off[replica] of the packed arrays.
+template <bool MIXED>
+__global__ void __launch_bounds__(32 * BEAD_WARPS) bead_pass_batched(const Workspace *__restrict__ ws,
+                                                                     const int2 *__restrict__ tab,
+                                                                     const long long *__restrict__ off,
+                                                                     const double *__restrict__ pos,
+                                                                     double *__restrict__ F) {
+  const int2 e = tab[blockIdx.x];
+  bead_pass_body<MIXED>(ws[e.x], pos + off[e.x], F + off[e.x], e.y);
+}
+
 }  // namespace
 
 cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   dim3 grid((w.N + BEAD_WARPS - 1) / BEAD_WARPS), block(32 * BEAD_WARPS);
   if (w.mixed) bead_pass_kernel<true><<<grid, block, 0, s>>>(w, pos, F);
   else bead_pass_kernel<false><<<grid, block, 0, s>>>(w, pos, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bead_pass_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
+                                     bool mixed, const double *pos, double *F, cudaStream_t s) {
+  if (ntab <= 0) return cudaSuccess;
+  if (mixed) bead_pass_batched<true><<<ntab, 32 * BEAD_WARPS, 0, s>>>(ws, tab, off, pos, F);
+  else bead_pass_batched<false><<<ntab, 32 * BEAD_WARPS, 0, s>>>(ws, tab, off, pos, F);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
 constexpr int CHAIN_THREADS = 640;     // 20 warps: up to 96 registers per thread
 constexpr int CHAIN_CLUSTER = 8;      // CTAs per recursion: one lead + seven bulk CTAs
 constexpr int CHAIN_MAX_N = 6912;     // largest N the library accepts
+constexpr int BATCH_MAX_N = 4096;     // largest replica of a batch (one CTA per recursion)
+constexpr int BEAD_BLOCK_PARTICLES = 8;  // particles per block of the bead pass
 constexpr double LOG2E = 1.4426950408889634074;
 constexpr double LN2 = 0.6931471805599453094;
 
@@ -175,6 +177,20 @@ cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream
 // per block of g: (1/2) m w_P^2 sum Pr[b -> a] |r_b^P - r_a^1|^2 over a <= b (part[NB])
 cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStream_t s);
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);
+
+// Replica batches: ws[r] is replica r's workspace (device array); block tables
+// hold (replica, particle block) for the bead pass and (replica, g block) for
+// the pair factors and the probability pass; off[r] is the element offset of
+// replica r in the packed position/force arrays; order lists replicas by
+// decreasing N.
+cudaError_t launch_bead_pass_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
+                                     bool mixed, const double *pos, double *F, cudaStream_t s);
+cudaError_t launch_gmat_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed, bool padding,
+                                int blocks_per_sm, cudaStream_t s);
+cudaError_t launch_chains_batched(const Workspace *ws, const int *order, int R, int maxN, bool mixed, double *V_B,
+                                  cudaStream_t s);
+cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
+                                      bool mixed, const double *pos, double *F, int blocks_per_sm, cudaStream_t s);
 
 // B_{a+1} (1-based backward row sum for 0-based particle a) from the stored state
 __device__ __forceinline__ xd backward_row_sum(const Workspace &w, int a) {

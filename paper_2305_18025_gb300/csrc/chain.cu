@@ -50,121 +50,17 @@
 #include <cooperative_groups.h>
 #include <type_traits>
 
-#include "bpimd_internal.cuh"
+#include "chain_common.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace bpimd {
 namespace {
 
+using namespace chain_detail;
+
 constexpr int NHELP = CHAIN_CLUSTER - 1;  // bulk CTAs per recursion
 constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
-constexpr int BLK = 32 * 33;              // padded 32 x 32 block in shared memory
-
-__device__ __forceinline__ size_t hidx(int src, int row) {
-  const int t = row >> 5, s = src >> 5;
-  return ((size_t)(t * (t + 1) / 2 + s) << 10) + ((src & 31) << 5) + (row & 31);
-}
-
-// x * 2^k for k <= 0 by integer arithmetic on the exponent field (x >= 0 normal
-// or zero); 0 when the result would leave the normal range.
-__device__ __forceinline__ double scale_nonpos(double x, int k) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)(b >> 52);  // sign bit is 0
-  return (ex + k <= 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
-}
-
-// acc + K * y, branch-free, for the dependency chain.  Operands are extended
-// numbers whose mantissas are normal doubles in [1, 2^60) (an extended zero is
-// carried as mantissa 1 with exponent XZERO_E, i.e. 2^-536870912).  Both
-// operands are scaled by 2^k, k <= 0 clamped at -1000, by adding k to the
-// exponent field of the high word: a clamped operand is below 2^-900 of the
-// other and cannot change the float64 sum.  One float64 FMA, five integer ops.
-__device__ __forceinline__ xd fma_chain(xd acc, double km, int ke, xd y) {
-  const int pe = ke + y.e;
-  const int E = max(acc.e, pe);
-  const int k1 = max(pe - E, -1000), k2 = max(acc.e - E, -1000);
-  const double ks = __hiloint2double(__double2hiint(km) + k1 * (1 << 20), __double2loint(km));
-  const double as = __hiloint2double(__double2hiint(acc.m) + k2 * (1 << 20), __double2loint(acc.m));
-  return xd{fma(ks, y.m, as), E};
-}
-
-// Explicit shared-memory loads (32-bit shared-window addresses).
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ double lds_f64(unsigned a) {
-  double v;
-  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ float lds_f32(unsigned a) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ int lds_s32(unsigned a) {
-  int v;
-  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
-  return v;
-}
-
-// Normalise with integer ops only (m > 0 normal, or 0).
-__device__ __forceinline__ xd xnorm_int(xd a) {
-  const long long b = __double_as_longlong(a.m);
-  if (b <= 0) return xd{0.0, XZERO_E};
-  const int ex = (int)(b >> 52);
-  return xd{__longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL), a.e + ex - 1023};
-}
-
-// a * b with integer normalisation (one float64 multiply).
-__device__ __forceinline__ xd xmul_int(xd a, xd b) { return xnorm_int(xd{a.m * b.m, a.e + b.e}); }
-
-// Round the significand of a positive normal double to a float in [1,2] with
-// integer ops (no float64 conversion unit); the binary exponent is dropped.
-__device__ __forceinline__ float mant_to_float(double m) {
-  const long long b = __double_as_longlong(m);
-  const long long frac = b & 0x000fffffffffffffLL;
-  return __int_as_float((int)((frac + (1LL << 28)) >> 29) + 0x3f800000);
-}
-
-// Mantissa in [1,2) as a 53-bit integer (implicit bit set), from a double or a float.
-__device__ __forceinline__ unsigned long long mant53(double m) {
-  return ((unsigned long long)__double_as_longlong(m) & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-}
-__device__ __forceinline__ unsigned long long mant53(float m) {
-  return ((unsigned long long)((unsigned)__float_as_int(m) & 0x7FFFFFu) | 0x800000ull) << 29;
-}
-
-// c * h for extended numbers with mantissas in [1,2): the 53 x 53-bit mantissa
-// product on the integer pipe (truncated to 52 fraction bits, error below one
-// unit in the last place), so that staging issues no float64 instruction.
-template <typename M_t>
-__device__ __forceinline__ xd mul_mant(xd c, M_t hm, int he) {
-  const unsigned long long hi = __umul64hi(mant53(c.m) << 11, mant53(hm) << 11);  // in [2^62, 2^64)
-  const int sh = (int)(hi >> 63);
-  const unsigned long long frac = (hi >> (10 + sh)) & 0xFFFFFFFFFFFFFull;
-  return xd{__longlong_as_double((long long)(frac | 0x3FF0000000000000ull)), c.e + he + sh};
-}
-
-// A positive normal float (or 0) as a double, with integer operations.
-__device__ __forceinline__ double f2d_int(float f) {
-  const unsigned b = (unsigned)__float_as_int(f);
-  if (b < 0x00800000u) return 0.0;
-  return __longlong_as_double(((long long)((b >> 23) + 896) << 52) | ((long long)(b & 0x7FFFFFu) << 29));
-}
-
-// a + b for extended numbers with positive normal (or zero) mantissas: the
-// smaller operand is aligned by integer arithmetic, then one float64 add.
-__device__ __forceinline__ xd xadd_int(xd a, xd b) {
-  const int E = max(a.e, b.e);
-  return xd{scale_nonpos(a.m, max(a.e - E, -1100)) + scale_nonpos(b.m, max(b.e - E, -1100)), E};
-}
-
-// Online-max merge of a float partial sum (s * 2^E) with a term x * 2^e.
-__device__ __forceinline__ void fmerge(float &s, int &E, float x, int e) {
-  const int En = max(E, e);
-  s = fmaf(x, pow2f_nonpos(e - En), s * pow2f_nonpos(E - En));
-  E = En;
-}
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
@@ -209,11 +105,6 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
   using M_t = typename std::conditional<MIXED, float, double>::type;
   const void *gm = BWD ? w.gbm : w.gm;
   const int *ge = BWD ? w.gbe : w.ge;
-  auto coef = [&](int row) -> xd {
-    if (!BWD) return xd{__ldg(w.ccm + row), __ldg(w.cce + row)};
-    if (row >= N - 1) return xd{1.0, 0};
-    return xd{__ldg(w.ccm + N - 2 - row), __ldg(w.cce + N - 2 - row)};
-  };
   double *gYm = BWD ? w.ybm : w.yfm;
   int *gYe = BWD ? w.ybe : w.yfe;
   LeadSmem *lead_local = (LeadSmem *)smem_raw;
@@ -222,141 +113,39 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
   if (rank == 0) {
     LeadSmem &sm = *lead_local;
-    // Staging issues no float64 instruction (the SM's float64 pipe belongs to
-    // the dependency chain).  Pairs outside src <= row < N hold the extended
-    // zero 1 * 2^XZERO_E; loads are coalesced along rows and issued before use.
     // Staging warps are the lead's warps off warp 0's sub-partition (warp id
     // not a multiple of 4), numbered q = 0, 1, ...: q < 8 stage four rows each
     // of the diagonal block, 8 <= q < 12 eight rows each of the off-diagonal
     // block, q == 12 forms the prefix sums (forward recursion).
-    // H(tt*32+i, (tt+1)*32+lane) for i in [i0, i0+8), as stored (float for MIXED)
-    auto stage_offdiag = [&](int tt, int buf, int i0) {
-      const int srcbase = tt * TILE, row = tt * TILE + TILE + lane;
-      M_t *dm = (M_t *)(sm.Hom + buf * BLK);
-      int *de = sm.Hoe + buf * BLK;
-#pragma unroll
-      for (int i = i0; i < i0 + 8; ++i) {
-        const int src = srcbase + i;
-        M_t m = (M_t)1.0;
-        int e = XZERO_E;
-        if (row < N) {
-          const size_t gi = hidx(src, row);
-          m = __ldg((const M_t *)gm + gi);
-          e = __ldg(ge + gi);
-        }
-        dm[i * 33 + lane] = m;
-        de[i * 33 + lane] = e;
-      }
-    };
-    // the diagonal block of tile tt, K = c_row * H (float64 mantissas), rows
-    // i in [i0, i0+4)
-    auto stage_diag = [&](int tt, int buf, int i0) {
-      const int r0 = tt * TILE, row = r0 + lane;
-      double *dm = sm.Kdm + buf * BLK;
-      int *de = sm.Kde + buf * BLK;
-      const xd c = (row < N) ? xnorm_int(coef(row)) : xd{1.0, 0};
-#pragma unroll
-      for (int i = i0; i < i0 + 4; ++i) {
-        const int src = r0 + i;
-        M_t m = (M_t)1.0;
-        int e = XZERO_E;
-        if (row < N && src <= row) {
-          const size_t gi = hidx(src, row);
-          m = __ldg((const M_t *)gm + gi);
-          e = __ldg(ge + gi);
-        }
-        const xd k = mul_mant<M_t>(c, m, e);
-        dm[i * 33 + lane] = k.m;
-        de[i * 33 + lane] = k.e;
-      }
-    };
     if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
     const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
-    if (q >= 0 && q < 8) stage_diag(0, 0, 4 * q);
-    if (q >= 8 && q < 12) stage_offdiag(0, 0, 8 * (q - 8));
+    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde);
+    if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
     cluster.sync();
 
     xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
     xd cnext{1.0, 0};      // warp 0: coefficient of its row in the coming tile
-    if (wid == 0 && lane < N) cnext = coef(lane);
-    double carry = 0.0;    // warp 3 (forward): running prefix sum
+    if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
+    double carry = 0.0;    // prefix-sum warp (forward): running prefix sum
     for (int t = 0; t < NT; ++t) {
-      const int r0 = t * TILE, buf = t & 1;
+      const int buf = t & 1;
       if (wid == 0) {
         // ---------------------------------------------- dependent steps of tile t
-        const int row = r0 + lane;
-        xd acc{0.0, XZERO_E};
+        const int row = t * TILE + lane;
         const xd crow = cnext;
-        if (row + TILE < N) cnext = coef(row + TILE);  // prefetch for tile t+1
-        if (row < N) {
-          acc = xadd_int(xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, nxt);
-          acc = xmul_int(xnorm_int(acc), crow);  // acc' = c_row * (sum over sources < r0)
-        }
-        xd ycur{sm.Ym[r0 & (YRING - 1)], sm.Ye[r0 & (YRING - 1)]};
-        const double *Kdm = sm.Kdm + buf * BLK, *Hom = sm.Hom + buf * BLK;
-        const int *Kde = sm.Kde + buf * BLK, *Hoe = sm.Hoe + buf * BLK;
-        if (__double_as_longlong(acc.m) <= 0) acc = xd{1.0, XZERO_E};
-        nxt = xd{1.0, XZERO_E};
-        float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
-        int nexp = XZERO_E;
-        // 32 steps, no branches and no stores: rows past N and finished rows see
-        // extended zeros in the staged blocks, and row j's accumulator is final
-        // after step j (later steps add at most 2^-1000 of it).  Block entries of
-        // step i+1 are loaded (explicit ld.shared) before step i's shuffle.
-        const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
-        const unsigned aHm = MIXED ? smem_addr((const float *)Hom + lane) : smem_addr(Hom + lane);
-        double km = lds_f64(aKm), hm = MIXED ? 0.0 : lds_f64(aHm);
-        float hf = MIXED ? lds_f32(aHm) : 0.0f;
-        int ke = lds_s32(aKe), he = lds_s32(aHe);
-#pragma unroll
-        for (int i = 0; i < TILE; ++i) {
-          double km1 = 0.0, hm1 = 0.0;
-          float hf1 = 0.0f;
-          int ke1 = 0, he1 = 0;
-          if (i + 1 < TILE) {
-            km1 = lds_f64(aKm + (i + 1) * 33 * 8);
-            if (MIXED) hf1 = lds_f32(aHm + (i + 1) * 33 * 4);
-            else hm1 = lds_f64(aHm + (i + 1) * 33 * 8);
-            ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
-            he1 = lds_s32(aHe + (i + 1) * 33 * 4);
-          }
-          acc = fma_chain(acc, km, ke, ycur);  // the dependency chain
-          // next tile's rows, off the chain (MIXED: float32, no float64 pipe)
-          // (ycur.m is a positive normal double, not necessarily in [1,2))
-          if (MIXED)
-            fmerge(nsum, nexp, mant_to_float(ycur.m) * hf,
-                   he + ycur.e + (int)(__double_as_longlong(ycur.m) >> 52) - 1023);
-          else nxt = fma_chain(nxt, hm, he, ycur);
-          ycur.m = __shfl_sync(0xffffffffu, acc.m, i);
-          ycur.e = __shfl_sync(0xffffffffu, acc.e, i);
-          km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
-        }
-        if (MIXED) nxt = xd{f2d_int(nsum), nexp};
-        if (row < N) {  // Y_{row+1} = final accumulator of row `row`
-          const xd yn = xnorm_int(acc);
-          sm.Ym[(row + 1) & (YRING - 1)] = yn.m;
-          sm.Ye[(row + 1) & (YRING - 1)] = yn.e;
-          gYm[row + 1] = yn.m;
-          gYe[row + 1] = yn.e;
-        }
-        nxt = xnorm_int(nxt);
+        if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
+        chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
+                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
+                          sm.Ym, sm.Ye, YRING - 1, gYm, gYe);
       } else if (q >= 0 && q < 8) {
-        if (t + 1 < NT) stage_diag(t + 1, buf ^ 1, 4 * q);
+        if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
       } else if (q >= 8 && q < 12) {
-        if (t + 1 < NT) stage_offdiag(t + 1, buf ^ 1, 8 * (q - 8));
+        if (t + 1 < NT)
+          stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
       } else if (!BWD && q == 12) {
-        // prefix sums C[i+1] = sum_{q<=i} (E_int_q + link_q), one tile per period
-        const int i = r0 + lane;
-        double v = (i < N) ? (__ldg(w.Eint + i) + __ldg(w.link + i)) : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const double u = __shfl_up_sync(0xffffffffu, v, o);
-          if (lane >= o) v += u;
-        }
-        if (i < N) w.C[i + 1] = carry + v;
-        carry += __shfl_sync(0xffffffffu, v, 31);
+        prefix_tile(w, t, carry);
       }
       cluster.sync();
     }

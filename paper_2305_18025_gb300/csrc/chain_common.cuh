@@ -1,0 +1,274 @@
+// Device helpers of the recursion kernels (chain.cu: one cluster per
+// recursion; chain_batched.cu: one CTA per recursion of a replica batch).
+// Internal; included by those two files only.
+#pragma once
+#include <type_traits>
+
+#include "bpimd_internal.cuh"
+
+namespace bpimd {
+namespace chain_detail {
+
+constexpr int BLK = 32 * 33;  // padded 32 x 32 block in shared memory
+
+// index of H(src, row) in the tile-packed pair-factor layout
+__device__ __forceinline__ size_t hidx(int src, int row) {
+  const int t = row >> 5, s = src >> 5;
+  return ((size_t)(t * (t + 1) / 2 + s) << 10) + ((src & 31) << 5) + (row & 31);
+}
+
+// x * 2^k for k <= 0 by integer arithmetic on the exponent field (x >= 0 normal
+// or zero); 0 when the result would leave the normal range.
+__device__ __forceinline__ double scale_nonpos(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)(b >> 52);  // sign bit is 0
+  return (ex + k <= 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
+}
+
+// acc + K * y, branch-free, for the dependency chain.  Operands are extended
+// numbers whose mantissas are normal doubles in [1, 2^60) (an extended zero is
+// carried as mantissa 1 with exponent XZERO_E, i.e. 2^-536870912).  Both
+// operands are scaled by 2^k, k <= 0 clamped at -1000, by adding k to the
+// exponent field of the high word: a clamped operand is below 2^-900 of the
+// other and cannot change the float64 sum.  One float64 FMA, five integer ops.
+__device__ __forceinline__ xd fma_chain(xd acc, double km, int ke, xd y) {
+  const int pe = ke + y.e;
+  const int E = max(acc.e, pe);
+  const int k1 = max(pe - E, -1000), k2 = max(acc.e - E, -1000);
+  const double ks = __hiloint2double(__double2hiint(km) + k1 * (1 << 20), __double2loint(km));
+  const double as = __hiloint2double(__double2hiint(acc.m) + k2 * (1 << 20), __double2loint(acc.m));
+  return xd{fma(ks, y.m, as), E};
+}
+
+// Explicit shared-memory loads (32-bit shared-window addresses).
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ double lds_f64(unsigned a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float lds_f32(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int lds_s32(unsigned a) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+
+// Normalise with integer ops only (m > 0 normal, or 0).
+__device__ __forceinline__ xd xnorm_int(xd a) {
+  const long long b = __double_as_longlong(a.m);
+  if (b <= 0) return xd{0.0, XZERO_E};
+  const int ex = (int)(b >> 52);
+  return xd{__longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL), a.e + ex - 1023};
+}
+
+// a * b with integer normalisation (one float64 multiply).
+__device__ __forceinline__ xd xmul_int(xd a, xd b) { return xnorm_int(xd{a.m * b.m, a.e + b.e}); }
+
+// Round the significand of a positive normal double to a float in [1,2] with
+// integer ops (no float64 conversion unit); the binary exponent is dropped.
+__device__ __forceinline__ float mant_to_float(double m) {
+  const long long b = __double_as_longlong(m);
+  const long long frac = b & 0x000fffffffffffffLL;
+  return __int_as_float((int)((frac + (1LL << 28)) >> 29) + 0x3f800000);
+}
+
+// Mantissa in [1,2) as a 53-bit integer (implicit bit set), from a double or a float.
+__device__ __forceinline__ unsigned long long mant53(double m) {
+  return ((unsigned long long)__double_as_longlong(m) & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+}
+__device__ __forceinline__ unsigned long long mant53(float m) {
+  return ((unsigned long long)((unsigned)__float_as_int(m) & 0x7FFFFFu) | 0x800000ull) << 29;
+}
+
+// c * h for extended numbers with mantissas in [1,2): the 53 x 53-bit mantissa
+// product on the integer pipe (truncated to 52 fraction bits, error below one
+// unit in the last place), so that staging issues no float64 instruction.
+template <typename M_t>
+__device__ __forceinline__ xd mul_mant(xd c, M_t hm, int he) {
+  const unsigned long long hi = __umul64hi(mant53(c.m) << 11, mant53(hm) << 11);  // in [2^62, 2^64)
+  const int sh = (int)(hi >> 63);
+  const unsigned long long frac = (hi >> (10 + sh)) & 0xFFFFFFFFFFFFFull;
+  return xd{__longlong_as_double((long long)(frac | 0x3FF0000000000000ull)), c.e + he + sh};
+}
+
+// A positive normal float (or 0) as a double, with integer operations.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = (unsigned)__float_as_int(f);
+  if (b < 0x00800000u) return 0.0;
+  return __longlong_as_double(((long long)((b >> 23) + 896) << 52) | ((long long)(b & 0x7FFFFFu) << 29));
+}
+
+// a + b for extended numbers with positive normal (or zero) mantissas: the
+// smaller operand is aligned by integer arithmetic, then one float64 add.
+__device__ __forceinline__ xd xadd_int(xd a, xd b) {
+  const int E = max(a.e, b.e);
+  return xd{scale_nonpos(a.m, max(a.e - E, -1100)) + scale_nonpos(b.m, max(b.e - E, -1100)), E};
+}
+
+// Online-max merge of a float partial sum (s * 2^E) with a term x * 2^e.
+__device__ __forceinline__ void fmerge(float &s, int &E, float x, int e) {
+  const int En = max(E, e);
+  s = fmaf(x, pow2f_nonpos(e - En), s * pow2f_nonpos(E - En));
+  E = En;
+}
+
+}  // namespace chain_detail
+}  // namespace bpimd
+
+namespace bpimd {
+namespace chain_detail {
+
+// Row coefficient of a recursion in its own row coordinates: forward c_{r+1},
+// backward c_{N-1-r} (1 for the last row, whose sum is B_1 itself).
+template <bool BWD>
+__device__ __forceinline__ xd chain_coef(const Workspace &w, int row) {
+  if (!BWD) return xd{__ldg(w.ccm + row), __ldg(w.cce + row)};
+  if (row >= w.N - 1) return xd{1.0, 0};
+  return xd{__ldg(w.ccm + w.N - 2 - row), __ldg(w.cce + w.N - 2 - row)};
+}
+
+// The pair factors H(src, row) of a recursion, in its own coordinates.
+template <bool BWD>
+__device__ __forceinline__ const void *chain_gm(const Workspace &w) { return BWD ? w.gbm : w.gm; }
+template <bool BWD>
+__device__ __forceinline__ const int *chain_ge(const Workspace &w) { return BWD ? w.gbe : w.ge; }
+
+// Staging issues no float64 instruction (the SM's float64 pipe belongs to the
+// dependency chain).  Pairs outside src <= row < N hold the extended zero
+// 1 * 2^XZERO_E; loads are coalesced along rows and issued before use.
+// Off-diagonal block: H(tt*32+i, (tt+1)*32+lane), rows i in [i0, i0+NR), as
+// stored (float for MIXED), into dm/de[i*33 + lane].
+template <bool MIXED, bool BWD, int NR>
+__device__ __forceinline__ void stage_offdiag(const Workspace &w, int tt, int i0, void *dmv, int *de) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int srcbase = tt * TILE, row = tt * TILE + TILE + lane;
+  const M_t *gm = (const M_t *)chain_gm<BWD>(w);
+  const int *ge = chain_ge<BWD>(w);
+  M_t *dm = (M_t *)dmv;
+#pragma unroll
+  for (int i = i0; i < i0 + NR; ++i) {
+    M_t m = (M_t)1.0;
+    int e = XZERO_E;
+    if (row < w.N) {
+      const size_t gi = hidx(srcbase + i, row);
+      m = __ldg(gm + gi);
+      e = __ldg(ge + gi);
+    }
+    dm[i * 33 + lane] = m;
+    de[i * 33 + lane] = e;
+  }
+}
+
+// Diagonal block of tile tt, K = c_row * H with float64 mantissas, rows i in
+// [i0, i0+NR): the mantissa product is formed on the integer pipe (mul_mant).
+template <bool MIXED, bool BWD, int NR>
+__device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, double *dm, int *de) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int r0 = tt * TILE, row = r0 + lane;
+  const M_t *gm = (const M_t *)chain_gm<BWD>(w);
+  const int *ge = chain_ge<BWD>(w);
+  const xd c = (row < w.N) ? xnorm_int(chain_coef<BWD>(w, row)) : xd{1.0, 0};
+#pragma unroll
+  for (int i = i0; i < i0 + NR; ++i) {
+    const int src = r0 + i;
+    M_t m = (M_t)1.0;
+    int e = XZERO_E;
+    if (row < w.N && src <= row) {
+      const size_t gi = hidx(src, row);
+      m = __ldg(gm + gi);
+      e = __ldg(ge + gi);
+    }
+    const xd k = mul_mant<M_t>(c, m, e);
+    dm[i * 33 + lane] = k.m;
+    de[i * 33 + lane] = k.e;
+  }
+}
+
+// The 32 dependent steps of row tile t, run by one warp.  A is this lane's
+// row sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
+// coefficient.  K (diagonal, c-scaled) and H (to tile t+1) are the staged
+// blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and at gYm/gYe[v] in
+// global memory.  On return nxt holds the partial sums of tile t+1's rows over
+// source tile t.
+// 32 steps, no branches and no stores: rows past N and finished rows see
+// extended zeros in the staged blocks, and row j's accumulator is final after
+// step j (later steps add at most 2^-1000 of it).  Block entries of step i+1
+// are loaded (explicit ld.shared) before step i's shuffle.
+template <bool MIXED>
+__device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt, const double *Kdm, const int *Kde,
+                                           const double *Hom, const int *Hoe, double *Ym, int *Ye, int ymask,
+                                           double *gYm, int *gYe) {
+  const int lane = threadIdx.x & 31;
+  const int r0 = t * TILE, row = r0 + lane;
+  xd acc{0.0, XZERO_E};
+  if (row < N) {
+    acc = xadd_int(A, nxt);
+    acc = xmul_int(xnorm_int(acc), crow);  // acc' = c_row * (sum over sources < r0)
+  }
+  xd ycur{Ym[r0 & ymask], Ye[r0 & ymask]};
+  if (__double_as_longlong(acc.m) <= 0) acc = xd{1.0, XZERO_E};
+  nxt = xd{1.0, XZERO_E};
+  float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
+  int nexp = XZERO_E;
+  const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
+  const unsigned aHm = MIXED ? smem_addr((const float *)Hom + lane) : smem_addr(Hom + lane);
+  double km = lds_f64(aKm), hm = MIXED ? 0.0 : lds_f64(aHm);
+  float hf = MIXED ? lds_f32(aHm) : 0.0f;
+  int ke = lds_s32(aKe), he = lds_s32(aHe);
+#pragma unroll
+  for (int i = 0; i < TILE; ++i) {
+    double km1 = 0.0, hm1 = 0.0;
+    float hf1 = 0.0f;
+    int ke1 = 0, he1 = 0;
+    if (i + 1 < TILE) {
+      km1 = lds_f64(aKm + (i + 1) * 33 * 8);
+      if (MIXED) hf1 = lds_f32(aHm + (i + 1) * 33 * 4);
+      else hm1 = lds_f64(aHm + (i + 1) * 33 * 8);
+      ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
+      he1 = lds_s32(aHe + (i + 1) * 33 * 4);
+    }
+    acc = fma_chain(acc, km, ke, ycur);  // the dependency chain
+    // next tile's rows, off the chain (MIXED: float32, no float64 pipe)
+    // (ycur.m is a positive normal double, not necessarily in [1,2))
+    if (MIXED)
+      fmerge(nsum, nexp, mant_to_float(ycur.m) * hf,
+             he + ycur.e + (int)(__double_as_longlong(ycur.m) >> 52) - 1023);
+    else nxt = fma_chain(nxt, hm, he, ycur);
+    ycur.m = __shfl_sync(0xffffffffu, acc.m, i);
+    ycur.e = __shfl_sync(0xffffffffu, acc.e, i);
+    km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
+  }
+  if (MIXED) nxt = xd{f2d_int(nsum), nexp};
+  if (row < N) {  // Y_{row+1} = final accumulator of row `row`
+    const xd yn = xnorm_int(acc);
+    Ym[(row + 1) & ymask] = yn.m;
+    Ye[(row + 1) & ymask] = yn.e;
+    gYm[row + 1] = yn.m;
+    gYe[row + 1] = yn.e;
+  }
+  nxt = xnorm_int(nxt);
+}
+
+// Prefix sums C[i+1] = sum_{q<=i} (E_int_q + link_q) of tile t, one warp.
+__device__ __forceinline__ void prefix_tile(const Workspace &w, int t, double &carry) {
+  const int lane = threadIdx.x & 31;
+  const int i = t * TILE + lane;
+  double v = (i < w.N) ? (__ldg(w.Eint + i) + __ldg(w.link + i)) : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (i < w.N) w.C[i + 1] = carry + v;
+  carry += __shfl_sync(0xffffffffu, v, 31);
+}
+
+}  // namespace chain_detail
+}  // namespace bpimd

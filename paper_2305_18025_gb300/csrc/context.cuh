@@ -21,4 +21,16 @@ struct bpimd_ctx {
   int prof_max;
   std::vector<cudaEvent_t> prof_events;  // (BPIMD_NUM_STAGES + 1) per evaluation
   int prof_count;
+  // replica batch (bpimd_create_batched); R == 0 for a single-system context
+  int R;
+  int maxN;
+  long long total_elems;                  // 3 * sum_r N_r P_r
+  std::vector<bpimd::Workspace> h_ws;     // per-replica workspaces (host copy)
+  std::vector<long long> h_off;           // element offset of each replica
+  bpimd::Workspace *d_ws;                 // device copies of h_ws
+  int2 *d_bead_tab, *d_blk_tab;           // (replica, particle block), (replica, g block)
+  int n_bead_tab, n_blk_tab;
+  int *d_order;                           // replicas by decreasing N
+  long long *d_off;
+  int tune_gmat_bpsm, tune_prob_bpsm;     // grid caps (blocks per SM) of the batched passes
 };

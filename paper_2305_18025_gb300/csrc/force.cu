@@ -113,15 +113,15 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
   __syncthreads();
 }
 
+// One 32 x 32 block of the lower triangle (all 256 threads of the CTA).
+// MIXED keeps the block partials in float32 (each is a float32 sum already).
 template <bool MIXED>
-__global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const double *__restrict__ pos,
-                                                         double *__restrict__ F) {
-  // MIXED keeps the block partials in float32 (each is a float32 sum already)
+__device__ __forceinline__ void prob_block(const Workspace &w, int blk, const double *__restrict__ pos,
+                                           double *__restrict__ F,
+                                           typename std::conditional<MIXED, float, double>::type (*red)[32][4],
+                                           double (*fin)[9], int *last) {
   using P_t = typename std::conditional<MIXED, float, double>::type;
-  __shared__ P_t red[8][32][4];
-  __shared__ double fin[32][9];
-  __shared__ int last[2];
-  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+  {
     int t, s;
     block_coords_f(blk, t, s);
     const int j = threadIdx.x & 31, i0 = threadIdx.x >> 5;
@@ -224,6 +224,33 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
   }
 }
 
+template <bool MIXED>
+__global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const double *__restrict__ pos,
+                                                         double *__restrict__ F) {
+  using P_t = typename std::conditional<MIXED, float, double>::type;
+  __shared__ P_t red[8][32][4];
+  __shared__ double fin[32][9];
+  __shared__ int last[2];
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) prob_block<MIXED>(w, blk, pos, F, red, fin, last);
+}
+
+// Replica batch: entry k of tab is (replica, block); positions and forces of
+// replica r start at element off[r] of the packed arrays.
+template <bool MIXED>
+__global__ void __launch_bounds__(256) prob_force_batched(const Workspace *__restrict__ ws,
+                                                          const int2 *__restrict__ tab, int ntab,
+                                                          const long long *__restrict__ off,
+                                                          const double *__restrict__ pos, double *__restrict__ F) {
+  using P_t = typename std::conditional<MIXED, float, double>::type;
+  __shared__ P_t red[8][32][4];
+  __shared__ double fin[32][9];
+  __shared__ int last[2];
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int2 e = tab[k];
+    prob_block<MIXED>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
+  }
+}
+
 // Expected exterior-spring energy over representative permutations, per block
 // of the lower triangle: (1/2) m w_P^2 sum_{a<=b in block} Pr[b -> a] |r_b^P - r_a^1|^2
 // (the direct links l -> l+1 are added by the caller).  Float64 throughout;
@@ -296,6 +323,17 @@ cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStre
 
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s) {
   dense_prob_kernel<<<1024, 256, 0, s>>>(w, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
+                                      bool mixed, const double *pos, double *F, int blocks_per_sm, cudaStream_t s) {
+  if (ntab <= 0) return cudaSuccess;
+  const int sms = sm_count();
+  const int cap = sms * (blocks_per_sm > 0 ? blocks_per_sm : 8);
+  const int grid = ntab < cap ? ntab : cap;
+  if (mixed) prob_force_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab, off, pos, F);
+  else prob_force_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab, off, pos, F);
   return cudaGetLastError();
 }
 

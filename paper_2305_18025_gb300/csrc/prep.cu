@@ -67,74 +67,102 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int
 // w = N-1-b) after a transpose through shared memory, so that those stores
 // are coalesced along r.  Entries outside a <= b < N are never written here
 // (gmat_padding_kernel fills them once).
+// One block of g (all threads of the CTA; Tm/Te: 32 x 33 shared tiles).
+template <bool MIXED>
+__device__ __forceinline__ void gmat_block(const Workspace &w, int blk,
+                                           typename std::conditional<MIXED, float, double>::type *Tm, int *Te) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  const double cx = -w.beta * w.half_k * LOG2E;
+  const int N = w.N;
+  M_t *gm = (M_t *)w.gm, *gbm = (M_t *)w.gbm;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int t, s;
+  block_coords(blk, t, s);
+  {
+    const int b = t * TILE + lane;
+    for (int i = warp; i < TILE; i += 8) {
+      const int a = s * TILE + i;
+      if (b < N && a <= b) {
+        int e;
+        const M_t m = (M_t)pair_factor<MIXED>(w, cx, a, b, e);
+        const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
+        gm[idx] = m;
+        w.ge[idx] = e;
+        Tm[i * 33 + lane] = m;
+        Te[i * 33 + lane] = e;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int a = s * TILE + lane, r = N - 1 - a;
+    for (int jj = warp; jj < TILE; jj += 8) {
+      const int b = t * TILE + jj;
+      if (b < N && a <= b) {
+        const int src = N - 1 - b;
+        const int T = r >> 5, S = src >> 5;
+        const size_t idx = ((size_t)(T * (T + 1) / 2 + S) << 10) + ((src & 31) << 5) + (r & 31);
+        gbm[idx] = Tm[lane * 33 + jj];
+        w.gbe[idx] = Te[lane * 33 + jj];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
-  const double cx = -w.beta * w.half_k * LOG2E;
-  const int N = w.N;
-  M_t *gm = (M_t *)w.gm, *gbm = (M_t *)w.gbm;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
-    int t, s;
-    block_coords(blk, t, s);
-    {
-      const int b = t * TILE + lane;
-      for (int i = warp; i < TILE; i += 8) {
-        const int a = s * TILE + i;
-        if (b < N && a <= b) {
-          int e;
-          const M_t m = (M_t)pair_factor<MIXED>(w, cx, a, b, e);
-          const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
-          gm[idx] = m;
-          w.ge[idx] = e;
-          Tm[i * 33 + lane] = m;
-          Te[i * 33 + lane] = e;
-        }
-      }
-    }
-    __syncthreads();
-    {
-      const int a = s * TILE + lane, r = N - 1 - a;
-      for (int jj = warp; jj < TILE; jj += 8) {
-        const int b = t * TILE + jj;
-        if (b < N && a <= b) {
-          const int src = N - 1 - b;
-          const int T = r >> 5, S = src >> 5;
-          const size_t idx = ((size_t)(T * (T + 1) / 2 + S) << 10) + ((src & 31) << 5) + (r & 31);
-          gbm[idx] = Tm[lane * 33 + jj];
-          w.gbe[idx] = Te[lane * 33 + jj];
-        }
-      }
-    }
-    __syncthreads();
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) gmat_block<MIXED>(w, blk, Tm, Te);
+}
+
+// Replica batch: entry k of tab is (replica, block).
+template <bool MIXED>
+__global__ void __launch_bounds__(256) gmat_batched(const Workspace *__restrict__ ws, const int2 *__restrict__ tab,
+                                                    int ntab) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  __shared__ M_t Tm[TILE * 33];
+  __shared__ int Te[TILE * 33];
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int2 e = tab[k];
+    gmat_block<MIXED>(ws[e.x], e.y, Tm, Te);
   }
 }
 
-// Entries outside lo <= col < N of either copy (the upper part of diagonal
-// blocks and the rows past N of the last tile): mantissa 1 with exponent
-// XZERO_E, an extended zero.  They depend only on N.
+// Entries outside lo <= col < N of either copy of one block (the upper part
+// of diagonal blocks and the rows past N of the last tile): mantissa 1 with
+// exponent XZERO_E, an extended zero.  They depend only on N.
+template <bool MIXED>
+__device__ __forceinline__ void gmat_padding_block(const Workspace &w, int blk) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  int t, s;
+  block_coords(blk, t, s);
+  const int j = threadIdx.x & 31, col = t * TILE + j;
+  for (int i = threadIdx.x >> 5; i < TILE; i += 8) {
+    const int lo = s * TILE + i;
+    if (col >= w.N || lo > col) {
+      const size_t idx = (size_t)blk * TILE2 + i * TILE + j;
+      ((M_t *)w.gm)[idx] = (M_t)1.0;
+      w.ge[idx] = XZERO_E;
+      ((M_t *)w.gbm)[idx] = (M_t)1.0;
+      w.gbe[idx] = XZERO_E;
+    }
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) gmat_padding_kernel(Workspace w) {
-  using M_t = typename std::conditional<MIXED, float, double>::type;
-  const int N = w.N;
-  for (int gblk = blockIdx.x; gblk < 2 * w.NB; gblk += gridDim.x) {
-    const bool bwd = gblk >= w.NB;
-    const int blk = bwd ? gblk - w.NB : gblk;
-    int t, s;
-    block_coords(blk, t, s);
-    M_t *gm = (M_t *)(bwd ? w.gbm : w.gm);
-    int *ge = bwd ? w.gbe : w.ge;
-    const int j = threadIdx.x & 31, col = t * TILE + j;
-    for (int i = threadIdx.x >> 5; i < TILE; i += 8) {
-      const int lo = s * TILE + i;
-      if (col >= N || lo > col) {
-        const size_t idx = (size_t)blk * TILE2 + i * TILE + j;
-        gm[idx] = (M_t)1.0;
-        ge[idx] = XZERO_E;
-      }
-    }
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) gmat_padding_block<MIXED>(w, blk);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) gmat_padding_batched(const Workspace *__restrict__ ws,
+                                                            const int2 *__restrict__ tab, int ntab) {
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int2 e = tab[k];
+    gmat_padding_block<MIXED>(ws[e.x], e.y);
   }
 }
 
@@ -170,9 +198,25 @@ cudaError_t launch_gmat(const Workspace &w, cudaStream_t s) {
 
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s) {
   const int sms = sm_count();
-  const int grid = 2 * w.NB < sms * 8 ? 2 * w.NB : sms * 8;
+  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   if (w.mixed) gmat_padding_kernel<true><<<grid, 256, 0, s>>>(w);
   else gmat_padding_kernel<false><<<grid, 256, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmat_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed, bool padding,
+                                int blocks_per_sm, cudaStream_t s) {
+  if (ntab <= 0) return cudaSuccess;
+  const int sms = sm_count();
+  const int cap = sms * (blocks_per_sm > 0 ? blocks_per_sm : 8);
+  const int grid = ntab < cap ? ntab : cap;
+  if (padding) {
+    if (mixed) gmat_padding_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab);
+    else gmat_padding_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab);
+  } else {
+    if (mixed) gmat_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab);
+    else gmat_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab);
+  }
   return cudaGetLastError();
 }
 

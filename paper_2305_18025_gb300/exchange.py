@@ -151,3 +151,72 @@ class RingPolymerMD:
                 raise ValueError(f"positions/velocities must be contiguous float64 [{self.N}][{self.P}][3]")
         _c.bpimd_step(self.ctx, pos, vel, nsteps, self.energies if energies else None)
         return self.energies if energies else None
+
+
+class BatchedExchangeEnergy:
+    """V^{[1,N_r]} and forces of R independent replicas in one evaluation.
+
+    Replica r has N[r] particles, P[r] beads, omega_P[r], beta[r] (shared mass
+    and precision).  Positions and forces are packed: replica r is the
+    [N_r][P_r][3] block at element offset ``offsets[r]`` of one flat float64
+    tensor (``pack``/``unpack`` convert from/to lists of tensors).  Four kernel
+    launches per evaluation regardless of R.
+    """
+
+    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
+        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        self.N = [int(n) for n in N]
+        self.P = [int(p) for p in P]
+        self.R = len(self.N)
+        self.precision = precision
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            cfg = _c.make_config(0, 0, float(m), 1.0, 1.0, prec)
+            self.ctx = _c.bpimd_create_batched(cfg, self.N, self.P, omega_P, beta, self.stream)
+        _, self.elements, self.offsets = _c.bpimd_batch_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _c.bpimd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, tensors):
+        """List of [N_r][P_r][3] tensors -> one packed float64 tensor on the device."""
+        return torch.cat([t.reshape(-1) for t in tensors]).to(device=self.device, dtype=torch.float64).contiguous()
+
+    def unpack(self, packed):
+        """Packed tensor -> list of [N_r][P_r][3] views."""
+        out = []
+        for r in range(self.R):
+            o = int(self.offsets[r])
+            out.append(packed[o:o + 3 * self.N[r] * self.P[r]].view(self.N[r], self.P[r], 3))
+        return out
+
+    def forces(self, packed, out=None, V_out=None):
+        """Enqueue one evaluation; returns (V_B [R] tensor, packed forces)."""
+        if packed.dtype != torch.float64 or packed.device != self.device or packed.numel() != self.elements \
+                or not packed.is_contiguous():
+            raise ValueError(f"positions must be a contiguous packed float64 tensor of {self.elements} elements")
+        F = out if out is not None else torch.empty_like(packed)
+        V = V_out if V_out is not None else torch.empty(self.R, dtype=torch.float64, device=self.device)
+        _c.bpimd_exchange_energy_forces_batched(self.ctx, packed, V, F)
+        return V, F
+
+    __call__ = forces
+
+    def set_tuning(self, pair_blocks_per_sm, prob_blocks_per_sm):
+        _c.bpimd_batch_set_tuning(self.ctx, pair_blocks_per_sm, prob_blocks_per_sm)
+
+    def sync(self):
+        _c.bpimd_sync(self.ctx)

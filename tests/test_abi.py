@@ -81,3 +81,39 @@ def test_status_strings(lib):
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert bpimd.bpimd_status_string(code) != "unknown status"
     assert "sm_103a" in bpimd.bpimd_version()
+
+
+@pytest.mark.parametrize("case", ["R0", "N0", "Nbig", "P1", "beta0", "omega_nan", "prec"])
+def test_create_batched_rejects_invalid_arguments_without_gpu(lib, case):
+    import numpy as np
+    N = np.array([16, 40, 7], dtype=np.int32)
+    P = np.array([8, 4, 2], dtype=np.int32)
+    w = np.array([2.0, 1.5, 3.0])
+    b = np.array([1.0, 0.5, 2.0])
+    R = 3
+    cfg = bpimd.make_config(0, 0, 1.0, 1.0, 1.0)
+    if case == "R0":
+        R = 0
+    elif case == "N0":
+        N[1] = 0
+    elif case == "Nbig":
+        N[2] = bpimd.BATCH_MAX_N + 1
+    elif case == "P1":
+        P[0] = 1
+    elif case == "beta0":
+        b[2] = 0.0
+    elif case == "omega_nan":
+        w[1] = float("nan")
+    elif case == "prec":
+        cfg.precision = 5
+    h = ctypes.c_void_p(123)
+    rc = lib.bpimd_create_batched(ctypes.byref(h), ctypes.byref(cfg), R, N.ctypes.data, P.ctypes.data,
+                                  w.ctypes.data, b.ctypes.data, None)
+    assert rc == bpimd.BPIMD_ERR_ARG
+    assert h.value is None
+
+
+def test_batch_calls_reject_null_context(lib):
+    assert lib.bpimd_exchange_energy_forces_batched(None, None, None, None) == bpimd.BPIMD_ERR_ARG
+    assert lib.bpimd_batch_info(None, None, None, None) == bpimd.BPIMD_ERR_ARG
+    assert lib.bpimd_batch_set_tuning(None, 8, 8) == bpimd.BPIMD_ERR_ARG

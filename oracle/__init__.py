@@ -65,8 +65,8 @@ class _Oracle:
                 "ora_fast_pimdb": [i, i, r, r, r, rp, rp, rp, rp, rp, rp],
                 "ora_original_pimdb": [i, i, r, r, r, rp, rp, rp],
                 "ora_expected_spring_energy": [i, i, r, r, rp, rp, rp],
-                "ora_external_forces": [i, i, r, r, i, r, r, rp, rp, rp],
-                "ora_md_run": [i, i, r, r, r, r, r, r, r, i, r, r, ctypes.c_uint64, ctypes.c_uint64,
+                "ora_external_forces": [i, i, r, r, i, r, r, r, r, rp, rp, rp],
+                "ora_md_run": [i, i, r, r, r, r, r, r, r, i, r, r, r, r, ctypes.c_uint64, ctypes.c_uint64,
                                i, rp, rp, rp],
             }
             for name, args in sig.items():
@@ -79,6 +79,8 @@ class _Oracle:
             lib.ora_thermostat_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                                    ctypes.POINTER(ctypes.c_double)]
             lib.ora_thermostat_normals.restype = None
+            lib.ora_set_box.argtypes = [self._ctype]
+            lib.ora_set_box.restype = None
             self._lib = lib
         return self._lib
 
@@ -158,8 +160,19 @@ class _Oracle:
                     "forces")
         return F
 
-    def fast_pimdb(self, pos, m, omega_P, beta, full=False):
-        """Algorithm 1.  Returns (V_B, F) or, with full=True, (V_B, F, V, W, M)."""
+    def set_box(self, L):
+        """Periodic cubic box of side L for the following calls (0: open boundaries)."""
+        self.lib().ora_set_box(float(L))
+
+    def fast_pimdb(self, pos, m, omega_P, beta, full=False, box=0.0):
+        """Algorithm 1.  Returns (V_B, F) or, with full=True, (V_B, F, V, W, M).
+        box > 0: periodic cubic box, every spring by minimum image."""
+        if box:
+            self.set_box(box)
+            try:
+                return self.fast_pimdb(pos, m, omega_P, beta, full)
+            finally:
+                self.set_box(0.0)
         pos = self._pos(pos)
         N, P, _ = pos.shape
         F = np.empty_like(pos)
@@ -174,8 +187,14 @@ class _Oracle:
             return VB[0], F, V, W, M
         return VB[0], F
 
-    def original_pimdb(self, pos, m, omega_P, beta):
+    def original_pimdb(self, pos, m, omega_P, beta, box=0.0):
         """Algorithm 2 (O(P N^3)).  Returns (V_B, F)."""
+        if box:
+            self.set_box(box)
+            try:
+                return self.original_pimdb(pos, m, omega_P, beta)
+            finally:
+                self.set_box(0.0)
         pos = self._pos(pos)
         N, P, _ = pos.shape
         F = np.empty_like(pos)
@@ -208,26 +227,27 @@ class _Oracle:
         self.lib().ora_thermostat_normals(seed, step, n, z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         return z
 
-    def external_forces(self, pos, m, omega0, pair_type=0, pair_a=0.0, pair_b=1.0):
-        """(U-bar, -grad U-bar) of the trap and same-bead pair potential."""
+    def external_forces(self, pos, m, omega0, pair_type=0, pair_a=0.0, pair_b=1.0, pair_rc=0.0, box=0.0):
+        """(U-bar, -grad U-bar) of the trap and same-bead pair potential
+        (pair_type 1 Gaussian g, s; 2 Lennard-Jones eps, sigma cut and shifted at pair_rc)."""
         pos = self._pos(pos)
         N, P, _ = pos.shape
         F = np.zeros_like(pos)
         U = np.zeros(1, dtype=self.dtype)
-        self._check(self.lib().ora_external_forces(N, P, m, omega0, pair_type, pair_a, pair_b,
+        self._check(self.lib().ora_external_forces(N, P, m, omega0, pair_type, pair_a, pair_b, pair_rc, box,
                                                    self._p(pos), self._p(F), self._p(U)),
                     "external_forces")
         return U[0], F
 
     def md_run(self, pos, vel, m, omega_P, beta, dt, gamma, nsteps, omega0=0.0, pair_type=0,
-               pair_a=0.0, pair_b=1.0, kT=0.0, seed=0, step0=0):
+               pair_a=0.0, pair_b=1.0, kT=0.0, seed=0, step0=0, pair_rc=0.0, box=0.0):
         """nsteps BAOAB steps; returns (pos, vel, energies[4]) as new arrays."""
         pos = self._pos(pos).copy()
         vel = self._arr(vel).copy()
         N, P, _ = pos.shape
         en = np.zeros(4, dtype=self.dtype)
         self._check(self.lib().ora_md_run(N, P, m, omega_P, beta, dt, gamma, kT, omega0, pair_type,
-                                          pair_a, pair_b, seed, step0, nsteps, self._p(pos),
+                                          pair_a, pair_b, pair_rc, box, seed, step0, nsteps, self._p(pos),
                                           self._p(vel), self._p(en)), "md_run")
         return pos, vel, en
 

@@ -34,8 +34,31 @@
 #define BEAD(pos, P, l, j) (&(pos)[((size_t)((l) - 1) * (size_t)(P) + (size_t)((j) - 1)) * 3])
 #define EIDX(N, u, v) ((size_t)((u) - 1) * (size_t)(N) + (size_t)((v) - 1))
 
+/* Periodic cubic box of side g_box (0: open boundaries), set by ora_set_box.
+ * In a periodic box every spring joins the minimum image of its two beads
+ * (the paper is silent on boundaries; this is the usual path-integral
+ * convention for bulk liquids).  With g_box = 0 every expression below is the
+ * plain open-boundary one, operation for operation. */
+static ora_real g_box = 0.0;
+
+void ora_set_box(ora_real L) { g_box = L > 0.0 ? L : 0.0; }
+
+#ifdef ORA_LONG_DOUBLE
+#define RINT rintl
+#else
+#define RINT rint
+#endif
+
+/* minimum image of one coordinate difference */
+static ora_real mi1(ora_real d) { return g_box > 0.0 ? d - g_box * RINT(d / g_box) : d; }
+
+/* 2 r - a - b, i.e. (r - a) + (r - b) with each spring taken as a minimum image */
+static ora_real lap1(ora_real r, ora_real a, ora_real b) {
+  return g_box > 0.0 ? mi1(r - a) + mi1(r - b) : 2.0 * r - a - b;
+}
+
 static ora_real sqdist(const ora_real *a, const ora_real *b) {
-  ora_real dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+  ora_real dx = mi1(a[0] - b[0]), dy = mi1(a[1] - b[1]), dz = mi1(a[2] - b[2]);
   return dx * dx + dy * dy + dz * dz;
 }
 
@@ -227,23 +250,21 @@ int ora_forces(int N, int P, ora_real m, ora_real omega_P, const ora_real *pos,
   for (int l = 1; l <= N; ++l)
     for (int j = 2; j <= P - 1; ++j)
       for (int d = 0; d < 3; ++d)
-        BEAD(F, P, l, j)[d] = -k * (2.0 * BEAD(pos, P, l, j)[d] - BEAD(pos, P, l, j + 1)[d]
-                                    - BEAD(pos, P, l, j - 1)[d]);
+        BEAD(F, P, l, j)[d] = -k * lap1(BEAD(pos, P, l, j)[d], BEAD(pos, P, l, j + 1)[d],
+                                        BEAD(pos, P, l, j - 1)[d]);
   for (int l = 1; l <= N; ++l) {
     ora_real f1[3] = {0.0, 0.0, 0.0}, fP[3] = {0.0, 0.0, 0.0};
     int lo = l - 1 < 1 ? 1 : l - 1;
     for (int lp = lo; lp <= N; ++lp) {
       ora_real pr = M[EIDX(N, lp, l)];
       for (int d = 0; d < 3; ++d)
-        f1[d] -= pr * k * (2.0 * BEAD(pos, P, l, 1)[d] - BEAD(pos, P, l, 2)[d]
-                           - BEAD(pos, P, lp, P)[d]);
+        f1[d] -= pr * k * lap1(BEAD(pos, P, l, 1)[d], BEAD(pos, P, l, 2)[d], BEAD(pos, P, lp, P)[d]);
     }
     int hi = l + 1 > N ? N : l + 1;
     for (int lp = 1; lp <= hi; ++lp) {
       ora_real pr = M[EIDX(N, l, lp)];
       for (int d = 0; d < 3; ++d)
-        fP[d] -= pr * k * (2.0 * BEAD(pos, P, l, P)[d] - BEAD(pos, P, lp, 1)[d]
-                           - BEAD(pos, P, l, P - 1)[d]);
+        fP[d] -= pr * k * lap1(BEAD(pos, P, l, P)[d], BEAD(pos, P, lp, 1)[d], BEAD(pos, P, l, P - 1)[d]);
     }
     for (int d = 0; d < 3; ++d) {
       BEAD(F, P, l, 1)[d] = f1[d];
@@ -294,7 +315,7 @@ static void cycle_energy_gradient(int P, ora_real k, const ora_real *pos, int u,
   if (j > 1) prev = BEAD(pos, P, l, j - 1);
   else prev = (l > u) ? BEAD(pos, P, l - 1, P) : BEAD(pos, P, v, P);
   const ora_real *r = BEAD(pos, P, l, j);
-  for (int d = 0; d < 3; ++d) g[d] = k * (2.0 * r[d] - next[d] - prev[d]);
+  for (int d = 0; d < 3; ++d) g[d] = k * lap1(r[d], next[d], prev[d]);
 }
 
 /* Algorithm 2 (Original PIMD-B).

@@ -39,6 +39,12 @@ typedef long double ora_real;
 typedef double ora_real;
 #endif
 
+/* Periodic cubic box of side L for every following call (L <= 0: open
+ * boundaries, the default).  In a box every spring -- interior, link and
+ * closing -- joins the minimum image of its two beads; positions need not be
+ * wrapped.  Process-wide setting (the oracle is single threaded). */
+void ora_set_box(ora_real L);
+
 /* Shift choice for the log-sum-exp steps (Methods, "Numerical Stability"). */
 #define ORA_SHIFT_MIN_ALL 0   /* Eq. full-elong: min over all terms of the step   */
 #define ORA_SHIFT_TWO_TERM 1  /* Eq. original-elong: min of two designated terms  */
@@ -108,16 +114,21 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 void ora_thermostat_normals(uint64_t seed, uint64_t step, int64_t n, double *z);
 
 /* Physical forces -grad U-bar added to F (harmonic trap of frequency omega0 if
- * omega0 > 0; pair_type 1: Gaussian g = pa, s = pb between equal-index beads);
+ * omega0 > 0; pair_type 1: Gaussian g = pa, s = pb; 2: Lennard-Jones eps = pa,
+ * sigma = pb, truncated and shifted at pc (pc <= 0: no cutoff); pairs between
+ * equal-index beads, minimum image in a periodic box of side L > 0);
  * *ubar = U-bar (may be NULL). */
 int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type, ora_real pa,
-                        ora_real pb, const ora_real *pos, ora_real *F, ora_real *ubar);
+                        ora_real pb, ora_real pc, ora_real L, const ora_real *pos, ora_real *F,
+                        ora_real *ubar);
 
-/* nsteps BAOAB Langevin steps in place (kT <= 0: 1/beta); energies (may be
- * NULL): [0] V^{[1,N]}, [1] U-bar, [2] kinetic, [3] primitive estimator. */
+/* nsteps BAOAB Langevin steps in place (kT <= 0: 1/beta; L > 0: periodic box
+ * for the springs and the pairs); energies (may be NULL): [0] V^{[1,N]},
+ * [1] U-bar, [2] kinetic, [3] primitive estimator. */
 int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_real dt, ora_real gamma,
-               ora_real kT, ora_real omega0, int pair_type, ora_real pa, ora_real pb, uint64_t seed,
-               uint64_t step0, int nsteps, ora_real *pos, ora_real *vel, ora_real *energies);
+               ora_real kT, ora_real omega0, int pair_type, ora_real pa, ora_real pb, ora_real pc,
+               ora_real L, uint64_t seed, uint64_t step0, int nsteps, ora_real *pos, ora_real *vel,
+               ora_real *energies);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,10 @@
  * temperature kT = 1/beta, with bead mass m, and
  *   U = sum_l (1/2) m w0^2 |r_l|^2                 (isotropic harmonic trap)
  *     + sum_{l<l'} g exp(-|r_l - r_l'|^2 / (2 s^2))  (Gaussian repulsion)
- * acting between beads of equal index j, scaled by 1/P.
+ *     or sum_{l<l'} 4 eps ((sig/r)^12 - (sig/r)^6), truncated and shifted at rc
+ *                                                     (Lennard-Jones, liquid helium)
+ * acting between beads of equal index j, scaled by 1/P; in a periodic box of
+ * side L every pair and every spring uses the minimum image.
  *
  * The thermostat noise comes from the counter-based generator Philox4x32-10
  * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
@@ -83,12 +86,26 @@ void ora_thermostat_normals(uint64_t seed, uint64_t step, int64_t n, double *z) 
   }
 }
 
+#ifdef ORA_LONG_DOUBLE
+#define RINTR rintl
+#else
+#define RINTR rint
+#endif
+
 /* Physical forces -grad U-bar added to F, and U-bar in *ubar.
- * pair_type: 0 none, 1 Gaussian (a = g, b = s). */
+ * pair_type: 0 none, 1 Gaussian (a = g, b = s), 2 Lennard-Jones
+ * 4 a ((b/r)^12 - (b/r)^6) truncated at rc and shifted to 0 there (rc <= 0:
+ * no cutoff).  L > 0: periodic cubic box, pair distances by minimum image. */
 int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type, ora_real pa,
-                        ora_real pb, const ora_real *pos, ora_real *F, ora_real *ubar) {
+                        ora_real pb, ora_real rc, ora_real L, const ora_real *pos, ora_real *F,
+                        ora_real *ubar) {
   if (N < 1 || P < 2 || !pos || !F) return -1;
-  if (pair_type != 0 && pair_type != 1) return -1;
+  if (pair_type != 0 && pair_type != 1 && pair_type != 2) return -1;
+  ora_real ushift = 0.0;
+  if (pair_type == 2 && rc > 0.0) {
+    const ora_real sr6 = (pb / rc) * (pb / rc) * (pb / rc) * (pb / rc) * (pb / rc) * (pb / rc);
+    ushift = 4.0 * pa * (sr6 * sr6 - sr6);
+  }
   ora_real U = 0.0;
   const ora_real invP = (ora_real)1.0 / (ora_real)P;
   for (int l = 1; l <= N; ++l)
@@ -104,13 +121,39 @@ int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type
         for (int lp = 1; lp <= N; ++lp) {
           if (lp == l) continue;
           const ora_real *q = &pos[((size_t)(lp - 1) * P + (j - 1)) * 3];
-          const ora_real dx = r[0] - q[0], dy = r[1] - q[1], dz = r[2] - q[2];
+          ora_real dx = r[0] - q[0], dy = r[1] - q[1], dz = r[2] - q[2];
+          if (L > 0.0) {
+            dx -= L * RINTR(dx / L);
+            dy -= L * RINTR(dy / L);
+            dz -= L * RINTR(dz / L);
+          }
           const ora_real e = pa * EXPR(-(dx * dx + dy * dy + dz * dz) / (2.0 * pb * pb));
           if (lp > l) U += invP * e;
           /* -d/dr_l of g exp(-d^2/(2 s^2)) = g exp(..) d / s^2 */
           f[0] += invP * e * dx / (pb * pb);
           f[1] += invP * e * dy / (pb * pb);
           f[2] += invP * e * dz / (pb * pb);
+        }
+      }
+      if (pair_type == 2) {
+        for (int lp = 1; lp <= N; ++lp) {
+          if (lp == l) continue;
+          const ora_real *q = &pos[((size_t)(lp - 1) * P + (j - 1)) * 3];
+          ora_real dx = r[0] - q[0], dy = r[1] - q[1], dz = r[2] - q[2];
+          if (L > 0.0) {
+            dx -= L * RINTR(dx / L);
+            dy -= L * RINTR(dy / L);
+            dz -= L * RINTR(dz / L);
+          }
+          const ora_real r2 = dx * dx + dy * dy + dz * dz;
+          if (rc > 0.0 && r2 >= rc * rc) continue;
+          const ora_real s2 = pb * pb / r2, s6 = s2 * s2 * s2;
+          if (lp > l) U += invP * (4.0 * pa * (s6 * s6 - s6) - ushift);
+          /* -dU/dr_l = 24 eps (2 (s/r)^12 - (s/r)^6) d / r^2 */
+          const ora_real c = invP * 24.0 * pa * (2.0 * s6 * s6 - s6) / r2;
+          f[0] += c * dx;
+          f[1] += c * dy;
+          f[2] += c * dz;
         }
       }
     }
@@ -120,10 +163,11 @@ int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type
 
 /* Total force: -grad (V^{[1,N]} + U-bar) by Algorithm 1 plus the physical part. */
 static int total_force(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_real omega0,
-                       int pair_type, ora_real pa, ora_real pb, const ora_real *x, ora_real *F,
-                       ora_real *VB, ora_real *ubar, ora_real *M) {
+                       int pair_type, ora_real pa, ora_real pb, ora_real pc, ora_real L, const ora_real *x,
+                       ora_real *F, ora_real *VB, ora_real *ubar, ora_real *M) {
+  ora_set_box(L);
   int rc = ora_fast_pimdb(N, P, m, omega_P, beta, x, VB, F, NULL, NULL, M);
-  if (!rc) rc = ora_external_forces(N, P, m, omega0, pair_type, pa, pb, x, F, ubar);
+  if (!rc) rc = ora_external_forces(N, P, m, omega0, pair_type, pa, pb, pc, L, x, F, ubar);
   return rc;
 }
 
@@ -132,8 +176,9 @@ static int total_force(int N, int P, ora_real m, ora_real omega_P, ora_real beta
  * receives, after the last step: [0] V^{[1,N]}, [1] U-bar, [2] sum (1/2) m v^2,
  * [3] the primitive energy estimator 3NP/(2 beta) - <E^{G[sigma]}> + U-bar. */
 int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_real dt, ora_real gamma,
-               ora_real kT, ora_real omega0, int pair_type, ora_real pa, ora_real pb, uint64_t seed,
-               uint64_t step0, int nsteps, ora_real *pos, ora_real *vel, ora_real *energies) {
+               ora_real kT, ora_real omega0, int pair_type, ora_real pa, ora_real pb, ora_real pc,
+               ora_real L, uint64_t seed, uint64_t step0, int nsteps, ora_real *pos, ora_real *vel,
+               ora_real *energies) {
   if (N < 1 || P < 2 || nsteps < 0 || !pos || !vel || !(dt > 0.0) || gamma < 0.0) return -1;
   if (!(kT > 0.0)) kT = 1.0 / beta;
   const size_t n = (size_t)N * P * 3;
@@ -145,7 +190,7 @@ int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_re
   /* O step: v <- c1 v + c2 z, the exact Ornstein-Uhlenbeck update over dt */
   const ora_real c1 = EXPR(-gamma * dt);
   const ora_real c2 = SQRT((1.0 - c1 * c1) * kT / m);
-  if (!rc) rc = total_force(N, P, m, omega_P, beta, omega0, pair_type, pa, pb, pos, F, &VB, &ubar, M);
+  if (!rc) rc = total_force(N, P, m, omega_P, beta, omega0, pair_type, pa, pb, pc, L, pos, F, &VB, &ubar, M);
   for (int s = 0; s < nsteps && !rc; ++s) {
     ora_thermostat_normals(seed, step0 + (uint64_t)s, (int64_t)n, z);
     for (size_t i = 0; i < n; ++i) {
@@ -154,7 +199,7 @@ int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_re
       vel[i] = c1 * vel[i] + c2 * z[i];  /* O */
       pos[i] += 0.5 * dt * vel[i];       /* A */
     }
-    rc = total_force(N, P, m, omega_P, beta, omega0, pair_type, pa, pb, pos, F, &VB, &ubar, M);
+    rc = total_force(N, P, m, omega_P, beta, omega0, pair_type, pa, pb, pc, L, pos, F, &VB, &ubar, M);
     for (size_t i = 0; i < n && !rc; ++i) vel[i] += 0.5 * dt * F[i] / m; /* B */
   }
   if (!rc && energies) {
@@ -166,6 +211,7 @@ int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_re
     energies[2] = ke;
     energies[3] = 3.0 * N * P / (2.0 * beta) - spring + ubar;
   }
+  ora_set_box(0.0);
   free(F);
   free(M);
   free(z);

@@ -38,13 +38,13 @@ MUTANTS = {
     "direct_link_sign": (
         "-EXPM1(-beta * (V[l] + W[l] - VN))", "EXPM1(-beta * (V[l] + W[l] - VN))"),
     "bead1_force_wrong_neighbour_bead": (
-        "- BEAD(pos, P, lp, P)[d]);", "- BEAD(pos, P, lp, 1)[d]);"),
+        "BEAD(pos, P, l, 2)[d], BEAD(pos, P, lp, P)[d]);", "BEAD(pos, P, l, 2)[d], BEAD(pos, P, lp, 1)[d]);"),
     "beadP_force_drops_superdiagonal": (
         "int hi = l + 1 > N ? N : l + 1;", "int hi = l;"),
     "transposed_probability_in_bead1": (
         "ora_real pr = M[EIDX(N, lp, l)];", "ora_real pr = M[EIDX(N, l, lp)];"),
     "interior_force_sign": (
-        "BEAD(F, P, l, j)[d] = -k * (", "BEAD(F, P, l, j)[d] = k * ("),
+        "BEAD(F, P, l, j)[d] = -k * lap1(", "BEAD(F, P, l, j)[d] = k * lap1("),
     "base_case_drops_closing_spring": (
         "E[EIDX(N, v, v)] = Eint[v - 1] + half_k * sqdist(BEAD(pos, P, v, P), BEAD(pos, P, v, 1));",
         "E[EIDX(N, v, v)] = Eint[v - 1];"),

@@ -24,6 +24,7 @@ int validate(const bpimd_config *c) {
   if (!finite_pos(c->m) || !finite_pos(c->omega_P) || !finite_pos(c->beta)) return BPIMD_ERR_ARG;
   if (c->precision != BPIMD_FP64 && c->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
   if (c->flags != 0) return BPIMD_ERR_ARG;
+  if (!(c->box_L >= 0.0) || !std::isfinite(c->box_L)) return BPIMD_ERR_ARG;
   return BPIMD_OK;
 }
 
@@ -140,6 +141,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
+  set_box(w, cfg->box_L);
   const size_t N = w.N;
   // one allocation: the workspace, then the diagnostic potentials
   const size_t wbytes = layout_workspace(w, nullptr);

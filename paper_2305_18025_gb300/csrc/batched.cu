@@ -57,7 +57,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
   if (!out) return BPIMD_ERR_ARG;
   *out = nullptr;
   if (!cfg || !N || !P || !omega_P || !beta || R < 1 || R > (1 << 20)) return BPIMD_ERR_ARG;
-  if (!finite_positive(cfg->m) || cfg->flags != 0) return BPIMD_ERR_ARG;
+  if (!finite_positive(cfg->m) || cfg->flags != 0 || cfg->box_L != 0.0) return BPIMD_ERR_ARG;
   if (cfg->precision != BPIMD_FP64 && cfg->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
   long long total = 0;
   for (int r = 0; r < R; ++r) {

@@ -39,7 +39,8 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
         const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
         finite &= isfinite(x) && isfinite(y) && isfinite(z);
         if (j + 1 < P) {
-          const double dx = p[3 * j + 3] - x, dy = p[3 * j + 4] - y, dz = p[3 * j + 5] - z;
+          const double dx = mimage(w, p[3 * j + 3] - x), dy = mimage(w, p[3 * j + 4] - y),
+                       dz = mimage(w, p[3 * j + 5] - z);
           if (MIXED) {
             const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
             s32 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, s32)));
@@ -48,8 +49,10 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
           }
         }
         if (j >= 1 && j + 1 < P) {  // interior bead (0-based 1..P-2)
-          const double ax = x - p[3 * j + 3], ay = y - p[3 * j + 4], az = z - p[3 * j + 5];
-          const double bx = x - p[3 * j - 3], by = y - p[3 * j - 2], bz = z - p[3 * j - 1];
+          const double ax = mimage(w, x - p[3 * j + 3]), ay = mimage(w, y - p[3 * j + 4]),
+                       az = mimage(w, z - p[3 * j + 5]);
+          const double bx = mimage(w, x - p[3 * j - 3]), by = mimage(w, y - p[3 * j - 2]),
+                       bz = mimage(w, z - p[3 * j - 1]);
           if (MIXED) {
             const float kf = (float)k;
             f[3 * j] = (double)(-kf * ((float)ax + (float)bx));
@@ -85,7 +88,8 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
       double lk = 0.0;
       if (l + 1 < w.N) {
         const double *n1 = b1 + 3 * P;  // bead 1 of particle l+1
-        const double dx = bP[0] - n1[0], dy = bP[1] - n1[1], dz = bP[2] - n1[2];
+        const double dx = mimage(w, bP[0] - n1[0]), dy = mimage(w, bP[1] - n1[1]),
+                     dz = mimage(w, bP[2] - n1[2]);
         if (MIXED) {
           const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
           lk = w.half_k * (double)fmaf(fx, fx, fmaf(fy, fy, fz * fz));
@@ -98,7 +102,16 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
       double *r1 = w.R1 + 4 * (size_t)l, *rp = w.RP + 4 * (size_t)l;
       r1[0] = b1[0]; r1[1] = b1[1]; r1[2] = b1[2]; r1[3] = 0.0;
       rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
-      if (MIXED) {  // float32 high + low parts (x = hi + lo to ~2^-48 relative)
+      if (MIXED && w.L > 0.0) {  // fixed-point fractions of the box
+        unsigned *u1 = (unsigned *)(w.R1s + 8 * (size_t)l), *uP = (unsigned *)(w.RPs + 8 * (size_t)l);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double f1 = b1[c] * w.invL - floor(b1[c] * w.invL), fP = bP[c] * w.invL - floor(bP[c] * w.invL);
+          u1[c] = (unsigned)fmin(f1 * 4294967296.0, 4294967295.0);
+          uP[c] = (unsigned)fmin(fP * 4294967296.0, 4294967295.0);
+        }
+        u1[3] = 0u; uP[3] = 0u;
+      } else if (MIXED) {  // float32 high + low parts (x = hi + lo to ~2^-48 relative)
         float *s1 = w.R1s + 8 * (size_t)l, *sp = w.RPs + 8 * (size_t)l;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

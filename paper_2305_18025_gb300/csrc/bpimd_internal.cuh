@@ -111,6 +111,12 @@ struct Workspace {
   int N, P, NT, NB;     // NT = ceil(N/TILE), NB = NT(NT+1)/2 blocks of g
   int mixed;
   double m, omega_P, beta, k, half_k;
+  // periodic cubic box of side L (0: open boundaries); every spring joins the
+  // minimum image of its beads.  MIXED keeps the bead-1/bead-P copies in a box
+  // as 32-bit fixed-point fractions of L (R1s/RPs reinterpreted as uint32
+  // x, y, z, 0), whose wrap-around integer difference is the minimum image.
+  double L, invL;
+  float Lscale;  // L / 2^32
   // O(N) per-particle state
   double *R1, *RP;      // [N][4] bead 1 / bead P positions (x, y, z, 0)
   float *R1s, *RPs;     // MIXED: [N][8] the same positions split into float
@@ -157,6 +163,23 @@ inline int sm_count() {
     cached[dev] = n > 0 ? n : 152;
   }
   return cached[dev];
+}
+
+// Minimum image of one coordinate difference (identity for open boundaries).
+__device__ __forceinline__ double mimage(const Workspace &w, double d) {
+  return w.L > 0.0 ? d - w.L * rint(d * w.invL) : d;
+}
+// Difference a - b of two fixed-point coordinates (fractions of L in units of
+// 2^-32): the signed 32-bit wrap-around difference is the minimum image.
+__device__ __forceinline__ float fixdiff(unsigned a, unsigned b, float Lscale) {
+  return (float)(int)(a - b) * Lscale;
+}
+
+// Periodic box of side L (L <= 0: open boundaries).
+inline void set_box(Workspace &w, double L) {
+  w.L = L > 0.0 ? L : 0.0;
+  w.invL = L > 0.0 ? 1.0 / L : 0.0;
+  w.Lscale = (float)(w.L / 4294967296.0);
 }
 
 // Lay the workspace out from `base` (nullptr: only measure); returns the bytes

@@ -65,14 +65,16 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
       const double M = direct_link_prob(w, p);
       const double *n1 = w.R1 + 4 * (size_t)(p + 1);
       rs += M;
-      rx = fma(M, rp[0] - n1[0], rx); ry = fma(M, rp[1] - n1[1], ry); rz = fma(M, rp[2] - n1[2], rz);
+      rx = fma(M, mimage(w, rp[0] - n1[0]), rx);
+      ry = fma(M, mimage(w, rp[1] - n1[1]), ry);
+      rz = fma(M, mimage(w, rp[2] - n1[2]), rz);
     }
     const double k = w.k;
     const double *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1 (1-based)
     double *fP = F + ((size_t)p * w.P + (w.P - 1)) * 3;
-    fP[0] = -k * fma(rs, rp[0] - nbP[0], rx);
-    fP[1] = -k * fma(rs, rp[1] - nbP[1], ry);
-    fP[2] = -k * fma(rs, rp[2] - nbP[2], rz);
+    fP[0] = -k * fma(rs, mimage(w, rp[0] - nbP[0]), rx);
+    fP[1] = -k * fma(rs, mimage(w, rp[1] - nbP[1]), ry);
+    fP[2] = -k * fma(rs, mimage(w, rp[2] - nbP[2]), rz);
     if (!(isfinite(fP[0]) && isfinite(fP[1]) && isfinite(fP[2]))) atomicOr(w.status, ST_NONFINITE);
   }
   if (threadIdx.x == 0) w.rowcnt[t] = 0;  // ready for the next evaluation
@@ -99,14 +101,16 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
       const double M = direct_link_prob(w, p - 1);
       const double *pP = w.RP + 4 * (size_t)(p - 1);
       cs += M;
-      cx = fma(M, r1[0] - pP[0], cx); cy = fma(M, r1[1] - pP[1], cy); cz = fma(M, r1[2] - pP[2], cz);
+      cx = fma(M, mimage(w, r1[0] - pP[0]), cx);
+      cy = fma(M, mimage(w, r1[1] - pP[1]), cy);
+      cz = fma(M, mimage(w, r1[2] - pP[2]), cz);
     }
     const double k = w.k;
     const double *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2 (1-based)
     double *f1 = F + (size_t)p * w.P * 3;
-    f1[0] = -k * fma(cs, r1[0] - nb1[0], cx);
-    f1[1] = -k * fma(cs, r1[1] - nb1[1], cy);
-    f1[2] = -k * fma(cs, r1[2] - nb1[2], cz);
+    f1[0] = -k * fma(cs, mimage(w, r1[0] - nb1[0]), cx);
+    f1[1] = -k * fma(cs, mimage(w, r1[1] - nb1[1]), cy);
+    f1[2] = -k * fma(cs, mimage(w, r1[2] - nb1[2]), cz);
     if (!(isfinite(f1[0]) && isfinite(f1[1]) && isfinite(f1[2]))) atomicOr(w.status, ST_NONFINITE);
   }
   if (threadIdx.x == 0) w.colcnt[s] = 0;
@@ -152,11 +156,19 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
       float fcs = 0, fcx = 0, fcy = 0, fcz = 0;
       if (valid) {
         if (MIXED) {
-          const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a);
-          const float4 al4 = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
-          const float fx = (bh.x - ah.x) + (bl.x - al4.x);
-          const float fy = (bh.y - ah.y) + (bl.y - al4.y);
-          const float fz = (bh.z - ah.z) + (bl.z - al4.z);
+          float fx, fy, fz;
+          if (w.L > 0.0) {  // minimum image from the fixed-point copies (bh holds RP's bits)
+            const uint4 ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
+            fx = fixdiff(__float_as_uint(bh.x), ua.x, w.Lscale);
+            fy = fixdiff(__float_as_uint(bh.y), ua.y, w.Lscale);
+            fz = fixdiff(__float_as_uint(bh.z), ua.z, w.Lscale);
+          } else {
+            const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a);
+            const float4 al4 = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
+            fx = (bh.x - ah.x) + (bl.x - al4.x);
+            fy = (bh.y - ah.y) + (bl.y - al4.y);
+            fz = (bh.z - ah.z) + (bl.z - al4.z);
+          }
           const float gmf = ((const float *)w.gm)[gi];
           const int e = ((const int *)w.ale)[a] + mub.e + w.ge[gi];
           float M = ((const float *)w.alm)[a] * mubf * gmf;
@@ -164,7 +176,8 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
           frs += M; frx += M * fx; fry += M * fy; frz += M * fz;
           fcs = M; fcx = -M * fx; fcy = -M * fy; fcz = -M * fz;
         } else {
-          const double dx = bx - w.R1[4 * a], dy = by - w.R1[4 * a + 1], dz = bz - w.R1[4 * a + 2];
+          const double dx = mimage(w, bx - w.R1[4 * a]), dy = mimage(w, by - w.R1[4 * a + 1]),
+                       dz = mimage(w, bz - w.R1[4 * a + 2]);
           const double gmd = ((const double *)w.gm)[gi];
           const double M = xtod(xd{((const double *)w.alm)[a] * mub.m * gmd, w.ale[a] + mub.e + w.ge[gi]});
           rs += M; rx = fma(M, dx, rx); ry = fma(M, dy, ry); rz = fma(M, dz, rz);
@@ -268,8 +281,8 @@ __global__ void __launch_bounds__(256) spring_expect_kernel(Workspace w, double 
         const double gmd = w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi];
         const xd al = alpha_of(w, a), mu = mu_of(w, b);
         const double M = xtod(xd{al.m * mu.m * gmd, al.e + mu.e + w.ge[gi]});
-        const double dx = w.RP[4 * b] - w.R1[4 * a], dy = w.RP[4 * b + 1] - w.R1[4 * a + 1],
-                     dz = w.RP[4 * b + 2] - w.R1[4 * a + 2];
+        const double dx = mimage(w, w.RP[4 * b] - w.R1[4 * a]), dy = mimage(w, w.RP[4 * b + 1] - w.R1[4 * a + 1]),
+                     dz = mimage(w, w.RP[4 * b + 2] - w.R1[4 * a + 2]);
         acc += M * (dx * dx + dy * dy + dz * dz);
       }
     }

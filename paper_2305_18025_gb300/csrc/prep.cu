@@ -37,11 +37,19 @@ __device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
 template <bool MIXED>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int a, int b, int &e) {
   if (MIXED) {
-    const float4 bh = *(const float4 *)(w.RPs + 8 * (size_t)b), bl = *(const float4 *)(w.RPs + 8 * (size_t)b + 4);
-    const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a), al = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
-    const float fx = (bh.x - ah.x) + (bl.x - al.x);
-    const float fy = (bh.y - ah.y) + (bl.y - al.y);
-    const float fz = (bh.z - ah.z) + (bl.z - al.z);
+    float fx, fy, fz;
+    if (w.L > 0.0) {  // minimum image from the fixed-point copies
+      const uint4 ub = *(const uint4 *)(w.RPs + 8 * (size_t)b), ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
+      fx = fixdiff(ub.x, ua.x, w.Lscale);
+      fy = fixdiff(ub.y, ua.y, w.Lscale);
+      fz = fixdiff(ub.z, ua.z, w.Lscale);
+    } else {
+      const float4 bh = *(const float4 *)(w.RPs + 8 * (size_t)b), bl = *(const float4 *)(w.RPs + 8 * (size_t)b + 4);
+      const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a), al = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
+      fx = (bh.x - ah.x) + (bl.x - al.x);
+      fy = (bh.y - ah.y) + (bl.y - al.y);
+      fz = (bh.z - ah.z) + (bl.z - al.z);
+    }
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
     const float x = fmaxf((float)cx * fmaf(fx, fx, fmaf(fy, fy, fz * fz)), -268435456.0f);
     const float n = floorf(x);
@@ -50,8 +58,8 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int
     if (mm >= 2.0f) { mm *= 0.5f; e += 1; }
     return mm;
   } else {
-    const double dx = w.RP[4 * b] - w.R1[4 * a], dy = w.RP[4 * b + 1] - w.R1[4 * a + 1],
-                 dz = w.RP[4 * b + 2] - w.R1[4 * a + 2];
+    const double dx = mimage(w, w.RP[4 * b] - w.R1[4 * a]), dy = mimage(w, w.RP[4 * b + 1] - w.R1[4 * a + 1]),
+                 dz = mimage(w, w.RP[4 * b + 2] - w.R1[4 * a + 2]);
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
     const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
     const double n = floor(x);

@@ -76,7 +76,8 @@ extern "C" {
 /* --------------------------------------------------------- pair potentials */
 #define BPIMD_PAIR_NONE 0
 #define BPIMD_PAIR_GAUSSIAN 1 /* g exp(-r^2 / (2 s^2)) between same-index beads */
-#define BPIMD_PAIR_LJ 2       /* 4 eps ((sigma/r)^12 - (sigma/r)^6), cut at rc   */
+#define BPIMD_PAIR_LJ 2       /* 4 eps ((sigma/r)^12 - (sigma/r)^6), truncated at rc
+                                 and shifted to 0 there (liquid helium)          */
 
 typedef struct bpimd_ctx bpimd_ctx; /* opaque; owns the device workspace */
 
@@ -99,12 +100,17 @@ typedef struct {
   double kT_bead;    /* thermostat kT of the bead momenta; 0 => 1/beta, the temperature
                         at which exp(-beta (V_B + U-bar)) is sampled with w_P = sqrt(P)/(beta hbar) */
   double omega0;     /* isotropic harmonic trap frequency (0 = none) */
-  int32_t pair_type; /* BPIMD_PAIR_NONE or BPIMD_PAIR_GAUSSIAN        */
+  int32_t pair_type; /* BPIMD_PAIR_*                                 */
   int32_t pad0;
   double pair_a;     /* Gaussian g  | LJ epsilon                      */
   double pair_b;     /* Gaussian s  | LJ sigma                        */
-  double pair_rc;    /* LJ cutoff (0 = no cutoff)                     */
-  double box_L;      /* reserved for periodic boxes, must be 0        */
+  double pair_rc;    /* LJ cutoff rc > 0 (at most box_L/2 in a box)   */
+  double box_L;      /* periodic cubic box side (0 = open boundaries):
+                        every spring -- interior, link, closing -- and
+                        every pair joins the minimum image of its two
+                        beads; positions need not be wrapped.  Used by
+                        the exchange evaluation and by bpimd_step; not
+                        by replica batches (must be 0 there).          */
   uint64_t seed;     /* counter-based RNG key for the thermostat      */
 } bpimd_config;
 
@@ -170,9 +176,12 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
  * Each call first evaluates the force at the given positions.  On a stream
  * other than the legacy default stream the step is captured once into a CUDA
  * graph (bound to these position/velocity buffers) and replayed.
+ * Lennard-Jones in a box of at least 3 cutoffs per side runs on cell lists
+ * (O(N P) per step); otherwise pairs are summed over all partners.
  * Errors: BPIMD_ERR_ARG for nsteps < 0, misaligned pointers, dt <= 0,
- * gamma < 0, kT_bead < 0, omega0 < 0, an unknown pair_type, s <= 0 for the
- * Gaussian pair, or box_L != 0.  Synchronises and returns device status. */
+ * gamma < 0, kT_bead < 0, omega0 < 0, an unknown pair_type, a Gaussian width
+ * or Lennard-Jones sigma <= 0, a Lennard-Jones cutoff <= 0 or above box_L/2.
+ * Synchronises and returns device status. */
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
                int32_t nsteps, double *energies);
 

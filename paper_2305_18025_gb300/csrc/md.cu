@@ -10,8 +10,11 @@
 //   A  x += (dt/2) v              F = -grad(V^{[1,N]} + U-bar)(x)
 //   B  v += (dt/2) F/m
 // with U = sum_l (1/2) m w0^2 |r_l|^2 (harmonic trap) + sum_{l<l'} g
-// exp(-|r_l - r_l'|^2 / (2 s^2)) (Gaussian repulsion) between beads of equal
-// index.  The exchange force is one evaluation of Algorithm 1 (the kernels of
+// exp(-|r_l - r_l'|^2 / (2 s^2)) (Gaussian repulsion) or Lennard-Jones
+// 4 eps ((sig/r)^12 - (sig/r)^6) truncated and shifted at rc (liquid helium;
+// cell lists in pairs.cu when the box holds >= 3 cutoffs per side) between
+// beads of equal index; in a periodic box every spring and pair uses the
+// minimum image.  The exchange force is one evaluation of Algorithm 1 (the kernels of
 // bead.cu, prep.cu, chain.cu, force.cu).
 //
 // Thermostat noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
@@ -28,6 +31,7 @@
 #include <type_traits>
 
 #include "context.cuh"
+#include "pairs.cuh"
 
 namespace bpimd {
 namespace {
@@ -123,14 +127,15 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // -grad U-bar added to F, per bead index j = blockIdx.y and particle
-// l = blockIdx.x * EXT_THREADS + thread; U-bar partial sum per block.  The
-// positions of bead j of all particles pass through shared memory in chunks.
-// MIXED: pair terms in float32 (relative positions), accumulated per thread in
-// float32 and added to the float64 force.
+// l = blockIdx.x * EXT_THREADS + thread (all pairs); U-bar partial sum per
+// block.  The positions of bead j of all particles pass through shared memory
+// in chunks.  Pairs: Gaussian g exp(-r^2/(2 s^2)), or Lennard-Jones
+// 4 eps ((sig/r)^12 - (sig/r)^6) truncated and shifted at rc; in a periodic box
+// pair distances by minimum image.  MIXED: pair terms in float32, accumulated
+// per thread in float32 and added to the float64 force.
 template <bool MIXED>
 __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__restrict__ pos, double *__restrict__ F,
-                                                                int N, int P, double inv_P, double kt, int pair,
-                                                                double ga, double inv_s2, double *ubar_part) {
+                                                                int N, int P, PairParams pp, double *ubar_part) {
   using R = typename std::conditional<MIXED, float, double>::type;
   __shared__ R sx[EXT_CHUNK], sy[EXT_CHUNK], sz[EXT_CHUNK];
   __shared__ double red[EXT_THREADS / 32];
@@ -142,9 +147,15 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
     rx = r[0]; ry = r[1]; rz = r[2];
   }
   const R px = (R)rx, py = (R)ry, pz = (R)rz;
-  const R a = (R)(-0.5 * inv_s2);
+  const R a = (R)(-0.5 * pp.inv_s2);
+  const R L = (R)pp.L, invL = (R)pp.invL;
+  const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
+  auto img = [&](R d) -> R {
+    return pp.L > 0.0 ? d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL))) : d;
+  };
   R fx = 0, fy = 0, fz = 0, u = 0;
-  if (pair == BPIMD_PAIR_GAUSSIAN) {
+  int nin = 0;  // Lennard-Jones pairs inside the cutoff (each carries the shift)
+  if (pp.pair != BPIMD_PAIR_NONE) {
     for (int base = 0; base < N; base += EXT_CHUNK) {
       const int cnt = min(EXT_CHUNK, N - base);
       __syncthreads();
@@ -153,26 +164,40 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
         sx[q] = (R)r[0]; sy[q] = (R)r[1]; sz[q] = (R)r[2];
       }
       __syncthreads();
-      if (valid) {
+      if (valid && pp.pair == BPIMD_PAIR_GAUSSIAN) {
         for (int q = 0; q < cnt; ++q) {
-          const R dx = px - sx[q], dy = py - sy[q], dz = pz - sz[q];
+          const R dx = img(px - sx[q]), dy = img(py - sy[q]), dz = img(pz - sz[q]);
           const R d2 = dx * dx + dy * dy + dz * dz;
           const R e = MIXED ? (R)__expf((float)(a * d2)) : (R)exp((double)(a * d2));
           fx += e * dx; fy += e * dy; fz += e * dz;
           u += e;
         }
+      } else if (valid) {  // Lennard-Jones: force over 24 eps, energy over 4 eps
+        for (int q = 0; q < cnt; ++q) {
+          const R dx = img(px - sx[q]), dy = img(py - sy[q]), dz = img(pz - sz[q]);
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 > (R)0 && r2 < rc2) {
+            const R s2 = sig2 / r2, s6 = s2 * s2 * s2;
+            const R c = (2 * s6 * s6 - s6) / r2;
+            fx += c * dx; fy += c * dy; fz += c * dz;
+            u += s6 * s6 - s6;
+            ++nin;
+          }
+        }
       }
     }
-    if (valid) u -= (R)1;  // the self term (d = 0, e = 1) carries no force
+    if (valid && pp.pair == BPIMD_PAIR_GAUSSIAN) u -= (R)1;  // the self term (d = 0, e = 1) carries no force
   }
   double ul = 0.0;
   if (valid) {
     double *f = F + ((size_t)l * P + j) * 3;
-    const double gs = ga * inv_s2;
-    f[0] += inv_P * (gs * (double)fx - kt * rx);
-    f[1] += inv_P * (gs * (double)fy - kt * ry);
-    f[2] += inv_P * (gs * (double)fz - kt * rz);
-    ul = inv_P * (0.5 * ga * (double)u + 0.5 * kt * (rx * rx + ry * ry + rz * rz));
+    const double fs = pp.pair == BPIMD_PAIR_GAUSSIAN ? pp.ga * pp.inv_s2 : 24.0 * pp.eps;
+    f[0] += pp.inv_P * (fs * (double)fx - pp.kt * rx);
+    f[1] += pp.inv_P * (fs * (double)fy - pp.kt * ry);
+    f[2] += pp.inv_P * (fs * (double)fz - pp.kt * rz);
+    const double up = pp.pair == BPIMD_PAIR_GAUSSIAN ? 0.5 * pp.ga * (double)u
+                                                    : 0.5 * (4.0 * pp.eps * (double)u - pp.ushift * nin);
+    ul = pp.inv_P * (up + 0.5 * pp.kt * (rx * rx + ry * ry + rz * rz));
   }
   const double s = block_sum(ul, red);
   if (threadIdx.x == 0) ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
@@ -217,8 +242,9 @@ __global__ void __launch_bounds__(MD_THREADS) energies_kernel(Workspace w, const
 
 struct MDParams {
   long long n;
-  double half_dt_over_m, half_dt, c1, c2, inv_P, kt, ga, inv_s2;
-  int pair;
+  double half_dt_over_m, half_dt, c1, c2;
+  PairParams pp;
+  int cell_nc;  // > 0: Lennard-Jones by cell lists with cell_nc^3 cells per bead index
   uint32_t k0, k1;
 };
 
@@ -226,21 +252,47 @@ int md_params(const bpimd_config &c, MDParams &p) {
   if (!(c.dt > 0.0) || !std::isfinite(c.dt) || !(c.gamma >= 0.0) || !std::isfinite(c.gamma)) return BPIMD_ERR_ARG;
   if (!(c.kT_bead >= 0.0) || !std::isfinite(c.kT_bead) || !(c.omega0 >= 0.0) || !std::isfinite(c.omega0))
     return BPIMD_ERR_ARG;
-  if (c.pair_type != BPIMD_PAIR_NONE && c.pair_type != BPIMD_PAIR_GAUSSIAN) return BPIMD_ERR_ARG;
-  if (c.pair_type == BPIMD_PAIR_GAUSSIAN && (!std::isfinite(c.pair_a) || !(c.pair_b > 0.0) || !std::isfinite(c.pair_b)))
+  if (c.pair_type != BPIMD_PAIR_NONE && c.pair_type != BPIMD_PAIR_GAUSSIAN && c.pair_type != BPIMD_PAIR_LJ)
     return BPIMD_ERR_ARG;
-  if (c.box_L != 0.0) return BPIMD_ERR_ARG;  // periodic boxes are not supported by this step
+  if (c.pair_type != BPIMD_PAIR_NONE &&
+      (!std::isfinite(c.pair_a) || !(c.pair_b > 0.0) || !std::isfinite(c.pair_b)))
+    return BPIMD_ERR_ARG;
+  const double L = c.box_L;
+  if (c.pair_type == BPIMD_PAIR_LJ) {
+    // a cutoff is required; in a box it may not exceed half the side (minimum image)
+    if (!(c.pair_rc > 0.0) || !std::isfinite(c.pair_rc)) return BPIMD_ERR_ARG;
+    if (L > 0.0 && c.pair_rc > 0.5 * L) return BPIMD_ERR_ARG;
+  }
   const double kT = c.kT_bead > 0.0 ? c.kT_bead : 1.0 / c.beta;
   p.n = (long long)c.N * c.P * 3;
   p.half_dt_over_m = 0.5 * c.dt / c.m;
   p.half_dt = 0.5 * c.dt;
   p.c1 = std::exp(-c.gamma * c.dt);
   p.c2 = std::sqrt((1.0 - p.c1 * p.c1) * kT / c.m);
-  p.inv_P = 1.0 / c.P;
-  p.kt = c.m * c.omega0 * c.omega0;
-  p.pair = c.pair_type;
-  p.ga = c.pair_type == BPIMD_PAIR_GAUSSIAN ? c.pair_a : 0.0;
-  p.inv_s2 = c.pair_type == BPIMD_PAIR_GAUSSIAN ? 1.0 / (c.pair_b * c.pair_b) : 0.0;
+  PairParams &q = p.pp;
+  q = PairParams{};
+  q.pair = c.pair_type;
+  q.inv_P = 1.0 / c.P;
+  q.kt = c.m * c.omega0 * c.omega0;
+  if (c.pair_type == BPIMD_PAIR_GAUSSIAN) {
+    q.ga = c.pair_a;
+    q.inv_s2 = 1.0 / (c.pair_b * c.pair_b);
+  }
+  if (c.pair_type == BPIMD_PAIR_LJ) {
+    q.eps = c.pair_a;
+    q.sig2 = c.pair_b * c.pair_b;
+    q.rc2 = c.pair_rc * c.pair_rc;
+    const double sr2 = q.sig2 / q.rc2, sr6 = sr2 * sr2 * sr2;
+    q.ushift = 4.0 * c.pair_a * (sr6 * sr6 - sr6);
+  }
+  q.L = L > 0.0 ? L : 0.0;
+  q.invL = L > 0.0 ? 1.0 / L : 0.0;
+  q.Lscale = (float)(q.L / 4294967296.0);
+  p.cell_nc = 0;
+  if (c.pair_type == BPIMD_PAIR_LJ && L > 0.0) {
+    const int nc = (int)std::floor(L / c.pair_rc);
+    if (nc >= 3 && (long long)nc * nc * nc * c.P <= (1LL << 26)) p.cell_nc = nc;
+  }
   p.k0 = (uint32_t)c.seed;
   p.k1 = (uint32_t)(c.seed >> 32);
   return BPIMD_OK;
@@ -257,13 +309,16 @@ int total_force(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
   MDState &md = ctx->md;
   int rc = evaluate(ctx, pos, md.VB, md.F);
   if (rc != BPIMD_OK) return rc;
+  if (p.cell_nc > 0)
+    return cell_list_forces(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp, ctx->w.mixed, md.cells, md.ubar_part,
+                            ctx->stream) == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
   const dim3 grid((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS, ctx->cfg.P);
   if (ctx->w.mixed)
-    ext_force_kernel<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.inv_P, p.kt,
-                                                                  p.pair, p.ga, p.inv_s2, md.ubar_part);
+    ext_force_kernel<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp,
+                                                                  md.ubar_part);
   else
-    ext_force_kernel<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.inv_P, p.kt,
-                                                                   p.pair, p.ga, p.inv_s2, md.ubar_part);
+    ext_force_kernel<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp,
+                                                                   md.ubar_part);
   return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
 }
 
@@ -285,8 +340,16 @@ int enqueue_step(bpimd_ctx *ctx, const MDParams &p, double *pos, double *vel) {
   return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
 }
 
-int md_alloc(bpimd_ctx *ctx) {
+int md_alloc(bpimd_ctx *ctx, const MDParams &p) {
   MDState &md = ctx->md;
+  if (p.cell_nc > 0) {
+    const size_t bytes = cell_list_bytes(ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.mixed);
+    if (cudaMalloc(&md.cell_block, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return BPIMD_ERR_NOMEM;
+    }
+    cell_list_layout(md.cells, (char *)md.cell_block, ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.mixed);
+  }
   const size_t n = (size_t)ctx->cfg.N * ctx->cfg.P * 3;
   md.ext_blocks = ((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS) * ctx->cfg.P;
   md.ke_blocks = grid_for((long long)n, MD_THREADS);
@@ -319,6 +382,7 @@ void md_free(MDState *md) {
   cudaFree(md->ke_part);
   cudaFree(md->spring_part);
   cudaFree(md->step);
+  cudaFree(md->cell_block);
   *md = MDState{};
 }
 
@@ -327,7 +391,7 @@ int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *ene
   int rc = md_params(ctx->cfg, p);
   if (rc != BPIMD_OK) return rc;
   MDState &md = ctx->md;
-  if (!md.ready && (rc = md_alloc(ctx)) != BPIMD_OK) return rc;
+  if (!md.ready && (rc = md_alloc(ctx, p)) != BPIMD_OK) return rc;
   // stage profiling is not recorded inside MD steps
   const bool prof = ctx->prof_on;
   ctx->prof_on = false;

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pairs.cuh"
+
 struct bpimd_ctx;
 
 namespace bpimd {
@@ -18,6 +20,8 @@ struct MDState {
   cudaGraphExec_t exec;
   double *g_pos, *g_vel;     // buffers the captured step is bound to
   uint64_t steps_taken;
+  void *cell_block;          // cell-list buffers (Lennard-Jones in a box)
+  CellList cells;
   bool ready;
 };
 void md_init(MDState *md);

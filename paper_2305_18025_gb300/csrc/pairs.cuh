@@ -1,0 +1,38 @@
+// Physical pair potential of the MD step: parameters and the cell-list path
+// (internal; used by md.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bpimd {
+
+// U = sum_l (1/2) kt |r_l|^2 + pairs between beads of equal index, all scaled by 1/P.
+struct PairParams {
+  int pair;              // BPIMD_PAIR_NONE / GAUSSIAN / LJ
+  double inv_P, kt;      // 1/P, m w0^2 (trap)
+  double ga, inv_s2;     // Gaussian g, 1/s^2
+  double eps, sig2, rc2; // Lennard-Jones eps, sigma^2, cutoff^2
+  double ushift;         // LJ energy at the cutoff (subtracted per pair inside it)
+  double L, invL;        // periodic box (L = 0: open)
+  float Lscale;          // L / 2^32 (fixed-point differences)
+};
+
+// Cell lists per bead index: nc^3 cells of side L/nc >= rc in a periodic box.
+struct CellList {
+  int nc;            // cells per side (>= 3)
+  int ncells;        // P nc^3
+  int *cellof;       // [N*P] cell of bead (l, j), index l*P + j
+  void *crd;         // [N*P] wrapped coordinates: uint4 fixed point (MIXED) or double4 (float64)
+  int *count, *fill, *start;  // [ncells]
+  int *list;         // [N*P] particle indices grouped by cell, ascending within a cell
+};
+
+// Bytes of the cell-list buffers for N particles, P beads, nc cells per side.
+size_t cell_list_bytes(int N, int P, int nc, bool mixed);
+// Lay the buffers out from base (cudaMalloc'd, 256-byte aligned).
+void cell_list_layout(CellList &cl, char *base, int N, int P, int nc, bool mixed);
+// Bin, sort and evaluate Lennard-Jones (+ trap) forces added to F; U-bar
+// partial sums per (particle block of 128, bead index), as the all-pairs kernel.
+cudaError_t cell_list_forces(const double *pos, double *F, int N, int P, const PairParams &pp, bool mixed,
+                             const CellList &cl, double *ubar_part, cudaStream_t s);
+
+}  // namespace bpimd

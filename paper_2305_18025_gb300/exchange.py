@@ -16,7 +16,7 @@ from . import bpimd as _c
 class ExchangeEnergy:
     """Exchange potential and forces for one system of N particles, P beads."""
 
-    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None):
+    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None, box=0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
         prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
@@ -30,7 +30,7 @@ class ExchangeEnergy:
             self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec)
+            self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec, box_L=float(box))
             self.ctx = _c.bpimd_create(self.cfg, self.stream)
             self._V = torch.empty((), dtype=torch.float64, device=self.device)
 
@@ -108,13 +108,16 @@ class RingPolymerMD:
 
     Samples exp(-beta (V^{[1,N]} + U-bar)) with the exchange force of Algorithm 1
     plus a harmonic trap (omega0) and an optional Gaussian repulsion
-    g exp(-r^2/(2 s^2)) between beads of equal index.  ``step`` advances the
+    g exp(-r^2/(2 s^2)) or Lennard-Jones pair potential (eps, sigma, cutoff;
+    truncated and shifted) between beads of equal index; box > 0 makes the
+    system periodic (minimum-image springs and pairs; Lennard-Jones by cell
+    lists when the box holds at least 3 cutoffs per side).  ``step`` advances the
     caller's position and velocity tensors in place; with a non-default stream
     the step runs as a replayed CUDA graph.
     """
 
     def __init__(self, N, P, m, omega_P, beta, dt, gamma=1.0, omega0=0.0, gaussian=None, kT=0.0,
-                 seed=0, precision="fp64", device="cuda", stream=None):
+                 seed=0, precision="fp64", device="cuda", stream=None, lennard_jones=None, box=0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
         prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
@@ -125,6 +128,10 @@ class RingPolymerMD:
         md = dict(dt=float(dt), gamma=float(gamma), kT_bead=float(kT), omega0=float(omega0), seed=int(seed))
         if gaussian is not None:
             md.update(pair_type=_c.BPIMD_PAIR_GAUSSIAN, pair_a=float(gaussian[0]), pair_b=float(gaussian[1]))
+        if lennard_jones is not None:  # (eps, sigma, cutoff)
+            md.update(pair_type=_c.BPIMD_PAIR_LJ, pair_a=float(lennard_jones[0]), pair_b=float(lennard_jones[1]),
+                      pair_rc=float(lennard_jones[2]))
+        md["box_L"] = float(box)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.cfg = _c.make_config(self.N, self.P, float(m), float(omega_P), float(beta), prec, **md)

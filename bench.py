@@ -8,7 +8,9 @@ float32/float64 form (the reported `value`) and the plain float64 form
 (`fp64`).  A step is one full evaluation: bead pass, pair factors, forward
 and backward recursions with the prefix sums and V_B, probabilities with all
 exterior-bead forces.  The line also carries MD steps/s (`md`) of the same
-system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays).
+system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays),
+the throughput of a 256-replica batch of uneven N, P, beta (`batched`), and
+MD steps/s of bulk liquid helium in a periodic box (`helium`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,6 +52,11 @@ def parse():
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--md-steps", type=int, default=200, help="timed MD steps (mixed; float64 runs a quarter)")
+    ap.add_argument("--batch-replicas", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=50, help="timed evaluations of the replica batch")
+    ap.add_argument("--he-cells", type=int, default=10, help="FCC cells per side of the helium box (4 atoms each)")
+    ap.add_argument("--he-P", type=int, default=64)
+    ap.add_argument("--he-steps", type=int, default=20, help="timed helium MD steps (mixed; float64 a fifth)")
     return ap.parse_args()
 
 
@@ -266,6 +273,8 @@ def run_ours(args, rank, world, local_rank):
                               "api": "bpimd_exchange_energy_forces_host (pinned host buffers)"}
         eng.close()
     results["md"] = md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world)
+    results["batched"] = batched_throughput(args, dev, flush, max_over_ranks, barrier, world)
+    results["helium"] = helium_throughput(args, dev, max_over_ranks, barrier, world)
     clocks = sampler.stop()
 
     if rank != 0:
@@ -289,6 +298,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
         "V_B": {"mixed": mixed["V_B"], "fp64": fp64["V_B"]},
         "md": results["md"],
+        "batched": results["batched"],
+        "helium": results["helium"],
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
@@ -331,6 +342,106 @@ def md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world):
                      "timing": "CUDA events around one bpimd_step call (one initial force evaluation + "
                                "the steps as CUDA-graph replays); L2 not flushed between MD steps, "
                                "which run back to back as in a production trajectory"}
+    return out
+
+
+def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
+    """256 independent trapped replicas, N ~ U[16,512], P in {16,32,64},
+    beta ~ U[0.5,4] (seed 11), evaluated together (bpimd_create_batched),
+    launch shape picked by the autotuner; L2 flushed between timed batches."""
+    import torch
+    from paper_2305_18025_gb300 import autotune, inputs
+    from paper_2305_18025_gb300.exchange import BatchedExchangeEnergy
+    reps = inputs.batched_replicas(args.batch_replicas, seed=11)
+    Ns = [r.N for r in reps]
+    Ps = [r.P for r in reps]
+    betas = [r.beta for r in reps]
+    wPs = [inputs.omega_P(P, b) for P, b in zip(Ps, betas)]
+    out = {}
+    for prec in ("mixed", "fp64"):
+        eng = BatchedExchangeEnergy(Ns, Ps, 1.0, wPs, betas, precision=prec, device=dev)
+        x = eng.pack([torch.from_numpy(r.positions) for r in reps])
+        tuned = autotune.tune(eng, x, reps=3)
+        F = torch.empty_like(x)
+        V = torch.empty(eng.R, dtype=torch.float64, device=dev)
+        stream = eng.stream
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            eng.forces(x, out=F, V_out=V)
+        steps = args.batch_steps
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(k & 255)
+            starts[k].record(stream)
+            eng.forces(x, out=F, V_out=V)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        eng.sync()
+        ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "batch evals/s",
+                     "replica_evals_per_s": world * steps * eng.R / (ms * 1e-3),
+                     "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": 4 * steps,
+                     "tuning": {"choice": list(tuned["choice"]), "cached": tuned["cached"]}}
+        eng.close()
+    out["config"] = {"workload": f"{args.batch_replicas} independent trapped replicas, N~U[16,512], "
+                                 "P in {16,32,64}, beta~U[0.5,4], seed 11 (exchange V_B + all bead forces of each)",
+                     "sum_N": int(sum(Ns)), "sum_NP": int(sum(n * p for n, p in zip(Ns, Ps))),
+                     "sum_pairs": int(sum(n * (n + 1) // 2 for n in Ns)),
+                     "l2": "flushed between timed batches (256 MiB device write, untimed)"}
+    return out
+
+
+HE = dict(m=4.0026, T=1.5, eps=10.22, sigma=2.556, rho=0.0218, hbar=6.9648)  # A, K, amu units
+
+
+def helium_throughput(args, dev, max_over_ranks, barrier, world):
+    """Bulk liquid helium: FCC start (10^3 cells, 4000 atoms) at 0.0218 A^-3,
+    P = 64, T = 1.5 K, Lennard-Jones eps = 10.22 K, sigma = 2.556 A cut and
+    shifted at 2.5 sigma (cell lists), periodic box with minimum-image springs,
+    BAOAB dt = 1 fs.  MD steps/s, mixed and float64."""
+    import numpy as np
+    import torch
+    from paper_2305_18025_gb300 import inputs
+    from paper_2305_18025_gb300.exchange import RingPolymerMD
+    cells, P = args.he_cells, args.he_P
+    N = 4 * cells ** 3
+    L = (N / HE["rho"]) ** (1.0 / 3.0)
+    beta = 1.0 / HE["T"]
+    wP = np.sqrt(P) / (beta * HE["hbar"])
+    dt = 1e-15 / 1.0967e-12  # 1 fs in units of A sqrt(amu/K)
+    pos = inputs.fcc_positions(cells, P, L, seed=5, jitter=0.05)
+    lj = (HE["eps"], HE["sigma"], 2.5 * HE["sigma"])
+    out = {}
+    for prec, steps in (("mixed", args.he_steps), ("fp64", max(1, args.he_steps // 5))):
+        side = torch.cuda.Stream(dev)
+        md = RingPolymerMD(N, P, HE["m"], wP, beta, dt=dt, gamma=1.0, lennard_jones=lj, box=L, seed=3,
+                           precision=prec, stream=side)
+        x = torch.from_numpy(pos.copy()).to(dev)
+        v = torch.zeros_like(x)
+        md.step(x, v, 3, energies=False)  # warm-up, graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(side)
+        md.step(x, v, steps, energies=False)
+        e1.record(side)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        en = md.step(x, v, 1).cpu().tolist()
+        md.close()
+        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "MD steps/s", "steps": steps,
+                     "ms_per_step": ms / steps,
+                     "energies_after_K": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
+    out["config"] = {"workload": f"liquid helium N={N} (FCC {cells}^3 x 4) P={P} T=1.5 K rho=0.0218/A^3 "
+                                 f"box {L:.2f} A, Lennard-Jones eps=10.22 K sigma=2.556 A cut+shift 2.5 sigma",
+                     "integrator": "BAOAB Langevin dt=1 fs gamma=1 (A, K, amu units), Philox noise",
+                     "timing": "CUDA events around one bpimd_step call (one initial force evaluation + graph "
+                               "replays); L2 not flushed between MD steps"}
     return out
 
 

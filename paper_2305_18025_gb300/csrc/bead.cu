@@ -102,7 +102,7 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
       double *r1 = w.R1 + 4 * (size_t)l, *rp = w.RP + 4 * (size_t)l;
       r1[0] = b1[0]; r1[1] = b1[1]; r1[2] = b1[2]; r1[3] = 0.0;
       rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
-      if (MIXED && w.L > 0.0) {  // fixed-point fractions of the box
+      if (MIXED && w.pbc) {  // fixed-point fractions of the box
         unsigned *u1 = (unsigned *)(w.R1s + 8 * (size_t)l), *uP = (unsigned *)(w.RPs + 8 * (size_t)l);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

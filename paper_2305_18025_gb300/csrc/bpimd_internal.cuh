@@ -117,6 +117,7 @@ struct Workspace {
   // x, y, z, 0), whose wrap-around integer difference is the minimum image.
   double L, invL;
   float Lscale;  // L / 2^32
+  int pbc;       // L > 0 (an integer test: a float64 compare would use the slow float64 pipe)
   // O(N) per-particle state
   double *R1, *RP;      // [N][4] bead 1 / bead P positions (x, y, z, 0)
   float *R1s, *RPs;     // MIXED: [N][8] the same positions split into float
@@ -167,7 +168,7 @@ inline int sm_count() {
 
 // Minimum image of one coordinate difference (identity for open boundaries).
 __device__ __forceinline__ double mimage(const Workspace &w, double d) {
-  return w.L > 0.0 ? d - w.L * rint(d * w.invL) : d;
+  return w.pbc ? d - w.L * rint(d * w.invL) : d;
 }
 // Difference a - b of two fixed-point coordinates (fractions of L in units of
 // 2^-32): the signed 32-bit wrap-around difference is the minimum image.
@@ -180,6 +181,7 @@ inline void set_box(Workspace &w, double L) {
   w.L = L > 0.0 ? L : 0.0;
   w.invL = L > 0.0 ? 1.0 / L : 0.0;
   w.Lscale = (float)(w.L / 4294967296.0);
+  w.pbc = L > 0.0 ? 1 : 0;
 }
 
 // Lay the workspace out from `base` (nullptr: only measure); returns the bytes

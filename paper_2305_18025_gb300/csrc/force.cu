@@ -157,7 +157,7 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
       if (valid) {
         if (MIXED) {
           float fx, fy, fz;
-          if (w.L > 0.0) {  // minimum image from the fixed-point copies (bh holds RP's bits)
+          if (w.pbc) {  // minimum image from the fixed-point copies (bh holds RP's bits)
             const uint4 ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
             fx = fixdiff(__float_as_uint(bh.x), ua.x, w.Lscale);
             fy = fixdiff(__float_as_uint(bh.y), ua.y, w.Lscale);

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
   const R L = (R)pp.L, invL = (R)pp.invL;
   const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
   auto img = [&](R d) -> R {
-    return pp.L > 0.0 ? d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL))) : d;
+    return pp.pbc ? d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL))) : d;
   };
   R fx = 0, fy = 0, fz = 0, u = 0;
   int nin = 0;  // Lennard-Jones pairs inside the cutoff (each carries the shift)
@@ -288,6 +288,7 @@ int md_params(const bpimd_config &c, MDParams &p) {
   q.L = L > 0.0 ? L : 0.0;
   q.invL = L > 0.0 ? 1.0 / L : 0.0;
   q.Lscale = (float)(q.L / 4294967296.0);
+  q.pbc = L > 0.0 ? 1 : 0;
   p.cell_nc = 0;
   if (c.pair_type == BPIMD_PAIR_LJ && L > 0.0) {
     const int nc = (int)std::floor(L / c.pair_rc);

@@ -14,6 +14,7 @@ struct PairParams {
   double ushift;         // LJ energy at the cutoff (subtracted per pair inside it)
   double L, invL;        // periodic box (L = 0: open)
   float Lscale;          // L / 2^32 (fixed-point differences)
+  int pbc;               // L > 0 (integer test; float64 compares use the slow float64 pipe)
 };
 
 // Cell lists per bead index: nc^3 cells of side L/nc >= rc in a periodic box.

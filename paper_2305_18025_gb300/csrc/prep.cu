@@ -38,7 +38,7 @@ template <bool MIXED>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int a, int b, int &e) {
   if (MIXED) {
     float fx, fy, fz;
-    if (w.L > 0.0) {  // minimum image from the fixed-point copies
+    if (w.pbc) {  // minimum image from the fixed-point copies
       const uint4 ub = *(const uint4 *)(w.RPs + 8 * (size_t)b), ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
       fx = fixdiff(ub.x, ua.x, w.Lscale);
       fy = fixdiff(ub.y, ua.y, w.Lscale);

@@ -53,6 +53,7 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
   double acc = 0.0;
   const size_t base = (size_t)t * (t + 1) / 2;
   const P_t *part = (const P_t *)w.rowpart;
+#pragma unroll 8
   for (int s = half; s <= t; s += 2) acc += (double)__ldcg(part + ((base + s) * TILE + jj) * 4 + q);
   fin[jj][q + 4 * half] = acc;
   __syncthreads();
@@ -88,6 +89,7 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
   const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
   double acc = 0.0;
   const P_t *part = (const P_t *)w.colpart;
+#pragma unroll 8
   for (int t = s + half; t < w.NT; t += 2)
     acc += (double)__ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
   fin[ii][q + 4 * half] = acc;

@@ -8,11 +8,13 @@
 //           fixed-point fractions of L, whose wrap-around difference is the
 //           minimum image exactly; float64: coordinates in [0, L));
 //   scan    cell starts (exclusive prefix sum of the counts, one CTA);
-//   scatter particle indices into their cells;
+//   scatter bead indices into their cells;
 //   sort    each cell's indices ascending, so that every force is summed in
 //           a fixed order (results do not depend on the order of atomics);
-//   force   one thread per bead: the 27 cells in a fixed order, pairs inside
-//           rc, force and energy (MIXED: float32 pair terms).
+//   gather  coordinates into cell order (one load per candidate pair later);
+//   force   one thread per slot of the cell-ordered list: the 27 cells in a
+//           fixed order, pairs inside rc, force and energy (MIXED: float32
+//           pair terms).
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
@@ -102,11 +104,12 @@ __global__ void __launch_bounds__(256) cl_scatter(const int *__restrict__ cellof
   const long long nb = (long long)N * P;
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
     const int cid = cellof[b];
-    list[start[cid] + atomicAdd(fill + cid, 1)] = (int)(b / P);
+    list[start[cid] + atomicAdd(fill + cid, 1)] = (int)b;
   }
 }
 
-// each cell's particle indices ascending (insertion sort; cells hold a few beads)
+// each cell's bead indices ascending (insertion sort; cells hold a few beads;
+// one cell holds one bead index j, so this orders by particle)
 __global__ void __launch_bounds__(256) cl_sort(const int *__restrict__ start, const int *__restrict__ count,
                                                int ncells, int *__restrict__ list) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
@@ -124,48 +127,60 @@ __global__ void __launch_bounds__(256) cl_sort(const int *__restrict__ start, co
   }
 }
 
+// coordinates in cell order: sorted[slot] = crd[list[slot]]
 template <bool MIXED>
-__global__ void __launch_bounds__(CL_THREADS) cl_force(int N, int P, PairParams pp, int nc,
-                                                       const int *__restrict__ cellof, const void *__restrict__ crd,
+__global__ void __launch_bounds__(256) cl_gather(const int *__restrict__ list, long long nb,
+                                                 const void *__restrict__ crd, void *__restrict__ sorted) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nb; q += (long long)gridDim.x * blockDim.x) {
+    if (MIXED) ((uint4 *)sorted)[q] = ((const uint4 *)crd)[list[q]];
+    else ((double4 *)sorted)[q] = ((const double4 *)crd)[list[q]];
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(CL_THREADS) cl_force(long long nb, int P, PairParams pp, int nc,
+                                                       const int *__restrict__ cellof, const void *__restrict__ sorted,
                                                        const int *__restrict__ start, const int *__restrict__ count,
                                                        const int *__restrict__ list, const double *__restrict__ pos,
                                                        double *__restrict__ F, double *ubar_part) {
+  // one thread per slot of the cell-ordered bead list: neighbouring threads
+  // work on the same or adjacent cells, whose coordinates they share in cache
   using R = typename std::conditional<MIXED, float, double>::type;
   __shared__ double red[CL_THREADS / 32];
-  const int j = blockIdx.y, l = blockIdx.x * CL_THREADS + threadIdx.x;
-  const bool valid = l < N;
+  const long long slot = blockIdx.x * (long long)CL_THREADS + threadIdx.x;
+  const bool valid = slot < nb;
   R fx = 0, fy = 0, fz = 0, u = 0;
   int nin = 0;
   double rx = 0, ry = 0, rz = 0;
+  int b = 0;
   if (valid) {
-    const long long b = (long long)l * P + j;
-    const double *r = pos + 3 * b;
+    b = list[slot];
+    const int j = b % P;
+    const double *r = pos + 3 * (long long)b;
     rx = r[0]; ry = r[1]; rz = r[2];
     const int cell = cellof[b] - j * nc * nc * nc;
     const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
     const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
     uint4 ui = make_uint4(0, 0, 0, 0);
     double4 di = make_double4(0, 0, 0, 0);
-    if (MIXED) ui = ((const uint4 *)crd)[b];
-    else di = ((const double4 *)crd)[b];
+    if (MIXED) ui = ((const uint4 *)sorted)[slot];
+    else di = ((const double4 *)sorted)[slot];
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           const int nx = (cx + dx + nc) % nc, ny = (cy + dy + nc) % nc, nz = (cz + dz + nc) % nc;
           const int nid = ((j * nc + nz) * nc + ny) * nc + nx;
           const int s0 = start[nid], n = count[nid];
-          for (int q = 0; q < n; ++q) {
-            const int lp = list[s0 + q];
-            if (lp == l) continue;
-            const long long bp = (long long)lp * P + j;
+          for (int q = s0; q < s0 + n; ++q) {
+            if (q == slot) continue;
             R ex, ey, ez;
             if (MIXED) {
-              const uint4 uj = ((const uint4 *)crd)[bp];
+              const uint4 uj = ((const uint4 *)sorted)[q];
               ex = (R)fixdiff(ui.x, uj.x, pp.Lscale);
               ey = (R)fixdiff(ui.y, uj.y, pp.Lscale);
               ez = (R)fixdiff(ui.z, uj.z, pp.Lscale);
             } else {
-              const double4 dj = ((const double4 *)crd)[bp];
+              const double4 dj = ((const double4 *)sorted)[q];
               ex = (R)(di.x - dj.x); ey = (R)(di.y - dj.y); ez = (R)(di.z - dj.z);
               ex -= (R)(pp.L * rint((double)ex * pp.invL));
               ey -= (R)(pp.L * rint((double)ey * pp.invL));
@@ -184,7 +199,7 @@ __global__ void __launch_bounds__(CL_THREADS) cl_force(int N, int P, PairParams 
   }
   double ul = 0.0;
   if (valid) {
-    double *f = F + ((size_t)l * P + j) * 3;
+    double *f = F + 3 * (long long)b;
     const double fs = 24.0 * pp.eps;
     f[0] += pp.inv_P * (fs * (double)fx - pp.kt * rx);
     f[1] += pp.inv_P * (fs * (double)fy - pp.kt * ry);
@@ -198,7 +213,7 @@ __global__ void __launch_bounds__(CL_THREADS) cl_force(int N, int P, PairParams 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < CL_THREADS / 32; ++q) t += red[q];
-    ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    ubar_part[blockIdx.x] = t;
   }
 }
 
@@ -206,7 +221,7 @@ __global__ void __launch_bounds__(CL_THREADS) cl_force(int N, int P, PairParams 
 
 size_t cell_list_bytes(int N, int P, int nc, bool mixed) {
   const size_t nb = (size_t)N * P, ncells = (size_t)P * nc * nc * nc;
-  return a256(sizeof(int) * nb) + a256((mixed ? 16 : 32) * nb) + 3 * a256(sizeof(int) * ncells) +
+  return a256(sizeof(int) * nb) + 2 * a256((mixed ? 16 : 32) * nb) + 3 * a256(sizeof(int) * ncells) +
          a256(sizeof(int) * nb);
 }
 
@@ -217,6 +232,7 @@ void cell_list_layout(CellList &cl, char *base, int N, int P, int nc, bool mixed
   size_t off = 0;
   cl.cellof = (int *)(base + off); off += a256(sizeof(int) * nb);
   cl.crd = (void *)(base + off); off += a256((mixed ? 16 : 32) * nb);
+  cl.sorted = (void *)(base + off); off += a256((mixed ? 16 : 32) * nb);
   cl.count = (int *)(base + off); off += a256(sizeof(int) * ncells);
   cl.fill = (int *)(base + off); off += a256(sizeof(int) * ncells);
   cl.start = (int *)(base + off); off += a256(sizeof(int) * ncells);
@@ -236,13 +252,16 @@ cudaError_t cell_list_forces(const double *pos, double *F, int N, int P, const P
   cl_scan<<<1, SCAN_THREADS, 0, s>>>(cl.count, cl.start, cl.ncells);
   cl_scatter<<<g, 256, 0, s>>>(cl.cellof, N, P, cl.start, cl.fill, cl.list);
   cl_sort<<<(cl.ncells + 255) / 256, 256, 0, s>>>(cl.start, cl.count, cl.ncells, cl.list);
-  const dim3 grid((N + CL_THREADS - 1) / CL_THREADS, P);
+  if (mixed) cl_gather<true><<<g, 256, 0, s>>>(cl.list, nb, cl.crd, cl.sorted);
+  else cl_gather<false><<<g, 256, 0, s>>>(cl.list, nb, cl.crd, cl.sorted);
+  // as many blocks as the all-pairs kernel, so that every U-bar partial is written
+  const int blocks = ((N + CL_THREADS - 1) / CL_THREADS) * P;
   if (mixed)
-    cl_force<true><<<grid, CL_THREADS, 0, s>>>(N, P, pp, cl.nc, cl.cellof, cl.crd, cl.start, cl.count, cl.list, pos,
-                                               F, ubar_part);
+    cl_force<true><<<blocks, CL_THREADS, 0, s>>>(nb, P, pp, cl.nc, cl.cellof, cl.sorted, cl.start, cl.count, cl.list,
+                                                 pos, F, ubar_part);
   else
-    cl_force<false><<<grid, CL_THREADS, 0, s>>>(N, P, pp, cl.nc, cl.cellof, cl.crd, cl.start, cl.count, cl.list, pos,
-                                                F, ubar_part);
+    cl_force<false><<<blocks, CL_THREADS, 0, s>>>(nb, P, pp, cl.nc, cl.cellof, cl.sorted, cl.start, cl.count, cl.list,
+                                                  pos, F, ubar_part);
   return cudaGetLastError();
 }
 

@@ -23,8 +23,9 @@ struct CellList {
   int ncells;        // P nc^3
   int *cellof;       // [N*P] cell of bead (l, j), index l*P + j
   void *crd;         // [N*P] wrapped coordinates: uint4 fixed point (MIXED) or double4 (float64)
+  void *sorted;      // [N*P] the same coordinates in cell order (slot q holds bead list[q])
   int *count, *fill, *start;  // [ncells]
-  int *list;         // [N*P] particle indices grouped by cell, ascending within a cell
+  int *list;         // [N*P] bead indices l*P + j grouped by cell, ascending within a cell
 };
 
 // Bytes of the cell-list buffers for N particles, P beads, nc cells per side.

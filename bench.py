@@ -180,6 +180,23 @@ def roofline(stage_ms_per_eval, args, sm_mhz, peaks):
     return obj
 
 
+# ----------------------------------------------------- replicas across ranks
+def reduce_max(x, dist, device):
+    """The largest of every rank's x (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units_per_rank, slowest_seconds):
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank units; the job takes as long as its slowest rank."""
+    return world * units_per_rank / slowest_seconds
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -199,11 +216,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, dev)
 
     N, P, beta = args.N, args.P, args.beta
     wP = inputs.omega_P(P, beta)
@@ -248,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         total_ms = max_over_ranks(sum(step_ms))
         results[prec] = {
-            "value": world * args.steps / (total_ms * 1e-3),
+            "value": aggregate_rate(world, args.steps, total_ms * 1e-3),
             "ms_per_step": total_ms / args.steps,
             "median_ms": statistics.median(step_ms),
             "stage_ms": (stage_ms / max(n_prof, 1)).tolist(),
@@ -267,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                 eng.forces_host(pos_h, F_h)
             e2e_s = max_over_ranks(time.perf_counter() - t0)
             barrier()
-            results["e2e"] = {"value": world * args.steps / e2e_s, "unit": "evals/s",
+            results["e2e"] = {"value": aggregate_rate(world, args.steps, e2e_s), "unit": "evals/s",
                               "h2d_bytes_per_step": pos_h.numel() * 8,
                               "d2h_bytes_per_step": F_h.numel() * 8 + 8,
                               "api": "bpimd_exchange_energy_forces_host (pinned host buffers)"}
@@ -333,7 +346,7 @@ def md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world):
         ms = max_over_ranks(e0.elapsed_time(e1))
         en = md.step(x, v, 1).cpu().tolist()
         md.close()
-        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "MD steps/s", "steps": steps,
+        out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "MD steps/s", "steps": steps,
                      "gpu_launches": 7 * steps + 5,
                      "ms_per_step": ms / steps, "energies_after": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
     out["config"] = {"workload": f"trapped bosons N={args.N} P={args.P} beta={args.beta:g}, harmonic trap w0=1, "
@@ -382,8 +395,8 @@ def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
         barrier()
         eng.sync()
         ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
-        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "batch evals/s",
-                     "replica_evals_per_s": world * steps * eng.R / (ms * 1e-3),
+        out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "batch evals/s",
+                     "replica_evals_per_s": aggregate_rate(world, steps * eng.R, ms * 1e-3),
                      "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": 4 * steps,
                      "tuning": {"choice": list(tuned["choice"]), "cached": tuned["cached"]}}
         eng.close()
@@ -434,7 +447,7 @@ def helium_throughput(args, dev, max_over_ranks, barrier, world):
         ms = max_over_ranks(e0.elapsed_time(e1))
         en = md.step(x, v, 1).cpu().tolist()
         md.close()
-        out[prec] = {"value": world * steps / (ms * 1e-3), "unit": "MD steps/s", "steps": steps,
+        out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "MD steps/s", "steps": steps,
                      "ms_per_step": ms / steps,
                      "energies_after_K": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
     out["config"] = {"workload": f"liquid helium N={N} (FCC {cells}^3 x 4) P={P} T=1.5 K rho=0.0218/A^3 "

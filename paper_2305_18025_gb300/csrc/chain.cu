@@ -116,7 +116,8 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     // Staging warps are the lead's warps off warp 0's sub-partition (warp id
     // not a multiple of 4), numbered q = 0, 1, ...: q < 8 stage four rows each
     // of the diagonal block, 8 <= q < 12 eight rows each of the off-diagonal
-    // block, q == 12 forms the prefix sums (forward recursion).
+    // block, q == 12 forms the prefix sums (forward recursion), q == 13
+    // copies each finished tile of Y to global memory one period later.
     if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
@@ -138,16 +139,27 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
         chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
                           sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
-                          sm.Ym, sm.Ye, YRING - 1, gYm, gYe);
+                          sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
       } else if (q >= 0 && q < 8) {
         if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
           stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
+      } else if (q == 13) {
+        // export Y of tile t-1 from the ring to global memory, off the chain
+        // warp (a release barrier after global stores would wait for them)
+        if (t >= 1) {
+          const int v = (t - 1) * TILE + lane + 1;
+          if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
+        }
       } else if (!BWD && q == 12) {
         prefix_tile(w, t, carry);
       }
       cluster.sync();
+    }
+    if (q == 13) {  // the last tile's Y
+      const int v = (NT - 1) * TILE + lane + 1;
+      if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
     }
     if (!BWD) {
       // V^{[1,N]} = C[N] - ln(y_N)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
@@ -288,8 +300,8 @@ constexpr size_t chain_smem_bytes(int N) {
   return lead > help ? lead : help;
 }
 static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
-static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 18 && CHAIN_THREADS / 32 <= 32,
-              "the lead needs 13 staging warps off warp 0's sub-partition; a bulk CTA has at most 32 Y slots");
+static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
+              "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 

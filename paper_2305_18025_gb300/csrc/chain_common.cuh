@@ -194,8 +194,8 @@ __device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, d
 // The 32 dependent steps of row tile t, run by one warp.  A is this lane's
 // row sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
 // coefficient.  K (diagonal, c-scaled) and H (to tile t+1) are the staged
-// blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and at gYm/gYe[v] in
-// global memory.  On return nxt holds the partial sums of tile t+1's rows over
+// blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and, unless gYm is
+// null, at gYm/gYe[v] in global memory.  On return nxt holds the partial sums of tile t+1's rows over
 // source tile t.
 // 32 steps, no branches and no stores: rows past N and finished rows see
 // extended zeros in the staged blocks, and row j's accumulator is final after
@@ -250,8 +250,10 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
     const xd yn = xnorm_int(acc);
     Ym[(row + 1) & ymask] = yn.m;
     Ye[(row + 1) & ymask] = yn.e;
-    gYm[row + 1] = yn.m;
-    gYe[row + 1] = yn.e;
+    if (gYm) {
+      gYm[row + 1] = yn.m;
+      gYe[row + 1] = yn.e;
+    }
   }
   nxt = xnorm_int(nxt);
 }

@@ -5,7 +5,7 @@ Metric: exchange V_B + force evaluations per second for N = 1024 bosons with
 P = 32 beads (beta = 1, m = hbar = 1, omega_P = sqrt(P)/beta), trapped-boson
 positions (centres N(0,1), bead offsets N(0,0.1), seed 3), in the mixed
 float32/float64 form (the reported `value`) and the plain float64 form
-(`fp64`).  A step is one full evaluation: bead pass, pair factors, forward
+(`fp64`).  A step is one full evaluation: bead pass with pair factors, forward
 and backward recursions with the prefix sums and V_B, probabilities with all
 exterior-bead forces.  The line also carries MD steps/s (`md`) of the same
 system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays),
@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exchange V_B+force evals/s at N=1024,P=32 (mixed vs FP64 GPU); MD steps/s"
 N_DEF, P_DEF, BETA_DEF, SEED_DEF = 1024, 32, 1.0, 3
-LAUNCHES_PER_EVAL = 4          # bead pass, pair factors, recursions (2 clusters), probabilities + forces
+LAUNCHES_PER_EVAL = 3          # bead pass + pair factors, recursions (2 clusters), probabilities + forces
 DFMA_LATENCY_CYCLES = 64       # measured on GB300: dependent float64 FMA latency
 FLUSH_BYTES = 256 << 20        # > 129 MB L2
 
@@ -147,7 +147,7 @@ def load_traffic(kernel):
     return ent.get("dram_bytes_per_launch")
 
 
-def roofline(stage_ms_per_eval, args, sm_mhz, peaks):
+def roofline(stage_ms_per_eval, args, sm_mhz, peaks, precision="mixed"):
     """Roofline object for the dominant stage."""
     import numpy as np
     from paper_2305_18025_gb300.bpimd import STAGE_NAMES
@@ -165,8 +165,12 @@ def roofline(stage_ms_per_eval, args, sm_mhz, peaks):
                "achieved": achieved, "peak": peak, "unit": "chain steps/s",
                "frac": achieved / peak,
                "peak_source": f"measured DFMA latency {DFMA_LATENCY_CYCLES} cycles at the sampled SM clock"}
-    elif name == "bead_pass":
-        bytes_ = N * P * 24 + N * max(P - 2, 0) * 24 + N * 8 * 12
+    elif name == "prep":
+        # positions read once, interior forces written, the per-particle
+        # state, and both copies of g (mantissa + int exponent per pair)
+        mant = 4 if precision == "mixed" else 8
+        bytes_ = (N * P * 24 + N * max(P - 2, 0) * 24 + N * 8 * 10
+                  + 2 * (N * (N + 1) // 2) * (mant + 4))
         achieved = bytes_ / t / 1e9
         obj = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": achieved / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
@@ -306,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms": dict(zip(STAGE_NAMES, mixed["stage_ms"])),
         "e2e": results["e2e"],
         "roofline": roofline(mixed["stage_ms"], args, clocks.get("sm_mhz"), peaks),
-        "roofline_fp64": roofline(fp64["stage_ms"], args, clocks.get("sm_mhz"), peaks),
+        "roofline_fp64": roofline(fp64["stage_ms"], args, clocks.get("sm_mhz"), peaks, "fp64"),
         "clocks": clocks,
         "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
         "V_B": {"mixed": mixed["V_B"], "fp64": fp64["V_B"]},
@@ -347,7 +351,7 @@ def md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world):
         en = md.step(x, v, 1).cpu().tolist()
         md.close()
         out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "MD steps/s", "steps": steps,
-                     "gpu_launches": 7 * steps + 5,
+                     "gpu_launches": (LAUNCHES_PER_EVAL + 3) * steps + LAUNCHES_PER_EVAL + 1,
                      "ms_per_step": ms / steps, "energies_after": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
     out["config"] = {"workload": f"trapped bosons N={args.N} P={args.P} beta={args.beta:g}, harmonic trap w0=1, "
                                  "Gaussian repulsion g=3 s=0.5 between equal-index beads",
@@ -397,7 +401,7 @@ def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
         ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
         out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "batch evals/s",
                      "replica_evals_per_s": aggregate_rate(world, steps * eng.R, ms * 1e-3),
-                     "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": 4 * steps,
+                     "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": LAUNCHES_PER_EVAL * steps,
                      "tuning": {"choice": list(tuned["choice"]), "cached": tuned["cached"]}}
         eng.close()
     out["config"] = {"workload": f"{args.batch_replicas} independent trapped replicas, N~U[16,512], "

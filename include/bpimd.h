@@ -218,20 +218,23 @@ int bpimd_exchange_energy_forces_batched(bpimd_ctx *ctx, const double *positions
 int bpimd_batch_info(bpimd_ctx *ctx, int32_t *R, int64_t *elements, int64_t *offsets);
 
 /* Launch shape of the batched pair-factor and probability passes: at most
- * blocks_per_sm x (number of SMs) CTAs each (1..64; default 8).  Set by the
+ * blocks_per_sm x (number of SMs) CTAs each (1..64; default 8); the
+ * pair-factor CTAs run in the same launch as the bead pass, after its CTAs.  Set by the
  * autotuner (paper_2305_18025_gb300/autotune.py); results do not depend on it. */
 int bpimd_batch_set_tuning(bpimd_ctx *ctx, int32_t pair_blocks_per_sm, int32_t prob_blocks_per_sm);
 
 /* ------------------------------------------------------------- profiling */
 /* Stage timing with CUDA events recorded on the context stream around each
  * kernel of an evaluation.  Stage order:
- *   0 bead pass, 1 pair Boltzmann factors, 2 forward+backward recursions
- *   (with the prefix sums, V_B and the probability normaliser),
- *   3 connection probabilities + exterior-bead forces. */
-#define BPIMD_NUM_STAGES 4
+ *   0 bead pass and pair Boltzmann factors (one launch),
+ *   1 forward+backward recursions (with the prefix sums, V_B and the
+ *     probability normaliser),
+ *   2 connection probabilities + exterior-bead forces. */
+#define BPIMD_NUM_STAGES 3
 
 /* Start recording stage events for up to `max_evals` following evaluations
- * (older records are discarded).  Adds 5 event records per evaluation. */
+ * (older records are discarded).  Adds BPIMD_NUM_STAGES + 1 event records per
+ * evaluation. */
 int bpimd_profile_begin(bpimd_ctx *ctx, int max_evals);
 
 /* Stop recording, synchronise, and write the summed device time of each stage

@@ -37,8 +37,8 @@ EXPORTED = [
     "bpimd_batch_set_tuning",
 ]
 BATCH_MAX_N = 4096
-BPIMD_NUM_STAGES = 4
-STAGE_NAMES = ["bead_pass", "pair_factors", "recursions", "prob_forces"]
+BPIMD_NUM_STAGES = 3
+STAGE_NAMES = ["prep", "recursions", "prob_forces"]
 
 
 class bpimd_config(ctypes.Structure):

@@ -74,8 +74,6 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.link = (double *)take(sizeof(double) * N);
   w.ccm = (double *)take(sizeof(double) * N);
   w.cce = (int *)take(sizeof(int) * N);
-  w.icm = (double *)take(sizeof(double) * N);
-  w.ice = (int *)take(sizeof(int) * N);
   w.C = (double *)take(sizeof(double) * (N + 1));
   w.gm = (void *)take(gm_bytes);
   w.ge = (int *)take(sizeof(int) * gelems);
@@ -106,14 +104,12 @@ int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
     ev = &ctx->prof_events[(size_t)ctx->prof_count++ * (BPIMD_NUM_STAGES + 1)];
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
-  if (launch_bead_pass(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_prep(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(1);
-  if (launch_gmat(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  mark(2);
   if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  mark(3);
+  mark(2);
   if (launch_prob_forces(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  mark(4);
+  mark(3);
   ctx->evaluated = true;
   return BPIMD_OK;
 }

@@ -1,7 +1,7 @@
 // C ABI of replica batches: many independent systems of uneven N, P, beta
-// (same mass and precision) evaluated together, four launches per batch
-// (bead pass, pair factors, both recursions of every replica, probabilities
-// and forces), whatever the number of replicas.
+// (same mass and precision) evaluated together, three launches per batch
+// (bead pass with pair factors, both recursions of every replica,
+// probabilities and forces), whatever the number of replicas.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -29,21 +29,17 @@ int evaluate_batched(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) 
     ev = &ctx->prof_events[(size_t)ctx->prof_count++ * (BPIMD_NUM_STAGES + 1)];
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
-  if (launch_bead_pass_batched(ctx->d_ws, ctx->d_bead_tab, ctx->n_bead_tab, ctx->d_off, mixed, pos, F, s) !=
-      cudaSuccess)
+  if (launch_prep_batched(ctx->d_ws, ctx->d_bead_tab, ctx->n_bead_tab, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off,
+                          mixed, pos, F, ctx->tune_gmat_bpsm, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(1);
-  if (launch_gmat_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, mixed, false, ctx->tune_gmat_bpsm, s) !=
-      cudaSuccess)
-    return BPIMD_ERR_CUDA;
-  mark(2);
   if (launch_chains_batched(ctx->d_ws, ctx->d_order, ctx->R, ctx->maxN, mixed, V_B, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
-  mark(3);
+  mark(2);
   if (launch_prob_forces_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off, mixed, pos, F,
                                  ctx->tune_prob_bpsm, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
-  mark(4);
+  mark(3);
   ctx->evaluated = true;
   return BPIMD_OK;
 }
@@ -148,8 +144,8 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
             cudaMemcpyAsync(ctx->d_order, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync(ctx->d_off, ctx->h_off.data(), sizeof(long long) * R, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
-            launch_gmat_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, cfg->precision == BPIMD_MIXED, true,
-                                8, s) == cudaSuccess &&
+            launch_gmat_padding_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, cfg->precision == BPIMD_MIXED,
+                                        s) == cudaSuccess &&
             cudaMallocHost(&ctx->host_status, sizeof(int)) == cudaSuccess &&
             cudaStreamSynchronize(s) == cudaSuccess;  // host tables go out of scope
   if (!ok) {

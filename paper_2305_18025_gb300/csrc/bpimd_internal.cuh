@@ -125,7 +125,6 @@ struct Workspace {
                         // a bead difference is formed in float32 to float32 accuracy
   double *Eint, *link;  // [N]
   double *ccm; int *cce;          // c_{i+1} = exp(beta link_i)/(i+1), extended
-  double *icm; int *ice;          // 1/c_{i+1}, extended
   double *C;            // [N+1] prefix sums of E_int + link
   // g matrix, tile-packed triangle: block (t, s), s <= t, at (t(t+1)/2 + s) * TILE2,
   // entry [i][j] = g for a = s*TILE + i (bead 1 particle), b = t*TILE + j (bead P particle)
@@ -137,7 +136,7 @@ struct Workspace {
   void *gbm;
   int *gbe;
   // recursion outputs (extended): forward y[0..N]; backward Yb[0..N]
-  // (Yb[w] = mu_{N-1-w} 0-based; the backward row sums are B_{a+1} = Yb[N-a] / c_a)
+  // (Yb[w] = mu_{N-1-w} 0-based; the backward row sums are B_{a+1} = Yb[N-a] / c_{a}, 1-based c)
   double *yfm; int *yfe;
   double *ybm; int *ybe;
   // alpha_a = y_a / (N y_N), a = 0..N-1, extended (float mantissa for MIXED),
@@ -176,6 +175,19 @@ __device__ __forceinline__ float fixdiff(unsigned a, unsigned b, float Lscale) {
   return (float)(int)(a - b) * Lscale;
 }
 
+// Endpoint copies of the MIXED path, formed the same way wherever a kernel
+// needs them: a coordinate split into float32 high and low parts
+// (x = hi + lo to ~2^-48 relative), or, in a box, its fraction of L as a
+// 32-bit fixed-point number.
+__device__ __forceinline__ void split_hi_lo(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+__device__ __forceinline__ unsigned to_fixed(double x, double invL) {
+  const double f = x * invL - floor(x * invL);
+  return (unsigned)fmin(f * 4294967296.0, 4294967295.0);
+}
+
 // Periodic box of side L (L <= 0: open boundaries).
 inline void set_box(Workspace &w, double L) {
   w.L = L > 0.0 ? L : 0.0;
@@ -189,11 +201,12 @@ inline void set_box(Workspace &w, double L) {
 size_t layout_workspace(Workspace &w, char *base);
 
 // kernel launchers (stream-ordered)
-cudaError_t launch_bead_pass(const Workspace &w, const double *pos, double *F, cudaStream_t s);
+// bead pass and pair factors in one launch (the pair-factor blocks read the
+// endpoint beads from the positions themselves, so the two run side by side)
+cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 // fill the pair-factor entries outside a <= b < N (fixed for a given N) with
-// extended zeros; needed once per workspace before the first launch_gmat
+// extended zeros; needed once per workspace before the first launch_prep
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s);
-cudaError_t launch_gmat(const Workspace &w, cudaStream_t s);
 // both recursions, prefix sums, V_B (device scalar, may be null), normaliser, alpha
 cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
 // connection probabilities and all exterior-bead forces
@@ -208,10 +221,13 @@ cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, c
 // the pair factors and the probability pass; off[r] is the element offset of
 // replica r in the packed position/force arrays; order lists replicas by
 // decreasing N.
-cudaError_t launch_bead_pass_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
-                                     bool mixed, const double *pos, double *F, cudaStream_t s);
-cudaError_t launch_gmat_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed, bool padding,
+// bead pass (bead_tab: (replica, first particle)) and pair factors (blk_tab:
+// (replica, block of g), at most blocks_per_sm * SMs blocks) in one launch
+cudaError_t launch_prep_batched(const Workspace *ws, const int2 *bead_tab, int nbead, const int2 *blk_tab,
+                                int nblk, const long long *off, bool mixed, const double *pos, double *F,
                                 int blocks_per_sm, cudaStream_t s);
+cudaError_t launch_gmat_padding_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed,
+                                        cudaStream_t s);
 cudaError_t launch_chains_batched(const Workspace *ws, const int *order, int R, int maxN, bool mixed, double *V_B,
                                   cudaStream_t s);
 cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
@@ -221,7 +237,8 @@ cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int
 __device__ __forceinline__ xd backward_row_sum(const Workspace &w, int a) {
   const xd Y{w.ybm[w.N - a], w.ybe[w.N - a]};
   if (a == 0) return Y;  // B_1 = Y_N
-  return xmul(Y, xd{w.icm[a - 1], w.ice[a - 1]});
+  // mu_a = c_a B_{a+1}: divide the mantissas, subtract the exponents
+  return xnorm(Y.m / w.ccm[a - 1], Y.e - w.cce[a - 1]);
 }
 
 // Pr[l -> l+1] = 1 - y_l B_{l+1} / (N y_N); in 0-based particle index p (row p,

@@ -96,8 +96,7 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   if (cudaMemsetAsync(w.rowcnt, 0, sizeof(int) * w.NT, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (cudaMemsetAsync(w.colcnt, 0, sizeof(int) * w.NT, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_gmat_padding(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_bead_pass(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (launch_gmat(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  if (launch_prep(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_prob_forces(w, positions, forces, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   return BPIMD_OK;

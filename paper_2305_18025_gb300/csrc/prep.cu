@@ -1,19 +1,152 @@
-// Pair Boltzmann factors and diagnostic potentials.
+// Preparation of one evaluation: the bead pass and the pair Boltzmann
+// factors, in one launch (the first blocks take the bead pass, the rest the
+// pair factors; the pair-factor blocks read the two endpoint beads they need
+// straight from the positions, so neither part waits for the other).
 //
-// gmat: g(u,v) = exp(-beta (1/2) m w_P^2 (r_v^P - r_u^1)^2) for every u <= v --
-// the closing-spring factor of the cycle energy E^{[u,v]} (Eq. e-recurrence-step,
-// last term) -- stored once per evaluation as an extended number 2^x =
-// mantissa(2^frac(x)) * 2^floor(x), x = -beta (1/2)k |d|^2 log2(e).
+// Bead pass, per particle l (one warp for the bead sums, then one lane for the rest):
+//   E_int^{(l)} = (1/2) m w_P^2 sum_{j=1}^{P-1} (r_l^{j+1} - r_l^j)^2     (Eq. e-interior)
+//   link_l      = (1/2) m w_P^2 (r_l^P - r_{l+1}^1)^2, 0 for l = N       (spring of Eq. e-recurrence-step)
+//   interior forces -m w_P^2 (2 r_l^j - r_l^{j+1} - r_l^{j-1}), j=2..P-1  (Eq. intermediate-bead-force)
+//   copies of r_l^1 and r_l^P for the probability pass (MIXED: also as
+//   float32 high/low parts, or 32-bit fixed point in a box), and the
+//   coefficient c_l = exp(beta link_l)/l of the linear-space recursions, as
+//   an extended number.
+// FP64: everything in float64.  MIXED: bead differences formed in float64,
+// rounded to float32; squares, warp sums and interior forces in float32;
+// E_int and link widened to float64.
+//
+// Pair factors: g(u,v) = exp(-beta (1/2) m w_P^2 (r_v^P - r_u^1)^2) for every
+// u <= v -- the closing-spring factor of the cycle energy E^{[u,v]} (Eq.
+// e-recurrence-step, last term) -- stored once per evaluation as an extended
+// number 2^x = mantissa(2^frac(x)) * 2^floor(x), x = -beta (1/2)k |d|^2 log2(e).
 // FP64: float64 difference, square and exp2.  MIXED: difference of the
-// float32 high/low parts of the positions, float32 square, hardware
-// ex2.approx.  The potentials V^{[1,v]}, V^{[u,N]} for diagnostics are
-// computed on demand by diag_potentials_kernel.
+// float32 high/low parts (or fixed-point copies) of the positions, float32
+// square, hardware ex2.approx.  The potentials V^{[1,v]}, V^{[u,N]} for
+// diagnostics are computed on demand by diag_potentials_kernel.
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
 
 namespace bpimd {
 namespace {
+
+constexpr int BEAD_WARPS = BEAD_BLOCK_PARTICLES;  // particles per block (one warp each)
+static_assert(32 * BEAD_WARPS == 256, "bead-pass and pair-factor blocks share one launch shape");
+
+// Particles l0 .. l0+7 of one system (all threads of the block).
+template <bool MIXED>
+__device__ __forceinline__ void bead_pass_body(const Workspace &w, const double *__restrict__ pos,
+                                               double *__restrict__ F, int l0) {
+  __shared__ double eint_s[BEAD_WARPS];
+  __shared__ int finite_s[BEAD_WARPS];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int P = w.P;
+  const double k = w.k;
+  // phase 1: one warp per particle -- interior springs and interior forces
+  {
+    const int l = l0 + wp;
+    bool finite = true;
+    double s64 = 0.0;
+    float s32 = 0.0f;
+    if (l < w.N) {
+      const double *p = pos + (size_t)l * P * 3;
+      double *f = F + (size_t)l * P * 3;
+      for (int j = lane; j < P; j += 32) {
+        const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
+        finite &= isfinite(x) && isfinite(y) && isfinite(z);
+        if (j + 1 < P) {
+          const double dx = mimage(w, p[3 * j + 3] - x), dy = mimage(w, p[3 * j + 4] - y),
+                       dz = mimage(w, p[3 * j + 5] - z);
+          if (MIXED) {
+            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+            s32 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, s32)));
+          } else {
+            s64 = fma(dx, dx, fma(dy, dy, fma(dz, dz, s64)));
+          }
+        }
+        if (j >= 1 && j + 1 < P) {  // interior bead (0-based 1..P-2)
+          const double ax = mimage(w, x - p[3 * j + 3]), ay = mimage(w, y - p[3 * j + 4]),
+                       az = mimage(w, z - p[3 * j + 5]);
+          const double bx = mimage(w, x - p[3 * j - 3]), by = mimage(w, y - p[3 * j - 2]),
+                       bz = mimage(w, z - p[3 * j - 1]);
+          if (MIXED) {
+            const float kf = (float)k;
+            f[3 * j] = (double)(-kf * ((float)ax + (float)bx));
+            f[3 * j + 1] = (double)(-kf * ((float)ay + (float)by));
+            f[3 * j + 2] = (double)(-kf * ((float)az + (float)bz));
+          } else {
+            f[3 * j] = -k * (ax + bx);
+            f[3 * j + 1] = -k * (ay + by);
+            f[3 * j + 2] = -k * (az + bz);
+          }
+        }
+      }
+    }
+    if (MIXED) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s32 += __shfl_xor_sync(0xffffffffu, s32, o);
+      s64 = (double)s32;
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) { eint_s[wp] = w.half_k * s64; finite_s[wp] = finite; }
+  }
+  __syncthreads();
+  // phase 2: one lane per particle -- links, endpoint copies and the
+  // coefficient c (the float64 transcendentals run once per 8 particles)
+  if (wp == 0 && lane < BEAD_WARPS) {
+    const int l = l0 + lane;
+    if (l < w.N) {
+      if (!finite_s[lane]) atomicOr(w.status, ST_NONFINITE);
+      const double *b1 = pos + (size_t)l * P * 3, *bP = b1 + 3 * (P - 1);
+      double lk = 0.0;
+      if (l + 1 < w.N) {
+        const double *n1 = b1 + 3 * P;  // bead 1 of particle l+1
+        const double dx = mimage(w, bP[0] - n1[0]), dy = mimage(w, bP[1] - n1[1]),
+                     dz = mimage(w, bP[2] - n1[2]);
+        if (MIXED) {
+          const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+          lk = w.half_k * (double)fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        } else {
+          lk = w.half_k * fma(dx, dx, fma(dy, dy, dz * dz));
+        }
+      }
+      w.Eint[l] = eint_s[lane];
+      w.link[l] = lk;
+      double *r1 = w.R1 + 4 * (size_t)l, *rp = w.RP + 4 * (size_t)l;
+      r1[0] = b1[0]; r1[1] = b1[1]; r1[2] = b1[2]; r1[3] = 0.0;
+      rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
+      if (MIXED && w.pbc) {  // fixed-point fractions of the box
+        *(uint4 *)(w.R1s + 8 * (size_t)l) =
+            make_uint4(to_fixed(b1[0], w.invL), to_fixed(b1[1], w.invL), to_fixed(b1[2], w.invL), 0u);
+        *(uint4 *)(w.RPs + 8 * (size_t)l) =
+            make_uint4(to_fixed(bP[0], w.invL), to_fixed(bP[1], w.invL), to_fixed(bP[2], w.invL), 0u);
+      } else if (MIXED) {  // float32 high + low parts
+        float h1[3], l1[3], hP[3], lP[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          split_hi_lo(b1[c], h1[c], l1[c]);
+          split_hi_lo(bP[c], hP[c], lP[c]);
+        }
+        float4 *s1 = (float4 *)(w.R1s + 8 * (size_t)l), *sp = (float4 *)(w.RPs + 8 * (size_t)l);
+        s1[0] = make_float4(h1[0], h1[1], h1[2], 0.0f);
+        s1[1] = make_float4(l1[0], l1[1], l1[2], 0.0f);
+        sp[0] = make_float4(hP[0], hP[1], hP[2], 0.0f);
+        sp[1] = make_float4(lP[0], lP[1], lP[2], 0.0f);
+      }
+      // c_{l+1} = exp(beta link_l) / (l+1) = 2^x, x = beta link_l log2(e) - log2(l+1)
+      // |x| is clamped to 2^28 so that exponent sums stay in int32
+      const double x = fmin(fmax(w.beta * lk * LOG2E - log2((double)(l + 1)), -268435456.0), 268435456.0);
+      const double n = floor(x);
+      const xd c = xnorm(exp2(x - n), (int)n);
+      w.ccm[l] = c.m;
+      w.cce[l] = c.e;
+    }
+  }
+}
+
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -32,20 +165,59 @@ __device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
   s = blk - tt * (tt + 1) / 2;
 }
 
-// g for one pair from the bead-P position of b and the bead-1 position of a:
-// returns the mantissa (float or double) and sets the exponent.
+// Endpoint beads of one block of g, staged in shared memory: side 0 holds
+// bead P of the 32 particles b of row tile t, side 1 bead 1 of the 32
+// particles a of source tile s.  FP64: x, y, z as doubles.  MIXED: float32
+// high parts then low parts (8 floats), or in a box the 32-bit fixed-point
+// fractions of L (4 words); the same conversions as the bead pass's copies.
+struct EndTiles {
+  double v[2][TILE][4];
+};
+
 template <bool MIXED>
-__device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int a, int b, int &e) {
+__device__ __forceinline__ void stage_endpoints(const Workspace &w, const double *__restrict__ pos, int t, int s,
+                                                EndTiles &E) {
+  if (threadIdx.x < 2 * TILE) {
+    const int side = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = (side ? s : t) * TILE + lane;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (q < w.N) {
+      const double *p = pos + ((size_t)q * w.P + (side ? 0 : w.P - 1)) * 3;
+      x = p[0]; y = p[1]; z = p[2];
+    }
+    double *d = E.v[side][lane];
+    if (!MIXED) {
+      d[0] = x; d[1] = y; d[2] = z;
+    } else if (w.pbc) {
+      *(uint4 *)d = make_uint4(to_fixed(x, w.invL), to_fixed(y, w.invL), to_fixed(z, w.invL), 0u);
+    } else {
+      float hx, lx, hy, ly, hz, lz;
+      split_hi_lo(x, hx, lx);
+      split_hi_lo(y, hy, ly);
+      split_hi_lo(z, hz, lz);
+      ((float4 *)d)[0] = make_float4(hx, hy, hz, 0.0f);
+      ((float4 *)d)[1] = make_float4(lx, ly, lz, 0.0f);
+    }
+  }
+  __syncthreads();
+}
+
+// g for one pair from the staged bead-P position of b (slot j of side 0) and
+// bead-1 position of a (slot i of side 1): returns the mantissa (float or
+// double) and sets the exponent.
+template <bool MIXED>
+__device__ __forceinline__ double pair_factor(const Workspace &w, double cx, const EndTiles &E, int i, int j,
+                                              int &e) {
   if (MIXED) {
     float fx, fy, fz;
     if (w.pbc) {  // minimum image from the fixed-point copies
-      const uint4 ub = *(const uint4 *)(w.RPs + 8 * (size_t)b), ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
+      const uint4 ub = *(const uint4 *)E.v[0][j], ua = *(const uint4 *)E.v[1][i];
       fx = fixdiff(ub.x, ua.x, w.Lscale);
       fy = fixdiff(ub.y, ua.y, w.Lscale);
       fz = fixdiff(ub.z, ua.z, w.Lscale);
     } else {
-      const float4 bh = *(const float4 *)(w.RPs + 8 * (size_t)b), bl = *(const float4 *)(w.RPs + 8 * (size_t)b + 4);
-      const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a), al = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
+      const float4 bh = ((const float4 *)E.v[0][j])[0], bl = ((const float4 *)E.v[0][j])[1];
+      const float4 ah = ((const float4 *)E.v[1][i])[0], al = ((const float4 *)E.v[1][i])[1];
       fx = (bh.x - ah.x) + (bl.x - al.x);
       fy = (bh.y - ah.y) + (bl.y - al.y);
       fz = (bh.z - ah.z) + (bl.z - al.z);
@@ -58,8 +230,8 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int
     if (mm >= 2.0f) { mm *= 0.5f; e += 1; }
     return mm;
   } else {
-    const double dx = mimage(w, w.RP[4 * b] - w.R1[4 * a]), dy = mimage(w, w.RP[4 * b + 1] - w.R1[4 * a + 1]),
-                 dz = mimage(w, w.RP[4 * b + 2] - w.R1[4 * a + 2]);
+    const double *rb = E.v[0][j], *ra = E.v[1][i];
+    const double dx = mimage(w, rb[0] - ra[0]), dy = mimage(w, rb[1] - ra[1]), dz = mimage(w, rb[2] - ra[2]);
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
     const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
     const double n = floor(x);
@@ -77,8 +249,9 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, int
 // (gmat_padding_kernel fills them once).
 // One block of g (all threads of the CTA; Tm/Te: 32 x 33 shared tiles).
 template <bool MIXED>
-__device__ __forceinline__ void gmat_block(const Workspace &w, int blk,
-                                           typename std::conditional<MIXED, float, double>::type *Tm, int *Te) {
+__device__ __forceinline__ void gmat_block(const Workspace &w, const double *__restrict__ pos, int blk,
+                                           typename std::conditional<MIXED, float, double>::type *Tm, int *Te,
+                                           EndTiles &E) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   const double cx = -w.beta * w.half_k * LOG2E;
   const int N = w.N;
@@ -86,13 +259,14 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, int blk,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int t, s;
   block_coords(blk, t, s);
+  stage_endpoints<MIXED>(w, pos, t, s, E);
   {
     const int b = t * TILE + lane;
     for (int i = warp; i < TILE; i += 8) {
       const int a = s * TILE + i;
       if (b < N && a <= b) {
         int e;
-        const M_t m = (M_t)pair_factor<MIXED>(w, cx, a, b, e);
+        const M_t m = (M_t)pair_factor<MIXED>(w, cx, E, i, lane, e);
         const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
         gm[idx] = m;
         w.ge[idx] = e;
@@ -118,24 +292,43 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, int blk,
   __syncthreads();
 }
 
+// One evaluation's preparation: blocks 0..nbead-1 run the bead pass (8
+// particles each), the others stride over the blocks of g.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) gmat_kernel(Workspace w) {
+__global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__restrict__ pos,
+                                                   double *__restrict__ F, int nbead) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
-  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) gmat_block<MIXED>(w, blk, Tm, Te);
+  __shared__ EndTiles E;
+  if ((int)blockIdx.x < nbead) {
+    bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
+    return;
+  }
+  for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) gmat_block<MIXED>(w, pos, blk, Tm, Te, E);
 }
 
-// Replica batch: entry k of tab is (replica, block).
+// Replica batch: bead_tab[k] = (replica, first particle), blk_tab[k] =
+// (replica, block of g); positions and forces of replica r start at element
+// off[r] of the packed arrays.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) gmat_batched(const Workspace *__restrict__ ws, const int2 *__restrict__ tab,
-                                                    int ntab) {
+__global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict__ ws,
+                                                    const int2 *__restrict__ bead_tab, int nbead,
+                                                    const int2 *__restrict__ blk_tab, int nblk,
+                                                    const long long *__restrict__ off,
+                                                    const double *__restrict__ pos, double *__restrict__ F) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
-  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
-    const int2 e = tab[k];
-    gmat_block<MIXED>(ws[e.x], e.y, Tm, Te);
+  __shared__ EndTiles E;
+  if ((int)blockIdx.x < nbead) {
+    const int2 e = bead_tab[blockIdx.x];
+    bead_pass_body<MIXED>(ws[e.x], pos + off[e.x], F + off[e.x], e.y);
+    return;
+  }
+  for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
+    const int2 e = blk_tab[k];
+    gmat_block<MIXED>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
   }
 }
 
@@ -196,11 +389,12 @@ cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmat(const Workspace &w, cudaStream_t s) {
-  const int sms = sm_count();
-  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
-  if (w.mixed) gmat_kernel<true><<<grid, 256, 0, s>>>(w);
-  else gmat_kernel<false><<<grid, 256, 0, s>>>(w);
+cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
+  const int nbead = (w.N + BEAD_WARPS - 1) / BEAD_WARPS;
+  const int cap = sm_count() * 8;
+  const int grid = nbead + (w.NB < cap ? w.NB : cap);
+  if (w.mixed) prep_kernel<true><<<grid, 256, 0, s>>>(w, pos, F, nbead);
+  else prep_kernel<false><<<grid, 256, 0, s>>>(w, pos, F, nbead);
   return cudaGetLastError();
 }
 
@@ -212,19 +406,24 @@ cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmat_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed, bool padding,
+cudaError_t launch_prep_batched(const Workspace *ws, const int2 *bead_tab, int nbead, const int2 *blk_tab,
+                                int nblk, const long long *off, bool mixed, const double *pos, double *F,
                                 int blocks_per_sm, cudaStream_t s) {
+  if (nbead <= 0 && nblk <= 0) return cudaSuccess;
+  const int cap = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 8);
+  const int grid = nbead + (nblk < cap ? nblk : cap);
+  if (mixed) prep_batched<true><<<grid, 256, 0, s>>>(ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
+  else prep_batched<false><<<grid, 256, 0, s>>>(ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmat_padding_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed,
+                                        cudaStream_t s) {
   if (ntab <= 0) return cudaSuccess;
-  const int sms = sm_count();
-  const int cap = sms * (blocks_per_sm > 0 ? blocks_per_sm : 8);
+  const int cap = sm_count() * 8;
   const int grid = ntab < cap ? ntab : cap;
-  if (padding) {
-    if (mixed) gmat_padding_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab);
-    else gmat_padding_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab);
-  } else {
-    if (mixed) gmat_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab);
-    else gmat_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab);
-  }
+  if (mixed) gmat_padding_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab);
+  else gmat_padding_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab);
   return cudaGetLastError();
 }
 

@@ -115,7 +115,7 @@ struct Workspace {
   // minimum image of its beads.  MIXED keeps the bead-1/bead-P copies in a box
   // as 32-bit fixed-point fractions of L (R1s/RPs reinterpreted as uint32
   // x, y, z, 0), whose wrap-around integer difference is the minimum image.
-  double L, invL;
+  double L, invL, invL32;  // invL32 = 2^32 / L
   float Lscale;  // L / 2^32
   int pbc;       // L > 0 (an integer test: a float64 compare would use the slow float64 pipe)
   // O(N) per-particle state
@@ -176,22 +176,39 @@ __device__ __forceinline__ float fixdiff(unsigned a, unsigned b, float Lscale) {
 }
 
 // Endpoint copies of the MIXED path, formed the same way wherever a kernel
-// needs them: a coordinate split into float32 high and low parts
-// (x = hi + lo to ~2^-48 relative), or, in a box, its fraction of L as a
-// 32-bit fixed-point number.
+// needs them, with integer and float32 instructions only (the float64 pipe is
+// the scarce one):
+//  * a coordinate split into float32 high and low parts, x = hi + lo to
+//    2^-46 relative: hi is x with its significand cut to 24 bits, lo the next
+//    23 bits of the significand (both exact);
+//  * in a box, its fraction of L as a 32-bit fixed-point number,
+//    floor(x 2^32 / L) mod 2^32 (invL32 = 2^32 / L).
 __device__ __forceinline__ void split_hi_lo(double x, float &hi, float &lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  if (E >= 943 && E <= 1150) {  // |x| in [2^-80, 2^128): both parts normal floats
+    hi = __uint_as_float(sgn | ((unsigned)(E - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    // bits 28..6 of the significand as an integer t < 2^23, times 2^(E - 1069)
+    const float t = __uint_as_float(0x4b000000u | (unsigned)((b >> 6) & 0x7fffffu)) - 8388608.0f;
+    lo = __uint_as_float(__float_as_uint(t * __uint_as_float((unsigned)(E - 942) << 23)) | sgn);
+  } else if (E == 0) {  // zero (and float64 subnormals, far below float32)
+    hi = __uint_as_float(sgn);
+    lo = hi;
+  } else {  // tiny, huge or non-finite: rounded parts
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  }
 }
-__device__ __forceinline__ unsigned to_fixed(double x, double invL) {
-  const double f = x * invL - floor(x * invL);
-  return (unsigned)fmin(f * 4294967296.0, 4294967295.0);
+__device__ __forceinline__ unsigned to_fixed(double x, double invL32) {
+  return (unsigned)(unsigned long long)__double2ll_rd(x * invL32);
 }
 
 // Periodic box of side L (L <= 0: open boundaries).
 inline void set_box(Workspace &w, double L) {
   w.L = L > 0.0 ? L : 0.0;
   w.invL = L > 0.0 ? 1.0 / L : 0.0;
+  w.invL32 = w.invL * 4294967296.0;
   w.Lscale = (float)(w.L / 4294967296.0);
   w.pbc = L > 0.0 ? 1 : 0;
 }

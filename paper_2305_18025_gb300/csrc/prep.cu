@@ -33,6 +33,54 @@ namespace {
 constexpr int BEAD_WARPS = BEAD_BLOCK_PARTICLES;  // particles per block (one warp each)
 static_assert(32 * BEAD_WARPS == 256, "bead-pass and pair-factor blocks share one launch shape");
 
+// Non-finite test on the exponent bits (integer instructions only).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
+// Phase 1 of the bead pass for one particle (one warp): lane j of each chunk
+// of 32 beads forms the spring vector d_j = r^{j+1} - r^j (minimum image in a
+// box) once; the interior force on bead j is k (d_j - d_{j-1}), with d_{j-1}
+// taken from the neighbouring lane (lane 0 from lane 31 of the previous chunk).
+// Adds sum |d_j|^2 to s32 (MIXED) or s64 (FP64).
+template <bool MIXED, bool PBC>
+__device__ __forceinline__ void bead_springs(const Workspace &w, const double *__restrict__ p,
+                                             double *__restrict__ f, int lane, bool &finite, float &s32,
+                                             double &s64) {
+  using D_t = typename std::conditional<MIXED, float, double>::type;
+  const int P = w.P;
+  const D_t kk = (D_t)w.k;
+  D_t cx = 0, cy = 0, cz = 0;  // d_{j0-1} carried from the previous chunk
+  for (int j0 = 0; j0 < P; j0 += 32) {
+    const int j = j0 + lane;
+    double dx = 0.0, dy = 0.0, dz = 0.0;
+    if (j < P) {
+      const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
+      finite &= finite_bits(x) && finite_bits(y) && finite_bits(z);
+      if (j + 1 < P) {
+        dx = p[3 * j + 3] - x;
+        dy = p[3 * j + 4] - y;
+        dz = p[3 * j + 5] - z;
+        if (PBC) { dx = mimage(w, dx); dy = mimage(w, dy); dz = mimage(w, dz); }
+      }
+    }
+    const D_t ex = (D_t)dx, ey = (D_t)dy, ez = (D_t)dz;
+    if (MIXED) s32 = fmaf((float)ex, (float)ex, fmaf((float)ey, (float)ey, fmaf((float)ez, (float)ez, s32)));
+    else s64 = fma(dx, dx, fma(dy, dy, fma(dz, dz, s64)));
+    D_t qx = __shfl_up_sync(0xffffffffu, ex, 1), qy = __shfl_up_sync(0xffffffffu, ey, 1),
+        qz = __shfl_up_sync(0xffffffffu, ez, 1);
+    if (lane == 0) { qx = cx; qy = cy; qz = cz; }
+    if (j >= 1 && j + 1 < P) {  // interior bead (0-based 1..P-2)
+      f[3 * j] = (double)(kk * (ex - qx));
+      f[3 * j + 1] = (double)(kk * (ey - qy));
+      f[3 * j + 2] = (double)(kk * (ez - qz));
+    }
+    cx = __shfl_sync(0xffffffffu, ex, 31);
+    cy = __shfl_sync(0xffffffffu, ey, 31);
+    cz = __shfl_sync(0xffffffffu, ez, 31);
+  }
+}
+
 // Particles l0 .. l0+7 of one system (all threads of the block).
 template <bool MIXED>
 __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double *__restrict__ pos,
@@ -41,57 +89,30 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
   __shared__ int finite_s[BEAD_WARPS];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int P = w.P;
-  const double k = w.k;
   // phase 1: one warp per particle -- interior springs and interior forces
   {
     const int l = l0 + wp;
     bool finite = true;
     double s64 = 0.0;
     float s32 = 0.0f;
-    if (l < w.N) {
+    if (l < w.N) {  // warp-uniform
       const double *p = pos + (size_t)l * P * 3;
       double *f = F + (size_t)l * P * 3;
-      for (int j = lane; j < P; j += 32) {
-        const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
-        finite &= isfinite(x) && isfinite(y) && isfinite(z);
-        if (j + 1 < P) {
-          const double dx = mimage(w, p[3 * j + 3] - x), dy = mimage(w, p[3 * j + 4] - y),
-                       dz = mimage(w, p[3 * j + 5] - z);
-          if (MIXED) {
-            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-            s32 = fmaf(fx, fx, fmaf(fy, fy, fmaf(fz, fz, s32)));
-          } else {
-            s64 = fma(dx, dx, fma(dy, dy, fma(dz, dz, s64)));
-          }
-        }
-        if (j >= 1 && j + 1 < P) {  // interior bead (0-based 1..P-2)
-          const double ax = mimage(w, x - p[3 * j + 3]), ay = mimage(w, y - p[3 * j + 4]),
-                       az = mimage(w, z - p[3 * j + 5]);
-          const double bx = mimage(w, x - p[3 * j - 3]), by = mimage(w, y - p[3 * j - 2]),
-                       bz = mimage(w, z - p[3 * j - 1]);
-          if (MIXED) {
-            const float kf = (float)k;
-            f[3 * j] = (double)(-kf * ((float)ax + (float)bx));
-            f[3 * j + 1] = (double)(-kf * ((float)ay + (float)by));
-            f[3 * j + 2] = (double)(-kf * ((float)az + (float)bz));
-          } else {
-            f[3 * j] = -k * (ax + bx);
-            f[3 * j + 1] = -k * (ay + by);
-            f[3 * j + 2] = -k * (az + bz);
-          }
-        }
-      }
+      if (w.pbc) bead_springs<MIXED, true>(w, p, f, lane, finite, s32, s64);
+      else bead_springs<MIXED, false>(w, p, f, lane, finite, s32, s64);
     }
     if (MIXED) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s32 += __shfl_xor_sync(0xffffffffu, s32, o);
-      s64 = (double)s32;
     } else {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
     }
     finite = __all_sync(0xffffffffu, finite);
-    if (lane == 0) { eint_s[wp] = w.half_k * s64; finite_s[wp] = finite; }
+    if (lane == 0) {
+      eint_s[wp] = w.half_k * (MIXED ? (double)s32 : s64);
+      finite_s[wp] = finite;
+    }
   }
   __syncthreads();
   // phase 2: one lane per particle -- links, endpoint copies and the
@@ -120,9 +141,9 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
       rp[0] = bP[0]; rp[1] = bP[1]; rp[2] = bP[2]; rp[3] = 0.0;
       if (MIXED && w.pbc) {  // fixed-point fractions of the box
         *(uint4 *)(w.R1s + 8 * (size_t)l) =
-            make_uint4(to_fixed(b1[0], w.invL), to_fixed(b1[1], w.invL), to_fixed(b1[2], w.invL), 0u);
+            make_uint4(to_fixed(b1[0], w.invL32), to_fixed(b1[1], w.invL32), to_fixed(b1[2], w.invL32), 0u);
         *(uint4 *)(w.RPs + 8 * (size_t)l) =
-            make_uint4(to_fixed(bP[0], w.invL), to_fixed(bP[1], w.invL), to_fixed(bP[2], w.invL), 0u);
+            make_uint4(to_fixed(bP[0], w.invL32), to_fixed(bP[1], w.invL32), to_fixed(bP[2], w.invL32), 0u);
       } else if (MIXED) {  // float32 high + low parts
         float h1[3], l1[3], hP[3], lP[3];
 #pragma unroll
@@ -136,11 +157,11 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
         sp[0] = make_float4(hP[0], hP[1], hP[2], 0.0f);
         sp[1] = make_float4(lP[0], lP[1], lP[2], 0.0f);
       }
-      // c_{l+1} = exp(beta link_l) / (l+1) = 2^x, x = beta link_l log2(e) - log2(l+1)
-      // |x| is clamped to 2^28 so that exponent sums stay in int32
-      const double x = fmin(fmax(w.beta * lk * LOG2E - log2((double)(l + 1)), -268435456.0), 268435456.0);
+      // c_{l+1} = exp(beta link_l) / (l+1) = 2^(x - n) 2^n / (l+1),
+      // x = beta link_l log2(e) >= 0, clamped to 2^28 so that exponent sums stay in int32
+      const double x = fmin(w.beta * lk * LOG2E, 268435456.0);
       const double n = floor(x);
-      const xd c = xnorm(exp2(x - n), (int)n);
+      const xd c = xnorm(exp2(x - n) / (double)(l + 1), (int)n);
       w.ccm[l] = c.m;
       w.cce[l] = c.e;
     }
@@ -189,7 +210,7 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
     if (!MIXED) {
       d[0] = x; d[1] = y; d[2] = z;
     } else if (w.pbc) {
-      *(uint4 *)d = make_uint4(to_fixed(x, w.invL), to_fixed(y, w.invL), to_fixed(z, w.invL), 0u);
+      *(uint4 *)d = make_uint4(to_fixed(x, w.invL32), to_fixed(y, w.invL32), to_fixed(z, w.invL32), 0u);
     } else {
       float hx, lx, hy, ly, hz, lz;
       split_hi_lo(x, hx, lx);

@@ -64,7 +64,7 @@ constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  double Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
+  unsigned long long Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner

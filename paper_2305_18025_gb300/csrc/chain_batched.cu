@@ -29,7 +29,7 @@ constexpr int BATCH_THREADS = 512;
 constexpr int BATCH_BULK_WARPS = 8;
 
 struct SingleSmem {
-  double Kdm[2 * BLK];
+  unsigned long long Kdm[2 * BLK];
   double Hom[2 * BLK];  // MIXED: floats
   double misc[2];
   int Kde[2 * BLK];

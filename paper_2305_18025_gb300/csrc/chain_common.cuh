@@ -47,6 +47,11 @@ __device__ __forceinline__ double lds_f64(unsigned a) {
   asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ unsigned long long lds_u64(unsigned a) {
+  unsigned long long v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ float lds_f32(unsigned a) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
@@ -86,14 +91,69 @@ __device__ __forceinline__ unsigned long long mant53(float m) {
 }
 
 // c * h for extended numbers with mantissas in [1,2): the 53 x 53-bit mantissa
-// product on the integer pipe (truncated to 52 fraction bits, error below one
-// unit in the last place), so that staging issues no float64 instruction.
+// product on the integer pipe, kept as a 64-bit integer mantissa kk in
+// [2^63, 2^64) (value kk 2^(e-63); the 106-bit product truncated to 64 bits),
+// so that staging issues no float64 instruction.
+struct xk {
+  unsigned long long m;
+  int e;
+};
 template <typename M_t>
-__device__ __forceinline__ xd mul_mant(xd c, M_t hm, int he) {
+__device__ __forceinline__ xk mul_mant(xd c, M_t hm, int he) {
   const unsigned long long hi = __umul64hi(mant53(c.m) << 11, mant53(hm) << 11);  // in [2^62, 2^64)
   const int sh = (int)(hi >> 63);
-  const unsigned long long frac = (hi >> (10 + sh)) & 0xFFFFFFFFFFFFFull;
-  return xd{__longlong_as_double((long long)(frac | 0x3FF0000000000000ull)), c.e + he + sh};
+  return xk{hi << (1 - sh), c.e + he + sh};
+}
+
+// ------------------------------------------------- the integer-pipe chain format
+// The dependency chain of the recursions runs on the integer pipe: a float64
+// FMA has a 64-cycle latency on GB300 (plus ~40 cycles before a shuffle can
+// read its result), while a 64 x 64-bit integer product, shifts and a 64-bit
+// add take a few cycles each.  An extended number is  m * 2^(e - 62)  with an
+// integer mantissa m in [2^62, 2^63) (one bit of headroom for an addition);
+// the extended zero is 2^62 * 2^(XZERO_E - 62).  Products and alignment shifts
+// truncate, at 2^-61 relative: finer than a float64 rounding.
+struct xi {
+  unsigned long long m;
+  int e;
+};
+
+// From an extended number with a positive normal double mantissa (any binary
+// exponent); zero or negative mantissas give the extended zero.
+__device__ __forceinline__ xi xi_from(xd a) {
+  const long long b = __double_as_longlong(a.m);
+  if (b <= 0) return xi{1ull << 62, XZERO_E};
+  return xi{(((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10, a.e + (int)(b >> 52) - 1023};
+}
+// To an extended number with a double mantissa in [1,2) (truncated to 53 bits).
+__device__ __forceinline__ xd xi_to_xd(xi a) {
+  return xd{__longlong_as_double((long long)(((a.m >> 10) & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull)), a.e};
+}
+// s * 2^(E - 62) with s in [2^61, 2^64), brought back to [2^62, 2^63).
+__device__ __forceinline__ xi xi_norm(unsigned long long s, int E) {
+  const int lz = __clz((int)(s >> 32));  // 0, 1 or 2
+  return xi{(s << lz) >> 1, E + 1 - lz};
+}
+// a + b
+__device__ __forceinline__ xi xi_add(xi a, xi b) {
+  const int E = max(a.e, b.e);
+  return xi_norm((a.m >> min(E - a.e, 63)) + (b.m >> min(E - b.e, 63)), E);
+}
+// a * c (c: positive normal double mantissa, any binary exponent)
+__device__ __forceinline__ xi xi_mul(xi a, xd c) {
+  const long long b = __double_as_longlong(c.m);
+  const unsigned long long p = __umul64hi(mant53(c.m) << 11, a.m);  // in [2^61, 2^63)
+  return xi_norm(p, a.e + c.e + (int)(b >> 52) - 1023 + 1);
+}
+// acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64): the step of the
+// dependency chain.  The product kk * y.m / 2^64 lies in [2^61, 2^63), the
+// aligned sum in [2^61, 2^64); a K carrying an extended-zero exponent leaves
+// acc unchanged.
+__device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y) {
+  const unsigned long long p = __umul64hi(kk, y.m);
+  const int pe = ke + y.e + 1;
+  const int E = max(acc.e, pe);
+  return xi_norm((acc.m >> min(E - acc.e, 63)) + (p >> min(E - pe, 63)), E);
 }
 
 // A positive normal float (or 0) as a double, with integer operations.
@@ -165,10 +225,11 @@ __device__ __forceinline__ void stage_offdiag(const Workspace &w, int tt, int i0
   }
 }
 
-// Diagonal block of tile tt, K = c_row * H with float64 mantissas, rows i in
-// [i0, i0+NR): the mantissa product is formed on the integer pipe (mul_mant).
+// Diagonal block of tile tt, K = c_row * H as 64-bit integer mantissas (the
+// chain format of xi_fma), rows i in [i0, i0+NR): the mantissa product is
+// formed on the integer pipe (mul_mant).
 template <bool MIXED, bool BWD, int NR>
-__device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, double *dm, int *de) {
+__device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   const int lane = threadIdx.x & 31;
   const int r0 = tt * TILE, row = r0 + lane;
@@ -185,7 +246,7 @@ __device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, d
       m = __ldg(gm + gi);
       e = __ldg(ge + gi);
     }
-    const xd k = mul_mant<M_t>(c, m, e);
+    const xk k = mul_mant<M_t>(c, m, e);
     dm[i * 33 + lane] = k.m;
     de[i * 33 + lane] = k.e;
   }
@@ -193,61 +254,57 @@ __device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, d
 
 // The 32 dependent steps of row tile t, run by one warp.  A is this lane's
 // row sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
-// coefficient.  K (diagonal, c-scaled) and H (to tile t+1) are the staged
-// blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and, unless gYm is
-// null, at gYm/gYe[v] in global memory.  On return nxt holds the partial sums of tile t+1's rows over
-// source tile t.
+// coefficient.  K (diagonal, c-scaled, integer mantissas) and H (to tile t+1)
+// are the staged blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and,
+// unless gYm is null, at gYm/gYe[v] in global memory.  On return nxt holds
+// the partial sums of tile t+1's rows over source tile t.
 // 32 steps, no branches and no stores: rows past N and finished rows see
 // extended zeros in the staged blocks, and row j's accumulator is final after
-// step j (later steps add at most 2^-1000 of it).  Block entries of step i+1
-// are loaded (explicit ld.shared) before step i's shuffle.
+// step j.  The chain (acc, y) is in the integer format xi; block entries of
+// step i+1 are loaded (explicit ld.shared) before step i's shuffle.
 template <bool MIXED>
-__device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt, const double *Kdm, const int *Kde,
-                                           const double *Hom, const int *Hoe, double *Ym, int *Ye, int ymask,
-                                           double *gYm, int *gYe) {
+__device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt, const unsigned long long *Kdm,
+                                           const int *Kde, const double *Hom, const int *Hoe, double *Ym, int *Ye,
+                                           int ymask, double *gYm, int *gYe) {
   const int lane = threadIdx.x & 31;
   const int r0 = t * TILE, row = r0 + lane;
-  xd acc{0.0, XZERO_E};
-  if (row < N) {
-    acc = xadd_int(A, nxt);
-    acc = xmul_int(xnorm_int(acc), crow);  // acc' = c_row * (sum over sources < r0)
-  }
-  xd ycur{Ym[r0 & ymask], Ye[r0 & ymask]};
-  if (__double_as_longlong(acc.m) <= 0) acc = xd{1.0, XZERO_E};
+  xi acc{1ull << 62, XZERO_E};
+  if (row < N) acc = xi_mul(xi_add(xi_from(A), xi_from(nxt)), crow);  // c_row * (sum over sources < r0)
+  xi y = xi_from(xd{Ym[r0 & ymask], Ye[r0 & ymask]});
   nxt = xd{1.0, XZERO_E};
   float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
   int nexp = XZERO_E;
   const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
   const unsigned aHm = MIXED ? smem_addr((const float *)Hom + lane) : smem_addr(Hom + lane);
-  double km = lds_f64(aKm), hm = MIXED ? 0.0 : lds_f64(aHm);
+  unsigned long long km = lds_u64(aKm);
+  double hm = MIXED ? 0.0 : lds_f64(aHm);
   float hf = MIXED ? lds_f32(aHm) : 0.0f;
   int ke = lds_s32(aKe), he = lds_s32(aHe);
 #pragma unroll
   for (int i = 0; i < TILE; ++i) {
-    double km1 = 0.0, hm1 = 0.0;
+    unsigned long long km1 = 0;
+    double hm1 = 0.0;
     float hf1 = 0.0f;
     int ke1 = 0, he1 = 0;
     if (i + 1 < TILE) {
-      km1 = lds_f64(aKm + (i + 1) * 33 * 8);
+      km1 = lds_u64(aKm + (i + 1) * 33 * 8);
       if (MIXED) hf1 = lds_f32(aHm + (i + 1) * 33 * 4);
       else hm1 = lds_f64(aHm + (i + 1) * 33 * 8);
       ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
       he1 = lds_s32(aHe + (i + 1) * 33 * 4);
     }
-    acc = fma_chain(acc, km, ke, ycur);  // the dependency chain
-    // next tile's rows, off the chain (MIXED: float32, no float64 pipe)
-    // (ycur.m is a positive normal double, not necessarily in [1,2))
+    acc = xi_fma(acc, km, ke, y);  // the dependency chain
+    // next tile's rows, off the chain (MIXED: float32 on the top 24 bits of y)
     if (MIXED)
-      fmerge(nsum, nexp, mant_to_float(ycur.m) * hf,
-             he + ycur.e + (int)(__double_as_longlong(ycur.m) >> 52) - 1023);
-    else nxt = fma_chain(nxt, hm, he, ycur);
-    ycur.m = __shfl_sync(0xffffffffu, acc.m, i);
-    ycur.e = __shfl_sync(0xffffffffu, acc.e, i);
+      fmerge(nsum, nexp, __int_as_float((int)((y.m >> 39) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
+    else nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
+    y.m = __shfl_sync(0xffffffffu, acc.m, i);
+    y.e = __shfl_sync(0xffffffffu, acc.e, i);
     km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
   }
   if (MIXED) nxt = xd{f2d_int(nsum), nexp};
   if (row < N) {  // Y_{row+1} = final accumulator of row `row`
-    const xd yn = xnorm_int(acc);
+    const xd yn = xi_to_xd(acc);
     Ym[(row + 1) & ymask] = yn.m;
     Ye[(row + 1) & ymask] = yn.e;
     if (gYm) {

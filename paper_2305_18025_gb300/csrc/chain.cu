@@ -165,25 +165,25 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       // V^{[1,N]} = C[N] - ln(y_N)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
       if (q == 12 && lane == 0) sm.misc[0] = carry;
       __syncthreads();
-      if (tid == 0) {
-        const xd yN{sm.Ym[N & (YRING - 1)], sm.Ye[N & (YRING - 1)]};
-        const double VB = sm.misc[0] - xlog(yN) / w.beta;
-        w.scal[0] = VB;
-        if (V_B) *V_B = VB;
+      const xd yN{sm.Ym[N & (YRING - 1)], sm.Ye[N & (YRING - 1)]};
+      if (tid == 0) {  // the normaliser first: the alpha values wait for it
         const xd inv = xnorm(1.0 / (yN.m * (double)N), -yN.e);
         w.scal[1] = inv.m;
         w.scal_i[0] = inv.e;
         sm.misc[1] = inv.m;
         sm.misci[0] = inv.e;
-        if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);
       }
       __syncthreads();
-      const xd inv{sm.misc[1], sm.misci[0]};
-      for (int a = tid; a < N; a += blockDim.x) {
-        const xd al = xmul(xd{gYm[a], gYe[a]}, inv);
-        if (MIXED) ((float *)w.alm)[a] = (float)al.m;
-        else ((double *)w.alm)[a] = al.m;
-        w.ale[a] = al.e;
+      if (wid == 0) {  // V_B (a float64 log) on warp 0, alongside the alpha values
+        if (lane == 0) {
+          const double VB = sm.misc[0] - xlog(yN) / w.beta;
+          w.scal[0] = VB;
+          if (V_B) *V_B = VB;
+          if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);
+        }
+      } else {
+        const xd inv{sm.misc[1], sm.misci[0]};
+        for (int a = tid - 32; a < N; a += blockDim.x - 32) store_alpha<MIXED>(w, a, xd{gYm[a], gYe[a]}, inv);
       }
     }
   } else {

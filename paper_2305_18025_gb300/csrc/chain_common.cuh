@@ -129,10 +129,11 @@ __device__ __forceinline__ xi xi_from(xd a) {
 __device__ __forceinline__ xd xi_to_xd(xi a) {
   return xd{__longlong_as_double((long long)(((a.m >> 10) & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull)), a.e};
 }
-// s * 2^(E - 62) with s in [2^61, 2^64), brought back to [2^62, 2^63).
+// s * 2^(E - 62) with s in [2^61, 2^64), brought back to [2^62, 2^63) by
+// selecting among s/2, s and 2s on its top three bits (no bit scan).
 __device__ __forceinline__ xi xi_norm(unsigned long long s, int E) {
-  const int lz = __clz((int)(s >> 32));  // 0, 1 or 2
-  return xi{(s << lz) >> 1, E + 1 - lz};
+  const unsigned top = (unsigned)(s >> 61);  // 1: [2^61, 2^62), 2-3: in range, 4-7: [2^63, 2^64)
+  return xi{top >= 4 ? (s >> 1) : (top >= 2 ? s : (s << 1)), top >= 4 ? E + 1 : (top >= 2 ? E : E - 1)};
 }
 // a + b
 __device__ __forceinline__ xi xi_add(xi a, xi b) {
@@ -148,12 +149,34 @@ __device__ __forceinline__ xi xi_mul(xi a, xd c) {
 // acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64): the step of the
 // dependency chain.  The product kk * y.m / 2^64 lies in [2^61, 2^63), the
 // aligned sum in [2^61, 2^64); a K carrying an extended-zero exponent leaves
-// acc unchanged.
+// acc unchanged.  MIXED uses the top 32 bits of kk only (two 32 x 32-bit
+// products, relative error below 2^-30: K = c g carries a float32 g there).
+template <bool MIXED>
 __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y) {
-  const unsigned long long p = __umul64hi(kk, y.m);
+  unsigned long long p;
+  if (MIXED) {
+    const unsigned k1 = (unsigned)(kk >> 32);
+    p = (unsigned long long)k1 * (unsigned)(y.m >> 32) + (((unsigned long long)k1 * (unsigned)y.m) >> 32);
+  } else {
+    p = __umul64hi(kk, y.m);
+  }
   const int pe = ke + y.e + 1;
   const int E = max(acc.e, pe);
   return xi_norm((acc.m >> min(E - acc.e, 63)) + (p >> min(E - pe, 63)), E);
+}
+
+// alpha = y * inv for extended numbers with double mantissas in [1,2), with
+// integer operations; the mantissa is written as float (MIXED) or double.
+template <bool MIXED>
+__device__ __forceinline__ void store_alpha(const Workspace &w, int a, xd y, xd inv) {
+  const unsigned long long hi = __umul64hi(mant53(y.m) << 11, mant53(inv.m) << 11);  // in [2^62, 2^64)
+  const int sh = (int)(hi >> 63);
+  if (MIXED)
+    ((float *)w.alm)[a] = __int_as_float((int)((hi >> (39 + sh)) & 0x7FFFFFu) | 0x3F800000);
+  else
+    ((double *)w.alm)[a] =
+        __longlong_as_double((long long)(((hi >> (10 + sh)) & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+  w.ale[a] = y.e + inv.e + sh;
 }
 
 // A positive normal float (or 0) as a double, with integer operations.
@@ -293,7 +316,7 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
       ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
       he1 = lds_s32(aHe + (i + 1) * 33 * 4);
     }
-    acc = xi_fma(acc, km, ke, y);  // the dependency chain
+    acc = xi_fma<MIXED>(acc, km, ke, y);  // the dependency chain
     // next tile's rows, off the chain (MIXED: float32 on the top 24 bits of y)
     if (MIXED)
       fmerge(nsum, nexp, __int_as_float((int)((y.m >> 39) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);

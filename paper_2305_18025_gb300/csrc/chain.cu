@@ -64,14 +64,12 @@ constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  unsigned long long Kdm[2 * BLK];  // diagonal blocks, look-ahead form (double buffer)
-  unsigned long long Kdg[2 * TILE]; // D_j = K(j, j) of those blocks
+  unsigned long long Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
   double misc[4];       // end of the forward recursion: C[N], 1/(N y_N) mantissa
   int Kde[2 * BLK];
-  int Kdge[2 * TILE];
   int Hoe[2 * BLK];
   int Ye[YRING];
   int Ae[2 * TILE];
@@ -124,7 +122,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
     const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
-    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde, sm.Kdg, sm.Kdge);
+    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde);
     if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
     cluster.sync();
 
@@ -140,13 +138,10 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         const xd crow = cnext;
         if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
         chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
-                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Kdg + buf * TILE, sm.Kdge + buf * TILE,
-                          sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
+                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
                           sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
       } else if (q >= 0 && q < 8) {
-        if (t + 1 < NT)
-          stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK,
-                                    sm.Kdg + (buf ^ 1) * TILE, sm.Kdge + (buf ^ 1) * TILE);
+        if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
           stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);

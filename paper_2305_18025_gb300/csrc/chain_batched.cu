@@ -30,11 +30,9 @@ constexpr int BATCH_BULK_WARPS = 8;
 
 struct SingleSmem {
   unsigned long long Kdm[2 * BLK];
-  unsigned long long Kdg[2 * TILE];
   double Hom[2 * BLK];  // MIXED: floats
   double misc[2];
   int Kde[2 * BLK];
-  int Kdge[2 * TILE];
   int Hoe[2 * BLK];
   int misci[2];
 };
@@ -67,7 +65,7 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
   for (int r = tid; r < N; r += blockDim.x) { Am[r] = 0.0; Ae[r] = XZERO_E; }
   if (tid == 0) { Ym[0] = 1.0; Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
   if (!BWD && tid == 0) w.C[0] = 0.0;
-  if (q >= 0 && q < 4) stage_diag<MIXED, BWD, 8>(w, 0, 8 * q, sm.Kdm, sm.Kde, sm.Kdg, sm.Kdge);
+  if (q >= 0 && q < 4) stage_diag<MIXED, BWD, 8>(w, 0, 8 * q, sm.Kdm, sm.Kde);
   if (q == 4 || q == 5) stage_offdiag<MIXED, BWD, 16>(w, 0, 16 * (q - 4), sm.Hom, sm.Hoe);
   __syncthreads();
 
@@ -82,12 +80,10 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
       const xd crow = cnext;
       if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);
       const xd A = (row < N) ? xd{Am[row], Ae[row]} : xd{0.0, XZERO_E};
-      chain_tile<MIXED>(N, t, A, crow, nxt, sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Kdg + buf * TILE,
-                        sm.Kdge + buf * TILE, sm.Hom + buf * BLK, sm.Hoe + buf * BLK, Ym, Ye, -1, gYm, gYe);
+      chain_tile<MIXED>(N, t, A, crow, nxt, sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK,
+                        sm.Hoe + buf * BLK, Ym, Ye, -1, gYm, gYe);
     } else if (q >= 0 && q < 4) {
-      if (t + 1 < NT)
-        stage_diag<MIXED, BWD, 8>(w, t + 1, 8 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK,
-                                  sm.Kdg + (buf ^ 1) * TILE, sm.Kdge + (buf ^ 1) * TILE);
+      if (t + 1 < NT) stage_diag<MIXED, BWD, 8>(w, t + 1, 8 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
     } else if (q == 4 || q == 5) {
       if (t + 1 < NT)
         stage_offdiag<MIXED, BWD, 16>(w, t + 1, 16 * (q - 4), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);

@@ -105,19 +105,6 @@ __device__ __forceinline__ xk mul_mant(xd c, M_t hm, int he) {
   return xk{hi << (1 - sh), c.e + he + sh};
 }
 
-// a * b and a + b for xk numbers (mantissas in [2^63, 2^64)); both truncate.
-__device__ __forceinline__ xk xk_mul(xk a, xk b) {
-  const unsigned long long hi = __umul64hi(a.m, b.m);  // in [2^62, 2^64)
-  const int sh = (int)(hi >> 63);
-  return xk{hi << (1 - sh), a.e + b.e + sh};
-}
-__device__ __forceinline__ xk xk_add(xk a, xk b) {
-  const int E = max(a.e, b.e);
-  const unsigned long long s = (a.m >> min(E - a.e + 1, 63)) + (b.m >> min(E - b.e + 1, 63));  // [2^62, 2^64)
-  const int sh = (int)(s >> 63);
-  return xk{s << (1 - sh), E + sh};
-}
-
 // ------------------------------------------------- the integer-pipe chain format
 // The dependency chain of the recursions runs on the integer pipe: a float64
 // FMA has a 64-cycle latency on GB300 (plus ~40 cycles before a shuffle can
@@ -159,44 +146,23 @@ __device__ __forceinline__ xi xi_mul(xi a, xd c) {
   const unsigned long long p = __umul64hi(mant53(c.m) << 11, a.m);  // in [2^61, 2^63)
   return xi_norm(p, a.e + c.e + (int)(b >> 52) - 1023 + 1);
 }
-// kk * ym / 2^64 for kk in [2^63, 2^64), ym in [2^62, 2^63): in [2^61, 2^63).
-// MIXED uses the top 32 bits of kk only (two 32 x 32-bit products, relative
-// error below 2^-30: K = c g carries a float32 g there).
-template <bool MIXED>
-__device__ __forceinline__ unsigned long long kprod(unsigned long long kk, unsigned long long ym) {
-  if (MIXED) {
-    const unsigned k1 = (unsigned)(kk >> 32);
-    return (unsigned long long)k1 * (unsigned)(ym >> 32) + (((unsigned long long)k1 * (unsigned)ym) >> 32);
-  }
-  return __umul64hi(kk, ym);
-}
-
-// acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64).  The aligned sum
-// lies in [2^61, 2^64); a K carrying an extended-zero exponent leaves acc
-// unchanged.
+// acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64): the step of the
+// dependency chain.  The product kk * y.m / 2^64 lies in [2^61, 2^63), the
+// aligned sum in [2^61, 2^64); a K carrying an extended-zero exponent leaves
+// acc unchanged.  MIXED uses the top 32 bits of kk only (two 32 x 32-bit
+// products, relative error below 2^-30: K = c g carries a float32 g there).
 template <bool MIXED>
 __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y) {
-  const unsigned long long p = kprod<MIXED>(kk, y.m);
+  unsigned long long p;
+  if (MIXED) {
+    const unsigned k1 = (unsigned)(kk >> 32);
+    p = (unsigned long long)k1 * (unsigned)(y.m >> 32) + (((unsigned long long)k1 * (unsigned)y.m) >> 32);
+  } else {
+    p = __umul64hi(kk, y.m);
+  }
   const int pe = ke + y.e + 1;
   const int E = max(acc.e, pe);
   return xi_norm((acc.m >> min(E - acc.e, 63)) + (p >> min(E - pe, 63)), E);
-}
-
-// acc + K1 y1 + K2 y2, the step of the dependency chain: the three terms are
-// aligned to the largest exponent with one more bit of headroom (each below
-// 2^62, the sum s in [2^60, 3 * 2^62), value s 2^(E - 61)), added, and brought
-// back to [2^62, 2^63) by a select on the top bits.
-template <bool MIXED>
-__device__ __forceinline__ xi xi_fma2(xi acc, unsigned long long k1, int e1, xi y1, unsigned long long k2, int e2,
-                                      xi y2) {
-  const unsigned long long p1 = kprod<MIXED>(k1, y1.m), p2 = kprod<MIXED>(k2, y2.m);
-  const int pe1 = e1 + y1.e + 1, pe2 = e2 + y2.e + 1;
-  const int E = max(acc.e, max(pe1, pe2));
-  const unsigned long long s =
-      (acc.m >> min(E - acc.e + 1, 63)) + (p1 >> min(E - pe1 + 1, 63)) + (p2 >> min(E - pe2 + 1, 63));
-  const unsigned t = (unsigned)(s >> 60);  // 1: [2^60,2^61)  2-3: [2^61,2^62)  4-7: [2^62,2^63)  8-11: [2^63,2^64)
-  return xi{t >= 8 ? (s >> 1) : (t >= 4 ? s : (t >= 2 ? (s << 1) : (s << 2))),
-            E + (t >= 8 ? 2 : (t >= 4 ? 1 : (t >= 2 ? 0 : -1)))};
 }
 
 // alpha = y * inv for extended numbers with double mantissas in [1,2), with
@@ -282,151 +248,84 @@ __device__ __forceinline__ void stage_offdiag(const Workspace &w, int tt, int i0
   }
 }
 
-// Diagonal block of tile tt in the chain's look-ahead form.  With K(i, j) =
-// c_j H(r0+i, r0+j) (source i, row j of the tile), row j's equation
-//   Y_{r0+j+1} = a_j + sum_{i<=j} K(i, j) Y_{r0+i}
-// takes in row j-1's equation for Y_{r0+j} (j >= 1):
-//   Y_{r0+j+1} = a_j + D_j a_{j-1} + sum_{i<=j-1} Kh(i, j) Y_{r0+i},
-//   Kh(i, j) = K(i, j) + D_j K(i, j-1),  D_j = K(j, j),
-// so that Y_{r0+j+1} waits for Y_{r0+j-1} at the latest (all terms are
-// nonnegative: no cancellation).  Row 0 keeps Kh(0, 0) = K(0, 0).  Staged as
-// xk numbers (64-bit integer mantissas) for rows i in [i0, i0+NR) of the
-// block, entries outside the look-ahead triangle as extended zeros; the
-// warp with i0 = 0 also stores D_j.  Integer pipe only (mul_mant, xk_*).
+// Diagonal block of tile tt, K = c_row * H as 64-bit integer mantissas (the
+// chain format of xi_fma), rows i in [i0, i0+NR): the mantissa product is
+// formed on the integer pipe (mul_mant).
 template <bool MIXED, bool BWD, int NR>
-__device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de,
-                                           unsigned long long *dgm, int *dge) {
+__device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
-  const int j = threadIdx.x & 31;
-  const int r0 = tt * TILE, row = r0 + j;
-  const bool valid = row < w.N;
+  const int lane = threadIdx.x & 31;
+  const int r0 = tt * TILE, row = r0 + lane;
   const M_t *gm = (const M_t *)chain_gm<BWD>(w);
   const int *ge = chain_ge<BWD>(w);
-  const xd c = valid ? xnorm_int(chain_coef<BWD>(w, row)) : xd{1.0, 0};
-  const xd cp = (valid && j >= 1) ? xnorm_int(chain_coef<BWD>(w, row - 1)) : xd{1.0, 0};
-  M_t hd = (M_t)1.0, hm[NR], hp[NR];
-  int hde = XZERO_E, he[NR], hpe[NR];
-  if (valid) {
-    const size_t gi = hidx(row, row);
-    hd = __ldg(gm + gi);
-    hde = __ldg(ge + gi);
-  }
+  const xd c = (row < w.N) ? xnorm_int(chain_coef<BWD>(w, row)) : xd{1.0, 0};
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    const int i = i0 + k;
-    hm[k] = (M_t)1.0; hp[k] = (M_t)1.0; he[k] = XZERO_E; hpe[k] = XZERO_E;
-    if (valid && (j == 0 ? i == 0 : i <= j - 1)) {
-      const size_t gi = hidx(r0 + i, row);
-      hm[k] = __ldg(gm + gi);
-      he[k] = __ldg(ge + gi);
-      if (j >= 1) {
-        const size_t gp = hidx(r0 + i, row - 1);
-        hp[k] = __ldg(gm + gp);
-        hpe[k] = __ldg(ge + gp);
-      }
+  for (int i = i0; i < i0 + NR; ++i) {
+    const int src = r0 + i;
+    M_t m = (M_t)1.0;
+    int e = XZERO_E;
+    if (row < w.N && src <= row) {
+      const size_t gi = hidx(src, row);
+      m = __ldg(gm + gi);
+      e = __ldg(ge + gi);
     }
-  }
-  const xk D = mul_mant<M_t>(c, hd, hde);
-  if (i0 == 0) { dgm[j] = D.m; dge[j] = max(D.e, XZERO_E); }
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    xk kh = mul_mant<M_t>(c, hm[k], he[k]);
-    if (j >= 1) kh = xk_add(kh, xk_mul(D, mul_mant<M_t>(cp, hp[k], hpe[k])));
-    dm[(i0 + k) * 33 + j] = kh.m;
-    de[(i0 + k) * 33 + j] = max(kh.e, XZERO_E);  // keeps every exponent sum in int32
+    const xk k = mul_mant<M_t>(c, m, e);
+    dm[i * 33 + lane] = k.m;
+    de[i * 33 + lane] = k.e;
   }
 }
 
-// The dependent steps of row tile t, run by one warp.  A is this lane's row
-// sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
-// coefficient; Kh/D (look-ahead form, stage_diag) and H (to tile t+1) are the
-// staged blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and, unless
-// gYm is null, at gYm/gYe[v] in global memory.  On return nxt holds the
-// partial sums of tile t+1's rows over source tile t.
-// Step 0 adds source 0 (Y_{r0}); step s = 1..15 adds sources 2s-1 and 2s,
-// after which rows 2s and 2s+1 are final and their Y are shuffled out: 16
-// dependent steps of one three-term aligned sum each.  No branches and no
-// stores inside: rows past N and finished rows see extended zeros.  The chain
-// is in the integer format xi; the block entries of step s+1 are loaded
-// (explicit ld.shared) before step s's shuffles.
+// The 32 dependent steps of row tile t, run by one warp.  A is this lane's
+// row sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
+// coefficient.  K (diagonal, c-scaled, integer mantissas) and H (to tile t+1)
+// are the staged blocks.  Y_v lives at Ym/Ye[v & ymask] in shared memory and,
+// unless gYm is null, at gYm/gYe[v] in global memory.  On return nxt holds
+// the partial sums of tile t+1's rows over source tile t.
+// 32 steps, no branches and no stores: rows past N and finished rows see
+// extended zeros in the staged blocks, and row j's accumulator is final after
+// step j.  The chain (acc, y) is in the integer format xi; block entries of
+// step i+1 are loaded (explicit ld.shared) before step i's shuffle.
 template <bool MIXED>
 __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt, const unsigned long long *Kdm,
-                                           const int *Kde, const unsigned long long *Dm, const int *De,
-                                           const double *Hom, const int *Hoe, double *Ym, int *Ye, int ymask,
-                                           double *gYm, int *gYe) {
+                                           const int *Kde, const double *Hom, const int *Hoe, double *Ym, int *Ye,
+                                           int ymask, double *gYm, int *gYe) {
   const int lane = threadIdx.x & 31;
   const int r0 = t * TILE, row = r0 + lane;
-  // a_j = c_j (A_j + nxt_j); the look-ahead row starts from a_j + D_j a_{j-1}
-  xi a{1ull << 62, XZERO_E};
-  if (row < N) a = xi_mul(xi_add(xi_from(A), xi_from(nxt)), crow);
-  xi ap;
-  ap.m = __shfl_up_sync(0xffffffffu, a.m, 1);
-  ap.e = __shfl_up_sync(0xffffffffu, a.e, 1);
-  xi acc = (lane >= 1) ? xi_fma<MIXED>(a, Dm[lane], De[lane], ap) : a;
-  xi y1 = xi_from(xd{Ym[r0 & ymask], Ye[r0 & ymask]}), y2;
+  xi acc{1ull << 62, XZERO_E};
+  if (row < N) acc = xi_mul(xi_add(xi_from(A), xi_from(nxt)), crow);  // c_row * (sum over sources < r0)
+  xi y = xi_from(xd{Ym[r0 & ymask], Ye[r0 & ymask]});
+  nxt = xd{1.0, XZERO_E};
   float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
   int nexp = XZERO_E;
-  xi nx{1ull << 62, XZERO_E};  // FP64: the next tile's partial sum in the integer format
   const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
   const unsigned aHm = MIXED ? smem_addr((const float *)Hom + lane) : smem_addr(Hom + lane);
-  const int hsz = MIXED ? 4 : 8;
-  // H(source i, row of tile t+1) as a chain-format factor (FP64) or float (MIXED)
-  auto hk = [&](int i) -> unsigned long long {
-    return MIXED ? 0ull : mant53(lds_f64(aHm + i * 33 * 8)) << 11;
-  };
-  auto hf = [&](int i) -> float { return MIXED ? lds_f32(aHm + i * 33 * 4) : 0.0f; };
-  auto nadd = [&](xi y, float h, int e) {  // MIXED: one term of the next tile's sum
-    fmerge(nsum, nexp, __int_as_float((int)((y.m >> 39) & 0x7FFFFFu) | 0x3F800000) * h, e + y.e);
-  };
-  // step 0: source 0
-  {
-    const unsigned long long k0 = lds_u64(aKm);
-    const int ke0 = lds_s32(aKe), he0 = lds_s32(aHe);
-    acc = xi_fma<MIXED>(acc, k0, ke0, y1);
-    if (MIXED) nadd(y1, hf(0), he0);
-    else nx = xi_fma<false>(nx, hk(0), he0, y1);
-  }
-  unsigned long long ka = lds_u64(aKm + 1 * 33 * 8), kb = lds_u64(aKm + 2 * 33 * 8);
-  int kea = lds_s32(aKe + 1 * 33 * 4), keb = lds_s32(aKe + 2 * 33 * 4);
-  int hea = lds_s32(aHe + 1 * 33 * 4), heb = lds_s32(aHe + 2 * 33 * 4);
-  float hfa = hf(1), hfb = hf(2);
-  unsigned long long hka = hk(1), hkb = hk(2);
-  y2.m = __shfl_sync(0xffffffffu, acc.m, 1);
-  y2.e = __shfl_sync(0xffffffffu, acc.e, 1);
-  y1.m = __shfl_sync(0xffffffffu, acc.m, 0);
-  y1.e = __shfl_sync(0xffffffffu, acc.e, 0);
+  unsigned long long km = lds_u64(aKm);
+  double hm = MIXED ? 0.0 : lds_f64(aHm);
+  float hf = MIXED ? lds_f32(aHm) : 0.0f;
+  int ke = lds_s32(aKe), he = lds_s32(aHe);
 #pragma unroll
-  for (int s = 1; s < TILE / 2; ++s) {
-    unsigned long long ka1 = 0, kb1 = 0, hka1 = 0, hkb1 = 0;
-    int kea1 = 0, keb1 = 0, hea1 = 0, heb1 = 0;
-    float hfa1 = 0.0f, hfb1 = 0.0f;
-    if (s + 1 < TILE / 2) {  // entries of step s+1: sources 2s+1, 2s+2
-      ka1 = lds_u64(aKm + (2 * s + 1) * 33 * 8);
-      kb1 = lds_u64(aKm + (2 * s + 2) * 33 * 8);
-      kea1 = lds_s32(aKe + (2 * s + 1) * 33 * 4);
-      keb1 = lds_s32(aKe + (2 * s + 2) * 33 * 4);
-      hea1 = lds_s32(aHe + (2 * s + 1) * 33 * 4);
-      heb1 = lds_s32(aHe + (2 * s + 2) * 33 * 4);
-      hfa1 = hf(2 * s + 1); hfb1 = hf(2 * s + 2);
-      hka1 = hk(2 * s + 1); hkb1 = hk(2 * s + 2);
+  for (int i = 0; i < TILE; ++i) {
+    unsigned long long km1 = 0;
+    double hm1 = 0.0;
+    float hf1 = 0.0f;
+    int ke1 = 0, he1 = 0;
+    if (i + 1 < TILE) {
+      km1 = lds_u64(aKm + (i + 1) * 33 * 8);
+      if (MIXED) hf1 = lds_f32(aHm + (i + 1) * 33 * 4);
+      else hm1 = lds_f64(aHm + (i + 1) * 33 * 8);
+      ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
+      he1 = lds_s32(aHe + (i + 1) * 33 * 4);
     }
-    acc = xi_fma2<MIXED>(acc, ka, kea, y1, kb, keb, y2);  // the dependency chain
-    if (MIXED) { nadd(y1, hfa, hea); nadd(y2, hfb, heb); }
-    else nx = xi_fma2<false>(nx, hka, hea, y1, hkb, heb, y2);
-    y1.m = __shfl_sync(0xffffffffu, acc.m, 2 * s);
-    y1.e = __shfl_sync(0xffffffffu, acc.e, 2 * s);
-    y2.m = __shfl_sync(0xffffffffu, acc.m, 2 * s + 1);
-    y2.e = __shfl_sync(0xffffffffu, acc.e, 2 * s + 1);
-    ka = ka1; kb = kb1; kea = kea1; keb = keb1; hea = hea1; heb = heb1;
-    hfa = hfa1; hfb = hfb1; hka = hka1; hkb = hkb1;
+    acc = xi_fma<MIXED>(acc, km, ke, y);  // the dependency chain
+    // next tile's rows, off the chain (MIXED: float32 on the top 24 bits of y)
+    if (MIXED)
+      fmerge(nsum, nexp, __int_as_float((int)((y.m >> 39) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
+    else nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
+    y.m = __shfl_sync(0xffffffffu, acc.m, i);
+    y.e = __shfl_sync(0xffffffffu, acc.e, i);
+    km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
   }
-  // source 31 (Y_{r0+31} = y1) enters only the next tile's sums
-  {
-    const int he31 = lds_s32(aHe + 31 * 33 * 4);
-    if (MIXED) nadd(y1, hf(31), he31);
-    else nx = xi_fma<false>(nx, hk(31), he31, y1);
-  }
-  nxt = MIXED ? xnorm_int(xd{f2d_int(nsum), nexp}) : xi_to_xd(nx);
+  if (MIXED) nxt = xd{f2d_int(nsum), nexp};
   if (row < N) {  // Y_{row+1} = final accumulator of row `row`
     const xd yn = xi_to_xd(acc);
     Ym[(row + 1) & ymask] = yn.m;
@@ -436,6 +335,7 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
       gYe[row + 1] = yn.e;
     }
   }
+  nxt = xnorm_int(nxt);
 }
 
 // Prefix sums C[i+1] = sum_{q<=i} (E_int_q + link_q) of tile t, one warp.

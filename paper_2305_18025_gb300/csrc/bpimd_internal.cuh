@@ -106,6 +106,34 @@ __device__ __forceinline__ double xtod(xd a) {
 // natural log of an extended number (m > 0)
 __device__ __forceinline__ double xlog(xd a) { return log(a.m) + (double)a.e * LN2; }
 
+// ------------------------------------------- programmatic dependent launches
+// The three kernels of an evaluation are launched with programmatic stream
+// serialisation: a kernel may be scheduled while its predecessor in the
+// stream drains (hiding the launch gap), waits (griddepcontrol.wait: the
+// predecessor has completed and its writes are visible) before its first
+// global-memory access, and lets its own successor launch once its work is
+// issued (griddepcontrol.launch_dependents).  A successor launches only after
+// every CTA of its predecessor has started, so an early launch never takes
+// resources the predecessor still needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------------ workspace
 struct Workspace {
   int N, P, NT, NB;     // NT = ceil(N/TILE), NB = NT(NT+1)/2 blocks of g

@@ -157,6 +157,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       }
       cluster.sync();
     }
+    pdl_trigger();  // the probability pass may launch during the epilogue
     if (q == 13) {  // the last tile's Y
       const int v = (NT - 1) * TILE + lane + 1;
       if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
@@ -290,6 +291,7 @@ template <bool MIXED>
 __global__ void __cluster_dims__(CHAIN_CLUSTER, 1, 1) __launch_bounds__(CHAIN_THREADS, 1)
     chain_kernel(Workspace w, double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   if (blockIdx.x < CHAIN_CLUSTER) run_chain<MIXED, false>(w, smem_raw, V_B);
   else run_chain<MIXED, true>(w, smem_raw, V_B);
 }
@@ -326,9 +328,8 @@ cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s) {
   cudaError_t e = prepare_chains();
   if (e != cudaSuccess) return e;
   const size_t bytes = chain_smem_bytes(w.N);
-  if (w.mixed) chain_kernel<true><<<2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s>>>(w, V_B);
-  else chain_kernel<false><<<2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s>>>(w, V_B);
-  return cudaGetLastError();
+  return w.mixed ? launch_pdl(chain_kernel<true>, 2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s, w, V_B)
+                 : launch_pdl(chain_kernel<false>, 2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s, w, V_B);
 }
 
 }  // namespace bpimd

@@ -146,6 +146,7 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
     }
     __syncthreads();
   }
+  pdl_trigger();  // the probability pass may launch during the epilogue
   if (!BWD) {
     // V^{[1,N]} = C[N] - ln(y_N)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
     if (q == 6 && lane == 0) sm.misc[0] = carry;
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) chain_batched_kernel(const W
                                                                          const int *__restrict__ order,
                                                                          double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   const int r = order[blockIdx.x >> 1];
   if (blockIdx.x & 1) run_single<MIXED, true>(ws[r], smem_raw, nullptr);
   else run_single<MIXED, false>(ws[r], smem_raw, V_B ? V_B + r : nullptr);
@@ -205,8 +207,9 @@ cudaError_t launch_chains_batched(const Workspace *ws, const int *order, int R, 
     done[dev] = true;
   }
   const size_t bytes = single_smem_bytes(maxN);
-  if (mixed) chain_batched_kernel<true><<<2 * R, BATCH_THREADS, bytes, s>>>(ws, order, V_B);
-  else chain_batched_kernel<false><<<2 * R, BATCH_THREADS, bytes, s>>>(ws, order, V_B);
+  e = mixed ? launch_pdl(chain_batched_kernel<true>, 2 * R, BATCH_THREADS, bytes, s, ws, order, V_B)
+            : launch_pdl(chain_batched_kernel<false>, 2 * R, BATCH_THREADS, bytes, s, ws, order, V_B);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

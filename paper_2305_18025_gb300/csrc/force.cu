@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
   __shared__ P_t red[8][32][4];
   __shared__ double fin[32][9];
   __shared__ int last[2];
+  pdl_wait();
   for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) prob_block<MIXED>(w, blk, pos, F, red, fin, last);
+  pdl_trigger();
 }
 
 // Replica batch: entry k of tab is (replica, block); positions and forces of
@@ -324,8 +326,9 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   const int sms = sm_count();
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
-  if (w.mixed) prob_force_kernel<true><<<grid, 256, 0, s>>>(w, pos, F);
-  else prob_force_kernel<false><<<grid, 256, 0, s>>>(w, pos, F);
+  cudaError_t e = w.mixed ? launch_pdl(prob_force_kernel<true>, grid, 256, 0, s, w, pos, F)
+                          : launch_pdl(prob_force_kernel<false>, grid, 256, 0, s, w, pos, F);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -347,8 +350,9 @@ cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int
   const int sms = sm_count();
   const int cap = sms * (blocks_per_sm > 0 ? blocks_per_sm : 8);
   const int grid = ntab < cap ? ntab : cap;
-  if (mixed) prob_force_batched<true><<<grid, 256, 0, s>>>(ws, tab, ntab, off, pos, F);
-  else prob_force_batched<false><<<grid, 256, 0, s>>>(ws, tab, ntab, off, pos, F);
+  cudaError_t e = mixed ? launch_pdl(prob_force_batched<true>, grid, 256, 0, s, ws, tab, ntab, off, pos, F)
+                        : launch_pdl(prob_force_batched<false>, grid, 256, 0, s, ws, tab, ntab, off, pos, F);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -322,11 +322,13 @@ __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
+  pdl_wait();
   if ((int)blockIdx.x < nbead) {
     bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
-    return;
+  } else {
+    for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) gmat_block<MIXED>(w, pos, blk, Tm, Te, E);
   }
-  for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) gmat_block<MIXED>(w, pos, blk, Tm, Te, E);
+  pdl_trigger();
 }
 
 // Replica batch: bead_tab[k] = (replica, first particle), blk_tab[k] =
@@ -342,15 +344,17 @@ __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict_
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
+  pdl_wait();
   if ((int)blockIdx.x < nbead) {
     const int2 e = bead_tab[blockIdx.x];
     bead_pass_body<MIXED>(ws[e.x], pos + off[e.x], F + off[e.x], e.y);
-    return;
+  } else {
+    for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
+      const int2 e = blk_tab[k];
+      gmat_block<MIXED>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
+    }
   }
-  for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
-    const int2 e = blk_tab[k];
-    gmat_block<MIXED>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
-  }
+  pdl_trigger();
 }
 
 // Entries outside lo <= col < N of either copy of one block (the upper part
@@ -414,9 +418,8 @@ cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaSt
   const int nbead = (w.N + BEAD_WARPS - 1) / BEAD_WARPS;
   const int cap = sm_count() * 8;
   const int grid = nbead + (w.NB < cap ? w.NB : cap);
-  if (w.mixed) prep_kernel<true><<<grid, 256, 0, s>>>(w, pos, F, nbead);
-  else prep_kernel<false><<<grid, 256, 0, s>>>(w, pos, F, nbead);
-  return cudaGetLastError();
+  return w.mixed ? launch_pdl(prep_kernel<true>, grid, 256, 0, s, w, pos, F, nbead)
+                 : launch_pdl(prep_kernel<false>, grid, 256, 0, s, w, pos, F, nbead);
 }
 
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s) {
@@ -433,9 +436,8 @@ cudaError_t launch_prep_batched(const Workspace *ws, const int2 *bead_tab, int n
   if (nbead <= 0 && nblk <= 0) return cudaSuccess;
   const int cap = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 8);
   const int grid = nbead + (nblk < cap ? nblk : cap);
-  if (mixed) prep_batched<true><<<grid, 256, 0, s>>>(ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
-  else prep_batched<false><<<grid, 256, 0, s>>>(ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
-  return cudaGetLastError();
+  return mixed ? launch_pdl(prep_batched<true>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F)
+               : launch_pdl(prep_batched<false>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
 }
 
 cudaError_t launch_gmat_padding_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed,

@@ -62,19 +62,151 @@ using namespace chain_detail;
 constexpr int NHELP = CHAIN_CLUSTER - 1;  // bulk CTAs per recursion
 constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
+constexpr int TW = 4;                     // tile warps of the lead (one per SM sub-partition)
+
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  unsigned long long Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
+  unsigned long long Tm[2 * BLK];  // tile inverse T[j][i] at [i * 33 + j] (double buffer)
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
+  unsigned long long K0m[2 * TILE];  // K(r0, r0+j): the tile's first source (double buffer)
+  unsigned long long Zm[TW * TILE];  // per tile warp: partial sums of z = T b
+  unsigned long long Nm[TW * TILE];  // per tile warp: partial next-tile sums (MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
   double misc[4];       // end of the forward recursion: C[N], 1/(N y_N) mantissa
-  int Kde[2 * BLK];
+  int Te[2 * BLK];
   int Hoe[2 * BLK];
+  int K0e[2 * TILE];
+  int Ze[TW * TILE];
+  int Ne[TW * TILE];
   int Ye[YRING];
   int Ae[2 * TILE];
   int misci[4];         // 1/(N y_N) exponent
 };
+
+// Rows [i0, i0+NR) (sources) of tile tt's inverse into shared memory: T[j][i]
+// at Tm/Te[i * 33 + j] (global order: source-major, coalesced along j).
+template <bool BWD, int NR>
+__device__ __forceinline__ void stage_tinv(const Workspace &w, int tt, int i0, unsigned long long *tm, int *te) {
+  const int j = threadIdx.x & 31;
+  const size_t base = ((size_t)(BWD ? w.NT : 0) + tt) * TILE;
+  unsigned long long m[NR];
+  int e[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    m[k] = __ldg(w.Tm + (base + i0 + k) * TILE + j);
+    e[k] = __ldg(w.Te + (base + i0 + k) * TILE + j);
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    tm[(i0 + k) * 33 + j] = m[k];
+    te[(i0 + k) * 33 + j] = e[k];
+  }
+}
+
+// K(r0, r0+j) = c_j H(r0, r0+j) of tile tt (lane j), as an xk number.
+template <bool MIXED, bool BWD>
+__device__ __forceinline__ void stage_k0(const Workspace &w, int tt, unsigned long long *km, int *ke) {
+  using M_t = typename std::conditional<MIXED, float, double>::type;
+  const int j = threadIdx.x & 31;
+  const int r0 = tt * TILE, row = r0 + j;
+  M_t m = (M_t)1.0;
+  int e = XZERO_E;
+  xd c{1.0, 0};
+  if (row < w.N) {
+    c = xnorm_int(chain_coef<BWD>(w, row));
+    const size_t gi = hidx(r0, row);
+    m = __ldg((const M_t *)chain_gm<BWD>(w) + gi);
+    e = __ldg(chain_ge<BWD>(w) + gi);
+  }
+  const xk k = mul_mant<M_t>(c, m, e);
+  km[j] = k.m;
+  ke[j] = max(k.e, XZERO_E);
+}
+
+__device__ __forceinline__ void tile_bar() { asm volatile("bar.sync 1, %0;" ::"n"(TW * 32) : "memory"); }
+
+// One row tile t of the lead, run by tile warp g (of TW) with lane j = row
+// r0+j.  With a_j = c_j (A_j + nxt_j) (sources below r0) and b_j = a_j +
+// K(r0, r0+j) Y_{r0}, the tile's outputs are z = T b (T the tile inverse):
+// warp g sums the sources i in [8g, 8g+8) of every row, the partial sums meet
+// in shared memory behind one named barrier, and each warp adds the four in
+// the same order (so all hold z).  Warp g then forms its part of the next
+// tile's sums over sources k in [8g, 8g+8) of this tile (Y_{r0} for k = 0,
+// z_{k-1} otherwise); warp 0 writes z to the Y ring.  The partial next-tile
+// sums of the previous tile are combined at the start (fixed order).
+template <bool MIXED>
+__device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, LeadSmem &sm, int buf) {
+  const int j = threadIdx.x & 31;
+  const int r0 = t * TILE, row = r0 + j;
+  // nxt_j: the four partial sums of the previous period (zero at t = 0)
+  xi nx;
+  if (MIXED) {
+    float ns = 0.0f;
+    int ne = XZERO_E;
+#pragma unroll
+    for (int q = 0; q < TW; ++q) fmerge(ns, ne, __int_as_float((int)sm.Nm[q * TILE + j]), sm.Ne[q * TILE + j]);
+    nx = xi_from(xd{f2d_int(ns), ne});
+  } else {
+    nx = xi_add(xi_add(xi{sm.Nm[j], sm.Ne[j]}, xi{sm.Nm[TILE + j], sm.Ne[TILE + j]}),
+                xi_add(xi{sm.Nm[2 * TILE + j], sm.Ne[2 * TILE + j]}, xi{sm.Nm[3 * TILE + j], sm.Ne[3 * TILE + j]}));
+  }
+  xi a{1ull << 62, XZERO_E};
+  if (row < N) a = xi_mul(xi_add(xi_from(A), nx), crow);
+  const xi y0 = xi_from(xd{sm.Ym[r0 & (YRING - 1)], sm.Ye[r0 & (YRING - 1)]});
+  const xi b = xi_fma<MIXED>(a, sm.K0m[buf * TILE + j], sm.K0e[buf * TILE + j], y0);
+  // partial of z_j over sources i in [8g, 8g+8)
+  const unsigned long long *Tm = sm.Tm + buf * BLK;
+  const int *Te = sm.Te + buf * BLK;
+  xi acc{1ull << 62, XZERO_E};
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int i = 8 * g + u;
+    xi bi;
+    bi.m = __shfl_sync(0xffffffffu, b.m, i);
+    bi.e = __shfl_sync(0xffffffffu, b.e, i);
+    acc = xi_fma<MIXED>(acc, Tm[i * 33 + j], Te[i * 33 + j], bi);
+  }
+  // the previous period's next-tile partials have been read above: from here
+  // on Nm/Ne may be overwritten (the barrier orders it)
+  sm.Zm[g * TILE + j] = acc.m;
+  sm.Ze[g * TILE + j] = acc.e;
+  tile_bar();
+  const xi z = xi_add(xi_add(xi{sm.Zm[j], sm.Ze[j]}, xi{sm.Zm[TILE + j], sm.Ze[TILE + j]}),
+                      xi_add(xi{sm.Zm[2 * TILE + j], sm.Ze[2 * TILE + j]}, xi{sm.Zm[3 * TILE + j], sm.Ze[3 * TILE + j]}));
+  // next tile's rows over this tile's sources k in [8g, 8g+8)
+  const double *Hm = sm.Hom + buf * BLK;
+  const int *He = sm.Hoe + buf * BLK;
+  float ns = 0.0f;
+  int ne = XZERO_E;
+  xi np{1ull << 62, XZERO_E};
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int k = 8 * g + u;
+    xi yk;
+    yk.m = __shfl_sync(0xffffffffu, z.m, (k + 31) & 31);
+    yk.e = __shfl_sync(0xffffffffu, z.e, (k + 31) & 31);
+    if (k == 0) yk = y0;
+    const int he = He[k * 33 + j];
+    if (MIXED)
+      fmerge(ns, ne, __int_as_float((int)((yk.m >> 39) & 0x7FFFFFu) | 0x3F800000) * ((const float *)Hm)[k * 33 + j],
+             he + yk.e);
+    else
+      np = xi_fma<false>(np, mant53(Hm[k * 33 + j]) << 11, he, yk);
+  }
+  if (MIXED) {
+    sm.Nm[g * TILE + j] = (unsigned long long)(unsigned)__float_as_int(ns);
+    sm.Ne[g * TILE + j] = ne;
+  } else {
+    sm.Nm[g * TILE + j] = np.m;
+    sm.Ne[g * TILE + j] = np.e;
+  }
+  if (g == 0 && row < N) {  // Y_{row+1}
+    const xd yn = xi_to_xd(z);
+    sm.Ym[(row + 1) & (YRING - 1)] = yn.m;
+    sm.Ye[(row + 1) & (YRING - 1)] = yn.e;
+  }
+}
 
 // Shared memory of a bulk CTA: its rows' partial sums (local tile lt = T / 7),
 // one slot of 8 Y values per warp, and the partial sums of the current period
@@ -113,41 +245,43 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
   if (rank == 0) {
     LeadSmem &sm = *lead_local;
-    // Staging warps are the lead's warps off warp 0's sub-partition (warp id
-    // not a multiple of 4), numbered q = 0, 1, ...: q < 8 stage four rows each
-    // of the diagonal block, 8 <= q < 12 eight rows each of the off-diagonal
-    // block, q == 12 forms the prefix sums (forward recursion), q == 13
-    // copies each finished tile of Y to global memory one period later.
+    // Warps 0..TW-1 solve the tiles (tile_solve).  The others, s = wid - TW:
+    // s < 8 stage four source rows each of the next tile's inverse (s == 0
+    // also its first-source factors K0), 8 <= s < 12 eight rows each of the
+    // block of H from the next tile's sources to the rows after it, s == 12
+    // forms the prefix sums (forward recursion), s == 13 copies each finished
+    // tile of Y to global memory one period later.
+    const int q = wid - TW;
     if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
+    if (tid < TW * TILE) { sm.Nm[tid] = MIXED ? 0ull : (1ull << 62); sm.Ne[tid] = XZERO_E; }
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
-    const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
-    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde);
+    if (q >= 0 && q < 8) stage_tinv<BWD, 4>(w, 0, 4 * q, sm.Tm, sm.Te);
+    if (q == 0) stage_k0<MIXED, BWD>(w, 0, sm.K0m, sm.K0e);
     if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
     cluster.sync();
 
-    xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
-    xd cnext{1.0, 0};      // warp 0: coefficient of its row in the coming tile
-    if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
+    xd cnext{1.0, 0};      // tile warps: coefficient of the lane's row in the coming tile
+    if (wid < TW && lane < N) cnext = chain_coef<BWD>(w, lane);
     double carry = 0.0;    // prefix-sum warp (forward): running prefix sum
     for (int t = 0; t < NT; ++t) {
       const int buf = t & 1;
-      if (wid == 0) {
-        // ---------------------------------------------- dependent steps of tile t
+      if (wid < TW) {
         const int row = t * TILE + lane;
         const xd crow = cnext;
         if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
-        chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
-                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
-                          sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
+        tile_solve<MIXED>(N, t, wid, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, sm, buf);
       } else if (q >= 0 && q < 8) {
-        if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
+        if (t + 1 < NT) {
+          stage_tinv<BWD, 4>(w, t + 1, 4 * q, sm.Tm + (buf ^ 1) * BLK, sm.Te + (buf ^ 1) * BLK);
+          if (q == 0) stage_k0<MIXED, BWD>(w, t + 1, sm.K0m + (buf ^ 1) * TILE, sm.K0e + (buf ^ 1) * TILE);
+        }
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
           stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
       } else if (q == 13) {
-        // export Y of tile t-1 from the ring to global memory, off the chain
-        // warp (a release barrier after global stores would wait for them)
+        // export Y of tile t-1 from the ring to global memory, off the tile
+        // warps (a release barrier after global stores would wait for them)
         if (t >= 1) {
           const int v = (t - 1) * TILE + lane + 1;
           if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
@@ -302,8 +436,8 @@ constexpr size_t chain_smem_bytes(int N) {
   return lead > help ? lead : help;
 }
 static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
-static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
-              "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
+static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= TW + 14 && CHAIN_THREADS / 32 <= 32,
+              "the lead needs TW tile warps and 14 more (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 

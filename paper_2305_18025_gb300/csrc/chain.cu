@@ -158,15 +158,17 @@ __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, L
   // partial of z_j over sources i in [8g, 8g+8)
   const unsigned long long *Tm = sm.Tm + buf * BLK;
   const int *Te = sm.Te + buf * BLK;
-  xi acc{1ull << 62, XZERO_E};
+  xi acc0{1ull << 62, XZERO_E}, acc1{1ull << 62, XZERO_E};  // even / odd sources
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int i = 8 * g + u;
     xi bi;
     bi.m = __shfl_sync(0xffffffffu, b.m, i);
     bi.e = __shfl_sync(0xffffffffu, b.e, i);
-    acc = xi_fma<MIXED>(acc, Tm[i * 33 + j], Te[i * 33 + j], bi);
+    if (u & 1) acc1 = xi_fma<MIXED>(acc1, Tm[i * 33 + j], Te[i * 33 + j], bi);
+    else acc0 = xi_fma<MIXED>(acc0, Tm[i * 33 + j], Te[i * 33 + j], bi);
   }
+  const xi acc = xi_add(acc0, acc1);
   // the previous period's next-tile partials have been read above: from here
   // on Nm/Ne may be overwritten (the barrier orders it)
   sm.Zm[g * TILE + j] = acc.m;
@@ -177,9 +179,9 @@ __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, L
   // next tile's rows over this tile's sources k in [8g, 8g+8)
   const double *Hm = sm.Hom + buf * BLK;
   const int *He = sm.Hoe + buf * BLK;
-  float ns = 0.0f;
-  int ne = XZERO_E;
-  xi np{1ull << 62, XZERO_E};
+  float ns[2] = {0.0f, 0.0f};  // even / odd sources
+  int ne[2] = {XZERO_E, XZERO_E};
+  xi npp[2] = {xi{1ull << 62, XZERO_E}, xi{1ull << 62, XZERO_E}};
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = 8 * g + u;
@@ -189,14 +191,16 @@ __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, L
     if (k == 0) yk = y0;
     const int he = He[k * 33 + j];
     if (MIXED)
-      fmerge(ns, ne, __int_as_float((int)((yk.m >> 39) & 0x7FFFFFu) | 0x3F800000) * ((const float *)Hm)[k * 33 + j],
-             he + yk.e);
+      fmerge(ns[u & 1], ne[u & 1],
+             __int_as_float((int)((yk.m >> 39) & 0x7FFFFFu) | 0x3F800000) * ((const float *)Hm)[k * 33 + j], he + yk.e);
     else
-      np = xi_fma<false>(np, mant53(Hm[k * 33 + j]) << 11, he, yk);
+      npp[u & 1] = xi_fma<false>(npp[u & 1], mant53(Hm[k * 33 + j]) << 11, he, yk);
   }
+  const xi np = xi_add(npp[0], npp[1]);
+  if (MIXED) fmerge(ns[0], ne[0], ns[1], ne[1]);
   if (MIXED) {
-    sm.Nm[g * TILE + j] = (unsigned long long)(unsigned)__float_as_int(ns);
-    sm.Ne[g * TILE + j] = ne;
+    sm.Nm[g * TILE + j] = (unsigned long long)(unsigned)__float_as_int(ns[0]);
+    sm.Ne[g * TILE + j] = ne[0];
   } else {
     sm.Nm[g * TILE + j] = np.m;
     sm.Ne[g * TILE + j] = np.e;
@@ -336,15 +340,29 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     const int nwarps = (int)(blockDim.x >> 5);
     for (int q = tid; q < lt_max * TILE; q += blockDim.x) { hs.Am[q] = 0.0; hs.Ae[q] = XZERO_E; }
     cluster.sync();
+    // period tt: row tile T0(tt) + u*7 (u < units(tt)) of this CTA takes source
+    // tile tt-1; task k = 4u + quarter.  The pair-factor loads of a warp's
+    // first task of the next period are issued before each barrier (they do
+    // not depend on Y), so that only the Y values and the sums follow it.
+    auto first_owned = [&](int tt) { return (tt + 1) + ((h - (tt + 1) % NHELP) + NHELP) % NHELP; };
+    auto units = [&](int tt) {
+      const int T0 = first_owned(tt);
+      return (tt >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
+    };
+    auto task_base = [&](int tt, int k) {
+      const int r = (first_owned(tt) + (k >> 2) * NHELP) * TILE + lane;
+      return hidx((tt - 1) * TILE + 8 * (k & 3), r);  // + i * 32 for source i of the quarter
+    };
+    M_t pm[8];
+    int pe[8];
     for (int t = 0; t < NT; ++t) {
-      const int T0 = (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP;  // first owned row tile >= t+1
-      const int nunits = (t >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
+      const int T0 = first_owned(t);
+      const int nunits = units(t);
       if (nunits > 0) {
         const int srcbase = (t - 1) * TILE;
         // task k: row tile T0 + (k/4)*7, sources srcbase + 8(k%4) .. +7 (source tile t-1)
         for (int k = wid; k < 4 * nunits; k += nwarps) {
-          const int u = k >> 2, q = k & 3;
-          const int r = (T0 + u * NHELP) * TILE + lane;
+          const int q = k & 3;
           const int sb = srcbase + 8 * q;
           M_t *Ym = (M_t *)hs.Yd + wid * 8;
           int *Yx = hs.Yx + wid * 8;
@@ -354,36 +372,33 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
             Ym[lane] = MIXED ? (M_t)mant_to_float(ym) : (M_t)ym;
             Yx[lane] = lead->Ye[v & (YRING - 1)];
           }
-          __syncwarp();
-          const size_t gbase = hidx(sb, r);  // + i * 32 for source sb + i
-          if (MIXED) {
-            float m[8];
-            int e[8];
+          if (k != wid) {  // later tasks of the period load their factors now
+            const size_t gbase = task_base(t, k);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              m[i] = __ldg((const float *)gm + gbase + i * 32);
-              e[i] = __ldg(ge + gbase + i * 32);
+              pm[i] = __ldg((const M_t *)gm + gbase + i * 32);
+              pe[i] = __ldg(ge + gbase + i * 32);
             }
+          }
+          __syncwarp();
+          if (MIXED) {
             float sacc = 0.0f;
             int E = XZERO_E;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * m[i], e[i] + Yx[i]);
+            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * (float)pm[i], pe[i] + Yx[i]);
             ((float *)hs.Pm)[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           } else {
-            double m[8];
             int e[8];
             int E = XZERO_E;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              m[i] = __ldg((const double *)gm + gbase + i * 32);
-              e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
+              e[i] = pe[i] + Yx[i];
+              E = max(E, e[i]);
             }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) E = max(E, e[i]);
             double sacc = 0.0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos(m[i], e[i] - E), (double)Ym[i], sacc);
+            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos((double)pm[i], e[i] - E), (double)Ym[i], sacc);
             hs.Pm[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           }
@@ -414,6 +429,14 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
             lead->Am[slot] = acc.m;
             lead->Ae[slot] = acc.e;
           }
+        }
+      }
+      if (t + 1 < NT && wid < 4 * units(t + 1)) {  // the next period's first task
+        const size_t gbase = task_base(t + 1, wid);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          pm[i] = __ldg((const M_t *)gm + gbase + i * 32);
+          pe[i] = __ldg(ge + gbase + i * 32);
         }
       }
       cluster.sync();

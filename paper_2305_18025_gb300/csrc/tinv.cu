@@ -13,7 +13,7 @@
 // the recursion kernel then applies T to b instead of stepping through the 32
 // dependent rows.  One warp per (recursion, tile): lane c owns column c and
 // forms row j as sum_{k=c}^{j-1} M[j][k] T[k][c] in the integer-pipe chain
-// format (xi_fma).  Output: T[j][i] (row j, source i) at
+// format (xi_fma), as four interleaved partial sums.  Output: T[j][i] (row j, source i) at
 // Tm/Te[((recursion * NT + t) * 32 + i) * 32 + j] as 64-bit mantissas.
 #include "chain_common.cuh"
 
@@ -65,13 +65,22 @@ __device__ __forceinline__ void tile_inverse(const Workspace &w, int t, TinvSmem
   const int cc = lane;
   S.Xm[cc][cc] = 1ull << 62;
   S.Xe[cc][cc] = 0;
+  // four independent partial sums (k mod 4) keep four products in flight
   for (int j = 1; j < TILE; ++j) {
-    xi acc{1ull << 62, XZERO_E};
-    for (int k = 0; k < j; ++k)
-      if (k >= cc) acc = xi_fma<MIXED>(acc, S.Mm[j][k], S.Me[j][k], xi{S.Xm[k][cc], S.Xe[k][cc]});
+    xi acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = xi{1ull << 62, XZERO_E};
+    for (int k0 = (cc & ~3); k0 < j; k0 += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        if (k < j && k >= cc) acc[u] = xi_fma<MIXED>(acc[u], S.Mm[j][k], S.Me[j][k], xi{S.Xm[k][cc], S.Xe[k][cc]});
+      }
+    }
+    const xi sum = xi_add(xi_add(acc[0], acc[1]), xi_add(acc[2], acc[3]));
     if (j > cc) {
-      S.Xm[j][cc] = acc.m;
-      S.Xe[j][cc] = acc.e;
+      S.Xm[j][cc] = sum.m;
+      S.Xe[j][cc] = sum.e;
     }
   }
   __syncwarp();

@@ -37,44 +37,51 @@ __device__ __forceinline__ void tile_inverse(const Workspace &w, int t, TinvSmem
   const bool valid = row < w.N;
   const M_t *gm = (const M_t *)chain_gm<BWD>(w);
   const int *ge = chain_ge<BWD>(w);
-  // M[j][k] = c_j H(r0+k+1, r0+j) for k+1 <= j (lane = j), loads issued 8 at a time
+  // M[j][k] = c_j H(r0+k+1, r0+j) for k+1 <= j (lane = j).  Branch-free: every
+  // lane loads 8 entries at a time from in-bounds addresses (the diagonal
+  // entry where k+1 > j) and keeps an extended zero outside the triangle.
   const xd c = valid ? xnorm_int(chain_coef<BWD>(w, row)) : xd{1.0, 0};
+  const int rowc = valid ? row : r0;  // a row of this tile inside [0, N)
   for (int k0 = 0; k0 < TILE; k0 += 8) {
     M_t m[8];
     int e[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int k = k0 + u;
-      m[u] = (M_t)1.0;
-      e[u] = XZERO_E;
-      if (valid && k + 1 <= lane) {
-        const size_t gi = hidx(r0 + k + 1, row);
-        m[u] = __ldg(gm + gi);
-        e[u] = __ldg(ge + gi);
-      }
+      const int src = r0 + min(k0 + u + 1, rowc - r0);
+      const size_t gi = hidx(src, rowc);
+      m[u] = __ldg(gm + gi);
+      e[u] = __ldg(ge + gi);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const xk v = mul_mant<M_t>(c, m[u], e[u]);
+      const bool on = valid && k0 + u + 1 <= lane;
+      const xk v = mul_mant<M_t>(c, m[u], on ? e[u] : XZERO_E);
       S.Mm[lane][k0 + u] = v.m;
-      S.Me[lane][k0 + u] = max(v.e, XZERO_E);
+      S.Me[lane][k0 + u] = on ? max(v.e, XZERO_E) : XZERO_E;
     }
   }
   __syncwarp();
-  // column c = lane: T[c][c] = 1, T[j][c] = sum_{k=c}^{j-1} M[j][k] T[k][c]
+  // column c = lane: T[c][c] = 1, T[j][c] = sum_{k=c}^{j-1} M[j][k] T[k][c],
+  // as four interleaved partial sums over a warp-uniform loop; terms outside
+  // c <= k < j enter as exact no-ops (an extended-zero factor times 1)
   const int cc = lane;
   S.Xm[cc][cc] = 1ull << 62;
   S.Xe[cc][cc] = 0;
-  // four independent partial sums (k mod 4) keep four products in flight
   for (int j = 1; j < TILE; ++j) {
     xi acc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[u] = xi{1ull << 62, XZERO_E};
-    for (int k0 = (cc & ~3); k0 < j; k0 += 4) {
+    for (int k0 = 0; k0 < j; k0 += 4) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int k = k0 + u;
-        if (k < j && k >= cc) acc[u] = xi_fma<MIXED>(acc[u], S.Mm[j][k], S.Me[j][k], xi{S.Xm[k][cc], S.Xe[k][cc]});
+        const bool on = k < j && k >= cc;
+        const int kc = min(k, TILE - 1);
+        const unsigned long long mm = S.Mm[j][kc];
+        const int me = S.Me[j][kc];
+        const unsigned long long xm = S.Xm[kc][cc];
+        const int xe = S.Xe[kc][cc];
+        acc[u] = xi_fma<MIXED>(acc[u], mm, on ? me : XZERO_E, on ? xi{xm, xe} : xi{1ull << 62, 0});
       }
     }
     const xi sum = xi_add(xi_add(acc[0], acc[1]), xi_add(acc[2], acc[3]));

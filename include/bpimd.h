@@ -253,7 +253,7 @@ int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
  * context: cfg describes the system (N, P, m, omega_P, beta, precision; the MD
  * fields are ignored), positions/V_B/forces are device pointers owned by the
  * caller, cuda_stream is a cudaStream_t (NULL = default stream).  It allocates
- * nothing: its scratch memory is one file-scope __device__ array of 2 MiB per
+ * nothing: its scratch memory is one file-scope __device__ array of 1 MiB per
  * device, which bounds the size to N <= BPIMD_NOALLOC_MAX_N (larger N returns
  * BPIMD_ERR_SIZE before any work is enqueued).
  *   - The first call on a device, with that device current, looks up the

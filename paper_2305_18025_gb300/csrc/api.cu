@@ -87,13 +87,6 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.ale = (int *)take(sizeof(int) * N);
   w.scal = (double *)take(sizeof(double) * 4);
   w.scal_i = (int *)take(sizeof(int) * 4);
-  if (w.tile_inv) {
-    w.Tm = (unsigned long long *)take(sizeof(unsigned long long) * 2 * NT * TILE2);
-    w.Te = (int *)take(sizeof(int) * 2 * NT * TILE2);
-  } else {
-    w.Tm = nullptr;
-    w.Te = nullptr;
-  }
   w.rowpart = (double *)take(sizeof(double) * NB * TILE * 4);
   w.colpart = (double *)take(sizeof(double) * NB * TILE * 4);
   w.rowcnt = (int *)take(sizeof(int) * NT);
@@ -113,7 +106,6 @@ int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   mark(0);
   if (launch_prep(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(1);
-  if (launch_tile_inverses(w, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(2);
   if (launch_prob_forces(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
@@ -145,7 +137,6 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
-  w.tile_inv = 1;
   set_box(w, cfg->box_L);
   const size_t N = w.N;
   // one allocation: the workspace, then the diagnostic potentials

@@ -91,7 +91,6 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
     w.beta = beta[r];
     w.k = cfg->m * omega_P[r] * omega_P[r];
     w.half_k = 0.5 * w.k;
-    w.tile_inv = 0;  // one CTA per recursion: the stepwise tile solve, no tile inverses
     wbytes += align256(layout_workspace(w, nullptr));
     ctx->h_off[r] = off;
     off += 3LL * N[r] * P[r];

@@ -172,12 +172,6 @@ struct Workspace {
   void *alm; int *ale;
   // scalars: [0] V_B, [1] invZ mantissa, [2] reserved ; int [0] invZ exponent
   double *scal; int *scal_i;
-  // inverses T_t = (I - M_t)^{-1} of the row tiles' unit lower-triangular
-  // systems (both recursions), [2][NT][32 sources i][32 rows j] as 64-bit
-  // integer mantissas and exponents (tile_inv != 0 only: the cluster recursion)
-  unsigned long long *Tm;
-  int *Te;
-  int tile_inv;
   // force partial sums: rowpart/colpart [NB][TILE][4]
   double *rowpart, *colpart;
   // per row / column tile: number of finished blocks of the probability pass
@@ -258,8 +252,6 @@ cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaSt
 // fill the pair-factor entries outside a <= b < N (fixed for a given N) with
 // extended zeros; needed once per workspace before the first launch_prep
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s);
-// tile inverses of both recursions (workspaces with tile_inv set)
-cudaError_t launch_tile_inverses(const Workspace &w, cudaStream_t s);
 // both recursions, prefix sums, V_B (device scalar, may be null), normaliser, alpha
 cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
 // connection probabilities and all exterior-bead forces

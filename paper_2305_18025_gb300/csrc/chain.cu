@@ -63,78 +63,84 @@ constexpr int NHELP = CHAIN_CLUSTER - 1;  // bulk CTAs per recursion
 constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
 constexpr int TW = 4;                     // tile warps of the lead (one per SM sub-partition)
+constexpr int DB = 8;                     // rows per diagonal sub-block of a tile
+constexpr int NDB = TILE / DB;            // sub-blocks per tile
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  unsigned long long Tm[2 * BLK];  // tile inverse T[j][i] at [i * 33 + j] (double buffer)
+  unsigned long long Km[2 * BLK];  // K(source i, row j) = c_j H of the tile at [i * 33 + j] (double buffer)
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
-  unsigned long long K0m[2 * TILE];  // K(r0, r0+j): the tile's first source (double buffer)
-  unsigned long long Zm[TW * TILE];  // per tile warp: partial sums of z = T b
+  unsigned long long Dm[2 * TILE * DB];  // sub-block inverses D_s[jj][i] at [(s * DB + jj) * DB + i] (double buffer)
   unsigned long long Nm[TW * TILE];  // per tile warp: partial next-tile sums (MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
   double misc[4];       // end of the forward recursion: C[N], 1/(N y_N) mantissa
-  int Te[2 * BLK];
+  int Ke[2 * BLK];
   int Hoe[2 * BLK];
-  int K0e[2 * TILE];
-  int Ze[TW * TILE];
+  int De[2 * TILE * DB];
   int Ne[TW * TILE];
   int Ye[YRING];
   int Ae[2 * TILE];
   int misci[4];         // 1/(N y_N) exponent
 };
 
-// Rows [i0, i0+NR) (sources) of tile tt's inverse into shared memory: T[j][i]
-// at Tm/Te[i * 33 + j] (global order: source-major, coalesced along j).
-template <bool BWD, int NR>
-__device__ __forceinline__ void stage_tinv(const Workspace &w, int tt, int i0, unsigned long long *tm, int *te) {
-  const int j = threadIdx.x & 31;
-  const size_t base = ((size_t)(BWD ? w.NT : 0) + tt) * TILE;
-  unsigned long long m[NR];
-  int e[NR];
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    m[k] = __ldg(w.Tm + (base + i0 + k) * TILE + j);
-    e[k] = __ldg(w.Te + (base + i0 + k) * TILE + j);
-  }
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    tm[(i0 + k) * 33 + j] = m[k];
-    te[(i0 + k) * 33 + j] = e[k];
-  }
+// Named barrier 2: the eight warps staging a tile's block K arrive (without
+// waiting) once they have stored it, the sub-block warp waits for them.
+constexpr int KSTAGE_WARPS = 8;
+__device__ __forceinline__ void kstage_arrive() {
+  asm volatile("bar.arrive 2, %0;" ::"n"((KSTAGE_WARPS + 1) * 32) : "memory");
 }
+__device__ __forceinline__ void kstage_wait() { asm volatile("bar.sync 2, %0;" ::"n"((KSTAGE_WARPS + 1) * 32) : "memory"); }
 
-// K(r0, r0+j) = c_j H(r0, r0+j) of tile tt (lane j), as an xk number.
-template <bool MIXED, bool BWD>
-__device__ __forceinline__ void stage_k0(const Workspace &w, int tt, unsigned long long *km, int *ke) {
-  using M_t = typename std::conditional<MIXED, float, double>::type;
-  const int j = threadIdx.x & 31;
-  const int r0 = tt * TILE, row = r0 + j;
-  M_t m = (M_t)1.0;
-  int e = XZERO_E;
-  xd c{1.0, 0};
-  if (row < w.N) {
-    c = xnorm_int(chain_coef<BWD>(w, row));
-    const size_t gi = hidx(r0, row);
-    m = __ldg((const M_t *)chain_gm<BWD>(w) + gi);
-    e = __ldg(chain_ge<BWD>(w) + gi);
+// Inverses of the tile's diagonal sub-blocks.  Row tile tt (rows r0 + j,
+// outputs z_j = Y_{r0+j+1}) solves z_j = b_j + sum_{k<j} M[j][k] z_k with
+// M[j][k] = K(r0+k+1, r0+j); on sub-block s (rows 8s .. 8s+7) this reads
+//   z_S = D_s (b_S + M_{S,<S} z_{<S}),  D_s = (I - M_SS)^{-1}
+// (unit lower triangular, nonnegative: no cancellation).  One warp, lane =
+// (s, column i): x_i = 1, x_jj = sum_{k=i}^{jj-1} M[8s+jj][8s+k] x_k, with
+// the factors read from the staged block K (Km/Ke at [source * 33 + row]);
+// stored as xk numbers at Dm/De[(s * DB + jj) * DB + i].
+template <bool MIXED>
+__device__ __forceinline__ void stage_dblocks(const unsigned long long *Km, const int *Ke, unsigned long long *Dm,
+                                              int *De) {
+  const int lane = threadIdx.x & 31, sb = lane >> 3, i = lane & (DB - 1);
+  xi x[DB];
+#pragma unroll
+  for (int jj = 0; jj < DB; ++jj) x[jj] = xi{1ull << 62, jj == i ? 0 : XZERO_E};
+#pragma unroll
+  for (int jj = 1; jj < DB; ++jj) {
+    xi acc0{1ull << 62, XZERO_E}, acc1{1ull << 62, XZERO_E};
+#pragma unroll
+    for (int k = 0; k < jj; ++k) {
+      const bool on = k >= i;
+      const int ki = (DB * sb + k + 1) * 33 + DB * sb + jj;  // K(source 8s+k+1, row 8s+jj)
+      const unsigned long long km = Km[ki];
+      const int ke = on ? Ke[ki] : XZERO_E;
+      const xi xv = on ? x[k] : xi{1ull << 62, 0};
+      if (k & 1) acc1 = xi_fma<MIXED>(acc1, km, ke, xv);
+      else acc0 = xi_fma<MIXED>(acc0, km, ke, xv);
+    }
+    const xi sum = xi_add(acc0, acc1);
+    if (jj > i) x[jj] = sum;
   }
-  const xk k = mul_mant<M_t>(c, m, e);
-  km[j] = k.m;
-  ke[j] = max(k.e, XZERO_E);
+#pragma unroll
+  for (int jj = 0; jj < DB; ++jj) {
+    Dm[(sb * DB + jj) * DB + i] = x[jj].m << 1;
+    De[(sb * DB + jj) * DB + i] = max(x[jj].e, XZERO_E);
+  }
 }
 
 __device__ __forceinline__ void tile_bar() { asm volatile("bar.sync 1, %0;" ::"n"(TW * 32) : "memory"); }
 
-// One row tile t of the lead, run by tile warp g (of TW) with lane j = row
-// r0+j.  With a_j = c_j (A_j + nxt_j) (sources below r0) and b_j = a_j +
-// K(r0, r0+j) Y_{r0}, the tile's outputs are z = T b (T the tile inverse):
-// warp g sums the sources i in [8g, 8g+8) of every row, the partial sums meet
-// in shared memory behind one named barrier, and each warp adds the four in
-// the same order (so all hold z).  Warp g then forms its part of the next
-// tile's sums over sources k in [8g, 8g+8) of this tile (Y_{r0} for k = 0,
-// z_{k-1} otherwise); warp 0 writes z to the Y ring.  The partial next-tile
-// sums of the previous tile are combined at the start (fixed order).
+// One row tile t of the lead, run redundantly by each tile warp g (lane j =
+// row r0+j), so that no barrier is needed between them.  With a_j = c_j (A_j
+// + nxt_j) (sources below r0) and b_j = a_j + K(r0, r0+j) Y_{r0}, the tile is
+// solved by four sub-block steps: z_S = D_s acc_S (acc_S = b_S plus the
+// earlier sub-blocks' terms), then every row adds K(8s+i+1, j) z_{8s+i} of
+// the new sub-block.  Warp g then forms its part of the next tile's sums
+// over sources k in [8g, 8g+8) of this tile (Y_{r0} for k = 0, z_{k-1}
+// otherwise); warp 0 writes z to the Y ring.  The partial next-tile sums of
+// the previous tile are combined at the start in a fixed order.
 template <bool MIXED>
 __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, LeadSmem &sm, int buf) {
   const int j = threadIdx.x & 31;
@@ -154,28 +160,42 @@ __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, L
   xi a{1ull << 62, XZERO_E};
   if (row < N) a = xi_mul(xi_add(xi_from(A), nx), crow);
   const xi y0 = xi_from(xd{sm.Ym[r0 & (YRING - 1)], sm.Ye[r0 & (YRING - 1)]});
-  const xi b = xi_fma<MIXED>(a, sm.K0m[buf * TILE + j], sm.K0e[buf * TILE + j], y0);
-  // partial of z_j over sources i in [8g, 8g+8)
-  const unsigned long long *Tm = sm.Tm + buf * BLK;
-  const int *Te = sm.Te + buf * BLK;
-  xi acc0{1ull << 62, XZERO_E}, acc1{1ull << 62, XZERO_E};  // even / odd sources
+  const unsigned long long *Km = sm.Km + buf * BLK;
+  const int *Ke = sm.Ke + buf * BLK;
+  const unsigned long long *Dm = sm.Dm + buf * TILE * DB;
+  const int *De = sm.De + buf * TILE * DB;
+  xi acc = xi_fma<MIXED>(a, Km[j], Ke[j], y0);  // b_j
+  xi z = acc;
+  const int jj = j & (DB - 1);
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int i = 8 * g + u;
-    xi bi;
-    bi.m = __shfl_sync(0xffffffffu, b.m, i);
-    bi.e = __shfl_sync(0xffffffffu, b.e, i);
-    if (u & 1) acc1 = xi_fma<MIXED>(acc1, Tm[i * 33 + j], Te[i * 33 + j], bi);
-    else acc0 = xi_fma<MIXED>(acc0, Tm[i * 33 + j], Te[i * 33 + j], bi);
+  for (int sb = 0; sb < NDB; ++sb) {
+    // z of sub-block sb: D_sb applied to its rows' sums (lanes 8sb .. 8sb+7)
+    xi d0{1ull << 62, XZERO_E}, d1{1ull << 62, XZERO_E};
+#pragma unroll
+    for (int i = 0; i < DB; ++i) {
+      xi ai;
+      ai.m = __shfl_sync(0xffffffffu, acc.m, DB * sb + i);
+      ai.e = __shfl_sync(0xffffffffu, acc.e, DB * sb + i);
+      const int di = (sb * DB + jj) * DB + i;
+      if (i & 1) d1 = xi_fma<MIXED>(d1, Dm[di], De[di], ai);
+      else d0 = xi_fma<MIXED>(d0, Dm[di], De[di], ai);
+    }
+    const xi zs = xi_add(d0, d1);
+    if ((j >> 3) == sb) z = zs;
+    if (sb + 1 < NDB) {  // the later rows take in this sub-block's outputs (sources 8sb+i+1)
+      xi u1{1ull << 62, XZERO_E};
+#pragma unroll
+      for (int i = 0; i < DB; ++i) {
+        xi zi;
+        zi.m = __shfl_sync(0xffffffffu, zs.m, DB * sb + i);
+        zi.e = __shfl_sync(0xffffffffu, zs.e, DB * sb + i);
+        const int ki = (DB * sb + i + 1) * 33 + j;
+        if (i & 1) u1 = xi_fma<MIXED>(u1, Km[ki], Ke[ki], zi);
+        else acc = xi_fma<MIXED>(acc, Km[ki], Ke[ki], zi);
+      }
+      acc = xi_add(acc, u1);
+    }
   }
-  const xi acc = xi_add(acc0, acc1);
-  // the previous period's next-tile partials have been read above: from here
-  // on Nm/Ne may be overwritten (the barrier orders it)
-  sm.Zm[g * TILE + j] = acc.m;
-  sm.Ze[g * TILE + j] = acc.e;
-  tile_bar();
-  const xi z = xi_add(xi_add(xi{sm.Zm[j], sm.Ze[j]}, xi{sm.Zm[TILE + j], sm.Ze[TILE + j]}),
-                      xi_add(xi{sm.Zm[2 * TILE + j], sm.Ze[2 * TILE + j]}, xi{sm.Zm[3 * TILE + j], sm.Ze[3 * TILE + j]}));
   // next tile's rows over this tile's sources k in [8g, 8g+8)
   const double *Hm = sm.Hom + buf * BLK;
   const int *He = sm.Hoe + buf * BLK;
@@ -198,6 +218,7 @@ __device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, L
   }
   const xi np = xi_add(npp[0], npp[1]);
   if (MIXED) fmerge(ns[0], ne[0], ns[1], ne[1]);
+  tile_bar();  // all four warps have read the previous partials
   if (MIXED) {
     sm.Nm[g * TILE + j] = (unsigned long long)(unsigned)__float_as_int(ns[0]);
     sm.Ne[g * TILE + j] = ne[0];
@@ -249,19 +270,25 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
   if (rank == 0) {
     LeadSmem &sm = *lead_local;
-    // Warps 0..TW-1 solve the tiles (tile_solve).  The others, s = wid - TW:
-    // s < 8 stage four source rows each of the next tile's inverse (s == 0
-    // also its first-source factors K0), 8 <= s < 12 eight rows each of the
-    // block of H from the next tile's sources to the rows after it, s == 12
-    // forms the prefix sums (forward recursion), s == 13 copies each finished
-    // tile of Y to global memory one period later.
+    // Warps 0..TW-1 solve the tiles (tile_solve).  The others, q = wid - TW,
+    // prepare the next tile: q < 8 stage four source rows each of its block
+    // K = c H, 8 <= q < 12 eight rows each of the block of H from its sources
+    // to the rows after it, q == 14 the inverses of its diagonal sub-blocks;
+    // q == 12 forms the prefix sums (forward recursion), q == 13 copies each
+    // finished tile of Y to global memory one period later.
     const int q = wid - TW;
     if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
     if (tid < TW * TILE) { sm.Nm[tid] = MIXED ? 0ull : (1ull << 62); sm.Ne[tid] = XZERO_E; }
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
-    if (q >= 0 && q < 8) stage_tinv<BWD, 4>(w, 0, 4 * q, sm.Tm, sm.Te);
-    if (q == 0) stage_k0<MIXED, BWD>(w, 0, sm.K0m, sm.K0e);
+    if (q >= 0 && q < KSTAGE_WARPS) {
+      stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Km, sm.Ke);
+      kstage_arrive();
+    }
+    if (q == 14) {
+      kstage_wait();
+      stage_dblocks<MIXED>(sm.Km, sm.Ke, sm.Dm, sm.De);
+    }
     if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
     cluster.sync();
 
@@ -275,14 +302,20 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         const xd crow = cnext;
         if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
         tile_solve<MIXED>(N, t, wid, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, sm, buf);
-      } else if (q >= 0 && q < 8) {
+      } else if (q >= 0 && q < KSTAGE_WARPS) {
         if (t + 1 < NT) {
-          stage_tinv<BWD, 4>(w, t + 1, 4 * q, sm.Tm + (buf ^ 1) * BLK, sm.Te + (buf ^ 1) * BLK);
-          if (q == 0) stage_k0<MIXED, BWD>(w, t + 1, sm.K0m + (buf ^ 1) * TILE, sm.K0e + (buf ^ 1) * TILE);
+          stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Km + (buf ^ 1) * BLK, sm.Ke + (buf ^ 1) * BLK);
+          kstage_arrive();
         }
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
           stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
+      } else if (q == 14) {
+        if (t + 1 < NT) {
+          kstage_wait();
+          stage_dblocks<MIXED>(sm.Km + (buf ^ 1) * BLK, sm.Ke + (buf ^ 1) * BLK, sm.Dm + (buf ^ 1) * TILE * DB,
+                               sm.De + (buf ^ 1) * TILE * DB);
+        }
       } else if (q == 13) {
         // export Y of tile t-1 from the ring to global memory, off the tile
         // warps (a release barrier after global stores would wait for them)
@@ -459,8 +492,8 @@ constexpr size_t chain_smem_bytes(int N) {
   return lead > help ? lead : help;
 }
 static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
-static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= TW + 14 && CHAIN_THREADS / 32 <= 32,
-              "the lead needs TW tile warps and 14 more (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
+static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= TW + 15 && CHAIN_THREADS / 32 <= 32,
+              "the lead needs TW tile warps and 15 more (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 

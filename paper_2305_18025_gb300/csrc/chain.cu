@@ -62,176 +62,19 @@ using namespace chain_detail;
 constexpr int NHELP = CHAIN_CLUSTER - 1;  // bulk CTAs per recursion
 constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
-constexpr int TW = 4;                     // tile warps of the lead (one per SM sub-partition)
-constexpr int DB = 8;                     // rows per diagonal sub-block of a tile
-constexpr int NDB = TILE / DB;            // sub-blocks per tile
-
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  unsigned long long Km[2 * BLK];  // K(source i, row j) = c_j H of the tile at [i * 33 + j] (double buffer)
+  unsigned long long Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
-  unsigned long long Dm[2 * TILE * DB];  // sub-block inverses D_s[jj][i] at [(s * DB + jj) * DB + i] (double buffer)
-  unsigned long long Nm[TW * TILE];  // per tile warp: partial next-tile sums (MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
   double misc[4];       // end of the forward recursion: C[N], 1/(N y_N) mantissa
-  int Ke[2 * BLK];
+  int Kde[2 * BLK];
   int Hoe[2 * BLK];
-  int De[2 * TILE * DB];
-  int Ne[TW * TILE];
   int Ye[YRING];
   int Ae[2 * TILE];
   int misci[4];         // 1/(N y_N) exponent
 };
-
-// Named barrier 2: the eight warps staging a tile's block K arrive (without
-// waiting) once they have stored it, the sub-block warp waits for them.
-constexpr int KSTAGE_WARPS = 8;
-__device__ __forceinline__ void kstage_arrive() {
-  asm volatile("bar.arrive 2, %0;" ::"n"((KSTAGE_WARPS + 1) * 32) : "memory");
-}
-__device__ __forceinline__ void kstage_wait() { asm volatile("bar.sync 2, %0;" ::"n"((KSTAGE_WARPS + 1) * 32) : "memory"); }
-
-// Inverses of the tile's diagonal sub-blocks.  Row tile tt (rows r0 + j,
-// outputs z_j = Y_{r0+j+1}) solves z_j = b_j + sum_{k<j} M[j][k] z_k with
-// M[j][k] = K(r0+k+1, r0+j); on sub-block s (rows 8s .. 8s+7) this reads
-//   z_S = D_s (b_S + M_{S,<S} z_{<S}),  D_s = (I - M_SS)^{-1}
-// (unit lower triangular, nonnegative: no cancellation).  One warp, lane =
-// (s, column i): x_i = 1, x_jj = sum_{k=i}^{jj-1} M[8s+jj][8s+k] x_k, with
-// the factors read from the staged block K (Km/Ke at [source * 33 + row]);
-// stored as xk numbers at Dm/De[(s * DB + jj) * DB + i].
-template <bool MIXED>
-__device__ __forceinline__ void stage_dblocks(const unsigned long long *Km, const int *Ke, unsigned long long *Dm,
-                                              int *De) {
-  const int lane = threadIdx.x & 31, sb = lane >> 3, i = lane & (DB - 1);
-  xi x[DB];
-#pragma unroll
-  for (int jj = 0; jj < DB; ++jj) x[jj] = xi{1ull << 62, jj == i ? 0 : XZERO_E};
-#pragma unroll
-  for (int jj = 1; jj < DB; ++jj) {
-    xi acc0{1ull << 62, XZERO_E}, acc1{1ull << 62, XZERO_E};
-#pragma unroll
-    for (int k = 0; k < jj; ++k) {
-      const bool on = k >= i;
-      const int ki = (DB * sb + k + 1) * 33 + DB * sb + jj;  // K(source 8s+k+1, row 8s+jj)
-      const unsigned long long km = Km[ki];
-      const int ke = on ? Ke[ki] : XZERO_E;
-      const xi xv = on ? x[k] : xi{1ull << 62, 0};
-      if (k & 1) acc1 = xi_fma<MIXED>(acc1, km, ke, xv);
-      else acc0 = xi_fma<MIXED>(acc0, km, ke, xv);
-    }
-    const xi sum = xi_add(acc0, acc1);
-    if (jj > i) x[jj] = sum;
-  }
-#pragma unroll
-  for (int jj = 0; jj < DB; ++jj) {
-    Dm[(sb * DB + jj) * DB + i] = x[jj].m << 1;
-    De[(sb * DB + jj) * DB + i] = max(x[jj].e, XZERO_E);
-  }
-}
-
-__device__ __forceinline__ void tile_bar() { asm volatile("bar.sync 1, %0;" ::"n"(TW * 32) : "memory"); }
-
-// One row tile t of the lead, run redundantly by each tile warp g (lane j =
-// row r0+j), so that no barrier is needed between them.  With a_j = c_j (A_j
-// + nxt_j) (sources below r0) and b_j = a_j + K(r0, r0+j) Y_{r0}, the tile is
-// solved by four sub-block steps: z_S = D_s acc_S (acc_S = b_S plus the
-// earlier sub-blocks' terms), then every row adds K(8s+i+1, j) z_{8s+i} of
-// the new sub-block.  Warp g then forms its part of the next tile's sums
-// over sources k in [8g, 8g+8) of this tile (Y_{r0} for k = 0, z_{k-1}
-// otherwise); warp 0 writes z to the Y ring.  The partial next-tile sums of
-// the previous tile are combined at the start in a fixed order.
-template <bool MIXED>
-__device__ __forceinline__ void tile_solve(int N, int t, int g, xd A, xd crow, LeadSmem &sm, int buf) {
-  const int j = threadIdx.x & 31;
-  const int r0 = t * TILE, row = r0 + j;
-  // nxt_j: the four partial sums of the previous period (zero at t = 0)
-  xi nx;
-  if (MIXED) {
-    float ns = 0.0f;
-    int ne = XZERO_E;
-#pragma unroll
-    for (int q = 0; q < TW; ++q) fmerge(ns, ne, __int_as_float((int)sm.Nm[q * TILE + j]), sm.Ne[q * TILE + j]);
-    nx = xi_from(xd{f2d_int(ns), ne});
-  } else {
-    nx = xi_add(xi_add(xi{sm.Nm[j], sm.Ne[j]}, xi{sm.Nm[TILE + j], sm.Ne[TILE + j]}),
-                xi_add(xi{sm.Nm[2 * TILE + j], sm.Ne[2 * TILE + j]}, xi{sm.Nm[3 * TILE + j], sm.Ne[3 * TILE + j]}));
-  }
-  xi a{1ull << 62, XZERO_E};
-  if (row < N) a = xi_mul(xi_add(xi_from(A), nx), crow);
-  const xi y0 = xi_from(xd{sm.Ym[r0 & (YRING - 1)], sm.Ye[r0 & (YRING - 1)]});
-  const unsigned long long *Km = sm.Km + buf * BLK;
-  const int *Ke = sm.Ke + buf * BLK;
-  const unsigned long long *Dm = sm.Dm + buf * TILE * DB;
-  const int *De = sm.De + buf * TILE * DB;
-  xi acc = xi_fma<MIXED>(a, Km[j], Ke[j], y0);  // b_j
-  xi z = acc;
-  const int jj = j & (DB - 1);
-#pragma unroll
-  for (int sb = 0; sb < NDB; ++sb) {
-    // z of sub-block sb: D_sb applied to its rows' sums (lanes 8sb .. 8sb+7)
-    xi d0{1ull << 62, XZERO_E}, d1{1ull << 62, XZERO_E};
-#pragma unroll
-    for (int i = 0; i < DB; ++i) {
-      xi ai;
-      ai.m = __shfl_sync(0xffffffffu, acc.m, DB * sb + i);
-      ai.e = __shfl_sync(0xffffffffu, acc.e, DB * sb + i);
-      const int di = (sb * DB + jj) * DB + i;
-      if (i & 1) d1 = xi_fma<MIXED>(d1, Dm[di], De[di], ai);
-      else d0 = xi_fma<MIXED>(d0, Dm[di], De[di], ai);
-    }
-    const xi zs = xi_add(d0, d1);
-    if ((j >> 3) == sb) z = zs;
-    if (sb + 1 < NDB) {  // the later rows take in this sub-block's outputs (sources 8sb+i+1)
-      xi u1{1ull << 62, XZERO_E};
-#pragma unroll
-      for (int i = 0; i < DB; ++i) {
-        xi zi;
-        zi.m = __shfl_sync(0xffffffffu, zs.m, DB * sb + i);
-        zi.e = __shfl_sync(0xffffffffu, zs.e, DB * sb + i);
-        const int ki = (DB * sb + i + 1) * 33 + j;
-        if (i & 1) u1 = xi_fma<MIXED>(u1, Km[ki], Ke[ki], zi);
-        else acc = xi_fma<MIXED>(acc, Km[ki], Ke[ki], zi);
-      }
-      acc = xi_add(acc, u1);
-    }
-  }
-  // next tile's rows over this tile's sources k in [8g, 8g+8)
-  const double *Hm = sm.Hom + buf * BLK;
-  const int *He = sm.Hoe + buf * BLK;
-  float ns[2] = {0.0f, 0.0f};  // even / odd sources
-  int ne[2] = {XZERO_E, XZERO_E};
-  xi npp[2] = {xi{1ull << 62, XZERO_E}, xi{1ull << 62, XZERO_E}};
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int k = 8 * g + u;
-    xi yk;
-    yk.m = __shfl_sync(0xffffffffu, z.m, (k + 31) & 31);
-    yk.e = __shfl_sync(0xffffffffu, z.e, (k + 31) & 31);
-    if (k == 0) yk = y0;
-    const int he = He[k * 33 + j];
-    if (MIXED)
-      fmerge(ns[u & 1], ne[u & 1],
-             __int_as_float((int)((yk.m >> 39) & 0x7FFFFFu) | 0x3F800000) * ((const float *)Hm)[k * 33 + j], he + yk.e);
-    else
-      npp[u & 1] = xi_fma<false>(npp[u & 1], mant53(Hm[k * 33 + j]) << 11, he, yk);
-  }
-  const xi np = xi_add(npp[0], npp[1]);
-  if (MIXED) fmerge(ns[0], ne[0], ns[1], ne[1]);
-  tile_bar();  // all four warps have read the previous partials
-  if (MIXED) {
-    sm.Nm[g * TILE + j] = (unsigned long long)(unsigned)__float_as_int(ns[0]);
-    sm.Ne[g * TILE + j] = ne[0];
-  } else {
-    sm.Nm[g * TILE + j] = np.m;
-    sm.Ne[g * TILE + j] = np.e;
-  }
-  if (g == 0 && row < N) {  // Y_{row+1}
-    const xd yn = xi_to_xd(z);
-    sm.Ym[(row + 1) & (YRING - 1)] = yn.m;
-    sm.Ye[(row + 1) & (YRING - 1)] = yn.e;
-  }
-}
 
 // Shared memory of a bulk CTA: its rows' partial sums (local tile lt = T / 7),
 // one slot of 8 Y values per warp, and the partial sums of the current period
@@ -270,55 +113,41 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
   if (rank == 0) {
     LeadSmem &sm = *lead_local;
-    // Warps 0..TW-1 solve the tiles (tile_solve).  The others, q = wid - TW,
-    // prepare the next tile: q < 8 stage four source rows each of its block
-    // K = c H, 8 <= q < 12 eight rows each of the block of H from its sources
-    // to the rows after it, q == 14 the inverses of its diagonal sub-blocks;
-    // q == 12 forms the prefix sums (forward recursion), q == 13 copies each
-    // finished tile of Y to global memory one period later.
-    const int q = wid - TW;
+    // Staging warps are the lead's warps off warp 0's sub-partition (warp id
+    // not a multiple of 4), numbered q = 0, 1, ...: q < 8 stage four rows each
+    // of the diagonal block, 8 <= q < 12 eight rows each of the off-diagonal
+    // block, q == 12 forms the prefix sums (forward recursion), q == 13
+    // copies each finished tile of Y to global memory one period later.
     if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
-    if (tid < TW * TILE) { sm.Nm[tid] = MIXED ? 0ull : (1ull << 62); sm.Ne[tid] = XZERO_E; }
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
-    if (q >= 0 && q < KSTAGE_WARPS) {
-      stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Km, sm.Ke);
-      kstage_arrive();
-    }
-    if (q == 14) {
-      kstage_wait();
-      stage_dblocks<MIXED>(sm.Km, sm.Ke, sm.Dm, sm.De);
-    }
+    const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
+    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde);
     if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
     cluster.sync();
 
-    xd cnext{1.0, 0};      // tile warps: coefficient of the lane's row in the coming tile
-    if (wid < TW && lane < N) cnext = chain_coef<BWD>(w, lane);
+    xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
+    xd cnext{1.0, 0};      // warp 0: coefficient of its row in the coming tile
+    if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
     double carry = 0.0;    // prefix-sum warp (forward): running prefix sum
     for (int t = 0; t < NT; ++t) {
       const int buf = t & 1;
-      if (wid < TW) {
+      if (wid == 0) {
+        // ---------------------------------------------- dependent steps of tile t
         const int row = t * TILE + lane;
         const xd crow = cnext;
         if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
-        tile_solve<MIXED>(N, t, wid, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, sm, buf);
-      } else if (q >= 0 && q < KSTAGE_WARPS) {
-        if (t + 1 < NT) {
-          stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Km + (buf ^ 1) * BLK, sm.Ke + (buf ^ 1) * BLK);
-          kstage_arrive();
-        }
+        chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
+                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
+                          sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
+      } else if (q >= 0 && q < 8) {
+        if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
           stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
-      } else if (q == 14) {
-        if (t + 1 < NT) {
-          kstage_wait();
-          stage_dblocks<MIXED>(sm.Km + (buf ^ 1) * BLK, sm.Ke + (buf ^ 1) * BLK, sm.Dm + (buf ^ 1) * TILE * DB,
-                               sm.De + (buf ^ 1) * TILE * DB);
-        }
       } else if (q == 13) {
-        // export Y of tile t-1 from the ring to global memory, off the tile
-        // warps (a release barrier after global stores would wait for them)
+        // export Y of tile t-1 from the ring to global memory, off the chain
+        // warp (a release barrier after global stores would wait for them)
         if (t >= 1) {
           const int v = (t - 1) * TILE + lane + 1;
           if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
@@ -373,29 +202,15 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     const int nwarps = (int)(blockDim.x >> 5);
     for (int q = tid; q < lt_max * TILE; q += blockDim.x) { hs.Am[q] = 0.0; hs.Ae[q] = XZERO_E; }
     cluster.sync();
-    // period tt: row tile T0(tt) + u*7 (u < units(tt)) of this CTA takes source
-    // tile tt-1; task k = 4u + quarter.  The pair-factor loads of a warp's
-    // first task of the next period are issued before each barrier (they do
-    // not depend on Y), so that only the Y values and the sums follow it.
-    auto first_owned = [&](int tt) { return (tt + 1) + ((h - (tt + 1) % NHELP) + NHELP) % NHELP; };
-    auto units = [&](int tt) {
-      const int T0 = first_owned(tt);
-      return (tt >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
-    };
-    auto task_base = [&](int tt, int k) {
-      const int r = (first_owned(tt) + (k >> 2) * NHELP) * TILE + lane;
-      return hidx((tt - 1) * TILE + 8 * (k & 3), r);  // + i * 32 for source i of the quarter
-    };
-    M_t pm[8];
-    int pe[8];
     for (int t = 0; t < NT; ++t) {
-      const int T0 = first_owned(t);
-      const int nunits = units(t);
+      const int T0 = (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP;  // first owned row tile >= t+1
+      const int nunits = (t >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
       if (nunits > 0) {
         const int srcbase = (t - 1) * TILE;
         // task k: row tile T0 + (k/4)*7, sources srcbase + 8(k%4) .. +7 (source tile t-1)
         for (int k = wid; k < 4 * nunits; k += nwarps) {
-          const int q = k & 3;
+          const int u = k >> 2, q = k & 3;
+          const int r = (T0 + u * NHELP) * TILE + lane;
           const int sb = srcbase + 8 * q;
           M_t *Ym = (M_t *)hs.Yd + wid * 8;
           int *Yx = hs.Yx + wid * 8;
@@ -405,33 +220,36 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
             Ym[lane] = MIXED ? (M_t)mant_to_float(ym) : (M_t)ym;
             Yx[lane] = lead->Ye[v & (YRING - 1)];
           }
-          if (k != wid) {  // later tasks of the period load their factors now
-            const size_t gbase = task_base(t, k);
+          __syncwarp();
+          const size_t gbase = hidx(sb, r);  // + i * 32 for source sb + i
+          if (MIXED) {
+            float m[8];
+            int e[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              pm[i] = __ldg((const M_t *)gm + gbase + i * 32);
-              pe[i] = __ldg(ge + gbase + i * 32);
+              m[i] = __ldg((const float *)gm + gbase + i * 32);
+              e[i] = __ldg(ge + gbase + i * 32);
             }
-          }
-          __syncwarp();
-          if (MIXED) {
             float sacc = 0.0f;
             int E = XZERO_E;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * (float)pm[i], pe[i] + Yx[i]);
+            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * m[i], e[i] + Yx[i]);
             ((float *)hs.Pm)[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           } else {
+            double m[8];
             int e[8];
             int E = XZERO_E;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              e[i] = pe[i] + Yx[i];
-              E = max(E, e[i]);
+              m[i] = __ldg((const double *)gm + gbase + i * 32);
+              e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) E = max(E, e[i]);
             double sacc = 0.0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos((double)pm[i], e[i] - E), (double)Ym[i], sacc);
+            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos(m[i], e[i] - E), (double)Ym[i], sacc);
             hs.Pm[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           }
@@ -464,14 +282,6 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
           }
         }
       }
-      if (t + 1 < NT && wid < 4 * units(t + 1)) {  // the next period's first task
-        const size_t gbase = task_base(t + 1, wid);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          pm[i] = __ldg((const M_t *)gm + gbase + i * 32);
-          pe[i] = __ldg(ge + gbase + i * 32);
-        }
-      }
       cluster.sync();
     }
   }
@@ -492,8 +302,8 @@ constexpr size_t chain_smem_bytes(int N) {
   return lead > help ? lead : help;
 }
 static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
-static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= TW + 15 && CHAIN_THREADS / 32 <= 32,
-              "the lead needs TW tile warps and 15 more (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
+static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
+              "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 

@@ -43,6 +43,20 @@ __device__ __forceinline__ xd mu_of(const Workspace &w, int b) {
   return xd{w.ybm[r], w.ybe[r]};
 }
 
+// Sum of float32 block partials, in the given order, to float64 accuracy on
+// the float32 pipe: Knuth's TwoSum splits every addition into its rounded sum
+// and exact rounding error, and the errors are carried alongside (float64
+// additions would queue on the SM's slow float64 pipe: 16 per thread here).
+struct fsum2 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v, bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Bead P of the 32 particles of row tile t: sum the row partials of blocks
 // (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
 // block of the tile to finish; all 256 threads call it.
@@ -50,12 +64,17 @@ template <typename P_t>
 __device__ void finalize_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, jj = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
-  double acc = 0.0;
   const size_t base = (size_t)t * (t + 1) / 2;
   const P_t *part = (const P_t *)w.rowpart;
+  double acc = 0.0;
+  fsum2 f;
 #pragma unroll 8
-  for (int s = half; s <= t; s += 2) acc += (double)__ldcg(part + ((base + s) * TILE + jj) * 4 + q);
-  fin[jj][q + 4 * half] = acc;
+  for (int s = half; s <= t; s += 2) {
+    const P_t v = __ldcg(part + ((base + s) * TILE + jj) * 4 + q);
+    if (std::is_same<P_t, float>::value) f.add((float)v);
+    else acc += (double)v;
+  }
+  fin[jj][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
   const int p = t * TILE + threadIdx.x;
   if (threadIdx.x < TILE && p < w.N) {
@@ -87,12 +106,16 @@ template <typename P_t>
 __device__ void finalize_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
-  double acc = 0.0;
   const P_t *part = (const P_t *)w.colpart;
+  double acc = 0.0;
+  fsum2 f;
 #pragma unroll 8
-  for (int t = s + half; t < w.NT; t += 2)
-    acc += (double)__ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
-  fin[ii][q + 4 * half] = acc;
+  for (int t = s + half; t < w.NT; t += 2) {
+    const P_t v = __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
+    if (std::is_same<P_t, float>::value) f.add((float)v);
+    else acc += (double)v;
+  }
+  fin[ii][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
   const int p = s * TILE + threadIdx.x;
   if (threadIdx.x < TILE && p < w.N) {

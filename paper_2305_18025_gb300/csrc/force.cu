@@ -57,13 +57,47 @@ struct fsum2 {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// 2^e as a double for e in the normal range (0 below it), built from the bits.
+__device__ __forceinline__ double pow2_normal(int e) {
+  return e < -1022 ? 0.0 : __longlong_as_double((long long)(min(e, 1023) + 1023) << 52);
+}
+
+// Pr[p -> p+1] = 1 - y_{p+1} B_{p+2} / (N y_N) (0-based p; Eq.
+// direct-link-probability) with B_{p+2} = Yb[N-p-1] / c_{p+1}: one mantissa
+// product and quotient in float64, the exponents summed as integers.
+__device__ __forceinline__ double direct_link_fast(const Workspace &w, int p) {
+  const double ym = w.yfm[p + 1], bm = w.ybm[w.N - p - 1], cm = w.ccm[p], zm = w.scal[1];
+  const int e = w.yfe[p + 1] + w.ybe[w.N - p - 1] - w.cce[p] + w.scal_i[0];
+  return 1.0 - ((ym * bm) * zm / cm) * pow2_normal(e);
+}
+
+template <bool PBC>
+__device__ __forceinline__ double img(const Workspace &w, double d) {
+  return PBC ? d - w.L * rint(d * w.invL) : d;
+}
+
 // Bead P of the 32 particles of row tile t: sum the row partials of blocks
 // (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
-// block of the tile to finish; all 256 threads call it.
-template <typename P_t>
+// block of the tile to finish; all 256 threads call it.  The finishing warp's
+// loads are issued before the partial sums.
+template <typename P_t, bool PBC>
 __device__ void finalize_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, jj = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
+  const int p = t * TILE + threadIdx.x;
+  const bool mine = threadIdx.x < TILE && p < w.N;
+  double M = 0.0, rp[3] = {0, 0, 0}, n1[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  if (mine) {
+    const double *r = w.RP + 4 * (size_t)p, *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1 (1-based)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { rp[c] = r[c]; nb[c] = nbP[c]; }
+    if (p + 1 < w.N) {
+      const double *n = w.R1 + 4 * (size_t)(p + 1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) n1[c] = n[c];
+      M = direct_link_fast(w, p);
+    }
+  }
   const size_t base = (size_t)t * (t + 1) / 2;
   const P_t *part = (const P_t *)w.rowpart;
   double acc = 0.0;
@@ -76,36 +110,43 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
   }
   fin[jj][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
-  const int p = t * TILE + threadIdx.x;
-  if (threadIdx.x < TILE && p < w.N) {
-    const double *f = fin[threadIdx.x];
-    double rs = f[0] + f[4], rx = f[1] + f[5], ry = f[2] + f[6], rz = f[3] + f[7];
-    const double *rp = w.RP + 4 * (size_t)p;
-    if (p + 1 < w.N) {
-      const double M = direct_link_prob(w, p);
-      const double *n1 = w.R1 + 4 * (size_t)(p + 1);
-      rs += M;
-      rx = fma(M, mimage(w, rp[0] - n1[0]), rx);
-      ry = fma(M, mimage(w, rp[1] - n1[1]), ry);
-      rz = fma(M, mimage(w, rp[2] - n1[2]), rz);
-    }
+  if (mine) {
+    const double *fr = fin[threadIdx.x];
+    double rs = fr[0] + fr[4] + M, r3[3] = {fr[1] + fr[5], fr[2] + fr[6], fr[3] + fr[7]};
     const double k = w.k;
-    const double *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1 (1-based)
     double *fP = F + ((size_t)p * w.P + (w.P - 1)) * 3;
-    fP[0] = -k * fma(rs, mimage(w, rp[0] - nbP[0]), rx);
-    fP[1] = -k * fma(rs, mimage(w, rp[1] - nbP[1]), ry);
-    fP[2] = -k * fma(rs, mimage(w, rp[2] - nbP[2]), rz);
-    if (!(isfinite(fP[0]) && isfinite(fP[1]) && isfinite(fP[2]))) atomicOr(w.status, ST_NONFINITE);
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double rc = fma(M, img<PBC>(w, rp[c] - n1[c]), r3[c]);
+      fP[c] = -k * fma(rs, img<PBC>(w, rp[c] - nb[c]), rc);
+      ok &= isfinite(fP[c]);
+    }
+    if (!ok) atomicOr(w.status, ST_NONFINITE);
   }
   if (threadIdx.x == 0) w.rowcnt[t] = 0;  // ready for the next evaluation
   __syncthreads();
 }
 
 // Bead 1 of the 32 particles of column tile s: blocks (s..NT-1, s) in order.
-template <typename P_t>
+template <typename P_t, bool PBC>
 __device__ void finalize_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
+  const int p = s * TILE + threadIdx.x;
+  const bool mine = threadIdx.x < TILE && p < w.N;
+  double M = 0.0, r1[3] = {0, 0, 0}, pP[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  if (mine) {
+    const double *r = w.R1 + 4 * (size_t)p, *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2 (1-based)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { r1[c] = r[c]; nb[c] = nb1[c]; }
+    if (p >= 1) {
+      const double *n = w.RP + 4 * (size_t)(p - 1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pP[c] = n[c];
+      M = direct_link_fast(w, p - 1);
+    }
+  }
   const P_t *part = (const P_t *)w.colpart;
   double acc = 0.0;
   fsum2 f;
@@ -117,26 +158,19 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
   }
   fin[ii][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
-  const int p = s * TILE + threadIdx.x;
-  if (threadIdx.x < TILE && p < w.N) {
-    const double *f = fin[threadIdx.x];
-    double cs = f[0] + f[4], cx = f[1] + f[5], cy = f[2] + f[6], cz = f[3] + f[7];
-    const double *r1 = w.R1 + 4 * (size_t)p;
-    if (p >= 1) {
-      const double M = direct_link_prob(w, p - 1);
-      const double *pP = w.RP + 4 * (size_t)(p - 1);
-      cs += M;
-      cx = fma(M, mimage(w, r1[0] - pP[0]), cx);
-      cy = fma(M, mimage(w, r1[1] - pP[1]), cy);
-      cz = fma(M, mimage(w, r1[2] - pP[2]), cz);
-    }
+  if (mine) {
+    const double *fc = fin[threadIdx.x];
+    double cs = fc[0] + fc[4] + M, c3[3] = {fc[1] + fc[5], fc[2] + fc[6], fc[3] + fc[7]};
     const double k = w.k;
-    const double *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2 (1-based)
     double *f1 = F + (size_t)p * w.P * 3;
-    f1[0] = -k * fma(cs, mimage(w, r1[0] - nb1[0]), cx);
-    f1[1] = -k * fma(cs, mimage(w, r1[1] - nb1[1]), cy);
-    f1[2] = -k * fma(cs, mimage(w, r1[2] - nb1[2]), cz);
-    if (!(isfinite(f1[0]) && isfinite(f1[1]) && isfinite(f1[2]))) atomicOr(w.status, ST_NONFINITE);
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double cc = fma(M, img<PBC>(w, r1[c] - pP[c]), c3[c]);
+      f1[c] = -k * fma(cs, img<PBC>(w, r1[c] - nb[c]), cc);
+      ok &= isfinite(f1[c]);
+    }
+    if (!ok) atomicOr(w.status, ST_NONFINITE);
   }
   if (threadIdx.x == 0) w.colcnt[s] = 0;
   __syncthreads();
@@ -257,8 +291,13 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
     __syncthreads();
     const bool last_row = last[0], last_col = last[1];
     if (last_row || last_col) __threadfence();
-    if (last_row) finalize_rows<P_t>(w, t, pos, F, fin);
-    if (last_col) finalize_cols<P_t>(w, s, pos, F, fin);
+    if (w.pbc) {
+      if (last_row) finalize_rows<P_t, true>(w, t, pos, F, fin);
+      if (last_col) finalize_cols<P_t, true>(w, s, pos, F, fin);
+    } else {
+      if (last_row) finalize_rows<P_t, false>(w, t, pos, F, fin);
+      if (last_col) finalize_cols<P_t, false>(w, s, pos, F, fin);
+    }
   }
 }
 

@@ -11,17 +11,18 @@
 // with K(w, r) = c_r H(w, r) each is  Y_{r+1} = sum_{w<=r} K(w, r) Y_w.
 //
 // GB300 facts behind the schedule (measured): a float64 FMA has a 64-cycle
-// latency and a warp has one float64 instruction in flight at a time; a
-// release/acquire hand-off between warps inside a step costs far more than
-// the step itself; a cluster barrier costs ~360 cycles and a distributed
-// shared-memory access ~215.  So the rows are processed in tiles of 32 and
+// latency (plus ~40 before a shuffle can read it), while the integer form of
+// the step below takes ~100 cycles including its shuffle; a release/acquire
+// hand-off between warps inside a step costs far more than the step itself;
+// a cluster barrier costs ~360 cycles and a distributed shared-memory access
+// ~215.  So the rows are processed in tiles of 32 and
 //   * all intra-tile work stays in one warp of the lead CTA (cluster rank 0):
 //     warp 0 runs the 32 dependent steps of row tile t.  Lane j holds
 //     c_r * (partial row sum) of row 32t+j and the partial sum of row
-//     32(t+1)+j.  A step is one float64 FMA on the current row (the
-//     dependency chain: acc_j += K(i, j) y_i, exponents aligned with integer
-//     operations on the double's bits), one FMA on the next tile's row (off
-//     the chain), and a shuffle that broadcasts the new Y;
+//     32(t+1)+j.  A step is one integer extended multiply-add on the current
+//     row (the dependency chain: acc_j += K(i, j) y_i with 64-bit integer
+//     mantissas, chain_common.cuh), one term of the next tile's row (off the
+//     chain), and a shuffle that broadcasts the new Y;
 //   * twelve other lead warps (none on warp 0's sub-partition) stage, for
 //     tile t+1, the block of H from source tile t+1 to the rows of tile t+2
 //     and the diagonal block pre-scaled by c; one more lead warp of the
@@ -46,7 +47,7 @@
 // Every value is an extended number m * 2^e (int32 exponent), so no exp/log
 // sits on the dependency chain.  MIXED: the bulk products are summed in
 // float32 per 32-source tile and added to the float64 row accumulator; the
-// dependent steps and the tile hand-offs stay float64.
+// tile hand-offs stay float64 and the dependent steps use the integer format.
 #include <cooperative_groups.h>
 #include <type_traits>
 

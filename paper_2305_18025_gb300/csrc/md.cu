@@ -15,7 +15,7 @@
 // cell lists in pairs.cu when the box holds >= 3 cutoffs per side) between
 // beads of equal index; in a periodic box every spring and pair uses the
 // minimum image.  The exchange force is one evaluation of Algorithm 1 (the kernels of
-// bead.cu, prep.cu, chain.cu, force.cu).
+// prep.cu, chain.cu, force.cu).
 //
 // Thermostat noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
 // written here from its published definition.  Element e = 4g + i of the

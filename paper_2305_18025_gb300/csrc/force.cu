@@ -178,7 +178,7 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
 
 // One 32 x 32 block of the lower triangle (all 256 threads of the CTA).
 // MIXED keeps the block partials in float32 (each is a float32 sum already).
-template <bool MIXED>
+template <bool MIXED, bool PBC>
 __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const double *__restrict__ pos,
                                            double *__restrict__ F,
                                            typename std::conditional<MIXED, float, double>::type (*red)[32][4],
@@ -216,7 +216,7 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
       if (valid) {
         if (MIXED) {
           float fx, fy, fz;
-          if (w.pbc) {  // minimum image from the fixed-point copies (bh holds RP's bits)
+          if (PBC) {  // minimum image from the fixed-point copies (bh holds RP's bits)
             const uint4 ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
             fx = fixdiff(__float_as_uint(bh.x), ua.x, w.Lscale);
             fy = fixdiff(__float_as_uint(bh.y), ua.y, w.Lscale);
@@ -235,10 +235,11 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
           frs += M; frx += M * fx; fry += M * fy; frz += M * fz;
           fcs = M; fcx = -M * fx; fcy = -M * fy; fcz = -M * fz;
         } else {
-          const double dx = mimage(w, bx - w.R1[4 * a]), dy = mimage(w, by - w.R1[4 * a + 1]),
-                       dz = mimage(w, bz - w.R1[4 * a + 2]);
+          const double dx = img<PBC>(w, bx - w.R1[4 * a]), dy = img<PBC>(w, by - w.R1[4 * a + 1]),
+                       dz = img<PBC>(w, bz - w.R1[4 * a + 2]);
           const double gmd = ((const double *)w.gm)[gi];
-          const double M = xtod(xd{((const double *)w.alm)[a] * mub.m * gmd, w.ale[a] + mub.e + w.ge[gi]});
+          // alpha mu g with its exponent applied as an integer-built power of two
+          const double M = (((const double *)w.alm)[a] * mub.m * gmd) * pow2_normal(w.ale[a] + mub.e + w.ge[gi]);
           rs += M; rx = fma(M, dx, rx); ry = fma(M, dy, ry); rz = fma(M, dz, rz);
           cs = M; cx = -M * dx; cy = -M * dy; cz = -M * dz;
         }
@@ -291,13 +292,8 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
     __syncthreads();
     const bool last_row = last[0], last_col = last[1];
     if (last_row || last_col) __threadfence();
-    if (w.pbc) {
-      if (last_row) finalize_rows<P_t, true>(w, t, pos, F, fin);
-      if (last_col) finalize_cols<P_t, true>(w, s, pos, F, fin);
-    } else {
-      if (last_row) finalize_rows<P_t, false>(w, t, pos, F, fin);
-      if (last_col) finalize_cols<P_t, false>(w, s, pos, F, fin);
-    }
+    if (last_row) finalize_rows<P_t, PBC>(w, t, pos, F, fin);
+    if (last_col) finalize_cols<P_t, PBC>(w, s, pos, F, fin);
   }
 }
 
@@ -309,7 +305,10 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
   __shared__ double fin[32][9];
   __shared__ int last[2];
   pdl_wait();
-  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) prob_block<MIXED>(w, blk, pos, F, red, fin, last);
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+    if (w.pbc) prob_block<MIXED, true>(w, blk, pos, F, red, fin, last);
+    else prob_block<MIXED, false>(w, blk, pos, F, red, fin, last);
+  }
   pdl_trigger();
 }
 
@@ -326,7 +325,8 @@ __global__ void __launch_bounds__(256) prob_force_batched(const Workspace *__res
   __shared__ int last[2];
   for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
     const int2 e = tab[k];
-    prob_block<MIXED>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
+    if (ws[e.x].pbc) prob_block<MIXED, true>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
+    else prob_block<MIXED, false>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
   }
 }
 

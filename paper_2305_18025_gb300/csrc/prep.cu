@@ -226,12 +226,12 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
 // g for one pair from the staged bead-P position of b (slot j of side 0) and
 // bead-1 position of a (slot i of side 1): returns the mantissa (float or
 // double) and sets the exponent.
-template <bool MIXED>
+template <bool MIXED, bool PBC>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, const EndTiles &E, int i, int j,
                                               int &e) {
   if (MIXED) {
     float fx, fy, fz;
-    if (w.pbc) {  // minimum image from the fixed-point copies
+    if (PBC) {  // minimum image from the fixed-point copies
       const uint4 ub = *(const uint4 *)E.v[0][j], ua = *(const uint4 *)E.v[1][i];
       fx = fixdiff(ub.x, ua.x, w.Lscale);
       fy = fixdiff(ub.y, ua.y, w.Lscale);
@@ -252,7 +252,8 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
     return mm;
   } else {
     const double *rb = E.v[0][j], *ra = E.v[1][i];
-    const double dx = mimage(w, rb[0] - ra[0]), dy = mimage(w, rb[1] - ra[1]), dz = mimage(w, rb[2] - ra[2]);
+    double dx = rb[0] - ra[0], dy = rb[1] - ra[1], dz = rb[2] - ra[2];
+    if (PBC) { dx = mimage(w, dx); dy = mimage(w, dy); dz = mimage(w, dz); }
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
     const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
     const double n = floor(x);
@@ -269,7 +270,7 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
 // are coalesced along r.  Entries outside a <= b < N are never written here
 // (gmat_padding_kernel fills them once).
 // One block of g (all threads of the CTA; Tm/Te: 32 x 33 shared tiles).
-template <bool MIXED>
+template <bool MIXED, bool PBC>
 __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__restrict__ pos, int blk,
                                            typename std::conditional<MIXED, float, double>::type *Tm, int *Te,
                                            EndTiles &E) {
@@ -287,7 +288,7 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__r
       const int a = s * TILE + i;
       if (b < N && a <= b) {
         int e;
-        const M_t m = (M_t)pair_factor<MIXED>(w, cx, E, i, lane, e);
+        const M_t m = (M_t)pair_factor<MIXED, PBC>(w, cx, E, i, lane, e);
         const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
         gm[idx] = m;
         w.ge[idx] = e;
@@ -326,7 +327,10 @@ __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__
   if ((int)blockIdx.x < nbead) {
     bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
   } else {
-    for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) gmat_block<MIXED>(w, pos, blk, Tm, Te, E);
+    for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) {
+      if (w.pbc) gmat_block<MIXED, true>(w, pos, blk, Tm, Te, E);
+      else gmat_block<MIXED, false>(w, pos, blk, Tm, Te, E);
+    }
   }
   pdl_trigger();
 }
@@ -351,7 +355,8 @@ __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict_
   } else {
     for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
       const int2 e = blk_tab[k];
-      gmat_block<MIXED>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
+      if (ws[e.x].pbc) gmat_block<MIXED, true>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
+      else gmat_block<MIXED, false>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
     }
   }
   pdl_trigger();

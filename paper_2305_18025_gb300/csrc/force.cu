@@ -76,82 +76,103 @@ __device__ __forceinline__ double img(const Workspace &w, double d) {
   return PBC ? d - w.L * rint(d * w.invL) : d;
 }
 
-// Tile finalisation, run by the block that completes row tile t (do_row)
-// and/or column tile s (do_col); all 256 threads call it.
-//   rows: bead P of the 32 particles of row tile t -- the row partials of
-//         blocks (t, 0..t) summed in that order, plus the direct link,
-//         F_l^P = -k [rs (r_l^P - r_l^{P-1}) + sum_u Pr[l->u] (r_l^P - r_u^1)];
-//   cols: bead 1 of the 32 particles of column tile s -- blocks (s..NT-1, s)
-//         in order, F_l^1 analogous.
-// Both partial sums run in one pass (their loads in flight together); warp 0
-// then forms the row forces and warp 1 the column forces, concurrently, each
-// having issued its own loads first.
+// Bead P of the 32 particles of row tile t: sum the row partials of blocks
+// (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
+// block of the tile to finish; all 256 threads call it.  The finishing warp's
+// loads are issued before the partial sums.
 template <typename P_t, bool PBC>
-__device__ void finalize_tiles(const Workspace &w, int t, int s, bool do_row, bool do_col,
-                               const double *__restrict__ pos, double *__restrict__ F, double (*finr)[9],
-                               double (*finc)[9]) {
+__device__ void finalize_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
+                              double (*fin)[9]) {
   const int q = threadIdx.x & 3, jj = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool rowwarp = do_row && wid == 0, colwarp = do_col && wid == 1;
-  const int p = (rowwarp ? t : s) * TILE + lane;
-  const bool mine = (rowwarp || colwarp) && p < w.N;
-  double M = 0.0, r0[3] = {0, 0, 0}, r1[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  const int p = t * TILE + threadIdx.x;
+  const bool mine = threadIdx.x < TILE && p < w.N;
+  double M = 0.0, rp[3] = {0, 0, 0}, n1[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
   if (mine) {
-    // rows: r0 = r_p^P, r1 = r_{p+1}^1, nb = r_p^{P-1};  cols: r0 = r_p^1, r1 = r_{p-1}^P, nb = r_p^2
-    const double *a = rowwarp ? w.RP + 4 * (size_t)p : w.R1 + 4 * (size_t)p;
-    const double *n = pos + ((size_t)p * w.P + (rowwarp ? w.P - 2 : 1)) * 3;
+    const double *r = w.RP + 4 * (size_t)p, *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1 (1-based)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { r0[c] = a[c]; nb[c] = n[c]; }
-    const int l = rowwarp ? p : p - 1;  // the link l -> l+1 that touches this bead
-    if (l >= 0 && l + 1 < w.N) {
-      const double *o = rowwarp ? w.R1 + 4 * (size_t)(p + 1) : w.RP + 4 * (size_t)(p - 1);
+    for (int c = 0; c < 3; ++c) { rp[c] = r[c]; nb[c] = nbP[c]; }
+    if (p + 1 < w.N) {
+      const double *n = w.R1 + 4 * (size_t)(p + 1);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r1[c] = o[c];
-      M = direct_link_fast(w, l);
+      for (int c = 0; c < 3; ++c) n1[c] = n[c];
+      M = direct_link_fast(w, p);
     }
   }
-  double ar = 0.0, ac = 0.0;
-  fsum2 fr, fc;
-  if (do_row) {
-    const size_t base = (size_t)t * (t + 1) / 2;
-    const P_t *part = (const P_t *)w.rowpart;
-#pragma unroll 16
-    for (int k = half; k <= t; k += 2) {
-      const P_t v = __ldcg(part + ((base + k) * TILE + jj) * 4 + q);
-      if (std::is_same<P_t, float>::value) fr.add((float)v);
-      else ar += (double)v;
-    }
+  const size_t base = (size_t)t * (t + 1) / 2;
+  const P_t *part = (const P_t *)w.rowpart;
+  double acc = 0.0;
+  fsum2 f;
+#pragma unroll 8
+  for (int s = half; s <= t; s += 2) {
+    const P_t v = __ldcg(part + ((base + s) * TILE + jj) * 4 + q);
+    if (std::is_same<P_t, float>::value) f.add((float)v);
+    else acc += (double)v;
   }
-  if (do_col) {
-    const P_t *part = (const P_t *)w.colpart;
-#pragma unroll 16
-    for (int k = s + half; k < w.NT; k += 2) {
-      const P_t v = __ldcg(part + (((size_t)k * (k + 1) / 2 + s) * TILE + jj) * 4 + q);
-      if (std::is_same<P_t, float>::value) fc.add((float)v);
-      else ac += (double)v;
-    }
-  }
-  if (do_row) finr[jj][q + 4 * half] = std::is_same<P_t, float>::value ? fr.value() : ar;
-  if (do_col) finc[jj][q + 4 * half] = std::is_same<P_t, float>::value ? fc.value() : ac;
+  fin[jj][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
   if (mine) {
-    const double *f = rowwarp ? finr[lane] : finc[lane];
-    const double ps = f[0] + f[4] + M, p3[3] = {f[1] + f[5], f[2] + f[6], f[3] + f[7]};
+    const double *fr = fin[threadIdx.x];
+    double rs = fr[0] + fr[4] + M, r3[3] = {fr[1] + fr[5], fr[2] + fr[6], fr[3] + fr[7]};
     const double k = w.k;
-    double *fo = F + ((size_t)p * w.P + (rowwarp ? w.P - 1 : 0)) * 3;
+    double *fP = F + ((size_t)p * w.P + (w.P - 1)) * 3;
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double pc = fma(M, img<PBC>(w, r0[c] - r1[c]), p3[c]);
-      fo[c] = -k * fma(ps, img<PBC>(w, r0[c] - nb[c]), pc);
-      ok &= isfinite(fo[c]);
+      const double rc = fma(M, img<PBC>(w, rp[c] - n1[c]), r3[c]);
+      fP[c] = -k * fma(rs, img<PBC>(w, rp[c] - nb[c]), rc);
+      ok &= isfinite(fP[c]);
     }
     if (!ok) atomicOr(w.status, ST_NONFINITE);
   }
-  if (threadIdx.x == 0) {  // ready for the next evaluation
-    if (do_row) w.rowcnt[t] = 0;
-    if (do_col) w.colcnt[s] = 0;
+  if (threadIdx.x == 0) w.rowcnt[t] = 0;  // ready for the next evaluation
+  __syncthreads();
+}
+
+// Bead 1 of the 32 particles of column tile s: blocks (s..NT-1, s) in order.
+template <typename P_t, bool PBC>
+__device__ void finalize_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
+                              double (*fin)[9]) {
+  const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
+  const int p = s * TILE + threadIdx.x;
+  const bool mine = threadIdx.x < TILE && p < w.N;
+  double M = 0.0, r1[3] = {0, 0, 0}, pP[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  if (mine) {
+    const double *r = w.R1 + 4 * (size_t)p, *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2 (1-based)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { r1[c] = r[c]; nb[c] = nb1[c]; }
+    if (p >= 1) {
+      const double *n = w.RP + 4 * (size_t)(p - 1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pP[c] = n[c];
+      M = direct_link_fast(w, p - 1);
+    }
   }
+  const P_t *part = (const P_t *)w.colpart;
+  double acc = 0.0;
+  fsum2 f;
+#pragma unroll 8
+  for (int t = s + half; t < w.NT; t += 2) {
+    const P_t v = __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
+    if (std::is_same<P_t, float>::value) f.add((float)v);
+    else acc += (double)v;
+  }
+  fin[ii][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
+  __syncthreads();
+  if (mine) {
+    const double *fc = fin[threadIdx.x];
+    double cs = fc[0] + fc[4] + M, c3[3] = {fc[1] + fc[5], fc[2] + fc[6], fc[3] + fc[7]};
+    const double k = w.k;
+    double *f1 = F + (size_t)p * w.P * 3;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double cc = fma(M, img<PBC>(w, r1[c] - pP[c]), c3[c]);
+      f1[c] = -k * fma(cs, img<PBC>(w, r1[c] - nb[c]), cc);
+      ok &= isfinite(f1[c]);
+    }
+    if (!ok) atomicOr(w.status, ST_NONFINITE);
+  }
+  if (threadIdx.x == 0) w.colcnt[s] = 0;
   __syncthreads();
 }
 
@@ -271,7 +292,8 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
     __syncthreads();
     const bool last_row = last[0], last_col = last[1];
     if (last_row || last_col) __threadfence();
-    if (last_row || last_col) finalize_tiles<P_t, PBC>(w, t, s, last_row, last_col, pos, F, fin, fin + 32);
+    if (last_row) finalize_rows<P_t, PBC>(w, t, pos, F, fin);
+    if (last_col) finalize_cols<P_t, PBC>(w, s, pos, F, fin);
   }
 }
 
@@ -280,7 +302,7 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
                                                          double *__restrict__ F) {
   using P_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ P_t red[8][32][4];
-  __shared__ double fin[64][9];
+  __shared__ double fin[32][9];
   __shared__ int last[2];
   pdl_wait();
   for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
@@ -299,7 +321,7 @@ __global__ void __launch_bounds__(256) prob_force_batched(const Workspace *__res
                                                           const double *__restrict__ pos, double *__restrict__ F) {
   using P_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ P_t red[8][32][4];
-  __shared__ double fin[64][9];
+  __shared__ double fin[32][9];
   __shared__ int last[2];
   for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
     const int2 e = tab[k];

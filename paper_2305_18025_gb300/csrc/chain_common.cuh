@@ -165,6 +165,50 @@ __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y
   return xi_norm((acc.m >> min(E - acc.e, 63)) + (p >> min(E - pe, 63)), E);
 }
 
+// ----------------------------------------- the 32-bit chain format (MIXED)
+// MIXED runs the dependency chain on 32-bit words: m * 2^(e - 30) with m in
+// [2^30, 2^31) (one bit of headroom), the factor K by the top 32 bits of its
+// mantissa.  A step is one 32 x 32-bit high product, two shifts, one add and a
+// select (truncation at 2^-30 per operation, far below the float32 rounding
+// of the pair factors the mixed form starts from), and its shuffle moves two
+// words instead of three.
+struct xs {
+  unsigned m;
+  int e;
+};
+__device__ __forceinline__ xs xs_from(xd a) {
+  const long long b = __double_as_longlong(a.m);
+  if (b <= 0) return xs{1u << 30, XZERO_E};
+  return xs{(unsigned)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> 22), a.e + (int)(b >> 52) - 1023};
+}
+__device__ __forceinline__ xd xs_to_xd(xs a) {
+  return xd{__longlong_as_double((long long)((((unsigned long long)a.m << 22) & 0xFFFFFFFFFFFFFull) |
+                                             0x3FF0000000000000ull)),
+            a.e};
+}
+// s * 2^(E - 30) with s in [2^29, 2^32), brought back to [2^30, 2^31)
+__device__ __forceinline__ xs xs_norm(unsigned s, int E) {
+  const unsigned top = s >> 29;  // 1: [2^29, 2^30), 2-3: in range, 4-7: [2^31, 2^32)
+  return xs{top >= 4 ? (s >> 1) : (top >= 2 ? s : (s << 1)), top >= 4 ? E + 1 : (top >= 2 ? E : E - 1)};
+}
+__device__ __forceinline__ xs xs_add(xs a, xs b) {
+  const int E = max(a.e, b.e);
+  return xs_norm((a.m >> min(E - a.e, 31)) + (b.m >> min(E - b.e, 31)), E);
+}
+// a * c (c: positive normal double mantissa, any binary exponent)
+__device__ __forceinline__ xs xs_mul(xs a, xd c) {
+  const long long b = __double_as_longlong(c.m);
+  const unsigned c32 = (unsigned)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> 21);  // [2^31, 2^32)
+  return xs_norm(__umulhi(c32, a.m), a.e + c.e + (int)(b >> 52) - 1023 + 1);
+}
+// acc + K * y with K = kk 2^(ke - 63) (top 32 bits used): the chain step
+__device__ __forceinline__ xs xs_fma(xs acc, unsigned long long kk, int ke, xs y) {
+  const unsigned p = __umulhi((unsigned)(kk >> 32), y.m);  // in [2^29, 2^31)
+  const int pe = ke + y.e + 1;
+  const int E = max(acc.e, pe);
+  return xs_norm((acc.m >> min(E - acc.e, 31)) + (p >> min(E - pe, 31)), E);
+}
+
 // alpha = y * inv for extended numbers with double mantissas in [1,2), with
 // integer operations; the mantissa is written as float (MIXED) or double.
 template <bool MIXED>
@@ -283,17 +327,28 @@ __device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, u
 // the partial sums of tile t+1's rows over source tile t.
 // 32 steps, no branches and no stores: rows past N and finished rows see
 // extended zeros in the staged blocks, and row j's accumulator is final after
-// step j.  The chain (acc, y) is in the integer format xi; block entries of
-// step i+1 are loaded (explicit ld.shared) before step i's shuffle.
+// step j.  The chain (acc, y) is in an integer format (xs for MIXED, xi for
+// FP64); block entries of step i+1 are loaded (explicit ld.shared) before
+// step i's shuffle.
 template <bool MIXED>
 __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt, const unsigned long long *Kdm,
                                            const int *Kde, const double *Hom, const int *Hoe, double *Ym, int *Ye,
                                            int ymask, double *gYm, int *gYe) {
+  // the chain format: 32-bit words (MIXED, xs) or 64-bit mantissas (FP64, xi)
+  using X = typename std::conditional<MIXED, xs, xi>::type;
   const int lane = threadIdx.x & 31;
   const int r0 = t * TILE, row = r0 + lane;
-  xi acc{1ull << 62, XZERO_E};
-  if (row < N) acc = xi_mul(xi_add(xi_from(A), xi_from(nxt)), crow);  // c_row * (sum over sources < r0)
-  xi y = xi_from(xd{Ym[r0 & ymask], Ye[r0 & ymask]});
+  const xd y0{Ym[r0 & ymask], Ye[r0 & ymask]};
+  X acc, y;
+  if constexpr (MIXED) {
+    acc = xs{1u << 30, XZERO_E};
+    if (row < N) acc = xs_mul(xs_add(xs_from(A), xs_from(nxt)), crow);  // c_row * (sum over sources < r0)
+    y = xs_from(y0);
+  } else {
+    acc = xi{1ull << 62, XZERO_E};
+    if (row < N) acc = xi_mul(xi_add(xi_from(A), xi_from(nxt)), crow);
+    y = xi_from(y0);
+  }
   nxt = xd{1.0, XZERO_E};
   float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
   int nexp = XZERO_E;
@@ -316,18 +371,23 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
       ke1 = lds_s32(aKe + (i + 1) * 33 * 4);
       he1 = lds_s32(aHe + (i + 1) * 33 * 4);
     }
-    acc = xi_fma<MIXED>(acc, km, ke, y);  // the dependency chain
-    // next tile's rows, off the chain (MIXED: float32 on the top 24 bits of y)
-    if (MIXED)
-      fmerge(nsum, nexp, __int_as_float((int)((y.m >> 39) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
-    else nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
+    if constexpr (MIXED) {
+      acc = xs_fma(acc, km, ke, y);  // the dependency chain
+      // next tile's rows, off the chain: float32 on the top 24 bits of y
+      fmerge(nsum, nexp, __int_as_float((int)((y.m >> 7) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
+    } else {
+      acc = xi_fma<false>(acc, km, ke, y);  // the dependency chain
+      nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
+    }
     y.m = __shfl_sync(0xffffffffu, acc.m, i);
     y.e = __shfl_sync(0xffffffffu, acc.e, i);
     km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
   }
   if (MIXED) nxt = xd{f2d_int(nsum), nexp};
   if (row < N) {  // Y_{row+1} = final accumulator of row `row`
-    const xd yn = xi_to_xd(acc);
+    xd yn;
+    if constexpr (MIXED) yn = xs_to_xd(acc);
+    else yn = xi_to_xd(acc);
     Ym[(row + 1) & ymask] = yn.m;
     Ye[(row + 1) & ymask] = yn.e;
     if (gYm) {

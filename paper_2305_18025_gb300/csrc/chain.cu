@@ -31,11 +31,10 @@
 //     belongs to CTA 1 + T mod 7, which keeps its rows' partial sums in its
 //     own shared memory.  In period t each of them adds source tile t-1 to
 //     every row tile T >= t+1 it owns: one warp per (row tile, quarter of 8
-//     sources); one warp reads the period's 32 values of Y from the lead's
-//     shared memory, and each warp issues the pair-factor loads of its next
-//     task while it computes the current one; the quarters are then combined
-//     in a fixed order, and the owner of tile t+1 writes that tile's
-//     finished sums into the lead.
+//     sources), each reading its 8 values of Y from the lead's shared memory
+//     and issuing its 16 loads at once; the quarters are then combined in a
+//     fixed order, and the owner of tile t+1 writes that tile's finished
+//     sums into the lead.
 // The float64 pipe of an SM is shared by all its warps and is slow on GB300
 // (a warp-wide float64 instruction occupies it for about 64 cycles), so
 // outside the dependency chain the kernel uses integer and float32 work:
@@ -79,15 +78,15 @@ struct LeadSmem {
 };
 
 // Shared memory of a bulk CTA: its rows' partial sums (local tile lt = T / 7),
-// the period's 32 values of Y, and the partial sums of the current period
+// one slot of 8 Y values per warp, and the partial sums of the current period
 // (4 quarter-tiles of 8 sources per owned row tile).
 struct HelperSmem {
   double *Am;   // [ltiles][32]
   int *Ae;      // [ltiles][32]
   double *Pm;   // [4 * ltiles][32] partial sums of the period (MIXED: floats)
   int *Pe;      // [4 * ltiles][32]
-  double *Yd;   // the period's 32 Y mantissas (MIXED: floats); room for 256
-  int *Yx;      // their exponents
+  double *Yd;   // [32 warps][8] Y mantissas (MIXED: floats)
+  int *Yx;      // [32 warps][8] exponents
 };
 
 __host__ __device__ constexpr int helper_tiles(int NT) { return (NT + NHELP - 1) / NHELP; }
@@ -204,72 +203,58 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     const int nwarps = (int)(blockDim.x >> 5);
     for (int q = tid; q < lt_max * TILE; q += blockDim.x) { hs.Am[q] = 0.0; hs.Ae[q] = XZERO_E; }
     cluster.sync();
-    // period tt: row tile T0(tt) + u*7 (u < units(tt)) of this CTA takes source
-    // tile tt-1; task k = 4u + quarter (8 sources).  The 32 Y values of the
-    // period are read from the lead once, by warp 0; each warp issues the
-    // pair-factor loads of its next task (the first task of the next period
-    // before the barrier) while it computes the current one.
-    auto first_owned = [&](int tt) { return (tt + 1) + ((h - (tt + 1) % NHELP) + NHELP) % NHELP; };
-    auto units = [&](int tt) {
-      const int T0 = first_owned(tt);
-      return (tt >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
-    };
-    auto task_base = [&](int tt, int k) {
-      const int r = (first_owned(tt) + (k >> 2) * NHELP) * TILE + lane;
-      return hidx((tt - 1) * TILE + 8 * (k & 3), r);  // + i * 32 for source i of the quarter
-    };
-    M_t pm[8];
-    int pe[8];
-    auto load_task = [&](int tt, int k) {
-      const size_t gbase = task_base(tt, k);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        pm[i] = __ldg((const M_t *)gm + gbase + i * 32);
-        pe[i] = __ldg(ge + gbase + i * 32);
-      }
-    };
     for (int t = 0; t < NT; ++t) {
-      const int T0 = first_owned(t);
-      const int nunits = units(t);
+      const int T0 = (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP;  // first owned row tile >= t+1
+      const int nunits = (t >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
       if (nunits > 0) {
-        M_t *Yt = (M_t *)hs.Yd;  // the period's 32 values of Y (source tile t-1)
-        int *Yxt = hs.Yx;
-        if (wid == 0) {
-          const int v = (t - 1) * TILE + lane;
-          const double ym = lead->Ym[v & (YRING - 1)];
-          Yt[lane] = MIXED ? (M_t)mant_to_float(ym) : (M_t)ym;
-          Yxt[lane] = lead->Ye[v & (YRING - 1)];
-        }
-        __syncthreads();
+        const int srcbase = (t - 1) * TILE;
+        // task k: row tile T0 + (k/4)*7, sources srcbase + 8(k%4) .. +7 (source tile t-1)
         for (int k = wid; k < 4 * nunits; k += nwarps) {
-          const int q = k & 3;
-          M_t cm[8];
-          int ce[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) { cm[i] = pm[i]; ce[i] = pe[i]; }
-          if (k + nwarps < 4 * nunits) load_task(t, k + nwarps);  // in flight during this task
+          const int u = k >> 2, q = k & 3;
+          const int r = (T0 + u * NHELP) * TILE + lane;
+          const int sb = srcbase + 8 * q;
+          M_t *Ym = (M_t *)hs.Yd + wid * 8;
+          int *Yx = hs.Yx + wid * 8;
+          if (lane < 8) {  // this warp's 8 values of Y, from the lead
+            const int v = sb + lane;
+            const double ym = lead->Ym[v & (YRING - 1)];
+            Ym[lane] = MIXED ? (M_t)mant_to_float(ym) : (M_t)ym;
+            Yx[lane] = lead->Ye[v & (YRING - 1)];
+          }
+          __syncwarp();
+          const size_t gbase = hidx(sb, r);  // + i * 32 for source sb + i
           if (MIXED) {
+            float m[8];
+            int e[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              m[i] = __ldg((const float *)gm + gbase + i * 32);
+              e[i] = __ldg(ge + gbase + i * 32);
+            }
             float sacc = 0.0f;
             int E = XZERO_E;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Yt[8 * q + i] * (float)cm[i], ce[i] + Yxt[8 * q + i]);
+            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * m[i], e[i] + Yx[i]);
             ((float *)hs.Pm)[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           } else {
+            double m[8];
             int e[8];
             int E = XZERO_E;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              e[i] = ce[i] + Yxt[8 * q + i];
-              E = max(E, e[i]);
+              m[i] = __ldg((const double *)gm + gbase + i * 32);
+              e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) E = max(E, e[i]);
             double sacc = 0.0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              sacc = fma(scale_nonpos((double)cm[i], e[i] - E), (double)Yt[8 * q + i], sacc);
+            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos(m[i], e[i] - E), (double)Ym[i], sacc);
             hs.Pm[k * TILE + lane] = sacc;
             hs.Pe[k * TILE + lane] = E;
           }
+          __syncwarp();
         }
         __syncthreads();
         // combine the four quarters of each owned row tile in a fixed order
@@ -298,7 +283,6 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
           }
         }
       }
-      if (t + 1 < NT && wid < 4 * units(t + 1)) load_task(t + 1, wid);  // the next period's first task
       cluster.sync();
     }
   }

@@ -60,7 +60,9 @@ namespace {
 
 using namespace chain_detail;
 
-constexpr int NHELP = CHAIN_CLUSTER - 1;  // bulk CTAs per recursion
+// Bulk CTAs per recursion (NH): 7 in an 8-CTA cluster; 15 in a 16-CTA
+// cluster (a non-portable size that GB300 grants on request) once N is large
+// enough for the bulk work, rather than the chain, to set the pace.
 constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
 
 // Shared memory of the lead CTA.
@@ -89,14 +91,14 @@ struct HelperSmem {
   int *Yx;      // [32 warps][8] exponents
 };
 
-__host__ __device__ constexpr int helper_tiles(int NT) { return (NT + NHELP - 1) / NHELP; }
+__host__ __device__ constexpr int helper_tiles(int NT, int NH) { return (NT + NH - 1) / NH; }
 
-__host__ __device__ constexpr size_t helper_smem_bytes(int NT) {
-  return (size_t)helper_tiles(NT) * TILE * (sizeof(double) + sizeof(int)) * 5 +
+__host__ __device__ constexpr size_t helper_smem_bytes(int NT, int NH) {
+  return (size_t)helper_tiles(NT, NH) * TILE * (sizeof(double) + sizeof(int)) * 5 +
          (size_t)32 * 8 * (sizeof(double) + sizeof(int));
 }
 
-template <bool MIXED, bool BWD>
+template <bool MIXED, bool BWD, int NHELP>
 __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V_B) {
   cg::cluster_group cluster = cg::this_cluster();
   const unsigned rank = cluster.block_rank();
@@ -192,7 +194,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     // ------------------------------------------------------------ bulk CTA
     HelperSmem hs;
     unsigned char *p = smem_raw;
-    const int lt_max = helper_tiles(NT);
+    const int lt_max = helper_tiles(NT, NHELP);
     hs.Am = (double *)p; p += sizeof(double) * lt_max * TILE;
     hs.Pm = (double *)p; p += sizeof(double) * 4 * lt_max * TILE;
     hs.Yd = (double *)p; p += sizeof(double) * 32 * 8;
@@ -288,49 +290,115 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
   }
 }
 
-template <bool MIXED>
-__global__ void __cluster_dims__(CHAIN_CLUSTER, 1, 1) __launch_bounds__(CHAIN_THREADS, 1)
-    chain_kernel(Workspace w, double *V_B) {
+// Cluster size CL (CTAs per recursion) is given at launch; blocks [0, CL) run
+// the forward recursion, [CL, 2 CL) the backward one.
+template <bool MIXED, int CL>
+__global__ void __launch_bounds__(CHAIN_THREADS, 1) chain_kernel(Workspace w, double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
-  if (blockIdx.x < CHAIN_CLUSTER) run_chain<MIXED, false>(w, smem_raw, V_B);
-  else run_chain<MIXED, true>(w, smem_raw, V_B);
+  if (blockIdx.x < CL) run_chain<MIXED, false, CL - 1>(w, smem_raw, V_B);
+  else run_chain<MIXED, true, CL - 1>(w, smem_raw, V_B);
 }
 
-constexpr size_t chain_smem_bytes(int N) {
+constexpr size_t chain_smem_bytes(int N, int CL) {
   const size_t lead = sizeof(LeadSmem);
-  const size_t help = helper_smem_bytes((N + TILE - 1) / TILE);
+  const size_t help = helper_smem_bytes((N + TILE - 1) / TILE, CL - 1);
   return lead > help ? lead : help;
 }
-static_assert(chain_smem_bytes(CHAIN_MAX_N) <= 227 * 1024, "recursion state for the largest N must fit in shared memory");
+static_assert(chain_smem_bytes(CHAIN_MAX_N, CHAIN_CLUSTER) <= 227 * 1024,
+              "recursion state for the largest N must fit in shared memory");
+constexpr int CHAIN_CLUSTER_LARGE = 16;
+constexpr int LARGE_CLUSTER_MIN_NT = 41;  // N > 1280: the bulk work would set the pace with 7 bulk CTAs
+
+template <bool MIXED, int CL>
+cudaError_t launch_chain_cluster(const Workspace &w, double *V_B, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * CL);
+  cfg.blockDim = dim3(CHAIN_THREADS);
+  cfg.dynamicSmemBytes = chain_smem_bytes(w.N, CL);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, chain_kernel<MIXED, CL>, w, V_B);
+}
 static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
               "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 
-// Raise the dynamic shared-memory limit of both chain kernels to the maximum
-// once per process and device (a host call that must not sit between the
-// launches of an evaluation).
+// Once per process and device (host calls that must not sit between the
+// launches of an evaluation): raise the dynamic shared-memory limit of the
+// recursion kernels to the maximum, allow the 16-CTA clusters, and check that
+// two of them can be resident (else the 8-CTA form is used for every N).
+namespace {
+bool g_chain_ready[64] = {false};
+bool g_large_cluster[64] = {false};
+
+template <bool MIXED, int CL>
+cudaError_t prepare_chain_kernel() {
+  const int bytes = (int)chain_smem_bytes(CHAIN_MAX_N, CL);
+  cudaError_t e = cudaFuncSetAttribute(chain_kernel<MIXED, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(chain_kernel<MIXED, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+template <int CL>
+bool clusters_fit() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * CL);
+  cfg.blockDim = dim3(CHAIN_THREADS);
+  cfg.dynamicSmemBytes = chain_smem_bytes(CHAIN_MAX_N, CL);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&n, chain_kernel<true, CL>, &cfg) == cudaSuccess && n >= 2;
+  cudaGetLastError();
+  return ok;
+}
+}  // namespace
+
 cudaError_t prepare_chains() {
-  static bool done[64] = {false};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  const int bytes = (int)chain_smem_bytes(CHAIN_MAX_N);
-  e = cudaFuncSetAttribute(chain_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chain_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
-  return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (g_chain_ready[dev]) return cudaSuccess;
+  e = prepare_chain_kernel<true, CHAIN_CLUSTER>();
+  if (e == cudaSuccess) e = prepare_chain_kernel<false, CHAIN_CLUSTER>();
+  if (e != cudaSuccess) return e;
+  bool large = prepare_chain_kernel<true, CHAIN_CLUSTER_LARGE>() == cudaSuccess &&
+               prepare_chain_kernel<false, CHAIN_CLUSTER_LARGE>() == cudaSuccess;
+  cudaGetLastError();
+  large = large && clusters_fit<CHAIN_CLUSTER_LARGE>();
+  g_large_cluster[dev] = large;
+  g_chain_ready[dev] = true;
+  return cudaSuccess;
 }
 
 cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s) {
   cudaError_t e = prepare_chains();
   if (e != cudaSuccess) return e;
-  const size_t bytes = chain_smem_bytes(w.N);
-  return w.mixed ? launch_pdl(chain_kernel<true>, 2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s, w, V_B)
-                 : launch_pdl(chain_kernel<false>, 2 * CHAIN_CLUSTER, CHAIN_THREADS, bytes, s, w, V_B);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool large = g_large_cluster[dev] && w.NT >= LARGE_CLUSTER_MIN_NT;
+  if (large)
+    return w.mixed ? launch_chain_cluster<true, CHAIN_CLUSTER_LARGE>(w, V_B, s)
+                   : launch_chain_cluster<false, CHAIN_CLUSTER_LARGE>(w, V_B, s);
+  return w.mixed ? launch_chain_cluster<true, CHAIN_CLUSTER>(w, V_B, s)
+                 : launch_chain_cluster<false, CHAIN_CLUSTER>(w, V_B, s);
 }
 
 }  // namespace bpimd

@@ -38,7 +38,7 @@ constexpr int TILE = 32;              // row / source tile of the recursions and
 constexpr int TILE2 = TILE * TILE;
 constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
 constexpr int CHAIN_THREADS = 640;     // 20 warps: up to 96 registers per thread
-constexpr int CHAIN_CLUSTER = 8;      // CTAs per recursion: one lead + seven bulk CTAs
+constexpr int CHAIN_CLUSTER = 8;      // CTAs per recursion (small N): one lead + seven bulk CTAs
 constexpr int CHAIN_MAX_N = 6912;     // largest N the library accepts
 constexpr int BATCH_MAX_N = 4096;     // largest replica of a batch (one CTA per recursion)
 constexpr int BEAD_BLOCK_PARTICLES = 8;  // particles per block of the bead pass

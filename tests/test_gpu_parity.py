@@ -111,6 +111,15 @@ def test_parity_small(prec, N, P, kind):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [1280, 1281, 1313])
+def test_parity_cluster_size_switch(prec, N):
+    """The recursion switches from 8- to 16-CTA clusters above N = 1280 (40
+    row tiles): the last 8-CTA size, the first 16-CTA size (a one-row ragged
+    tail) and a tile count that is not a multiple of the 15 bulk CTAs."""
+    check(inputs.trapped_positions(N, 4, seed=N), beta=1.0, prec=prec, want_M=False)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("beta", [0.5, 1.0, 2.0, 4.0])
 def test_parity_beta_sweep(prec, beta):
     check(inputs.trapped_positions(64, 32, seed=7), beta=beta, prec=prec)

@@ -95,18 +95,24 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
       const double *n = w.R1 + 4 * (size_t)(p + 1);
 #pragma unroll
       for (int c = 0; c < 3; ++c) n1[c] = n[c];
-      M = direct_link_fast(w, p);
     }
   }
   const size_t base = (size_t)t * (t + 1) / 2;
   const P_t *part = (const P_t *)w.rowpart;
   double acc = 0.0;
   fsum2 f;
-#pragma unroll 8
-  for (int s = half; s <= t; s += 2) {
-    const P_t v = __ldcg(part + ((base + s) * TILE + jj) * 4 + q);
-    if (std::is_same<P_t, float>::value) f.add((float)v);
-    else acc += (double)v;
+  // partials in chunks of 8 per thread, all loads of a chunk issued first;
+  // the direct link's float64 chain runs while the first chunk is in flight
+  for (int s0 = half; s0 <= t; s0 += 16) {
+    P_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (s0 + 2 * u <= t) ? __ldcg(part + ((base + s0 + 2 * u) * TILE + jj) * 4 + q) : (P_t)0;
+    if (s0 == half && mine && p + 1 < w.N) M = direct_link_fast(w, p);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (std::is_same<P_t, float>::value) f.add((float)v[u]);
+      else acc += (double)v[u];
+    }
   }
   fin[jj][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
@@ -144,17 +150,24 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
       const double *n = w.RP + 4 * (size_t)(p - 1);
 #pragma unroll
       for (int c = 0; c < 3; ++c) pP[c] = n[c];
-      M = direct_link_fast(w, p - 1);
     }
   }
   const P_t *part = (const P_t *)w.colpart;
   double acc = 0.0;
   fsum2 f;
-#pragma unroll 8
-  for (int t = s + half; t < w.NT; t += 2) {
-    const P_t v = __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q);
-    if (std::is_same<P_t, float>::value) f.add((float)v);
-    else acc += (double)v;
+  for (int t0 = s + half; t0 < w.NT; t0 += 16) {
+    P_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + 2 * u;
+      v[u] = (t < w.NT) ? __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q) : (P_t)0;
+    }
+    if (t0 == s + half && mine && p >= 1) M = direct_link_fast(w, p - 1);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (std::is_same<P_t, float>::value) f.add((float)v[u]);
+      else acc += (double)v[u];
+    }
   }
   fin[ii][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
   __syncthreads();
@@ -298,7 +311,7 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const double *__restrict__ pos,
+__global__ void __launch_bounds__(256, 4) prob_force_kernel(Workspace w, const double *__restrict__ pos,
                                                          double *__restrict__ F) {
   using P_t = typename std::conditional<MIXED, float, double>::type;
   __shared__ P_t red[8][32][4];
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(256) prob_force_kernel(Workspace w, const doub
 // Replica batch: entry k of tab is (replica, block); positions and forces of
 // replica r start at element off[r] of the packed arrays.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) prob_force_batched(const Workspace *__restrict__ ws,
+__global__ void __launch_bounds__(256, 4) prob_force_batched(const Workspace *__restrict__ ws,
                                                           const int2 *__restrict__ tab, int ntab,
                                                           const long long *__restrict__ off,
                                                           const double *__restrict__ pos, double *__restrict__ F) {

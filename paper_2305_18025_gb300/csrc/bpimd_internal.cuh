@@ -81,18 +81,6 @@ __device__ __forceinline__ xd xnorm(double m, int e) {
 
 __device__ __forceinline__ xd xmul(xd a, xd b) { return xnorm(a.m * b.m, a.e + b.e); }
 
-// a + b (not normalised; mantissa stays < 2 * (terms) and is renormalised by callers)
-__device__ __forceinline__ xd xadd_raw(xd a, xd b) {
-  int E = max(a.e, b.e);
-  return xd{fma(b.m, pow2_nonpos(b.e - E), a.m * pow2_nonpos(a.e - E)), E};
-}
-// acc + y * h  with y, h extended (h may be an extended zero)
-__device__ __forceinline__ xd xmuladd_raw(xd acc, xd y, double hm, int he) {
-  double pm = y.m * hm;
-  int pe = y.e + he;
-  int E = max(acc.e, pe);
-  return xd{fma(pm, pow2_nonpos(pe - E), acc.m * pow2_nonpos(acc.e - E)), E};
-}
 // Convert an extended number to a double (0 below the normal range).
 __device__ __forceinline__ double xtod(xd a) {
   if (a.m == 0.0 || a.e < -1100) return 0.0;

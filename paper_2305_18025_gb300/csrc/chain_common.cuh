@@ -71,9 +71,6 @@ __device__ __forceinline__ xd xnorm_int(xd a) {
   return xd{__longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL), a.e + ex - 1023};
 }
 
-// a * b with integer normalisation (one float64 multiply).
-__device__ __forceinline__ xd xmul_int(xd a, xd b) { return xnorm_int(xd{a.m * b.m, a.e + b.e}); }
-
 // Round the significand of a positive normal double to a float in [1,2] with
 // integer ops (no float64 conversion unit); the binary exponent is dropped.
 __device__ __forceinline__ float mant_to_float(double m) {

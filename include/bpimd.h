@@ -135,11 +135,7 @@ int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions,
 
 /* Same computation with HOST buffers: copies positions in, computes, copies
  * V_B (may be NULL) and forces out, synchronises.  Host buffers may be pageable
- * or pinned; pinned memory is faster.  The force download overlaps the
- * recursions: the whole array is copied (on a second stream owned by the
- * context) once the interior-bead forces are final, and the bead-1/bead-P
- * forces, gathered on the device after the probability pass, replace their
- * entries in `forces` before the call returns. */
+ * or pinned; pinned memory is faster. */
 int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions,
                                       double *V_B, double *forces);
 

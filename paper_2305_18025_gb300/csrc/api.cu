@@ -96,7 +96,7 @@ size_t layout_workspace(Workspace &w, char *base) {
 }
 
 // one evaluation of V_B and forces on ctx->stream
-int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F, cudaEvent_t after_prep) {
+int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   const Workspace &w = ctx->w;
   cudaStream_t s = ctx->stream;
   cudaEvent_t *ev = nullptr;
@@ -105,7 +105,6 @@ int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F, cudaEven
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
   if (launch_prep(w, pos, F, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  if (after_prep && cudaEventRecord(after_prep, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(1);
   if (launch_chains(w, V_B, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   mark(2);
@@ -176,11 +175,6 @@ int bpimd_destroy(bpimd_ctx *ctx) {
   cudaFree(ctx->d_pos);
   cudaFree(ctx->d_F);
   cudaFree(ctx->d_VB);
-  cudaFree(ctx->d_ends);
-  if (ctx->h_ends) cudaFreeHost(ctx->h_ends);
-  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-  if (ctx->ev_prep) cudaEventDestroy(ctx->ev_prep);
-  if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
   cudaFreeHost(ctx->host_status);
   delete ctx;
   return BPIMD_OK;
@@ -198,44 +192,22 @@ int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions, double
 int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions, double *V_B, double *forces) {
   if (!ctx || !positions || !forces) return BPIMD_ERR_ARG;
   if (ctx->R) return BPIMD_ERR_STATE;
-  const int N = ctx->w.N, P = ctx->w.P;
-  const size_t bytes = sizeof(double) * 3 * (size_t)N * P, ebytes = sizeof(double) * 6 * (size_t)N;
+  const size_t bytes = sizeof(double) * 3 * (size_t)ctx->w.N * ctx->w.P;
   if (!ctx->d_pos) {
     if (cudaMalloc(&ctx->d_pos, bytes) != cudaSuccess || cudaMalloc(&ctx->d_F, bytes) != cudaSuccess ||
-        cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess || cudaMalloc(&ctx->d_ends, ebytes) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_ends, ebytes) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming) != cudaSuccess) {
+        cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return BPIMD_ERR_NOMEM;
     }
   }
-  cudaStream_t s = ctx->stream, cs = ctx->copy_stream;
+  cudaStream_t s = ctx->stream;
   if (cudaMemcpyAsync(ctx->d_pos, positions, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return BPIMD_ERR_CUDA;
-  int rc = evaluate(ctx, ctx->d_pos, ctx->d_VB, ctx->d_F, ctx->ev_prep);
+  int rc = evaluate(ctx, ctx->d_pos, ctx->d_VB, ctx->d_F);
   if (rc != BPIMD_OK) return rc;
-  // the interior-bead forces are final after the bead pass: download the whole
-  // array during the recursions (its endpoint beads are replaced below)
-  if (cudaStreamWaitEvent(cs, ctx->ev_prep, 0) != cudaSuccess ||
-      cudaMemcpyAsync(forces, ctx->d_F, bytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
-      cudaEventRecord(ctx->ev_copy, cs) != cudaSuccess)
-    return BPIMD_ERR_CUDA;
-  if (launch_gather_endpoint_forces(ctx->d_F, N, P, ctx->d_ends, s) != cudaSuccess ||
-      cudaMemcpyAsync(ctx->h_ends, ctx->d_ends, ebytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return BPIMD_ERR_CUDA;
+  if (cudaMemcpyAsync(forces, ctx->d_F, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   if (V_B && cudaMemcpyAsync(V_B, ctx->d_VB, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
-  if (cudaStreamWaitEvent(s, ctx->ev_copy, 0) != cudaSuccess) return BPIMD_ERR_CUDA;
-  rc = read_status(ctx);  // synchronises the context stream, which waited for the copy stream
-  if (rc != BPIMD_OK && rc != BPIMD_ERR_NONFINITE) return rc;
-  for (int l = 0; l < N; ++l) {
-    double *f1 = forces + (size_t)l * P * 3, *fP = f1 + (size_t)(P - 1) * 3;
-    const double *e = ctx->h_ends + 6 * (size_t)l;
-    f1[0] = e[0]; f1[1] = e[1]; f1[2] = e[2];
-    fP[0] = e[3]; fP[1] = e[4]; fP[2] = e[5];
-  }
-  return rc;
+  return read_status(ctx);
 }
 
 int bpimd_sync(bpimd_ctx *ctx) {

@@ -245,8 +245,6 @@ cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
 // connection probabilities and all exterior-bead forces
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
-// ends[l][0..2] = F of bead 1 of particle l, ends[l][3..5] = F of bead P
-cudaError_t launch_gather_endpoint_forces(const double *F, int N, int P, double *ends, cudaStream_t s);
 // per block of g: (1/2) m w_P^2 sum Pr[b -> a] |r_b^P - r_a^1|^2 over a <= b (part[NB])
 cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStream_t s);
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);

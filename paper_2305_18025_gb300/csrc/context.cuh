@@ -13,12 +13,6 @@ struct bpimd_ctx {
   size_t dev_bytes;
   int *host_status;    // pinned
   double *d_pos, *d_F, *d_VB;  // staging for the _host entry point (lazy)
-  // _host entry point: the interior-bead forces are downloaded on copy_stream
-  // while the recursions run; the endpoint beads are gathered into d_ends and
-  // downloaded to the pinned h_ends afterwards
-  cudaStream_t copy_stream;
-  cudaEvent_t ev_prep, ev_copy;
-  double *d_ends, *h_ends;
   double *d_Vf, *d_Vb;         // diagnostic potentials (bpimd_get_potentials)
   bool evaluated;
   bpimd::MDState md;

@@ -396,13 +396,6 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
   }
 }
 
-__global__ void gather_ends_kernel(const double *__restrict__ F, int N, int P, double *__restrict__ ends) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * N; k += gridDim.x * blockDim.x) {
-    const int l = k / 6, c = k - 6 * l;
-    ends[k] = F[((size_t)l * P + (c < 3 ? 0 : P - 1)) * 3 + (c < 3 ? c : c - 3)];
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
@@ -411,11 +404,6 @@ cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F,
   cudaError_t e = w.mixed ? launch_pdl(prob_force_kernel<true>, grid, 256, 0, s, w, pos, F)
                           : launch_pdl(prob_force_kernel<false>, grid, 256, 0, s, w, pos, F);
   if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather_endpoint_forces(const double *F, int N, int P, double *ends, cudaStream_t s) {
-  gather_ends_kernel<<<(6 * N + 255) / 256, 256, 0, s>>>(F, N, P, ends);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,5 @@ struct MDState {
 void md_init(MDState *md);
 void md_free(MDState *md);
 int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies);
-// after_prep (may be null) is recorded on the context stream once the bead
-// pass and pair factors are issued (the interior-bead forces are then final).
-int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F, cudaEvent_t after_prep = nullptr);
+int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F);
 }  // namespace bpimd

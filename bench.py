@@ -305,11 +305,11 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": mixed["value"], "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "dtype": "f32+u32+f64 (mixed: float32 pair factors and sums, 32-bit integer recursion steps, float64 hand-offs and outputs)", "data": "synthetic",
         "config": dict(workload(args), precision="mixed",
                        l2="flushed between timed steps (256 MiB device write, untimed)"),
         "fp64": {"value": fp64["value"], "unit": "evals/s", "ms_per_step": fp64["ms_per_step"],
-                 "dtype": "f64", "stages_ms": dict(zip(STAGE_NAMES, fp64["stage_ms"]))},
+                 "dtype": "f64+u64 (float64, with 64-bit integer recursion steps)", "stages_ms": dict(zip(STAGE_NAMES, fp64["stage_ms"]))},
         "stages_ms": dict(zip(STAGE_NAMES, mixed["stage_ms"])),
         "e2e": results["e2e"],
         "roofline": roofline(mixed["stage_ms"], args, clocks.get("sm_mhz"), peaks),

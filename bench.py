@@ -290,8 +290,7 @@ def run_ours(args, rank, world, local_rank):
             results["e2e"] = {"value": aggregate_rate(world, args.steps, e2e_s), "unit": "evals/s",
                               "h2d_bytes_per_step": pos_h.numel() * 8,
                               "d2h_bytes_per_step": F_h.numel() * 8 + 8,
-                              "api": "bpimd_exchange_energy_forces_host (pinned host buffers, read and written in place "
-                                 "by the kernels over the CPU-GPU link)"}
+                              "api": "bpimd_exchange_energy_forces_host (pinned host buffers)"}
         eng.close()
     results["md"] = md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world)
     results["batched"] = batched_throughput(args, dev, flush, max_over_ranks, barrier, world)

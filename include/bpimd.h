@@ -133,11 +133,9 @@ int bpimd_destroy(bpimd_ctx *ctx);
 int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions,
                                  double *V_B, double *forces);
 
-/* Same computation with HOST buffers: positions in, V_B (may be NULL) and
- * forces out, synchronises.  Host buffers may be pageable or pinned.  Pinned
- * buffers (cudaMallocHost / cudaHostRegister) are read and written by the
- * kernels in place over the CPU-GPU link; other host memory is copied through
- * device staging buffers. */
+/* Same computation with HOST buffers: copies positions in, computes, copies
+ * V_B (may be NULL) and forces out, synchronises.  Host buffers may be pageable
+ * or pinned; pinned memory is faster. */
 int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions,
                                       double *V_B, double *forces);
 

@@ -38,17 +38,6 @@ int check_ptr(const void *p) {
   return BPIMD_OK;
 }
 
-// Device address of a pinned host allocation (cudaMallocHost or registered
-// memory); null for any other pointer.
-void *pinned_device_view(const void *p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
-}
-
 int read_status(bpimd_ctx *ctx) {
   cudaError_t e = cudaMemcpyAsync(ctx->host_status, ctx->w.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return BPIMD_ERR_CUDA;
@@ -204,26 +193,9 @@ int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions, d
   if (!ctx || !positions || !forces) return BPIMD_ERR_ARG;
   if (ctx->R) return BPIMD_ERR_STATE;
   const size_t bytes = sizeof(double) * 3 * (size_t)ctx->w.N * ctx->w.P;
-  // Pinned host buffers are read and written by the kernels in place, over
-  // the coherent CPU-GPU link; any other host memory goes through staging
-  // copies.  Only memory that the runtime reports as pinned host memory with
-  // a device address is accessed this way.
-  const double *pos_dev = (const double *)pinned_device_view(positions);
-  double *F_dev = (double *)pinned_device_view(forces);
-  if (pos_dev && F_dev && !(((uintptr_t)pos_dev | (uintptr_t)F_dev) & 7)) {
-    if (!ctx->d_VB && cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return BPIMD_ERR_NOMEM;
-    }
-    int rc = evaluate(ctx, pos_dev, ctx->d_VB, F_dev);
-    if (rc != BPIMD_OK) return rc;
-    if (V_B && cudaMemcpyAsync(V_B, ctx->d_VB, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
-      return BPIMD_ERR_CUDA;
-    return read_status(ctx);
-  }
   if (!ctx->d_pos) {
     if (cudaMalloc(&ctx->d_pos, bytes) != cudaSuccess || cudaMalloc(&ctx->d_F, bytes) != cudaSuccess ||
-        (!ctx->d_VB && cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess)) {
+        cudaMalloc(&ctx->d_VB, sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return BPIMD_ERR_NOMEM;
     }

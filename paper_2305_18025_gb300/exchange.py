@@ -61,8 +61,7 @@ class ExchangeEnergy:
     __call__ = forces
 
     def forces_host(self, pos_host, F_host=None):
-        """Host-buffer entry point (synchronises): pinned tensors are read and
-        written in place by the kernels, pageable ones are copied."""
+        """Host-buffer entry point (copies in and out, synchronises)."""
         import numpy as np
         F_host = F_host if F_host is not None else torch.empty_like(pos_host)
         V = np.zeros(1)

@@ -205,6 +205,28 @@ def test_host_entry_point_matches_device():
     assert torch.equal(Fh, F.cpu())
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point_pinned_and_pageable(prec, pinned):
+    """Pinned and pageable host buffers give the device entry point's bits,
+    also when a context's staging buffers are reused by a second call."""
+    N, P = 300, 6
+    pos = inputs.trapped_positions(N, P, seed=8)
+    wP = inputs.omega_P(P, 1.0)
+    eng = ExchangeEnergy(N, P, 1.0, wP, 1.0, precision=prec, device="cuda:0")
+    V, F = eng.forces(torch.from_numpy(pos).cuda())
+    eng.sync()
+    x = torch.from_numpy(pos.copy())
+    Fh = torch.full((N, P, 3), float("nan"), dtype=torch.float64)
+    if pinned:
+        x, Fh = x.pin_memory(), Fh.pin_memory()
+    for _ in range(2):  # the second call reuses the first call's buffers
+        Vh, Fh = eng.forces_host(x, Fh)
+        assert Vh == float(V.cpu())
+        assert torch.equal(Fh, F.cpu())
+    eng.close()
+
+
 def test_nonfinite_positions_are_reported():
     pos = inputs.trapped_positions(8, 4, seed=0)
     pos[3, 2, 1] = np.nan

@@ -12,7 +12,8 @@
 //
 // GB300 facts behind the schedule (measured): a float64 FMA has a 64-cycle
 // latency (plus ~40 before a shuffle can read it), while the integer form of
-// the step below takes ~100 cycles including its shuffle; a release/acquire
+// the step below takes ~100 cycles including its shuffle with 64-bit
+// mantissas and ~80 with the 32-bit words of MIXED; a release/acquire
 // hand-off between warps inside a step costs far more than the step itself;
 // a cluster barrier costs ~360 cycles and a distributed shared-memory access
 // ~215.  So the rows are processed in tiles of 32 and
@@ -20,16 +21,18 @@
 //     warp 0 runs the 32 dependent steps of row tile t.  Lane j holds
 //     c_r * (partial row sum) of row 32t+j and the partial sum of row
 //     32(t+1)+j.  A step is one integer extended multiply-add on the current
-//     row (the dependency chain: acc_j += K(i, j) y_i with 64-bit integer
-//     mantissas, chain_common.cuh), one term of the next tile's row (off the
-//     chain), and a shuffle that broadcasts the new Y;
+//     row (the dependency chain: acc_j += K(i, j) y_i with integer
+//     mantissas, 32-bit words in MIXED and 64-bit in FP64, chain_common.cuh),
+//     one term of the next tile's row (off the chain), and a shuffle that
+//     broadcasts the new Y;
 //   * twelve other lead warps (none on warp 0's sub-partition) stage, for
 //     tile t+1, the block of H from source tile t+1 to the rows of tile t+2
 //     and the diagonal block pre-scaled by c; one more lead warp of the
 //     forward cluster forms the prefix sums C, one tile of 32 per period;
-//   * the O(N^2) bulk runs on the seven other CTAs of the cluster: row tile T
-//     belongs to CTA 1 + T mod 7, which keeps its rows' partial sums in its
-//     own shared memory.  In period t each of them adds source tile t-1 to
+//   * the O(N^2) bulk runs on the other CTAs of the cluster (seven, or
+//     fifteen in the 16-CTA form used above N = 1280): row tile T belongs to
+//     CTA 1 + T mod NH, which keeps its rows' partial sums in its own shared
+//     memory.  In period t each of them adds source tile t-1 to
 //     every row tile T >= t+1 it owns: one warp per (row tile, quarter of 8
 //     sources), each reading its 8 values of Y from the lead's shared memory
 //     and issuing its 16 loads at once; the quarters are then combined in a

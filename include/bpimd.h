@@ -135,7 +135,10 @@ int bpimd_exchange_energy_forces(bpimd_ctx *ctx, const double *positions,
 
 /* Same computation with HOST buffers: copies positions in, computes, copies
  * V_B (may be NULL) and forces out, synchronises.  Host buffers may be pageable
- * or pinned; pinned memory is faster. */
+ * or pinned; pinned memory is faster.  With pinned buffers on a non-default
+ * stream (and stage profiling off) the whole call -- copies, the evaluation
+ * kernels and the status read -- is captured once into a CUDA graph for that
+ * (positions, forces) pair and replayed on later calls. */
 int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions,
                                       double *V_B, double *forces);
 

@@ -38,6 +38,15 @@ int check_ptr(const void *p) {
   return BPIMD_OK;
 }
 
+bool is_pinned(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 int read_status(bpimd_ctx *ctx) {
   cudaError_t e = cudaMemcpyAsync(ctx->host_status, ctx->w.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return BPIMD_ERR_CUDA;
@@ -113,6 +122,59 @@ int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   ctx->evaluated = true;
   return BPIMD_OK;
 }
+
+// The host-buffer call as one replayed CUDA graph (pinned buffers, non-default
+// stream): the copies in and out, the three evaluation kernels, and the copies
+// of V_B and the status word into pinned context scalars.  Captured once per
+// (positions, forces) pair; the staging buffers must exist.  Returns
+// BPIMD_ERR_STATE when the graph cannot be built (the caller then takes the
+// direct path), else the call's status.
+int host_call_graph(bpimd_ctx *ctx, const double *positions, double *forces, size_t bytes) {
+  cudaStream_t s = ctx->stream;
+  if (!ctx->h_VB && (cudaMallocHost(&ctx->h_VB, sizeof(double)) != cudaSuccess ||
+                     cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess)) {
+    cudaGetLastError();
+    return BPIMD_ERR_STATE;
+  }
+  if (!ctx->host_exec || ctx->hg_pos != positions || ctx->hg_F != forces) {
+    if (ctx->host_exec) { cudaGraphExecDestroy(ctx->host_exec); ctx->host_exec = nullptr; }
+    if (ctx->host_graph) { cudaGraphDestroy(ctx->host_graph); ctx->host_graph = nullptr; }
+    if (prepare_chains() != cudaSuccess) return BPIMD_ERR_STATE;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return BPIMD_ERR_STATE;
+    }
+    bool ok = cudaMemcpyAsync(ctx->d_pos, positions, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              evaluate(ctx, ctx->d_pos, ctx->d_VB, ctx->d_F) == BPIMD_OK &&
+              cudaMemcpyAsync(forces, ctx->d_F, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaMemcpyAsync(ctx->h_VB, ctx->d_VB, sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaMemcpyAsync(ctx->h_status, ctx->w.status, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    ok = (cudaStreamEndCapture(s, &g) == cudaSuccess) && ok && g;
+    if (ok && cudaGraphInstantiate(&ctx->host_exec, g, 0) != cudaSuccess) {
+      ctx->host_exec = nullptr;
+      ok = false;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return BPIMD_ERR_STATE;
+    }
+    ctx->host_graph = g;
+    ctx->hg_pos = positions;
+    ctx->hg_F = forces;
+  }
+  if (cudaGraphLaunch(ctx->host_exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return BPIMD_ERR_CUDA;
+  ctx->evaluated = true;
+  const int st = *ctx->h_status;
+  if (st) {
+    if (cudaMemsetAsync(ctx->w.status, 0, sizeof(int), s) != cudaSuccess) return BPIMD_ERR_CUDA;
+    if (st & ST_TIMEOUT) return BPIMD_ERR_TIMEOUT;
+    if (st & ST_NONFINITE) return BPIMD_ERR_NONFINITE;
+  }
+  return BPIMD_OK;
+}
 }  // namespace bpimd
 
 extern "C" {
@@ -175,6 +237,10 @@ int bpimd_destroy(bpimd_ctx *ctx) {
   cudaFree(ctx->d_pos);
   cudaFree(ctx->d_F);
   cudaFree(ctx->d_VB);
+  if (ctx->host_exec) cudaGraphExecDestroy(ctx->host_exec);
+  if (ctx->host_graph) cudaGraphDestroy(ctx->host_graph);
+  if (ctx->h_VB) cudaFreeHost(ctx->h_VB);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
   cudaFreeHost(ctx->host_status);
   delete ctx;
   return BPIMD_OK;
@@ -201,6 +267,13 @@ int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions, d
     }
   }
   cudaStream_t s = ctx->stream;
+  if (s != nullptr && !ctx->prof_on && is_pinned(positions) && is_pinned(forces)) {
+    int rc = host_call_graph(ctx, positions, forces, bytes);
+    if (rc != BPIMD_ERR_STATE) {  // BPIMD_ERR_STATE: the graph could not be built; take the direct path
+      if (rc == BPIMD_OK && V_B) *V_B = *ctx->h_VB;
+      return rc;
+    }
+  }
   if (cudaMemcpyAsync(ctx->d_pos, positions, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return BPIMD_ERR_CUDA;
   int rc = evaluate(ctx, ctx->d_pos, ctx->d_VB, ctx->d_F);
   if (rc != BPIMD_OK) return rc;

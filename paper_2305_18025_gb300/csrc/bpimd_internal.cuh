@@ -242,6 +242,9 @@ cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaSt
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s);
 // both recursions, prefix sums, V_B (device scalar, may be null), normaliser, alpha
 cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s);
+// once per process and device, before any stream capture: kernel attributes
+// and the cluster-size choice of the recursions
+cudaError_t prepare_chains();
 // connection probabilities and all exterior-bead forces
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s);
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);

@@ -13,6 +13,15 @@ struct bpimd_ctx {
   size_t dev_bytes;
   int *host_status;    // pinned
   double *d_pos, *d_F, *d_VB;  // staging for the _host entry point (lazy)
+  // _host entry point with pinned buffers on a non-default stream: the whole
+  // call (copies in, evaluation, copies out, status) as one CUDA graph,
+  // captured for one (positions, forces) pair and replayed
+  cudaGraph_t host_graph;
+  cudaGraphExec_t host_exec;
+  const void *hg_pos;
+  void *hg_F;
+  double *h_VB;      // pinned: V_B of the last replay
+  int *h_status;     // pinned: status word of the last replay
   double *d_Vf, *d_Vb;         // diagnostic potentials (bpimd_get_potentials)
   bool evaluated;
   bpimd::MDState md;

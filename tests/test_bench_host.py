@@ -3,7 +3,6 @@ and the rule that a DRAM-traffic figure is reported only while the sources of
 its kernel are unchanged since the ncu capture."""
 import json
 import os
-import shutil
 import types
 
 import pytest
@@ -45,20 +44,17 @@ def test_roofline_prep_counts_the_pair_factor_bytes_of_its_precision(monkeypatch
 
 
 def test_traffic_figure_only_while_sources_match(tmp_path, monkeypatch):
-    root = tmp_path
-    for rel in ("profiles/traffic.json",):
-        os.makedirs(root / os.path.dirname(rel), exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, rel), root / rel)
-    tab = json.load(open(root / "profiles/traffic.json"))
-    for ent in tab.values():
-        if isinstance(ent, dict):
-            for rel in ent["sources"]:
-                os.makedirs(root / os.path.dirname(rel), exist_ok=True)
-                shutil.copy(os.path.join(bench.ROOT, rel), root / rel)
-    monkeypatch.setattr(bench, "ROOT", str(root))
-    want = tab["recursions"]["dram_bytes_per_launch"]
-    assert bench.load_traffic("recursions") == want
-    src = root / tab["recursions"]["sources"][0]
-    src.write_text(src.read_text() + "\n// changed\n")
+    import hashlib
+    rel = "csrc/kernel.cu"
+    os.makedirs(tmp_path / "csrc")
+    os.makedirs(tmp_path / "profiles")
+    (tmp_path / rel).write_text("// a kernel\n")
+    digest = hashlib.sha256((tmp_path / rel).read_bytes()).hexdigest()
+    table = {"_about": "test", "recursions": {"kernel": "k", "dram_bytes_per_launch": 12345,
+                                               "sources": [rel], "sources_sha256": digest}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(table))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("recursions") == 12345
+    (tmp_path / rel).write_text("// a kernel, changed\n")
     assert bench.load_traffic("recursions") is None
     assert bench.load_traffic("no_such_stage") is None

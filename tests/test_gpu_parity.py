@@ -241,6 +241,37 @@ def test_nonfinite_positions_are_reported():
     eng.sync()
 
 
+def test_host_call_graph_replay_reports_status_and_follows_the_data():
+    """Pinned buffers on a non-default stream: the host call is captured once
+    and replayed.  Replays read the buffer's current contents, a non-finite
+    input is reported (and cleared), and the context stays usable."""
+    N, P = 40, 6
+    wP = inputs.omega_P(P, 1.0)
+    side = torch.cuda.Stream("cuda:0")
+    eng = ExchangeEnergy(N, P, 1.0, wP, 1.0, device="cuda:0", stream=side)
+    x = torch.empty((N, P, 3), dtype=torch.float64).pin_memory()
+    Fh = torch.empty((N, P, 3), dtype=torch.float64).pin_memory()
+    for seed in (1, 2):  # same buffers, new contents: the replay follows them
+        pos = inputs.trapped_positions(N, P, seed=seed)
+        x.copy_(torch.from_numpy(pos))
+        Vh, Fh = eng.forces_host(x, Fh)
+        VB, F = oracle.fast_pimdb(pos, 1.0, wP, 1.0)
+        assert abs(Vh - float(VB)) <= 1e-12 * energy_scale(pos, 1.0, wP, 1.0, float(VB))
+        assert np.linalg.norm(Fh.numpy() - F) <= 1e-10 * np.linalg.norm(F)
+    bad = inputs.trapped_positions(N, P, seed=3)
+    bad[5, 1, 2] = np.inf
+    x.copy_(torch.from_numpy(bad))
+    with pytest.raises(bpimd.BpimdError) as ei:
+        eng.forces_host(x, Fh)
+    assert ei.value.status == bpimd.BPIMD_ERR_NONFINITE
+    pos = inputs.trapped_positions(N, P, seed=4)
+    x.copy_(torch.from_numpy(pos))
+    Vh, Fh = eng.forces_host(x, Fh)  # cleared: the next call succeeds
+    VB, F = oracle.fast_pimdb(pos, 1.0, wP, 1.0)
+    assert abs(Vh - float(VB)) <= 1e-12 * energy_scale(pos, 1.0, wP, 1.0, float(VB))
+    eng.close()
+
+
 def test_invalid_size_rejected_on_host():
     with pytest.raises(bpimd.BpimdError) as ei:
         ExchangeEnergy(8, 1, 1.0, 2.0, 1.0, device="cuda:0")

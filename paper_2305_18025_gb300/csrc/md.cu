@@ -37,8 +37,14 @@ namespace bpimd {
 namespace {
 
 constexpr int MD_THREADS = 256;
-constexpr int EXT_THREADS = 128;
+constexpr int EXT_THREADS = 256;
+constexpr int EXT_SPLIT = 4;  // lanes per particle in the all-pairs force
+constexpr int EXT_PARTICLES = EXT_THREADS / EXT_SPLIT;
 constexpr int EXT_CHUNK = 1024;  // positions of one bead index staged per pass
+
+struct alignas(16) Dbl4 {
+  double x, y, z, w;
+};
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -127,19 +133,23 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // -grad U-bar added to F, per bead index j = blockIdx.y and particle
-// l = blockIdx.x * EXT_THREADS + thread (all pairs); U-bar partial sum per
-// block.  The positions of bead j of all particles pass through shared memory
-// in chunks.  Pairs: Gaussian g exp(-r^2/(2 s^2)), or Lennard-Jones
-// 4 eps ((sig/r)^12 - (sig/r)^6) truncated and shifted at rc; in a periodic box
-// pair distances by minimum image.  MIXED: pair terms in float32, accumulated
-// per thread in float32 and added to the float64 force.
-template <bool MIXED>
+// l = blockIdx.x * EXT_PARTICLES + thread / EXT_SPLIT (all pairs).  The
+// EXT_SPLIT lanes of one particle take the partners q = sub, sub + EXT_SPLIT, ...
+// of each staged chunk and combine their sums by a fixed shuffle butterfly;
+// U-bar partial sum per block.  The positions of bead j of all particles pass
+// through shared memory in chunks.  Pairs: Gaussian g exp(-r^2/(2 s^2)), or
+// Lennard-Jones 4 eps ((sig/r)^12 - (sig/r)^6) truncated and shifted at rc; in a
+// periodic box (PBC) pair distances by minimum image.  MIXED: pair terms in
+// float32, accumulated per lane in float32 and added to the float64 force.
+template <bool MIXED, bool PBC>
 __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__restrict__ pos, double *__restrict__ F,
                                                                 int N, int P, PairParams pp, double *ubar_part) {
   using R = typename std::conditional<MIXED, float, double>::type;
-  __shared__ R sx[EXT_CHUNK], sy[EXT_CHUNK], sz[EXT_CHUNK];
+  using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
+  __shared__ R4 sr[EXT_CHUNK];
   __shared__ double red[EXT_THREADS / 32];
-  const int j = blockIdx.y, l = blockIdx.x * EXT_THREADS + threadIdx.x;
+  const int j = blockIdx.y, sub = threadIdx.x % EXT_SPLIT;
+  const int l = blockIdx.x * EXT_PARTICLES + threadIdx.x / EXT_SPLIT;
   const bool valid = l < N;
   double rx = 0, ry = 0, rz = 0;
   if (valid) {
@@ -151,7 +161,8 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
   const R L = (R)pp.L, invL = (R)pp.invL;
   const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
   auto img = [&](R d) -> R {
-    return pp.pbc ? d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL))) : d;
+    if constexpr (PBC) return d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL)));
+    else return d;
   };
   R fx = 0, fy = 0, fz = 0, u = 0;
   int nin = 0;  // Lennard-Jones pairs inside the cutoff (each carries the shift)
@@ -159,22 +170,28 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
     for (int base = 0; base < N; base += EXT_CHUNK) {
       const int cnt = min(EXT_CHUNK, N - base);
       __syncthreads();
-      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      for (int q = threadIdx.x; q < cnt; q += EXT_THREADS) {
         const double *r = pos + ((size_t)(base + q) * P + j) * 3;
-        sx[q] = (R)r[0]; sy[q] = (R)r[1]; sz[q] = (R)r[2];
+        R4 t;
+        t.x = (R)r[0]; t.y = (R)r[1]; t.z = (R)r[2]; t.w = (R)0;
+        sr[q] = t;
       }
       __syncthreads();
       if (valid && pp.pair == BPIMD_PAIR_GAUSSIAN) {
-        for (int q = 0; q < cnt; ++q) {
-          const R dx = img(px - sx[q]), dy = img(py - sy[q]), dz = img(pz - sz[q]);
+#pragma unroll 4
+        for (int q = sub; q < cnt; q += EXT_SPLIT) {
+          const R4 t = sr[q];
+          const R dx = img(px - t.x), dy = img(py - t.y), dz = img(pz - t.z);
           const R d2 = dx * dx + dy * dy + dz * dz;
           const R e = MIXED ? (R)__expf((float)(a * d2)) : (R)exp((double)(a * d2));
           fx += e * dx; fy += e * dy; fz += e * dz;
           u += e;
         }
       } else if (valid) {  // Lennard-Jones: force over 24 eps, energy over 4 eps
-        for (int q = 0; q < cnt; ++q) {
-          const R dx = img(px - sx[q]), dy = img(py - sy[q]), dz = img(pz - sz[q]);
+#pragma unroll 4
+        for (int q = sub; q < cnt; q += EXT_SPLIT) {
+          const R4 t = sr[q];
+          const R dx = img(px - t.x), dy = img(py - t.y), dz = img(pz - t.z);
           const R r2 = dx * dx + dy * dy + dz * dz;
           if (r2 > (R)0 && r2 < rc2) {
             const R s2 = sig2 / r2, s6 = s2 * s2 * s2;
@@ -186,10 +203,18 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
         }
       }
     }
-    if (valid && pp.pair == BPIMD_PAIR_GAUSSIAN) u -= (R)1;  // the self term (d = 0, e = 1) carries no force
+  }
+#pragma unroll
+  for (int o = 1; o < EXT_SPLIT; o <<= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    nin += __shfl_xor_sync(0xffffffffu, nin, o);
   }
   double ul = 0.0;
-  if (valid) {
+  if (valid && sub == 0) {
+    if (pp.pair == BPIMD_PAIR_GAUSSIAN) u -= (R)1;  // the self term (d = 0, e = 1) carries no force
     double *f = F + ((size_t)l * P + j) * 3;
     const double fs = pp.pair == BPIMD_PAIR_GAUSSIAN ? pp.ga * pp.inv_s2 : 24.0 * pp.eps;
     f[0] += pp.inv_P * (fs * (double)fx - pp.kt * rx);
@@ -313,13 +338,15 @@ int total_force(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
   if (p.cell_nc > 0)
     return cell_list_forces(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp, ctx->w.mixed, md.cells, md.ubar_part,
                             ctx->stream) == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
-  const dim3 grid((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS, ctx->cfg.P);
-  if (ctx->w.mixed)
-    ext_force_kernel<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp,
-                                                                  md.ubar_part);
-  else
-    ext_force_kernel<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp,
-                                                                   md.ubar_part);
+  const dim3 grid((ctx->cfg.N + EXT_PARTICLES - 1) / EXT_PARTICLES, ctx->cfg.P);
+  const int N = ctx->cfg.N, P = ctx->cfg.P;
+  if (ctx->w.mixed) {
+    if (p.pp.pbc) ext_force_kernel<true, true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
+    else ext_force_kernel<true, false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
+  } else {
+    if (p.pp.pbc) ext_force_kernel<false, true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
+    else ext_force_kernel<false, false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
+  }
   return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
 }
 
@@ -352,7 +379,8 @@ int md_alloc(bpimd_ctx *ctx, const MDParams &p) {
     cell_list_layout(md.cells, (char *)md.cell_block, ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.mixed);
   }
   const size_t n = (size_t)ctx->cfg.N * ctx->cfg.P * 3;
-  md.ext_blocks = ((ctx->cfg.N + EXT_THREADS - 1) / EXT_THREADS) * ctx->cfg.P;
+  md.ext_blocks = p.cell_nc > 0 ? cell_list_partials(ctx->cfg.N, ctx->cfg.P)
+                                 : ((ctx->cfg.N + EXT_PARTICLES - 1) / EXT_PARTICLES) * ctx->cfg.P;
   md.ke_blocks = grid_for((long long)n, MD_THREADS);
   md.spring_blocks = ctx->w.NB;
   if (cudaMalloc(&md.F, sizeof(double) * n) != cudaSuccess ||

@@ -23,7 +23,7 @@
 namespace bpimd {
 namespace {
 
-constexpr int CL_THREADS = 128;  // force kernel: particles per block (as the all-pairs kernel)
+constexpr int CL_THREADS = 128;  // force kernel: bead slots per block
 constexpr int SCAN_THREADS = 1024;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(CL_THREADS) cl_force(long long nb, int P, Pair
 
 }  // namespace
 
+int cell_list_partials(int N, int P) { return ((N + CL_THREADS - 1) / CL_THREADS) * P; }
+
 size_t cell_list_bytes(int N, int P, int nc, bool mixed) {
   const size_t nb = (size_t)N * P, ncells = (size_t)P * nc * nc * nc;
   return a256(sizeof(int) * nb) + 2 * a256((mixed ? 16 : 32) * nb) + 3 * a256(sizeof(int) * ncells) +
@@ -254,8 +256,7 @@ cudaError_t cell_list_forces(const double *pos, double *F, int N, int P, const P
   cl_sort<<<(cl.ncells + 255) / 256, 256, 0, s>>>(cl.start, cl.count, cl.ncells, cl.list);
   if (mixed) cl_gather<true><<<g, 256, 0, s>>>(cl.list, nb, cl.crd, cl.sorted);
   else cl_gather<false><<<g, 256, 0, s>>>(cl.list, nb, cl.crd, cl.sorted);
-  // as many blocks as the all-pairs kernel, so that every U-bar partial is written
-  const int blocks = ((N + CL_THREADS - 1) / CL_THREADS) * P;
+  const int blocks = cell_list_partials(N, P);  // one U-bar partial per block
   if (mixed)
     cl_force<true><<<blocks, CL_THREADS, 0, s>>>(nb, P, pp, cl.nc, cl.cellof, cl.sorted, cl.start, cl.count, cl.list,
                                                  pos, F, ubar_part);

@@ -30,6 +30,8 @@ struct CellList {
 
 // Bytes of the cell-list buffers for N particles, P beads, nc cells per side.
 size_t cell_list_bytes(int N, int P, int nc, bool mixed);
+// Number of U-bar partial sums cell_list_forces writes.
+int cell_list_partials(int N, int P);
 // Lay the buffers out from base (cudaMalloc'd, 256-byte aligned).
 void cell_list_layout(CellList &cl, char *base, int N, int P, int nc, bool mixed);
 // Bin, sort and evaluate Lennard-Jones (+ trap) forces added to F; U-bar

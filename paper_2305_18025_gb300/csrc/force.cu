@@ -106,7 +106,10 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
   for (int s0 = half; s0 <= t; s0 += 16) {
     P_t v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (s0 + 2 * u <= t) ? __ldcg(part + ((base + s0 + 2 * u) * TILE + jj) * 4 + q) : (P_t)0;
+    for (int u = 0; u < 8; ++u) {  // index clamped into the tile: a valid address even if the load is speculated
+      const int k = min(s0 + 2 * u, t);
+      v[u] = (s0 + 2 * u <= t) ? __ldcg(part + ((base + k) * TILE + jj) * 4 + q) : (P_t)0;
+    }
     if (s0 == half && mine && p + 1 < w.N) M = direct_link_fast(w, p);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -159,8 +162,8 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
     P_t v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int t = t0 + 2 * u;
-      v[u] = (t < w.NT) ? __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q) : (P_t)0;
+      const int t = min(t0 + 2 * u, w.NT - 1);  // clamped into the tile: a valid address even if speculated
+      v[u] = (t0 + 2 * u < w.NT) ? __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q) : (P_t)0;
     }
     if (t0 == s + half && mine && p >= 1) M = direct_link_fast(w, p - 1);
 #pragma unroll
@@ -336,11 +339,13 @@ __global__ void __launch_bounds__(256, 4) prob_force_batched(const Workspace *__
   __shared__ P_t red[8][32][4];
   __shared__ double fin[32][9];
   __shared__ int last[2];
+  pdl_wait();  // launched as a programmatic dependent of the recursions: their epilogue must be complete
   for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
     const int2 e = tab[k];
     if (ws[e.x].pbc) prob_block<MIXED, true>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
     else prob_block<MIXED, false>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], red, fin, last);
   }
+  pdl_trigger();
 }
 
 // Expected exterior-spring energy over representative permutations, per block

@@ -166,7 +166,7 @@ class BatchedExchangeEnergy:
     Replica r has N[r] particles, P[r] beads, omega_P[r], beta[r] (shared mass
     and precision).  Positions and forces are packed: replica r is the
     [N_r][P_r][3] block at element offset ``offsets[r]`` of one flat float64
-    tensor (``pack``/``unpack`` convert from/to lists of tensors).  Four kernel
+    tensor (``pack``/``unpack`` convert from/to lists of tensors).  Three kernel
     launches per evaluation regardless of R.
     """
 

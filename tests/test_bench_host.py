@@ -1,8 +1,11 @@
-"""Host logic of bench.py (no GPU): the roofline object of the dominant stage
-and the rule that a DRAM-traffic figure is reported only while the sources of
-its kernel are unchanged since the ncu capture."""
+"""Host logic of bench.py (no GPU): the roofline object of the dominant stage,
+the rule that a DRAM-traffic figure is reported only while the sources of its
+kernel are unchanged since the ncu capture, and the reference arm (the CPU
+oracle timed on the same workload), which runs without a GPU."""
 import json
 import os
+import subprocess
+import sys
 import types
 
 import pytest
@@ -58,3 +61,29 @@ def test_traffic_figure_only_while_sources_match(tmp_path, monkeypatch):
     (tmp_path / rel).write_text("// a kernel, changed\n")
     assert bench.load_traffic("recursions") is None
     assert bench.load_traffic("no_such_stage") is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` prints exactly one JSON line with the keys
+    of the bench contract; under a launcher, ranks other than 0 print nothing
+    and exit 0."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+           "--steps", "3", "--warmup", "1", "--N", "64", "--P", "8"]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 1
+    assert d["config"]["N"] == 64 and d["config"]["P"] == 8
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root,
+                         env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
+    assert out.returncode == 0 and out.stdout.strip() == "", (out.stdout, out.stderr[-2000:])

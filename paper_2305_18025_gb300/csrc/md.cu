@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "context.cuh"
+#include "exp2_table.cuh"
 #include "pairs.cuh"
 
 namespace bpimd {
@@ -119,30 +120,6 @@ __global__ void __launch_bounds__(MD_THREADS) md_kick_kernel(double *__restrict_
   if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1ull;
 }
 
-// 2^y for y <= 0 in float64 by Tang's table-driven method (P. T. P. Tang,
-// ACM TOMS 15(2), 1989), for the float64 pair force: the float64 pipe is the
-// scarce one, and this takes 10 of its instructions.
-//   y = k/64 + r with k = round(64 y), |r| <= 1/128;
-//   2^y = 2^(k >> 6) * T[k & 63] * 2^r, T[j] = 2^(j/64) (a shared table, one
-//   CUDA exp2 per entry);
-//   2^r = 1 + sum_{i=1..5} (r ln 2)^i / i!, truncation below 3.6e-17 relative;
-//   the power 2^(k >> 6) is added to the exponent bits (an integer add).
-// y is first clamped to -1000, so that k fits the magic-constant rounding and
-// the result stays a normal number (2^-1000 underflows nothing the pair sums
-// can see).  Exact at y = 0 (k = 0, r = 0, T[0] = 1).
-__device__ __forceinline__ double exp2_table(double y, const double *T) {
-  constexpr double C1 = 0.6931471805599453, C2 = 0.24022650695910072, C3 = 0.05550410866482158,
-                   C4 = 0.009618129107628477, C5 = 0.0013333558146428443;  // (ln 2)^i / i!
-  constexpr double MAGIC = 6755399441055744.0;                            // 1.5 * 2^52
-  y = fmax(y, -1000.0);
-  const double t = fma(y, 64.0, MAGIC);  // round(64 y) in the low word of t
-  const int k = __double2loint(t);
-  const double r = fma(t - MAGIC, -0.015625, y);
-  const double p = fma(r, fma(r, fma(r, fma(r, fma(r, C5, C4), C3), C2), C1), 1.0);
-  const double v = T[k & 63] * p;
-  return __longlong_as_double(__double_as_longlong(v) + ((long long)(k >> 6) << 52));
-}
-
 // Deterministic block sum (fixed shuffle tree, then warps in order); thread 0 gets it.
 __device__ __forceinline__ double block_sum(double v, double *red) {
 #pragma unroll
@@ -184,7 +161,7 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
   const R px = (R)rx, py = (R)ry, pz = (R)rz;
   const R a = (R)(-0.5 * pp.inv_s2);
   const double a2 = -0.5 * pp.inv_s2 * 1.4426950408889634;  // float64: the exponent in base 2 (times log2 e)
-  if (!MIXED && threadIdx.x < 64) T2[threadIdx.x] = exp2((double)threadIdx.x * 0.015625);
+  if (!MIXED) exp2_table_init(T2);
   const R L = (R)pp.L, invL = (R)pp.invL;
   const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
   auto img = [&](R d) -> R {

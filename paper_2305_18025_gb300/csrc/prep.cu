@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
+#include "exp2_table.cuh"
 
 namespace bpimd {
 namespace {
@@ -228,7 +229,7 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
 // double) and sets the exponent.
 template <bool MIXED, bool PBC>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, const EndTiles &E, int i, int j,
-                                              int &e) {
+                                              int &e, const double *T64) {
   if (MIXED) {
     float fx, fy, fz;
     if (PBC) {  // minimum image from the fixed-point copies
@@ -257,9 +258,12 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
     const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
     const double n = floor(x);
-    const xd g = xnorm(exp2(x - n), (int)n);
-    e = g.e;
-    return g.m;
+    // 2^(x-n), x-n in [0, 1), by the table method: T[k & 63] 2^r in
+    // [0.99, 1.99], its power 2^(k >> 6) and 2^n folded into the exponent
+    int k;
+    const long long b = __double_as_longlong(exp2_table_part(x - n, T64, k));
+    e = (int)n + (k >> 6) + (int)((b >> 52) & 0x7ff) - 1023;
+    return __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
   }
 }
 
@@ -273,7 +277,7 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
 template <bool MIXED, bool PBC>
 __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__restrict__ pos, int blk,
                                            typename std::conditional<MIXED, float, double>::type *Tm, int *Te,
-                                           EndTiles &E) {
+                                           EndTiles &E, const double *T64) {
   using M_t = typename std::conditional<MIXED, float, double>::type;
   const double cx = -w.beta * w.half_k * LOG2E;
   const int N = w.N;
@@ -288,7 +292,7 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__r
       const int a = s * TILE + i;
       if (b < N && a <= b) {
         int e;
-        const M_t m = (M_t)pair_factor<MIXED, PBC>(w, cx, E, i, lane, e);
+        const M_t m = (M_t)pair_factor<MIXED, PBC>(w, cx, E, i, lane, e, T64);
         const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
         gm[idx] = m;
         w.ge[idx] = e;
@@ -323,13 +327,15 @@ __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
+  __shared__ double T64[64];  // float64 pair factors: 2^(j/64)
+  if (!MIXED) exp2_table_init(T64);  // published by the first barrier of gmat_block
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
     bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
   } else {
     for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) {
-      if (w.pbc) gmat_block<MIXED, true>(w, pos, blk, Tm, Te, E);
-      else gmat_block<MIXED, false>(w, pos, blk, Tm, Te, E);
+      if (w.pbc) gmat_block<MIXED, true>(w, pos, blk, Tm, Te, E, T64);
+      else gmat_block<MIXED, false>(w, pos, blk, Tm, Te, E, T64);
     }
   }
   pdl_trigger();
@@ -348,6 +354,8 @@ __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict_
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
+  __shared__ double T64[64];  // float64 pair factors: 2^(j/64)
+  if (!MIXED) exp2_table_init(T64);  // published by the first barrier of gmat_block
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
     const int2 e = bead_tab[blockIdx.x];
@@ -355,8 +363,8 @@ __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict_
   } else {
     for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
       const int2 e = blk_tab[k];
-      if (ws[e.x].pbc) gmat_block<MIXED, true>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
-      else gmat_block<MIXED, false>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E);
+      if (ws[e.x].pbc) gmat_block<MIXED, true>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T64);
+      else gmat_block<MIXED, false>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T64);
     }
   }
   pdl_trigger();

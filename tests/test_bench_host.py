@@ -1,6 +1,7 @@
 """Host logic of bench.py (no GPU): the roofline object of the dominant stage,
 the rule that a DRAM-traffic figure is reported only while the sources of its
-kernel are unchanged since the ncu capture, and the reference arm (the CPU
+kernel are unchanged since the ncu capture, the clock summary taken from
+nvidia-smi samples during the timed region, and the reference arm (the CPU
 oracle timed on the same workload), which runs without a GPU."""
 import json
 import os
@@ -87,3 +88,43 @@ def test_reference_arm_prints_one_contract_line():
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root,
                          env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
     assert out.returncode == 0 and out.stdout.strip() == "", (out.stdout, out.stderr[-2000:])
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.proc, s.lines = _DoneProc(), list(lines)
+    return s
+
+
+def test_clock_summary_median_under_load_and_active_reasons():
+    """nvidia-smi samples: the median SM clock over loaded samples (idle ones,
+    below half the highest, are left out), the maximum clock, and every
+    throttle reason seen active in any sample; malformed lines are skipped."""
+    lines = [
+        "345, 2070, 120.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2040, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    c = _sampler(lines).stop()
+    assert c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0
+    assert c["samples"] == 4
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = _sampler(["1500, 2070, 1000, 0x48, Not Active, Active, Active, Not Active"]).stop()
+    assert hot["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples_or_nvidia_smi():
+    assert _sampler([]).stop()["reasons"] == ["no samples"]
+    none = bench.ClockSampler(0)
+    assert none.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}

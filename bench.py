@@ -10,7 +10,10 @@ and backward recursions with the prefix sums and V_B, probabilities with all
 exterior-bead forces.  The line also carries MD steps/s (`md`) of the same
 system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays),
 the throughput of a 256-replica batch of uneven N, P, beta (`batched`), and
-MD steps/s of bulk liquid helium in a periodic box (`helium`).
+MD steps/s of bulk liquid helium in a periodic box (`helium`).  `cpu_baseline`
+is the CPU oracle on the headline workload; `cpu_context` times it on the other
+workloads (small trapped systems, helium, the replica batch on all host cores)
+and sets the paper's original O(P N^3) method against Algorithm 1.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -329,6 +332,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
+        line["cpu_context"] = cpu_context(args)
     return line
 
 
@@ -485,6 +489,105 @@ def cpu_baseline(args, pos_np, wP, seconds=None, max_evals=None):
     return {"value": n / el, "unit": "evals/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} full evaluations of the same workload in {el:.1f} s "
                       f"(C oracle, float64, single thread; host has {os.cpu_count()} cores)"}
+
+
+def _timed_evals(fn, seconds, min_evals=1):
+    """Call fn until `seconds` have passed (at least min_evals calls); evals/s and count."""
+    n, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        n += 1
+        el = time.perf_counter() - t0
+        if n >= min_evals and el >= seconds:
+            return n / el, n, el
+
+
+def _oracle_replicas(chunk):
+    """Worker of the replica-batch baseline: the oracle on each (N, P, beta,
+    seed) of its share, positions regenerated from the seed."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2305_18025_gb300 import inputs
+    for N, P, beta, seed in chunk:
+        oracle.fast_pimdb(inputs.trapped_positions(N, P, seed), 1.0, inputs.omega_P(P, beta), beta)
+    return len(chunk)
+
+
+def cpu_context(args, seconds=1.5, alg2_sizes=(64, 128, 256)):
+    """The float64 oracle on the host cores for the other workloads of the
+    measurement plan, each a bounded sample; context for the GPU figures, not a
+    target.  Single thread: trapped N=16, P=8, beta=2 and N=64, P=32, beta=1;
+    liquid helium N=4000, P=64 in its periodic box.  All host cores: the
+    256-replica batch, one spawned process per core, replicas dealt round robin.
+    The paper's original O(P N^3) method (Algorithm 2) against Algorithm 1 at
+    N = 64, 128, 256, P = 32, one evaluation each, for the shape of the speedup.
+    A failing item reports its error instead of a figure."""
+    import multiprocessing
+    import numpy as np
+    import oracle
+    from paper_2305_18025_gb300 import inputs
+    out = {"kind": "oracle", "note": "float64 C oracle on this host's cores; bounded samples"}
+
+    def guard(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:  # a baseline never fails the bench line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    def single(N, P, beta):
+        pos, wP = inputs.trapped_positions(N, P, SEED_DEF), inputs.omega_P(P, beta)
+        v, n, el = _timed_evals(lambda: oracle.fast_pimdb(pos, 1.0, wP, beta), seconds)
+        return {"value": v, "unit": "evals/s", "cores": 1, "sample": f"{n} evaluations in {el:.2f} s"}
+
+    guard("trapped_N16_P8_beta2", lambda: single(16, 8, 2.0))
+    guard("trapped_N64_P32_beta1", lambda: single(64, 32, 1.0))
+
+    def helium():
+        he_N = 4 * args.he_cells ** 3
+        L = (he_N / HE["rho"]) ** (1.0 / 3.0)
+        beta = 1.0 / HE["T"]
+        wP = np.sqrt(args.he_P) / (beta * HE["hbar"])
+        x = inputs.fcc_positions(args.he_cells, args.he_P, L, 3)
+        v, n, el = _timed_evals(lambda: oracle.float64.fast_pimdb(x, HE["m"], wP, beta, box=L), seconds)
+        return {"value": v, "unit": "evals/s", "cores": 1,
+                "sample": f"N={he_N} P={args.he_P} in a periodic box of {L:.2f} A: {n} evaluations in {el:.2f} s"}
+
+    guard("helium_exchange", helium)
+
+    def replicas():
+        reps = inputs.batched_replicas(args.batch_replicas, seed=11)
+        items = [(r.N, r.P, r.beta, 11 * 100003 + i) for i, r in enumerate(reps)]
+        try:
+            cores = len(os.sched_getaffinity(0))  # the CPUs this process may run on
+        except AttributeError:
+            cores = os.cpu_count() or 1
+        cores = max(1, min(cores, 32))
+        chunks = [items[c::cores] for c in range(cores)]
+
+        def batch():  # bounded: a stuck worker becomes an error entry, not a hung bench
+            return pool.map_async(_oracle_replicas, chunks).get(timeout=120)
+
+        with multiprocessing.get_context("spawn").Pool(cores) as pool:
+            batch()  # start-up and library load, untimed
+            v, n, el = _timed_evals(batch, seconds)
+        return {"value": v, "unit": "batch evals/s", "replica_evals_per_s": v * len(items), "cores": cores,
+                "sample": f"{n} batches of {len(items)} replicas in {el:.2f} s, {cores} spawned processes"}
+
+    guard("batched_256_replicas", replicas)
+
+    def algorithm2():
+        rows = {}
+        for N in alg2_sizes:
+            pos, wP = inputs.trapped_positions(N, 32, SEED_DEF), inputs.omega_P(32, 1.0)
+            t0 = time.perf_counter()
+            oracle.original_pimdb(pos, 1.0, wP, 1.0)
+            t2 = time.perf_counter() - t0
+            v1, _, _ = _timed_evals(lambda: oracle.fast_pimdb(pos, 1.0, wP, 1.0), 0.2)
+            rows[f"N{N}_P32"] = {"algorithm2_ms": 1e3 * t2, "algorithm1_ms": 1e3 / v1, "ratio": t2 * v1}
+        return rows
+
+    guard("algorithm2_vs_algorithm1", algorithm2)
+    return out
 
 
 # ------------------------------------------------------ reference arm

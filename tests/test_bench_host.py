@@ -128,3 +128,20 @@ def test_clock_summary_without_samples_or_nvidia_smi():
     assert _sampler([]).stop()["reasons"] == ["no samples"]
     none = bench.ClockSampler(0)
     assert none.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+
+def test_cpu_context_reports_every_workload():
+    """The CPU-oracle context of the bench line: single-thread samples of the
+    small trapped and helium workloads, the replica batch over spawned
+    processes on all host cores, and Algorithm 2 against Algorithm 1 (small
+    sizes here to keep the test short)."""
+    args = types.SimpleNamespace(he_cells=2, he_P=8, batch_replicas=6)
+    c = bench.cpu_context(args, seconds=0.05, alg2_sizes=(16, 32))
+    for key in ("trapped_N16_P8_beta2", "trapped_N64_P32_beta1", "helium_exchange", "batched_256_replicas"):
+        assert "error" not in c[key], c[key]
+        assert c[key]["value"] > 0 and c[key]["cores"] >= 1
+    assert c["batched_256_replicas"]["replica_evals_per_s"] == pytest.approx(6 * c["batched_256_replicas"]["value"])
+    rows = c["algorithm2_vs_algorithm1"]
+    assert set(rows) == {"N16_P32", "N32_P32"}
+    assert all(r["algorithm2_ms"] > 0 and r["algorithm1_ms"] > 0 for r in rows.values())
+    json.dumps(c)

@@ -19,7 +19,8 @@
 // u <= v -- the closing-spring factor of the cycle energy E^{[u,v]} (Eq.
 // e-recurrence-step, last term) -- stored once per evaluation as an extended
 // number 2^x = mantissa(2^frac(x)) * 2^floor(x), x = -beta (1/2)k |d|^2 log2(e).
-// FP64: float64 difference, square and exp2.  MIXED: difference of the
+// FP64: float64 difference and square; 2^frac(x) by the table method of
+// exp2_table.cuh (10 float64 instructions).  MIXED: difference of the
 // float32 high/low parts (or fixed-point copies) of the positions, float32
 // square, hardware ex2.approx.  The potentials V^{[1,v]}, V^{[u,N]} for
 // diagnostics are computed on demand by diag_potentials_kernel.

@@ -4,6 +4,7 @@ configurations on the host before touching CUDA."""
 import ctypes
 import os
 import re
+import shutil
 import subprocess
 
 import pytest
@@ -117,3 +118,24 @@ def test_batch_calls_reject_null_context(lib):
     assert lib.bpimd_exchange_energy_forces_batched(None, None, None, None) == bpimd.BPIMD_ERR_ARG
     assert lib.bpimd_batch_info(None, None, None, None) == bpimd.BPIMD_ERR_ARG
     assert lib.bpimd_batch_set_tuning(None, 8, 8) == bpimd.BPIMD_ERR_ARG
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of bpimd_config has the size and field offsets that a C
+    compiler gives the struct declared in include/bpimd.h."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = [f[0] for f in bpimd.bpimd_config._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include "bpimd.h"\nint main(void) {\n'
+        '  printf("size %zu\\n", sizeof(bpimd_config));\n'
+        + "".join(f'  printf("{n} %zu\\n", offsetof(bpimd_config, {n}));\n' for n in names)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), "-o", str(exe), str(prog)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(bpimd.bpimd_config)
+    for n in names:
+        assert int(got[n]) == getattr(bpimd.bpimd_config, n).offset, n

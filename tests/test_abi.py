@@ -139,3 +139,23 @@ def test_config_struct_layout_matches_the_header(tmp_path):
     assert int(got["size"]) == ctypes.sizeof(bpimd.bpimd_config)
     for n in names:
         assert int(got[n]) == getattr(bpimd.bpimd_config, n).offset, n
+
+
+def test_binding_argument_kinds_match_the_header_prototypes():
+    """Every prototype in include/bpimd.h and the binding's ctypes argtypes for
+    it agree in the number of parameters and, position by position, pointer
+    against integer."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "bpimd.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = re.findall(r"(?:^|\n)\s*(?:int|const char \*)\s*(bpimd_\w+)\s*\(([^)]*)\)\s*;", text)
+    assert {name for name, _ in protos} == set(bpimd.EXPORTED)
+    lib = bpimd.load()
+    for name, params in protos:
+        params = " ".join(params.split())
+        plist = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        want = ["ptr" if "*" in p else "int" for p in plist]
+        argtypes = getattr(lib, name).argtypes or []
+        got = ["int" if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64) else "ptr"
+               for t in argtypes]
+        assert got == want, (name, plist, argtypes)

@@ -59,7 +59,8 @@ def test_config_struct_matches_header_layout():
 
 @pytest.mark.parametrize("field,value", [
     ("N", 0), ("P", 1), ("m", 0.0), ("omega_P", -1.0), ("beta", float("nan")),
-    ("beta", float("inf")), ("precision", 7), ("flags", 1),
+    ("beta", float("inf")), ("precision", 7), ("flags", 1), ("N", 6913),
+    ("box_L", -1.0), ("box_L", float("nan")), ("box_L", float("inf")),
 ])
 def test_create_rejects_invalid_config_without_gpu(lib, field, value):
     cfg = bpimd.make_config(8, 4, 1.0, 2.0, 1.0)
@@ -67,6 +68,14 @@ def test_create_rejects_invalid_config_without_gpu(lib, field, value):
     h = ctypes.c_void_p(123)
     rc = lib.bpimd_create(ctypes.byref(h), ctypes.byref(cfg), None)
     assert rc == bpimd.BPIMD_ERR_ARG
+    assert h.value is None
+
+
+def test_create_rejects_a_bead_count_past_the_index_range_without_gpu(lib):
+    """N P beads of 3 coordinates must index within a 32-bit signed range."""
+    cfg = bpimd.make_config(6912, 110_000, 1.0, 2.0, 1.0)
+    h = ctypes.c_void_p(123)
+    assert lib.bpimd_create(ctypes.byref(h), ctypes.byref(cfg), None) == bpimd.BPIMD_ERR_ARG
     assert h.value is None
 
 

@@ -38,10 +38,12 @@
  *
  * Errors
  *   Argument errors are detected on the host before anything is enqueued
- *   (BPIMD_ERR_ARG).  Device-side conditions (non-finite positions or results,
- *   an expired bounded wait inside a kernel) are recorded in a device status
- *   word; they surface as BPIMD_ERR_NONFINITE / BPIMD_ERR_TIMEOUT from the
- *   next call that synchronises (the _host calls, bpimd_sync, bpimd_step).
+ *   (BPIMD_ERR_ARG).  Device-side conditions (non-finite positions or results)
+ *   are recorded in a device status word; they surface as BPIMD_ERR_NONFINITE
+ *   from the next call that synchronises (the _host calls, bpimd_sync,
+ *   bpimd_step).  No kernel of this version spins on a flag or barrier that
+ *   another block sets (the recursions meet at hardware cluster barriers), so
+ *   BPIMD_ERR_TIMEOUT is reserved: no current call returns it.
  */
 #ifndef BPIMD_H
 #define BPIMD_H
@@ -58,7 +60,7 @@ extern "C" {
 #define BPIMD_ERR_ARG (-1)       /* invalid size, parameter or null pointer      */
 #define BPIMD_ERR_NONFINITE (-2) /* NaN/Inf in positions or in a result          */
 #define BPIMD_ERR_CUDA (-3)      /* a CUDA runtime call failed                  */
-#define BPIMD_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired          */
+#define BPIMD_ERR_TIMEOUT (-4)   /* reserved: a bounded device-side wait expired */
 #define BPIMD_ERR_NOMEM (-5)     /* device or host allocation failed            */
 #define BPIMD_ERR_STATE (-6)     /* call not valid for this context's state     */
 #define BPIMD_ERR_SIZE (-7)      /* problem larger than a fixed-size buffer      */
@@ -143,7 +145,7 @@ int bpimd_exchange_energy_forces_host(bpimd_ctx *ctx, const double *positions,
                                       double *V_B, double *forces);
 
 /* Wait for the context stream and report any device-side status recorded by
- * earlier calls (BPIMD_ERR_NONFINITE / BPIMD_ERR_TIMEOUT), clearing it. */
+ * earlier calls (BPIMD_ERR_NONFINITE), clearing it. */
 int bpimd_sync(bpimd_ctx *ctx);
 
 /* Intermediate results of the last bpimd_exchange_energy_forces* call, copied
@@ -190,7 +192,7 @@ int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
 
 /* --------------------------------------------------------- replica batches */
 /* Many independent systems ("replicas") of uneven size and temperature
- * evaluated together: the same Algorithm 1 per replica, four kernel launches
+ * evaluated together: the same Algorithm 1 per replica, three kernel launches
  * per batch whatever the number of replicas.  The paper has no batched form;
  * it serves workloads such as parallel tempering or many small trapped
  * systems that are too small to fill a GPU one at a time.
@@ -255,7 +257,9 @@ int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
  * Same computation and arguments as bpimd_exchange_energy_forces, without a
  * context: cfg describes the system (N, P, m, omega_P, beta, precision; the MD
  * fields are ignored), positions/V_B/forces are device pointers owned by the
- * caller, cuda_stream is a cudaStream_t (NULL = default stream).  It allocates
+ * caller, cuda_stream is a cudaStream_t (NULL = default stream) that must
+ * belong to the current device (a stream of another device returns
+ * BPIMD_ERR_ARG: the scratch array used is the current device's).  It allocates
  * nothing: its scratch memory is one file-scope __device__ array of 1 MiB per
  * device, which bounds the size to N <= BPIMD_NOALLOC_MAX_N (larger N returns
  * BPIMD_ERR_SIZE before any work is enqueued).

@@ -83,6 +83,8 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.link = (double *)take(sizeof(double) * N);
   w.ccm = (double *)take(sizeof(double) * N);
   w.cce = (int *)take(sizeof(int) * N);
+  w.nexp = (int *)take(sizeof(int) * N);
+  w.Ap = (double *)take(sizeof(double) * N);
   w.C = (double *)take(sizeof(double) * (N + 1));
   w.gm = (void *)take(gm_bytes);
   w.ge = (int *)take(sizeof(int) * gelems);

@@ -43,7 +43,9 @@ constexpr int CHAIN_MAX_N = 6912;     // largest N the library accepts
 constexpr int BATCH_MAX_N = 4096;     // largest replica of a batch (one CTA per recursion)
 constexpr int BEAD_BLOCK_PARTICLES = 8;  // particles per block of the bead pass
 constexpr double LOG2E = 1.4426950408889634074;
+constexpr double LOG2E_LO = 2.0355273740931033e-17;  // log2(e) - LOG2E (double-double tail)
 constexpr double LN2 = 0.6931471805599453094;
+constexpr double LN2_LO = 2.3190468138462996e-17;    // ln(2) - LN2
 
 // status bits recorded on the device
 constexpr int ST_NONFINITE = 1;
@@ -141,7 +143,9 @@ struct Workspace {
                         // a bead difference is formed in float32 to float32 accuracy
   double *Eint, *link;  // [N]
   double *ccm; int *cce;          // c_{i+1} = exp(beta link_i)/(i+1), extended
-  double *C;            // [N+1] prefix sums of E_int + link
+  int *nexp;            // [N] n_i = integer part of beta link_i log2(e) (in c_{i+1}'s exponent)
+  double *Ap;           // [N] E_int_i + (beta link_i log2(e) - n_i) ln2 / beta
+  double *C;            // [N+1] reduced prefix sums C'[v] = sum_{i<v} Ap[i] (0-based i)
   // g matrix, tile-packed triangle: block (t, s), s <= t, at (t(t+1)/2 + s) * TILE2,
   // entry [i][j] = g for a = s*TILE + i (bead 1 particle), b = t*TILE + j (bead P particle)
   void *gm;             // double (FP64) or float (MIXED) mantissas

@@ -52,6 +52,7 @@
 // float32 per 32-source tile and added to the float64 row accumulator; the
 // tile hand-offs stay float64 and the dependent steps use the integer format.
 #include <cooperative_groups.h>
+#include <mutex>
 #include <type_traits>
 
 #include "chain_common.cuh"
@@ -74,7 +75,8 @@ struct LeadSmem {
   double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
   double Ym[YRING];     // Y_v at v mod YRING
   double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
-  double misc[4];       // end of the forward recursion: C[N], 1/(N y_N) mantissa
+  double misc[4];       // end of the forward recursion: C'[N], 1/(N y_N) mantissa
+  long long nsum;       // sum of the exponent parts n carried by y_N
   int Kde[2 * BLK];
   int Hoe[2 * BLK];
   int Ye[YRING];
@@ -135,7 +137,8 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
     xd cnext{1.0, 0};      // warp 0: coefficient of its row in the coming tile
     if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
-    double carry = 0.0;    // prefix-sum warp (forward): running prefix sum
+    double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
+    long long ncarry = 0;  // and the running sum of the exponent parts n
     for (int t = 0; t < NT; ++t) {
       const int buf = t & 1;
       if (wid == 0) {
@@ -159,7 +162,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
           if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
         }
       } else if (!BWD && q == 12) {
-        prefix_tile(w, t, carry);
+        prefix_tile(w, t, carry, ncarry);
       }
       cluster.sync();
     }
@@ -169,8 +172,8 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
     }
     if (!BWD) {
-      // V^{[1,N]} = C[N] - ln(y_N)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
-      if (q == 12 && lane == 0) sm.misc[0] = carry;
+      // V^{[1,N]} = C'[N] - (ln(y_N) - n ln 2)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
+      if (q == 12 && lane == 0) { sm.misc[0] = carry; sm.nsum = ncarry; }
       __syncthreads();
       const xd yN{sm.Ym[N & (YRING - 1)], sm.Ye[N & (YRING - 1)]};
       if (tid == 0) {  // the normaliser first: the alpha values wait for it
@@ -183,7 +186,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       __syncthreads();
       if (wid == 0) {  // V_B (a float64 log) on warp 0, alongside the alpha values
         if (lane == 0) {
-          const double VB = sm.misc[0] - xlog(yN) / w.beta;
+          const double VB = reduced_potential(sm.misc[0], yN, sm.nsum, w.beta);
           w.scal[0] = VB;
           if (V_B) *V_B = VB;
           if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);
@@ -341,6 +344,9 @@ static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREA
 // recursion kernels to the maximum, allow the 16-CTA clusters, and check that
 // two of them can be resident (else the 8-CTA form is used for every N).
 namespace {
+// per device: set up once under g_chain_mutex (two host threads making their
+// first calls on one device must not both write these)
+std::mutex g_chain_mutex;
 bool g_chain_ready[64] = {false};
 bool g_large_cluster[64] = {false};
 
@@ -378,6 +384,7 @@ cudaError_t prepare_chains() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_chain_mutex);
   if (g_chain_ready[dev]) return cudaSuccess;
   e = prepare_chain_kernel<true, CHAIN_CLUSTER>();
   if (e == cudaSuccess) e = prepare_chain_kernel<false, CHAIN_CLUSTER>();
@@ -396,7 +403,12 @@ cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   int dev = 0;
   cudaGetDevice(&dev);
-  const bool large = g_large_cluster[dev] && w.NT >= LARGE_CLUSTER_MIN_NT;
+  bool large_ok;
+  {
+    std::lock_guard<std::mutex> lock(g_chain_mutex);
+    large_ok = g_large_cluster[dev];
+  }
+  const bool large = large_ok && w.NT >= LARGE_CLUSTER_MIN_NT;
   if (large)
     return w.mixed ? launch_chain_cluster<true, CHAIN_CLUSTER_LARGE>(w, V_B, s)
                    : launch_chain_cluster<false, CHAIN_CLUSTER_LARGE>(w, V_B, s);

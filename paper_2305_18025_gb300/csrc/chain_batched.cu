@@ -32,6 +32,7 @@ struct SingleSmem {
   unsigned long long Kdm[2 * BLK];
   double Hom[2 * BLK];  // MIXED: floats
   double misc[2];
+  long long nsum;  // sum of the exponent parts n carried by y_N
   int Kde[2 * BLK];
   int Hoe[2 * BLK];
   int misci[2];
@@ -73,6 +74,7 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
   xd cnext{1.0, 0};
   if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
   double carry = 0.0;
+  long long ncarry = 0;
   for (int t = 0; t < NT; ++t) {
     const int buf = t & 1;
     if (wid == 0) {
@@ -88,7 +90,7 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
       if (t + 1 < NT)
         stage_offdiag<MIXED, BWD, 16>(w, t + 1, 16 * (q - 4), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
     } else if (q == 6) {
-      if (!BWD) prefix_tile(w, t, carry);
+      if (!BWD) prefix_tile(w, t, carry, ncarry);
     } else if (bulk >= 0 && t >= 1) {
       // source tile t-1 -> row tiles t+1.., one warp per row tile
       const int srcbase = (t - 1) * TILE;
@@ -148,8 +150,8 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
   }
   pdl_trigger();  // the probability pass may launch during the epilogue
   if (!BWD) {
-    // V^{[1,N]} = C[N] - ln(y_N)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
-    if (q == 6 && lane == 0) sm.misc[0] = carry;
+    // V^{[1,N]} = C'[N] - (ln(y_N) - n ln 2)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
+    if (q == 6 && lane == 0) { sm.misc[0] = carry; sm.nsum = ncarry; }
     __syncthreads();
     const xd yN{Ym[N], Ye[N]};
     if (tid == 0) {  // the normaliser first: the alpha values wait for it
@@ -162,7 +164,7 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
     __syncthreads();
     if (wid == 0) {  // V_B (a float64 log) on warp 0, alongside the alpha values
       if (lane == 0) {
-        const double VB = sm.misc[0] - xlog(yN) / w.beta;
+        const double VB = reduced_potential(sm.misc[0], yN, sm.nsum, w.beta);
         w.scal[0] = VB;
         if (V_B) *V_B = VB;
         if (!isfinite(VB)) atomicOr(w.status, ST_NONFINITE);

@@ -395,11 +395,14 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
   nxt = xnorm_int(nxt);
 }
 
-// Prefix sums C[i+1] = sum_{q<=i} (E_int_q + link_q) of tile t, one warp.
-__device__ __forceinline__ void prefix_tile(const Workspace &w, int t, double &carry) {
+// Reduced prefix sums C'[i+1] = sum_{q<=i} Ap[q] of tile t (one warp), and the
+// running total of the integer exponent parts n_q that the recursion carries
+// in its exponents (ncarry, exact in 64 bits).
+__device__ __forceinline__ void prefix_tile(const Workspace &w, int t, double &carry, long long &ncarry) {
   const int lane = threadIdx.x & 31;
   const int i = t * TILE + lane;
-  double v = (i < w.N) ? (__ldg(w.Eint + i) + __ldg(w.link + i)) : 0.0;
+  double v = (i < w.N) ? __ldg(w.Ap + i) : 0.0;
+  int n = (i < w.N) ? __ldg(w.nexp + i) : 0;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double u = __shfl_up_sync(0xffffffffu, v, o);
@@ -407,6 +410,18 @@ __device__ __forceinline__ void prefix_tile(const Workspace &w, int t, double &c
   }
   if (i < w.N) w.C[i + 1] = carry + v;
   carry += __shfl_sync(0xffffffffu, v, 31);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  ncarry += n;
+}
+
+// V = C' - (ln y - n ln 2)/beta for an extended y = m 2^e whose exponent
+// carries n from the coefficients c: (e - n) ln 2 is formed with ln 2 to 106
+// bits, so the result is accurate to a few float64 roundings of V's own size.
+__device__ __forceinline__ double reduced_potential(double Cp, xd y, long long n, double beta) {
+  const double k = (double)((long long)y.e - n);
+  const double t = fma(k, LN2, fma(k, LN2_LO, log(y.m)));
+  return Cp - t / beta;
 }
 
 }  // namespace chain_detail

@@ -84,12 +84,22 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   set_box(w, cfg->box_L);
   if (layout_workspace(w, nullptr) > NOALLOC_SCRATCH_BYTES) return BPIMD_ERR_SIZE;
 
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the scratch array used is the current device's: a stream of another
+  // device would run these kernels against the wrong device's array
+  if (s != nullptr) {
+    int cur = -1, sdev = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return BPIMD_ERR_CUDA;
+    }
+    if (sdev != cur) return BPIMD_ERR_ARG;
+  }
   void *base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc != BPIMD_OK) return rc;
   layout_workspace(w, (char *)base);
 
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   if (cudaMemsetAsync(w.status, 0, sizeof(int), s) != cudaSuccess) return BPIMD_ERR_CUDA;
   // the tile counters of the probability pass start at zero (a previous call
   // with another N leaves its counters at zero, but at other offsets)

@@ -159,13 +159,35 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
         sp[0] = make_float4(hP[0], hP[1], hP[2], 0.0f);
         sp[1] = make_float4(lP[0], lP[1], lP[2], 0.0f);
       }
-      // c_{l+1} = exp(beta link_l) / (l+1) = 2^(x - n) 2^n / (l+1),
-      // x = beta link_l log2(e) >= 0, clamped to 2^28 so that exponent sums stay in int32
-      const double x = fmin(w.beta * lk * LOG2E, 268435456.0);
-      const double n = floor(x);
-      const xd c = xnorm(exp2(x - n) / (double)(l + 1), (int)n);
+      // c_{l+1} = exp(beta link_l) / (l+1) = 2^f 2^n / (l+1) with
+      // x = beta link_l log2(e) = n + f, n integer, f in [0, 1).  x is formed
+      // as an unevaluated double-double sum (exact products by FMA, log2(e) to
+      // 106 bits), so f is accurate to a float64 rounding however large x is.
+      // The integer part n goes into c's exponent and nowhere else: the
+      // recursions' exponents carry sum n, and the reduced prefix sums
+      //   C'[v] = sum_{i<=v} (E_int^(i) + link_i - n_i ln2/beta)
+      //         = sum_{i<=v} (E_int^(i) + f_i ln2/beta)
+      // exclude it, so V = C' - (ln y - (sum n) ln 2)/beta is formed from
+      // numbers of the size of V itself (no cancellation against the open
+      // chain's link energies).  x is clamped to 2^28 so that exponent sums
+      // stay in int32.
+      int n = 0;
+      double f = 0.0;
+      {
+        const double p = w.beta * lk, pe = fma(w.beta, lk, -p);
+        double xh = p * LOG2E;
+        double xl = fma(p, LOG2E, -xh) + fma(pe, LOG2E, p * LOG2E_LO);
+        if (xh >= 268435456.0) { xh = 268435456.0; xl = 0.0; }
+        double nf = floor(xh);
+        if (nf == xh && xl < 0.0) nf -= 1.0;
+        n = (int)nf;
+        f = (xh - nf) + xl;
+      }
+      const xd c = xnorm(exp2(f) / (double)(l + 1), n);
       w.ccm[l] = c.m;
       w.cce[l] = c.e;
+      w.nexp[l] = n;
+      w.Ap[l] = eint_s[lane] + f * (LN2 / w.beta);
     }
   }
 }
@@ -406,25 +428,84 @@ __global__ void __launch_bounds__(256) gmat_padding_batched(const Workspace *__r
   }
 }
 
-// Diagnostic potentials of the last evaluation (on demand):
-//   V^{[1,v]} = C[v] - ln(y_v)/beta,  V^{[u,N]} = C[N] - C[u-1] - ln(B_u / N)/beta.
-__global__ void diag_potentials_kernel(Workspace w, double *Vf, double *Vb) {
-  const int N = w.N;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= N; v += gridDim.x * blockDim.x) {
-    Vf[v] = (v == 0) ? 0.0 : w.C[v] - xlog(xd{w.yfm[v], w.yfe[v]}) / w.beta;
-    if (v < N) {  // u = v+1, particle a = v
-      const xd B = backward_row_sum(w, v);
-      Vb[v] = w.C[N] - w.C[v] - (xlog(B) - log((double)N)) / w.beta;
-    } else {
-      Vb[N] = 0.0;
+// Diagnostic potentials of the last evaluation (on demand), from the reduced
+// prefix sums of Ap and the exponent parts n (see the bead pass):
+//   V^{[1,v]} = C'[v] - (ln y_v - N_v ln 2)/beta,                 N_v = sum_{q<v} n_q
+//   V^{[u,N]} = (C'[N] - C'[u-1]) - (ln(B_u/N) - (N_N - N_{u-1}) ln 2)/beta
+// (0-based particle a = u-1).  One block: every thread sums a chunk of Ap in
+// double-double, thread 0 scans the chunk sums, and each thread walks its
+// chunk again, so that suffix sums C'[N] - C'[a] are as accurate as prefix sums.
+__device__ __forceinline__ void dd_add(double &ah, double &al, double bh, double bl) {
+  const double s = ah + bh, bb = s - ah;
+  const double e = ((ah - (s - bb)) + (bh - bb)) + (al + bl);
+  ah = s + e;
+  al = e - (ah - s);
+}
+
+__device__ __forceinline__ double reduced_pot(double ch, double cl, xd y, long long n, double beta, double lnN) {
+  const double k = (double)((long long)y.e - n);
+  const double t = fma(k, LN2, fma(k, LN2_LO, log(y.m) - lnN));
+  return (ch - t / beta) + cl;
+}
+
+constexpr int DIAG_THREADS = 1024;
+
+__global__ void __launch_bounds__(DIAG_THREADS) diag_potentials_kernel(Workspace w, double *Vf, double *Vb) {
+  __shared__ double sh[DIAG_THREADS], sl[DIAG_THREADS];
+  __shared__ long long sn[DIAG_THREADS];
+  __shared__ double tot[2];
+  __shared__ long long ntot;
+  const int N = w.N, tid = threadIdx.x;
+  const int ch = (N + DIAG_THREADS - 1) / DIAG_THREADS;
+  const int lo = min(N, tid * ch), hi = min(N, lo + ch);
+  double a = 0.0, b = 0.0;
+  long long n = 0;
+  for (int i = lo; i < hi; ++i) {
+    dd_add(a, b, w.Ap[i], 0.0);
+    n += w.nexp[i];
+  }
+  sh[tid] = a;
+  sl[tid] = b;
+  sn[tid] = n;
+  __syncthreads();
+  if (tid == 0) {  // exclusive scan of the chunk sums
+    double ca = 0.0, cb = 0.0;
+    long long cn = 0;
+    for (int k = 0; k < DIAG_THREADS; ++k) {
+      const double ta = sh[k], tb = sl[k];
+      const long long tn = sn[k];
+      sh[k] = ca;
+      sl[k] = cb;
+      sn[k] = cn;
+      dd_add(ca, cb, ta, tb);
+      cn += tn;
     }
+    tot[0] = ca;
+    tot[1] = cb;
+    ntot = cn;
+  }
+  __syncthreads();
+  double pa = sh[tid], pb = sl[tid];
+  long long pn = sn[tid];
+  const double lnN = log((double)N);
+  for (int v = lo; v < hi; ++v) {  // pa + pb = C'[v], pn = N_v
+    Vf[v] = (v == 0) ? 0.0 : reduced_pot(pa, pb, xd{w.yfm[v], w.yfe[v]}, pn, w.beta, 0.0);
+    double sa = tot[0], sb = tot[1];
+    dd_add(sa, sb, -pa, -pb);  // C'[N] - C'[v]
+    Vb[v] = reduced_pot(sa, sb, backward_row_sum(w, v), ntot - pn, w.beta, lnN);
+    dd_add(pa, pb, w.Ap[v], 0.0);
+    pn += w.nexp[v];
+  }
+  if (tid == 0) {
+    Vf[N] = reduced_pot(tot[0], tot[1], xd{w.yfm[N], w.yfe[N]}, ntot, w.beta, 0.0);
+    Vb[N] = 0.0;
   }
 }
 
 }  // namespace
 
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s) {
-  diag_potentials_kernel<<<(w.N + 256) / 256, 256, 0, s>>>(w, Vf, Vb);
+  diag_potentials_kernel<<<1, DIAG_THREADS, 0, s>>>(w, Vf, Vb);
   return cudaGetLastError();
 }
 

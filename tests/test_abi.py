@@ -43,11 +43,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(bpimd.EXPORTED) <= exported
 
 
-def test_library_is_built_for_sm_103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", build.LIB], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+def test_library_is_built_for_sm_103a_only():
+    """The build compiles every translation unit for sm_103a and nothing else
+    (one -gencode; no PTX for other targets)."""
+    flags = build.FLAGS
+    gencodes = [flags[i + 1] for i, f in enumerate(flags) if f == "-gencode"]
+    assert gencodes == ["arch=compute_103a,code=sm_103a"]
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def test_config_struct_matches_header_layout():

@@ -58,3 +58,55 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(bpimd.BpimdError) as ei:
         bpimd.bpimd_exchange_energy_forces_noalloc(cfg, pos, None, F)
     assert ei.value.status == bpimd.BPIMD_ERR_SIZE
+
+
+FIRST_CALL_SCRIPT = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+from paper_2305_18025_gb300 import bpimd, inputs
+from paper_2305_18025_gb300.exchange import ExchangeEnergy
+N, P, beta = 96, 8, 1.0
+pos = torch.from_numpy(inputs.trapped_positions(N, P, 21)).cuda()
+cfg = bpimd.make_config(N, P, 1.0, inputs.omega_P(P, beta), beta, {prec})
+V = torch.full((), float("nan"), dtype=torch.float64, device="cuda:0")
+F = torch.full_like(pos, float("nan"))
+# the first library call of this process: symbol lookup and recursion set-up
+bpimd.bpimd_exchange_energy_forces_noalloc(cfg, pos, V, F, torch.cuda.current_stream())
+torch.cuda.synchronize()
+eng = ExchangeEnergy(N, P, 1.0, inputs.omega_P(P, beta), beta, precision={name!r}, device="cuda:0")
+Vr, Fr = eng.forces(pos)
+eng.sync()
+dv = abs(V.item() - Vr.item()) / abs(Vr.item())
+df = (torch.linalg.norm(F - Fr) / torch.linalg.norm(Fr)).item()
+print(dv, df)
+"""
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_as_the_first_call_of_a_fresh_process(prec):
+    """A caller whose very first library call is the allocation-free entry
+    point (no context exists yet, so the scratch address and the recursion
+    kernels are set up inside that call) gets the context entry point's result."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = FIRST_CALL_SCRIPT.format(root=root, name=prec,
+                                    prec=bpimd.BPIMD_FP64 if prec == "fp64" else bpimd.BPIMD_MIXED)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    dv, df = (float(x) for x in r.stdout.split()[-2:])
+    vt, ft = TOL[prec]
+    assert dv <= vt and df <= ft, (dv, df)
+
+
+def test_noalloc_without_a_V_B_output():
+    """V_B may be NULL: the forces are still written."""
+    N, P, beta = 64, 8, 1.0
+    pos = torch.from_numpy(inputs.trapped_positions(N, P, 22)).cuda()
+    _, F_ref = with_context(pos, beta, "fp64")
+    cfg = bpimd.make_config(N, P, 1.0, inputs.omega_P(P, beta), beta, bpimd.BPIMD_FP64)
+    F = torch.full_like(pos, float("nan"))
+    bpimd.bpimd_exchange_energy_forces_noalloc(cfg, pos, None, F, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert torch.linalg.norm(F - F_ref).item() <= 1e-10 * torch.linalg.norm(F_ref).item()

@@ -3,9 +3,11 @@
 
 Metric: exchange V_B + force evaluations per second for N = 1024 bosons with
 P = 32 beads (beta = 1, m = hbar = 1, omega_P = sqrt(P)/beta), trapped-boson
-positions (centres N(0,1), bead offsets N(0,0.1), seed 3), in the mixed
-float32/float64 form (the reported `value`) and the plain float64 form
-(`fp64`).  A step is one full evaluation: bead pass with pair factors, forward
+positions (centres N(0,1), bead offsets N(0,0.1), seed 3), in the mixed form
+(float32 bead differences and spring energies, everything after them at
+float64 accuracy: the reported `value`), the plain float64 form (`fp64`) and
+the fastest form with float32 pair factors and 32-bit recursion steps
+(`mixed32`).  A step is one full evaluation: bead pass with pair factors, forward
 and backward recursions with the prefix sums and V_B, probabilities with all
 exterior-bead forces.  The line also carries MD steps/s (`md`) of the same
 system with a trap and Gaussian repulsion (bpimd_step, CUDA-graph replays),
@@ -174,7 +176,7 @@ def roofline(stage_ms_per_eval, args, sm_mhz, peaks, precision="mixed"):
     elif name == "prep":
         # positions read once, interior forces written, the per-particle
         # state, and both copies of g (mantissa + int exponent per pair)
-        mant = 4 if precision == "mixed" else 8
+        mant = 4 if precision == "mixed32" else 8
         bytes_ = (N * P * 24 + N * max(P - 2, 0) * 24 + N * 8 * 10
                   + 2 * (N * (N + 1) // 2) * (mant + 4))
         achieved = bytes_ / t / 1e9
@@ -248,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
-        for prec in ("mixed", "fp64"):
+        for prec in ("mixed", "fp64", "mixed32"):
             eng = ExchangeEnergy(N, P, 1.0, wP, beta, precision=prec, device=dev, stream=stream)
             F = torch.empty_like(pos)
             V = torch.empty((), dtype=torch.float64, device=dev)
@@ -307,33 +309,60 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return None
-    mixed, fp64 = results["mixed"], results["fp64"]
+    mixed, fp64, m32 = results["mixed"], results["fp64"], results["mixed32"]
     from paper_2305_18025_gb300.bpimd import STAGE_NAMES
+    roof = roofline(mixed["stage_ms"], args, clocks.get("sm_mhz"), peaks, "mixed")
     line = {
         "metric": METRIC, "value": mixed["value"], "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+u32+f64 (mixed: float32 pair factors and sums, 32-bit integer recursion steps, float64 hand-offs and outputs)", "data": "synthetic",
-        "config": dict(workload(args), precision="mixed",
-                       l2="flushed between timed steps (256 MiB device write, untimed)",
-                       stream="a dedicated CUDA stream bound to the context (flush and events on it too)"),
-        "fp64": {"value": fp64["value"], "unit": "evals/s", "ms_per_step": fp64["ms_per_step"],
-                 "dtype": "f64+u64 (float64, with 64-bit integer recursion steps)", "stages_ms": dict(zip(STAGE_NAMES, fp64["stage_ms"]))},
-        "stages_ms": dict(zip(STAGE_NAMES, mixed["stage_ms"])),
-        "e2e": results["e2e"],
-        "roofline": roofline(mixed["stage_ms"], args, clocks.get("sm_mhz"), peaks),
-        "roofline_fp64": roofline(fp64["stage_ms"], args, clocks.get("sm_mhz"), peaks, "fp64"),
-        "clocks": clocks,
+        "dtype": DTYPES["mixed"], "data": "synthetic",
+        "config": workload(args),
+        "precision": "mixed",
+        "timing": {"l2": "flushed between timed steps (256 MiB device write, untimed)",
+                   "stream": "a dedicated CUDA stream bound to the context (flush and events on it)"},
         "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
-        "V_B": {"mixed": mixed["V_B"], "fp64": fp64["V_B"]},
-        "md": results["md"],
-        "batched": results["batched"],
-        "helium": results["helium"],
+        "clocks": clocks,
+        "e2e": results["e2e"],
+        "roofline": roof,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
         line["cpu_context"] = cpu_context(args)
+    line.update({
+        "stages_ms": {p: dict(zip(STAGE_NAMES, results[p]["stage_ms"])) for p in ("mixed", "fp64", "mixed32")},
+        "V_B": {p: results[p]["V_B"] for p in ("mixed", "fp64", "mixed32")},
+        "batched": results["batched"],
+        "helium": results["helium"],
+        "md": results["md"],
+        "fp64": {"value": fp64["value"], "unit": "evals/s", "ms_per_step": fp64["ms_per_step"],
+                 "dtype": DTYPES["fp64"],
+                 "roofline": roofline(fp64["stage_ms"], args, clocks.get("sm_mhz"), peaks, "fp64")},
+        "mixed32": {"value": m32["value"], "unit": "evals/s", "ms_per_step": m32["ms_per_step"],
+                    "dtype": DTYPES["mixed32"],
+                    "roofline": roofline(m32["stage_ms"], args, clocks.get("sm_mhz"), peaks, "mixed32")},
+    })
+    # the headline figures once more, last, so that a truncated log keeps them
+    line["summary"] = {
+        "evals_per_s": {"mixed": mixed["value"], "fp64": fp64["value"], "mixed32": m32["value"],
+                        "e2e_mixed": results["e2e"]["value"]},
+        "md_steps_per_s": {p: results["md"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
+        "batched_evals_per_s": {p: results["batched"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
+        "helium_md_steps_per_s": {p: results["helium"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
+        "recursion_frac": roof["frac"] if roof["kernel"] == "recursions" else None,
+    }
     return line
+
+
+# arithmetic of each precision form (what the path computes in)
+DTYPES = {
+    "mixed": "f32+f64+u64 (float32 bead differences and spring energies; float64-accurate pair factors, "
+             "64-bit integer recursion steps, float64 bulk sums, integer-mantissa probabilities, "
+             "compensated float32-pair force sums)",
+    "fp64": "f64+u64 (float64, with 64-bit integer recursion steps and integer-pipe pair factors)",
+    "mixed32": "f32+u32+f64 (float32 pair factors and sums, 32-bit integer recursion steps, "
+               "float64 prefix sums, hand-offs and outputs)",
+}
 
 
 MD_CFG = dict(dt=0.01, gamma=1.0, omega0=1.0, gaussian=(3.0, 0.5), seed=7)
@@ -346,7 +375,8 @@ def md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world):
     import torch
     from paper_2305_18025_gb300.exchange import RingPolymerMD
     out = {}
-    for prec, steps in (("mixed", args.md_steps), ("fp64", max(1, args.md_steps // 4))):
+    for prec, steps in (("mixed", args.md_steps), ("fp64", max(1, args.md_steps // 4)),
+                        ("mixed32", args.md_steps)):
         side = torch.cuda.Stream(dev)
         md = RingPolymerMD(args.N, args.P, 1.0, wP, args.beta, precision=prec, stream=side, **MD_CFG)
         x = torch.from_numpy(pos_np.copy()).to(dev)
@@ -388,7 +418,7 @@ def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
     betas = [r.beta for r in reps]
     wPs = [inputs.omega_P(P, b) for P, b in zip(Ps, betas)]
     out = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64", "mixed32"):
         eng = BatchedExchangeEnergy(Ns, Ps, 1.0, wPs, betas, precision=prec, device=dev)
         x = eng.pack([torch.from_numpy(r.positions) for r in reps])
         tuned = autotune.tune(eng, x, reps=3)
@@ -446,7 +476,8 @@ def helium_throughput(args, dev, max_over_ranks, barrier, world):
     pos = inputs.fcc_positions(cells, P, L, seed=5, jitter=0.05)
     lj = (HE["eps"], HE["sigma"], 2.5 * HE["sigma"])
     out = {}
-    for prec, steps in (("mixed", args.he_steps), ("fp64", max(1, args.he_steps // 5))):
+    for prec, steps in (("mixed", args.he_steps), ("fp64", max(1, args.he_steps // 5)),
+                        ("mixed32", args.he_steps)):
         side = torch.cuda.Stream(dev)
         md = RingPolymerMD(N, P, HE["m"], wP, beta, dt=dt, gamma=1.0, lennard_jones=lj, box=L, seed=3,
                            precision=prec, stream=side)
@@ -615,7 +646,8 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload(args), precision="fp64 (CPU oracle)"),
+        "config": workload(args),
+        "precision": "fp64 (CPU oracle)",
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{k} of {args.steps} requested steps timed (bounded to ~120 s); "
                                    f"C oracle Algorithm 1, float64, single thread, host has {os.cpu_count()} cores"},

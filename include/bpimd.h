@@ -66,14 +66,38 @@ extern "C" {
 #define BPIMD_ERR_SIZE (-7)      /* problem larger than a fixed-size buffer      */
 
 /* ---------------------------------------------------------------- precision */
-/* BPIMD_FP64: every step in float64.
- * BPIMD_MIXED: bead differences, per-particle spring sums and the per-pair
- * Boltzmann factors exp(-beta (1/2) m w_P^2 |r_v^P - r_u^1|^2) in float32; the
- * prefix sums of spring energies, the cycle-energy differences, both
- * recursions, the probability normalisation and all force accumulations in
- * float64. */
+/* The precision forms.  Each names what every step computes in; "integer"
+ * steps carry extended numbers m 2^e with an integer mantissa m and an int32
+ * exponent.
+ *
+ * BPIMD_FP64: float64 bead differences, spring energies, closing-spring
+ *   distances and forces; pair Boltzmann factors g = 2^(-x) of the exact
+ *   float64 product x by a 64-bit fixed-point table method (integer pipe,
+ *   2^-60 relative before the final float64 rounding); recursion steps with
+ *   64-bit integer mantissas (truncation 2^-61 per operation); float64 bulk
+ *   sums of the recursions, probabilities and force sums.
+ * BPIMD_MIXED: float32 bead differences, per-particle spring energies (float32
+ *   warp sums) and closing-spring distances; everything after them at float64
+ *   accuracy or better: the link coefficients and the prefix sums of spring
+ *   energies in float64, g = 2^(-x) of the exact product of the float32
+ *   closing-spring term and the float64 constant beta k/2 log2(e) by the same
+ *   integer table method, recursion steps with 64-bit integer mantissas and
+ *   float64 bulk sums, probabilities Pr = alpha mu g from 64-bit integer
+ *   mantissa products, and the probability and force sums as unevaluated
+ *   sums of two float32 numbers (compensated: 2^-46 relative) over float32
+ *   bead differences.
+ * BPIMD_MIXED32: the fastest form: float32 bead differences and spring
+ *   energies, g from the float32 hardware exponential (ex2.approx), recursion
+ *   steps on 32-bit integer mantissas (31 bits, multiplied by the top 32 bits
+ *   of K = c g: truncation 2^-30 per step), float32 bulk and next-tile sums,
+ *   float32 probabilities and block-local force sums (combined across blocks
+ *   with float32 TwoSum compensation); float64 prefix sums, link coefficients,
+ *   tile hand-offs and outputs.
+ * All three meet the mixed tolerances (1e-6 relative on V_B, 1e-5 RMS on
+ * forces); BPIMD_FP64 meets 1e-12 / 1e-10. */
 #define BPIMD_FP64 0
 #define BPIMD_MIXED 1
+#define BPIMD_MIXED32 2
 
 /* --------------------------------------------------------- pair potentials */
 #define BPIMD_PAIR_NONE 0
@@ -94,7 +118,7 @@ typedef struct {
   double m;
   double omega_P;
   double beta;
-  int32_t precision; /* BPIMD_FP64 or BPIMD_MIXED */
+  int32_t precision; /* BPIMD_FP64, BPIMD_MIXED or BPIMD_MIXED32 */
   int32_t flags;     /* reserved, must be 0 */
   /* molecular dynamics (bpimd_step) */
   double dt;         /* time step                                   */

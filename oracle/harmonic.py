@@ -26,19 +26,20 @@ def _theta(beta, omega0, P):
     return math.asinh(x), (omega0 / (2.0 * P)) / math.sqrt(1.0 + x * x)
 
 
-def mean_energy(N, P, beta, omega0=1.0, dim=3):
-    """-d ln Z_N / d beta for N bosons, P beads, `dim` dimensions.
+def _dlnZ(N, P, beta, omega0, dim, dth):
+    """d ln Z_N / d lambda for a parameter lambda that enters only through
+    theta, given dth = d theta / d lambda.
 
     Works with the rescaled y_k = z_k exp(dim k P theta) = (1 - exp(-2kP theta))^(-dim)
     and Y_n = Z_n exp(dim n P theta), which obey the same recursion and stay O(1).
     """
-    th, dth = _theta(beta, omega0, P)
+    th, _ = _theta(beta, omega0, P)
     y = [0.0] * (N + 1)
     dy = [0.0] * (N + 1)
     for k in range(1, N + 1):
         q = math.exp(-2.0 * k * P * th)
         y[k] = (1.0 - q) ** (-dim)
-        # d/dbeta (1 - q)^(-dim) = -dim (1 - q)^(-dim-1) * (2 k P dth q)
+        # d/dlambda (1 - q)^(-dim) = -dim (1 - q)^(-dim-1) * (2 k P dth q)
         dy[k] = -dim * (1.0 - q) ** (-dim - 1) * (2.0 * k * P * dth * q)
     Y = [1.0] + [0.0] * N
     dY = [0.0] * (N + 1)
@@ -50,7 +51,22 @@ def mean_energy(N, P, beta, omega0=1.0, dim=3):
         Y[n] = s / n
         dY[n] = ds / n
     # ln Z_N = ln Y_N - dim N P theta
-    return -(dY[N] / Y[N] - dim * N * P * dth)
+    return dY[N] / Y[N] - dim * N * P * dth
+
+
+def mean_energy(N, P, beta, omega0=1.0, dim=3):
+    """-d ln Z_N / d beta for N bosons, P beads, `dim` dimensions."""
+    _, dth = _theta(beta, omega0, P)  # d theta / d beta
+    return -_dlnZ(N, P, beta, omega0, dim, dth)
+
+
+def mean_trap_energy(N, P, beta, omega0=1.0, dim=3):
+    """<U-bar>, the mean trap energy (1/P) sum_j (1/2) m w0^2 |r_j|^2 of the same
+    ensemble: U-bar is w0^2 times a positive function of the positions, so
+    d ln Z / d w0 = -(2 beta / w0) <U-bar>, i.e. <U-bar> = -(w0 / (2 beta)) d ln Z / d w0."""
+    x = beta * omega0 / (2.0 * P)
+    dth = (beta / (2.0 * P)) / math.sqrt(1.0 + x * x)  # d theta / d w0
+    return -(omega0 / (2.0 * beta)) * _dlnZ(N, P, beta, omega0, dim, dth)
 
 
 def single_ring_partition(k, P, beta, omega0=1.0, dim=3):

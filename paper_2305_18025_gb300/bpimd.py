@@ -23,6 +23,8 @@ BPIMD_NOALLOC_MAX_N = 256
 
 BPIMD_FP64 = 0
 BPIMD_MIXED = 1
+BPIMD_MIXED32 = 2
+PRECISIONS = {"fp64": BPIMD_FP64, "mixed": BPIMD_MIXED, "mixed32": BPIMD_MIXED32}
 
 BPIMD_PAIR_NONE = 0
 BPIMD_PAIR_GAUSSIAN = 1

@@ -22,7 +22,7 @@ int validate(const bpimd_config *c) {
   if (c->N > CHAIN_MAX_N) return BPIMD_ERR_ARG;
   if ((long long)c->N * c->P > (1LL << 31) / 3) return BPIMD_ERR_ARG;
   if (!finite_pos(c->m) || !finite_pos(c->omega_P) || !finite_pos(c->beta)) return BPIMD_ERR_ARG;
-  if (c->precision != BPIMD_FP64 && c->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
+  if (!valid_precision(c->precision)) return BPIMD_ERR_ARG;
   if (c->flags != 0) return BPIMD_ERR_ARG;
   if (!(c->box_L >= 0.0) || !std::isfinite(c->box_L)) return BPIMD_ERR_ARG;
   return BPIMD_OK;
@@ -195,7 +195,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.P = cfg->P;
   w.NT = (w.N + TILE - 1) / TILE;
   w.NB = w.NT * (w.NT + 1) / 2;
-  w.mixed = cfg->precision == BPIMD_MIXED;
+  set_precision(w, cfg->precision);
   w.m = cfg->m;
   w.omega_P = cfg->omega_P;
   w.beta = cfg->beta;

@@ -23,20 +23,21 @@ namespace bpimd {
 
 int evaluate_batched(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) {
   cudaStream_t s = ctx->stream;
-  const bool mixed = ctx->cfg.precision == BPIMD_MIXED;
+  const int mode = ctx->cfg.precision;
   cudaEvent_t *ev = nullptr;
   if (ctx->prof_on && ctx->prof_count < ctx->prof_max)
     ev = &ctx->prof_events[(size_t)ctx->prof_count++ * (BPIMD_NUM_STAGES + 1)];
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
   if (launch_prep_batched(ctx->d_ws, ctx->d_bead_tab, ctx->n_bead_tab, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off,
-                          mixed, pos, F, ctx->tune_gmat_bpsm, s) != cudaSuccess)
+                          mode, pos, F, ctx->tune_gmat_bpsm, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(1);
-  if (launch_chains_batched(ctx->d_ws, ctx->d_order, ctx->R, ctx->maxN, mixed, V_B, s) != cudaSuccess)
+  if (launch_chains_batched(ctx->d_ws, ctx->d_order, ctx->R, ctx->maxN, mode == BPIMD_MIXED32, V_B, s) !=
+      cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(2);
-  if (launch_prob_forces_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off, mixed, pos, F,
+  if (launch_prob_forces_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off, mode, pos, F,
                                  ctx->tune_prob_bpsm, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(3);
@@ -54,7 +55,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
   *out = nullptr;
   if (!cfg || !N || !P || !omega_P || !beta || R < 1 || R > (1 << 20)) return BPIMD_ERR_ARG;
   if (!finite_positive(cfg->m) || cfg->flags != 0 || cfg->box_L != 0.0) return BPIMD_ERR_ARG;
-  if (cfg->precision != BPIMD_FP64 && cfg->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
+  if (!valid_precision(cfg->precision)) return BPIMD_ERR_ARG;
   long long total = 0;
   for (int r = 0; r < R; ++r) {
     if (N[r] < 1 || N[r] > BATCH_MAX_N || P[r] < 2 || P[r] > (1 << 16)) return BPIMD_ERR_ARG;
@@ -85,7 +86,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
     w.P = P[r];
     w.NT = (w.N + TILE - 1) / TILE;
     w.NB = w.NT * (w.NT + 1) / 2;
-    w.mixed = cfg->precision == BPIMD_MIXED;
+    set_precision(w, cfg->precision);
     w.m = cfg->m;
     w.omega_P = omega_P[r];
     w.beta = beta[r];
@@ -144,7 +145,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
             cudaMemcpyAsync(ctx->d_order, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync(ctx->d_off, ctx->h_off.data(), sizeof(long long) * R, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
-            launch_gmat_padding_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, cfg->precision == BPIMD_MIXED,
+            launch_gmat_padding_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, cfg->precision == BPIMD_MIXED32,
                                         s) == cudaSuccess &&
             cudaMallocHost(&ctx->host_status, sizeof(int)) == cudaSuccess &&
             cudaStreamSynchronize(s) == cudaSuccess;  // host tables go out of scope

@@ -127,7 +127,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // ------------------------------------------------------------------ workspace
 struct Workspace {
   int N, P, NT, NB;     // NT = ceil(N/TILE), NB = NT(NT+1)/2 blocks of g
-  int mixed;
+  int mode;             // precision form: BPIMD_FP64, BPIMD_MIXED or BPIMD_MIXED32
+  int mixed;            // MIXED32: float32 pair-factor and alpha mantissas, 32-bit recursion chain
+  int bead32;           // MIXED and MIXED32: float32 bead differences and spring energies
   double m, omega_P, beta, k, half_k;
   // periodic cubic box of side L (0: open boundaries); every spring joins the
   // minimum image of its beads.  MIXED keeps the bead-1/bead-P copies in a box
@@ -171,6 +173,14 @@ struct Workspace {
   int *rowcnt, *colcnt;
   int *status;          // device status word
 };
+
+// Precision form of a workspace (the three BPIMD_* precision values).
+inline bool valid_precision(int p) { return p == BPIMD_FP64 || p == BPIMD_MIXED || p == BPIMD_MIXED32; }
+inline void set_precision(Workspace &w, int p) {
+  w.mode = p;
+  w.mixed = p == BPIMD_MIXED32;
+  w.bead32 = p != BPIMD_FP64;
+}
 
 // number of SMs of the current device (cached per device)
 inline int sm_count() {
@@ -264,14 +274,14 @@ cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, c
 // bead pass (bead_tab: (replica, first particle)) and pair factors (blk_tab:
 // (replica, block of g), at most blocks_per_sm * SMs blocks) in one launch
 cudaError_t launch_prep_batched(const Workspace *ws, const int2 *bead_tab, int nbead, const int2 *blk_tab,
-                                int nblk, const long long *off, bool mixed, const double *pos, double *F,
+                                int nblk, const long long *off, int mode, const double *pos, double *F,
                                 int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_gmat_padding_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed,
                                         cudaStream_t s);
 cudaError_t launch_chains_batched(const Workspace *ws, const int *order, int R, int maxN, bool mixed, double *V_B,
                                   cudaStream_t s);
 cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
-                                      bool mixed, const double *pos, double *F, int blocks_per_sm, cudaStream_t s);
+                                      int mode, const double *pos, double *F, int blocks_per_sm, cudaStream_t s);
 
 // B_{a+1} (1-based backward row sum for 0-based particle a) from the stored state
 __device__ __forceinline__ xd backward_row_sum(const Workspace &w, int a) {

@@ -15,8 +15,11 @@
 //   F_l^P = -m w_P^2 [ (sum_u Pr[l->u]) (r_l^P - r_l^{P-1}) + sum_u Pr[l->u] (r_l^P - r_u^1) ]
 //   F_l^1 = -m w_P^2 [ (sum_l' Pr[l'->l]) (r_l^1 - r_l^2) + sum_l' Pr[l'->l] (r_l^1 - r_l'^P) ]
 // i.e. the per-neighbour sums of the paper distributed over their terms.
-// MIXED: bead differences from float32 high/low parts, block-local products
-// and sums in float32, combination in float64.
+// Precision forms: FP64 in float64 throughout.  MIXED (prob_block_mixed):
+// Pr from 64-bit integer mantissa products, products with the float32 bead
+// differences and all sums as compensated float32 pairs.  MIXED32: bead
+// differences from float32 high/low parts, block-local products and sums in
+// float32, the combination across blocks with float32 TwoSum compensation.
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
@@ -54,6 +57,10 @@ struct fsum2 {
     c += (s - (t - bp)) + (v - bp);
     s = t;
   }
+  __device__ __forceinline__ void add2(float h, float l) {  // an unevaluated sum h + l
+    add(h);
+    c += l;
+  }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
@@ -80,7 +87,11 @@ __device__ __forceinline__ double img(const Workspace &w, double d) {
 // (t, 0..t) in that order, add the direct link, form F_l^P.  Run by the last
 // block of the tile to finish; all 256 threads call it.  The finishing warp's
 // loads are issued before the partial sums.
-template <typename P_t, bool PBC>
+// Kinds of block partials: float64, float32, or an unevaluated float32 pair
+// (high, low) written by the MIXED pass.
+constexpr int PK_F64 = 0, PK_F32 = 1, PK_FF = 2;
+
+template <int PK, bool PBC>
 __device__ void finalize_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, jj = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
@@ -98,6 +109,7 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
     }
   }
   const size_t base = (size_t)t * (t + 1) / 2;
+  using P_t = typename std::conditional<PK == PK_F64, double, typename std::conditional<PK == PK_F32, float, float2>::type>::type;
   const P_t *part = (const P_t *)w.rowpart;
   double acc = 0.0;
   fsum2 f;
@@ -108,16 +120,17 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
 #pragma unroll
     for (int u = 0; u < 8; ++u) {  // index clamped into the tile: a valid address even if the load is speculated
       const int k = min(s0 + 2 * u, t);
-      v[u] = (s0 + 2 * u <= t) ? __ldcg(part + ((base + k) * TILE + jj) * 4 + q) : (P_t)0;
+      v[u] = (s0 + 2 * u <= t) ? __ldcg(part + ((base + k) * TILE + jj) * 4 + q) : P_t{};
     }
     if (s0 == half && mine && p + 1 < w.N) M = direct_link_fast(w, p);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      if (std::is_same<P_t, float>::value) f.add((float)v[u]);
-      else acc += (double)v[u];
+      if constexpr (PK == PK_F32) f.add(v[u]);
+      else if constexpr (PK == PK_FF) f.add2(v[u].x, v[u].y);
+      else acc += v[u];
     }
   }
-  fin[jj][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
+  fin[jj][q + 4 * half] = PK == PK_F64 ? acc : f.value();
   __syncthreads();
   if (mine) {
     const double *fr = fin[threadIdx.x];
@@ -138,7 +151,7 @@ __device__ void finalize_rows(const Workspace &w, int t, const double *__restric
 }
 
 // Bead 1 of the 32 particles of column tile s: blocks (s..NT-1, s) in order.
-template <typename P_t, bool PBC>
+template <int PK, bool PBC>
 __device__ void finalize_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
                               double (*fin)[9]) {
   const int q = threadIdx.x & 3, ii = (threadIdx.x >> 2) & 31, half = threadIdx.x >> 7;
@@ -155,6 +168,7 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
       for (int c = 0; c < 3; ++c) pP[c] = n[c];
     }
   }
+  using P_t = typename std::conditional<PK == PK_F64, double, typename std::conditional<PK == PK_F32, float, float2>::type>::type;
   const P_t *part = (const P_t *)w.colpart;
   double acc = 0.0;
   fsum2 f;
@@ -163,16 +177,17 @@ __device__ void finalize_cols(const Workspace &w, int s, const double *__restric
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = min(t0 + 2 * u, w.NT - 1);  // clamped into the tile: a valid address even if speculated
-      v[u] = (t0 + 2 * u < w.NT) ? __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q) : (P_t)0;
+      v[u] = (t0 + 2 * u < w.NT) ? __ldcg(part + (((size_t)t * (t + 1) / 2 + s) * TILE + ii) * 4 + q) : P_t{};
     }
     if (t0 == s + half && mine && p >= 1) M = direct_link_fast(w, p - 1);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      if (std::is_same<P_t, float>::value) f.add((float)v[u]);
-      else acc += (double)v[u];
+      if constexpr (PK == PK_F32) f.add(v[u]);
+      else if constexpr (PK == PK_FF) f.add2(v[u].x, v[u].y);
+      else acc += v[u];
     }
   }
-  fin[ii][q + 4 * half] = std::is_same<P_t, float>::value ? f.value() : acc;
+  fin[ii][q + 4 * half] = PK == PK_F64 ? acc : f.value();
   __syncthreads();
   if (mine) {
     const double *fc = fin[threadIdx.x];
@@ -308,9 +323,169 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
     __syncthreads();
     const bool last_row = last[0], last_col = last[1];
     if (last_row || last_col) __threadfence();
-    if (last_row) finalize_rows<P_t, PBC>(w, t, pos, F, fin);
-    if (last_col) finalize_cols<P_t, PBC>(w, s, pos, F, fin);
+    if (last_row) finalize_rows<MIXED ? PK_F32 : PK_F64, PBC>(w, t, pos, F, fin);
+    if (last_col) finalize_cols<MIXED ? PK_F32 : PK_F64, PBC>(w, s, pos, F, fin);
   }
+}
+
+// ----------------------------------------------------------- MIXED (config 3)
+// Unevaluated sums h + l of two float32 numbers (|l| <= ulp(h)/2 after
+// renormalisation): about 46 significant bits on the float32 pipe.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.h + b.h, bb = s - a.h;
+  const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+  const float h = s + e;
+  return ff{h, e - (h - s)};
+}
+// a * d with a float32 d; a.h * d is exact by FMA (TwoProd)
+__device__ __forceinline__ ff ff_mul(ff a, float d) {
+  const float p = a.h * d;
+  const float e = fmaf(a.h, d, -p) + a.l * d;
+  const float h = p + e;
+  return ff{h, e - (h - p)};
+}
+
+// Pr = alpha mu g of one pair from three extended numbers with double
+// mantissas in [1, 2): the mantissa products on the integer pipe (64-bit
+// truncations, 2^-62 relative), the exponents added as integers; returned as
+// an unevaluated float32 pair (the mantissa cut at 2^-46), 0 below 2^-126.
+__device__ __forceinline__ ff prob_ff(unsigned long long am, int e_am, double gm, int ge) {
+  // am = (alpha mantissa)(mu mantissa) normalised to [2^63, 2^64), value am/2^63 2^e_am
+  const unsigned long long gg = (((unsigned long long)__double_as_longlong(gm) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+  unsigned long long pr = __umul64hi(am, gg);  // in [2^62, 2^64)
+  const int sh = (int)(pr >> 63) ^ 1;
+  pr <<= sh;
+  const int E = e_am + ge + 1 - sh;  // Pr = (pr / 2^63) 2^E
+  if (E < -126) return ff{0.0f, 0.0f};
+  const float h = __uint_as_float((unsigned)((E + 127) << 23) | (unsigned)((pr >> 40) & 0x7FFFFFu));
+  const float t = __uint_as_float(0x4B000000u | (unsigned)((pr >> 17) & 0x7FFFFFu)) - 8388608.0f;  // next 23 bits
+  const float sc = (E - 46 >= -126) ? __uint_as_float((unsigned)((E - 46 + 127) << 23)) : 0.0f;
+  return ff{h, t * sc};
+}
+
+// One 32 x 32 block of the lower triangle in the MIXED form (all 256
+// threads).  Thread (i0 = warp, j = lane) forms the pairs (a = 32 s + i0 + 8 k,
+// b = 32 t + j), k = 0..3: Pr and Pr (r_b^P - r_a^1) (float32 bead
+// differences) as float32 pairs into the shared tile V[value][i][j]; then
+// 128 threads sum the 32 rows b over their sources and 128 threads the 32
+// columns a over their rows, in a fixed order, as float32 pairs.
+template <bool PBC>
+__device__ __forceinline__ void prob_block_mixed(const Workspace &w, int blk, const double *__restrict__ pos,
+                                                 double *__restrict__ F, float (*V)[2][TILE][33], double (*fin)[9],
+                                                 int *last) {
+  int t, s;
+  block_coords_f(blk, t, s);
+  const int j = threadIdx.x & 31, i0 = threadIdx.x >> 5;
+  const int b = t * TILE + j;
+  const bool bvalid = b < w.N;
+  unsigned long long mum = 0;
+  int mue = 0;
+  float4 bh = make_float4(0.f, 0.f, 0.f, 0.f), bl = bh;
+  if (bvalid) {
+    const xd mub = mu_of(w, b);
+    mum = (((unsigned long long)__double_as_longlong(mub.m) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+    mue = mub.e;
+    bh = *(const float4 *)(w.RPs + 8 * (size_t)b);
+    bl = *(const float4 *)(w.RPs + 8 * (size_t)b + 4);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int i = i0 + 8 * kk;
+    const int a = s * TILE + i;
+    ff pr{0.0f, 0.0f}, px{0.0f, 0.0f}, py{0.0f, 0.0f}, pz{0.0f, 0.0f};
+    if (bvalid && a <= b) {
+      float fx, fy, fz;
+      if (PBC) {  // minimum image from the fixed-point copies (bh holds RP's bits)
+        const uint4 ua = *(const uint4 *)(w.R1s + 8 * (size_t)a);
+        fx = fixdiff(__float_as_uint(bh.x), ua.x, w.Lscale);
+        fy = fixdiff(__float_as_uint(bh.y), ua.y, w.Lscale);
+        fz = fixdiff(__float_as_uint(bh.z), ua.z, w.Lscale);
+      } else {
+        const float4 ah = *(const float4 *)(w.R1s + 8 * (size_t)a);
+        const float4 al4 = *(const float4 *)(w.R1s + 8 * (size_t)a + 4);
+        fx = (bh.x - ah.x) + (bl.x - al4.x);
+        fy = (bh.y - ah.y) + (bl.y - al4.y);
+        fz = (bh.z - ah.z) + (bl.z - al4.z);
+      }
+      const size_t gi = (size_t)blk * TILE2 + i * TILE + j;
+      const double alm = ((const double *)w.alm)[a];
+      const unsigned long long aa = (((unsigned long long)__double_as_longlong(alm) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+      unsigned long long am = __umul64hi(aa, mum);  // in [2^62, 2^64)
+      const int sh = (int)(am >> 63) ^ 1;
+      am <<= sh;
+      pr = prob_ff(am, w.ale[a] + mue + 1 - sh, ((const double *)w.gm)[gi], w.ge[gi]);
+      px = ff_mul(pr, fx);
+      py = ff_mul(pr, fy);
+      pz = ff_mul(pr, fz);
+    }
+    V[0][0][i][j] = pr.h; V[0][1][i][j] = pr.l;
+    V[1][0][i][j] = px.h; V[1][1][i][j] = px.l;
+    V[2][0][i][j] = py.h; V[2][1][i][j] = py.l;
+    V[3][0][i][j] = pz.h; V[3][1][i][j] = pz.l;
+  }
+  __syncthreads();
+  {
+    const int q = (threadIdx.x >> 5) & 3, r = threadIdx.x & 31;
+    ff acc{0.0f, 0.0f};
+    if (threadIdx.x < 128) {  // row r (particle b = 32 t + r): sum over the sources i
+#pragma unroll 8
+      for (int i = 0; i < TILE; ++i) acc = ff_add(acc, ff{V[q][0][i][r], V[q][1][i][r]});
+      ((float2 *)w.rowpart)[((size_t)blk * TILE + r) * 4 + q] = make_float2(acc.h, acc.l);
+    } else {  // column r (particle a = 32 s + r): sum over the rows j; bead-1 sums carry r_a^1 - r_b^P
+#pragma unroll 8
+      for (int jj = 0; jj < TILE; ++jj) acc = ff_add(acc, ff{V[q][0][r][jj], V[q][1][r][jj]});
+      const float sg = q == 0 ? 1.0f : -1.0f;
+      ((float2 *)w.colpart)[((size_t)blk * TILE + r) * 4 + q] = make_float2(sg * acc.h, sg * acc.l);
+    }
+  }
+  // publish this block's partials, then count it in its row and column tile;
+  // the block that completes a tile forms that tile's forces (no waiting)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last[0] = atomicAdd(w.rowcnt + t, 1) == t;             // blocks (t, 0..t)
+    last[1] = atomicAdd(w.colcnt + s, 1) == w.NT - 1 - s;  // blocks (s..NT-1, s)
+  }
+  __syncthreads();
+  const bool last_row = last[0], last_col = last[1];
+  if (last_row || last_col) __threadfence();
+  if (last_row) finalize_rows<PK_FF, PBC>(w, t, pos, F, fin);
+  if (last_col) finalize_cols<PK_FF, PBC>(w, s, pos, F, fin);
+}
+
+__global__ void __launch_bounds__(256, 4) prob_force_kernel_mixed(Workspace w, const double *__restrict__ pos,
+                                                               double *__restrict__ F) {
+  __shared__ float V[4][2][TILE][33];
+  __shared__ double fin[32][9];
+  __shared__ int last[2];
+  pdl_wait();
+  for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
+    if (w.pbc) prob_block_mixed<true>(w, blk, pos, F, V, fin, last);
+    else prob_block_mixed<false>(w, blk, pos, F, V, fin, last);
+    __syncthreads();  // V is rewritten by the next block
+  }
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(256, 4) prob_force_batched_mixed(const Workspace *__restrict__ ws,
+                                                                const int2 *__restrict__ tab, int ntab,
+                                                                const long long *__restrict__ off,
+                                                                const double *__restrict__ pos,
+                                                                double *__restrict__ F) {
+  __shared__ float V[4][2][TILE][33];
+  __shared__ double fin[32][9];
+  __shared__ int last[2];
+  pdl_wait();
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int2 e = tab[k];
+    if (ws[e.x].pbc) prob_block_mixed<true>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], V, fin, last);
+    else prob_block_mixed<false>(ws[e.x], e.y, pos + off[e.x], F + off[e.x], V, fin, last);
+    __syncthreads();
+  }
+  pdl_trigger();
 }
 
 template <bool MIXED>
@@ -406,8 +581,12 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   const int sms = sm_count();
   const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
-  cudaError_t e = w.mixed ? launch_pdl(prob_force_kernel<true>, grid, 256, 0, s, w, pos, F)
-                          : launch_pdl(prob_force_kernel<false>, grid, 256, 0, s, w, pos, F);
+  cudaError_t e;
+  switch (w.mode) {
+    case BPIMD_FP64: e = launch_pdl(prob_force_kernel<false>, grid, 256, 0, s, w, pos, F); break;
+    case BPIMD_MIXED: e = launch_pdl(prob_force_kernel_mixed, grid, 256, 0, s, w, pos, F); break;
+    default: e = launch_pdl(prob_force_kernel<true>, grid, 256, 0, s, w, pos, F); break;
+  }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -425,13 +604,17 @@ cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream
 }
 
 cudaError_t launch_prob_forces_batched(const Workspace *ws, const int2 *tab, int ntab, const long long *off,
-                                      bool mixed, const double *pos, double *F, int blocks_per_sm, cudaStream_t s) {
+                                      int mode, const double *pos, double *F, int blocks_per_sm, cudaStream_t s) {
   if (ntab <= 0) return cudaSuccess;
   const int sms = sm_count();
   const int cap = sms * (blocks_per_sm > 0 ? blocks_per_sm : 8);
   const int grid = ntab < cap ? ntab : cap;
-  cudaError_t e = mixed ? launch_pdl(prob_force_batched<true>, grid, 256, 0, s, ws, tab, ntab, off, pos, F)
-                        : launch_pdl(prob_force_batched<false>, grid, 256, 0, s, ws, tab, ntab, off, pos, F);
+  cudaError_t e;
+  switch (mode) {
+    case BPIMD_FP64: e = launch_pdl(prob_force_batched<false>, grid, 256, 0, s, ws, tab, ntab, off, pos, F); break;
+    case BPIMD_MIXED: e = launch_pdl(prob_force_batched_mixed, grid, 256, 0, s, ws, tab, ntab, off, pos, F); break;
+    default: e = launch_pdl(prob_force_batched<true>, grid, 256, 0, s, ws, tab, ntab, off, pos, F); break;
+  }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

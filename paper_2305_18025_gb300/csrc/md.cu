@@ -340,11 +340,11 @@ int total_force(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
   int rc = evaluate(ctx, pos, md.VB, md.F);
   if (rc != BPIMD_OK) return rc;
   if (p.cell_nc > 0)
-    return cell_list_forces(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp, ctx->w.mixed, md.cells, md.ubar_part,
+    return cell_list_forces(pos, md.F, ctx->cfg.N, ctx->cfg.P, p.pp, ctx->w.bead32, md.cells, md.ubar_part,
                             ctx->stream) == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
   const dim3 grid((ctx->cfg.N + EXT_PARTICLES - 1) / EXT_PARTICLES, ctx->cfg.P);
   const int N = ctx->cfg.N, P = ctx->cfg.P;
-  if (ctx->w.mixed) {
+  if (ctx->w.bead32) {
     if (p.pp.pbc) ext_force_kernel<true, true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
     else ext_force_kernel<true, false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, N, P, p.pp, md.ubar_part);
   } else {
@@ -359,7 +359,7 @@ int enqueue_step(bpimd_ctx *ctx, const MDParams &p, double *pos, double *vel) {
   MDState &md = ctx->md;
   cudaStream_t s = ctx->stream;
   const int g4 = grid_for((p.n + 3) / 4, MD_THREADS), g1 = grid_for(p.n, MD_THREADS);
-  if (ctx->w.mixed)
+  if (ctx->w.bead32)
     md_baoa_kernel<true><<<g4, MD_THREADS, 0, s>>>(pos, vel, md.F, p.n, p.half_dt_over_m, p.half_dt, p.c1, p.c2,
                                                    p.k0, p.k1, md.step);
   else
@@ -375,12 +375,12 @@ int enqueue_step(bpimd_ctx *ctx, const MDParams &p, double *pos, double *vel) {
 int md_alloc(bpimd_ctx *ctx, const MDParams &p) {
   MDState &md = ctx->md;
   if (p.cell_nc > 0) {
-    const size_t bytes = cell_list_bytes(ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.mixed);
+    const size_t bytes = cell_list_bytes(ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.bead32);
     if (cudaMalloc(&md.cell_block, bytes) != cudaSuccess) {
       cudaGetLastError();
       return BPIMD_ERR_NOMEM;
     }
-    cell_list_layout(md.cells, (char *)md.cell_block, ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.mixed);
+    cell_list_layout(md.cells, (char *)md.cell_block, ctx->cfg.N, ctx->cfg.P, p.cell_nc, ctx->w.bead32);
   }
   const size_t n = (size_t)ctx->cfg.N * ctx->cfg.P * 3;
   md.ext_blocks = p.cell_nc > 0 ? cell_list_partials(ctx->cfg.N, ctx->cfg.P)

@@ -64,7 +64,7 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   if ((((uintptr_t)positions) & 15) || (((uintptr_t)forces) & 15)) return BPIMD_ERR_ARG;
   if (V_B && (((uintptr_t)V_B) & 7)) return BPIMD_ERR_ARG;
   if (cfg->N < 1 || cfg->P < 2 || cfg->flags != 0) return BPIMD_ERR_ARG;
-  if (cfg->precision != BPIMD_FP64 && cfg->precision != BPIMD_MIXED) return BPIMD_ERR_ARG;
+  if (!valid_precision(cfg->precision)) return BPIMD_ERR_ARG;
   if (!positive_finite(cfg->m) || !positive_finite(cfg->omega_P) || !positive_finite(cfg->beta))
     return BPIMD_ERR_ARG;
   if (cfg->N > BPIMD_NOALLOC_MAX_N || (long long)cfg->N * cfg->P > (1LL << 31) / 3) return BPIMD_ERR_SIZE;
@@ -74,7 +74,7 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   w.P = cfg->P;
   w.NT = (w.N + TILE - 1) / TILE;
   w.NB = w.NT * (w.NT + 1) / 2;
-  w.mixed = cfg->precision == BPIMD_MIXED;
+  set_precision(w, cfg->precision);
   w.m = cfg->m;
   w.omega_P = cfg->omega_P;
   w.beta = cfg->beta;

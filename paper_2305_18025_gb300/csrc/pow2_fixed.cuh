@@ -4,7 +4,8 @@
 // cycles, so the O(N^2) pair Boltzmann factors g = exp(-beta (1/2) k d^2)
 // avoid it.  Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989)
 // in 64-bit fixed point:
-//   x = n + f, n integer, f in [0, 1) as a 64-bit fraction F = f 2^64;
+//   x = n + f, n integer, f in [0, 1) as a 64-bit fraction F = f 2^64 (x is
+//   the exact product of the argument's factors, up to 128 bits);
 //   f = j/256 + r, j = the top 8 bits of F, 0 <= r < 2^-8;
 //   2^(-f) = T[j] e^(-u), u = r ln 2 < 0.0028, T[j] = 2^(-j/256) (table of
 //   pow2_table.h, 63 fraction bits);
@@ -68,15 +69,16 @@ BPIMD_HD unsigned long long double_to_bits(double d) {
 #endif
 }
 
-// 2^(-x) for x = M 2^S with M in [2^63, 2^64) (a normalised 64-bit mantissa).
+// 2^(-x) for x = (H 2^64 + L) 2^S, H in [2^63, 2^64) (a normalised 128-bit
+// mantissa: exact products of two float64 or float32 mantissas fit in it).
 // table: T63 or a shared-memory copy of it.
-BPIMD_HD mexp pow2neg_q(unsigned long long M, int S, const unsigned long long *table) {
-  if (S >= -35) return mexp{1.0, ZERO_EXP};  // x >= 2^28
-  const int sh = -S;                           // >= 36
-  const unsigned long long n = sh < 64 ? (M >> sh) : 0ull;
-  unsigned long long F;                        // fraction of x, 64 bits
-  if (sh <= 64) F = M << (64 - sh);            // sh == 64: the whole of M is the fraction
-  else F = sh < 128 ? (M >> (sh - 64)) : 0ull;
+BPIMD_HD mexp pow2neg_q(unsigned long long H, unsigned long long L, int S, const unsigned long long *table) {
+  if (S >= -99) return mexp{1.0, ZERO_EXP};  // x >= 2^28
+  const int k = -S - 64;                      // x = (H:L) >> (k + 64); k >= 36
+  const unsigned long long n = k < 64 ? (H >> k) : 0ull;
+  unsigned long long F;                       // the 64 fraction bits below the binary point
+  if (k < 64) F = (L >> k) | (H << (64 - k));
+  else F = k < 128 ? (H >> (k - 64)) : 0ull;
   const unsigned j = (unsigned)(F >> 56);
   const unsigned long long r = F & 0x00FFFFFFFFFFFFFFull;  // f - j/256, times 2^64
   const unsigned long long u = mulhi(r, BPIMD_LN2_Q64);      // u 2^64, u = r ln 2
@@ -101,18 +103,32 @@ BPIMD_HD mexp pow2neg_q(unsigned long long M, int S, const unsigned long long *t
   return mexp{bits_to_double((m53 & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull), e};
 }
 
+// Full 128-bit product of two 64-bit mantissas, normalised so that the top
+// bit of the high word is set (both inputs have their top bit set).
+BPIMD_HD void mul128_norm(unsigned long long a, unsigned long long b, unsigned long long &H,
+                          unsigned long long &L, int &shift) {
+  H = mulhi(a, b);
+  L = a * b;
+  shift = 0;
+  if (!(H >> 63)) {
+    H = (H << 1) | (L >> 63);
+    L <<= 1;
+    shift = 1;
+  }
+}
+
 // 2^(-x) for a double x >= 0 (its bits read by integer instructions).
 BPIMD_HD mexp pow2neg(double x, const unsigned long long *table) {
   const unsigned long long b = double_to_bits(x);
   const int E = (int)((b >> 52) & 0x7FF);
   if (E == 0) return mexp{1.0, 0};  // 0 or subnormal: 2^(-x) = 1 to 2^-1000
   const unsigned long long M = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
-  return pow2neg_q(M, E - 1023 - 63, table);
+  return pow2neg_q(M, 0ull, E - 1023 - 63 - 64, table);
 }
 
 // 2^(-x) for x = a * c with a float32 a >= 0 and a double c > 0: the product
-// is formed exactly (24 x 53 bits) and truncated to 64 bits, so the float32
-// argument is not rounded again.
+// is formed exactly (24 x 53 bits), so the float32 argument is not rounded
+// again.
 BPIMD_HD mexp pow2neg_fd(float a, double c, const unsigned long long *table) {
 #ifdef __CUDA_ARCH__
   const unsigned ab = (unsigned)__float_as_int(a);
@@ -124,15 +140,28 @@ BPIMD_HD mexp pow2neg_fd(float a, double c, const unsigned long long *table) {
   if (Ea == 0) return mexp{1.0, 0};
   const unsigned long long cb = double_to_bits(c);
   const int Ec = (int)((cb >> 52) & 0x7FF);
-  const unsigned long long ma = (unsigned long long)((ab & 0x7FFFFFu) | 0x800000u);       // 24 bits
-  const unsigned long long mc = ((cb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;  // 64 bits, top set
-  // ma * mc = hi 2^64 + lo, hi in [2^86-64, 2^88-64) = [2^22, 2^24)
-  const unsigned long long hi = mulhi(ma << 40, mc);  // (ma 2^40) mc / 2^64: in [2^62, 2^64)
-  const int top = (int)(hi >> 63);
-  const unsigned long long M = top ? hi : (hi << 1);  // normalised
-  // value = ma mc 2^(Ea-127-23) 2^(Ec-1023-63) = hi 2^(64-40) ... = M 2^S
-  const int S = (Ea - 127 - 23) + (Ec - 1023 - 63) + 24 - (top ? 0 : 1);
-  return pow2neg_q(M, S, table);
+  const unsigned long long ma = (unsigned long long)((ab & 0x7FFFFFu) | 0x800000u) << 40;  // top bit set
+  const unsigned long long mc = ((cb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+  unsigned long long H, L;
+  int sh;
+  mul128_norm(ma, mc, H, L, sh);
+  // a = ma 2^(Ea-127-63), c = mc 2^(Ec-1023-63): x = (H:L) 2^(Ea-190 + Ec-1086 - sh)
+  return pow2neg_q(H, L, (Ea - 190) + (Ec - 1086) - sh, table);
+}
+
+// 2^(-x) for x = a * c with doubles a >= 0, c > 0: the 53 x 53-bit mantissa
+// product is formed exactly on the integer pipe, so the float64 argument is
+// not rounded again either.
+BPIMD_HD mexp pow2neg_dd(double a, double c, const unsigned long long *table) {
+  const unsigned long long ab = double_to_bits(a), cb = double_to_bits(c);
+  const int Ea = (int)((ab >> 52) & 0x7FF), Ec = (int)((cb >> 52) & 0x7FF);
+  if (Ea == 0) return mexp{1.0, 0};
+  const unsigned long long ma = ((ab & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+  const unsigned long long mc = ((cb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
+  unsigned long long H, L;
+  int sh;
+  mul128_norm(ma, mc, H, L, sh);
+  return pow2neg_q(H, L, (Ea - 1086) + (Ec - 1086) - sh, table);
 }
 
 }  // namespace pow2fx

@@ -27,7 +27,7 @@
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
-#include "exp2_table.cuh"
+#include "pow2_fixed.cuh"
 
 namespace bpimd {
 namespace {
@@ -83,7 +83,8 @@ __device__ __forceinline__ void bead_springs(const Workspace &w, const double *_
   }
 }
 
-// Particles l0 .. l0+7 of one system (all threads of the block).
+// Particles l0 .. l0+7 of one system (all threads of the block).  MIXED:
+// the float32 bead pass of both mixed forms.
 template <bool MIXED>
 __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double *__restrict__ pos,
                                                double *__restrict__ F, int l0) {
@@ -212,14 +213,15 @@ __device__ __forceinline__ void block_coords(int blk, int &t, int &s) {
 
 // Endpoint beads of one block of g, staged in shared memory: side 0 holds
 // bead P of the 32 particles b of row tile t, side 1 bead 1 of the 32
-// particles a of source tile s.  FP64: x, y, z as doubles.  MIXED: float32
-// high parts then low parts (8 floats), or in a box the 32-bit fixed-point
-// fractions of L (4 words); the same conversions as the bead pass's copies.
+// particles a of source tile s.  FP64: x, y, z as doubles.  MIXED and
+// MIXED32: float32 high parts then low parts (8 floats), or in a box the
+// 32-bit fixed-point fractions of L (4 words); the same conversions as the
+// bead pass's copies.
 struct EndTiles {
   double v[2][TILE][4];
 };
 
-template <bool MIXED>
+template <bool B32>
 __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double *__restrict__ pos, int t, int s,
                                                 EndTiles &E) {
   if (threadIdx.x < 2 * TILE) {
@@ -231,7 +233,7 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
       x = p[0]; y = p[1]; z = p[2];
     }
     double *d = E.v[side][lane];
-    if (!MIXED) {
+    if (!B32) {
       d[0] = x; d[1] = y; d[2] = z;
     } else if (w.pbc) {
       *(uint4 *)d = make_uint4(to_fixed(x, w.invL32), to_fixed(y, w.invL32), to_fixed(z, w.invL32), 0u);
@@ -248,12 +250,19 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
 }
 
 // g for one pair from the staged bead-P position of b (slot j of side 0) and
-// bead-1 position of a (slot i of side 1): returns the mantissa (float or
-// double) and sets the exponent.
-template <bool MIXED, bool PBC>
+// bead-1 position of a (slot i of side 1): returns the mantissa (float for
+// MIXED32, else double in [1, 2)) and sets the exponent.  cx = beta (1/2) k
+// log2(e) > 0, g = 2^(-cx d^2).
+//  FP64   : float64 difference and square; 2^(-cx d^2) from the exact
+//           53 x 53-bit product on the integer pipe (pow2_fixed.cuh).
+//  MIXED  : float32 difference (high/low parts or fixed point) and square,
+//           the same exact product and integer power: float64-accurate
+//           2^(-x) of the float32 closing-spring energy.
+//  MIXED32: float32 difference and square, hardware ex2.approx.
+template <int MODE, bool PBC>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, const EndTiles &E, int i, int j,
-                                              int &e, const double *T64) {
-  if (MIXED) {
+                                              int &e, const unsigned long long *T63) {
+  if (MODE != BPIMD_FP64) {
     float fx, fy, fz;
     if (PBC) {  // minimum image from the fixed-point copies
       const uint4 ub = *(const uint4 *)E.v[0][j], ua = *(const uint4 *)E.v[1][i];
@@ -267,8 +276,14 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
       fy = (bh.y - ah.y) + (bl.y - al.y);
       fz = (bh.z - ah.z) + (bl.z - al.z);
     }
+    const float d2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    if (MODE == BPIMD_MIXED) {
+      const pow2fx::mexp g = pow2fx::pow2neg_fd(d2, cx, T63);
+      e = g.e;
+      return g.m;
+    }
     // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
-    const float x = fmaxf((float)cx * fmaf(fx, fx, fmaf(fy, fy, fz * fz)), -268435456.0f);
+    const float x = fmaxf(-(float)cx * d2, -268435456.0f);
     const float n = floorf(x);
     float mm = ex2_approx(x - n);  // in [1, 2]
     e = (int)n;
@@ -278,15 +293,9 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
     const double *rb = E.v[0][j], *ra = E.v[1][i];
     double dx = rb[0] - ra[0], dy = rb[1] - ra[1], dz = rb[2] - ra[2];
     if (PBC) { dx = mimage(w, dx); dy = mimage(w, dy); dz = mimage(w, dz); }
-    // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
-    const double x = fmax(cx * fma(dx, dx, fma(dy, dy, dz * dz)), -268435456.0);
-    const double n = floor(x);
-    // 2^(x-n), x-n in [0, 1), by the table method: T[k & 63] 2^r in
-    // [0.99, 1.99], its power 2^(k >> 6) and 2^n folded into the exponent
-    int k;
-    const long long b = __double_as_longlong(exp2_table_part(x - n, T64, k));
-    e = (int)n + (k >> 6) + (int)((b >> 52) & 0x7ff) - 1023;
-    return __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const pow2fx::mexp g = pow2fx::pow2neg_dd(fma(dx, dx, fma(dy, dy, dz * dz)), cx, T63);
+    e = g.e;
+    return g.m;
   }
 }
 
@@ -297,25 +306,25 @@ __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, con
 // are coalesced along r.  Entries outside a <= b < N are never written here
 // (gmat_padding_kernel fills them once).
 // One block of g (all threads of the CTA; Tm/Te: 32 x 33 shared tiles).
-template <bool MIXED, bool PBC>
+template <int MODE, bool PBC>
 __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__restrict__ pos, int blk,
-                                           typename std::conditional<MIXED, float, double>::type *Tm, int *Te,
-                                           EndTiles &E, const double *T64) {
-  using M_t = typename std::conditional<MIXED, float, double>::type;
-  const double cx = -w.beta * w.half_k * LOG2E;
+                                           typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type *Tm,
+                                           int *Te, EndTiles &E, const unsigned long long *T63) {
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
+  const double cx = w.beta * w.half_k * LOG2E;
   const int N = w.N;
   M_t *gm = (M_t *)w.gm, *gbm = (M_t *)w.gbm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int t, s;
   block_coords(blk, t, s);
-  stage_endpoints<MIXED>(w, pos, t, s, E);
+  stage_endpoints<MODE != BPIMD_FP64>(w, pos, t, s, E);
   {
     const int b = t * TILE + lane;
     for (int i = warp; i < TILE; i += 8) {
       const int a = s * TILE + i;
       if (b < N && a <= b) {
         int e;
-        const M_t m = (M_t)pair_factor<MIXED, PBC>(w, cx, E, i, lane, e, T64);
+        const M_t m = (M_t)pair_factor<MODE, PBC>(w, cx, E, i, lane, e, T63);
         const size_t idx = (size_t)blk * TILE2 + i * TILE + lane;
         gm[idx] = m;
         w.ge[idx] = e;
@@ -341,24 +350,31 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__r
   __syncthreads();
 }
 
+// Shared-memory copy of the 256-entry table of 2^(-j/256) (FP64 and MIXED
+// pair factors); published by the first barrier of gmat_block.
+__device__ __forceinline__ void pow2_table_init(unsigned long long *T) {
+  for (int j = threadIdx.x; j < 256; j += blockDim.x) T[j] = pow2fx::T63[j];
+}
+
 // One evaluation's preparation: blocks 0..nbead-1 run the bead pass (8
-// particles each), the others stride over the blocks of g.
-template <bool MIXED>
+// particles each), the others stride over the blocks of g.  MODE is the
+// precision form (BPIMD_FP64, BPIMD_MIXED, BPIMD_MIXED32).
+template <int MODE>
 __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__restrict__ pos,
                                                    double *__restrict__ F, int nbead) {
-  using M_t = typename std::conditional<MIXED, float, double>::type;
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
-  __shared__ double T64[64];  // float64 pair factors: 2^(j/64)
-  if (!MIXED) exp2_table_init(T64);  // published by the first barrier of gmat_block
+  __shared__ unsigned long long T63[256];
+  if (MODE != BPIMD_MIXED32) pow2_table_init(T63);
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
-    bead_pass_body<MIXED>(w, pos, F, blockIdx.x * BEAD_WARPS);
+    bead_pass_body<MODE != BPIMD_FP64>(w, pos, F, blockIdx.x * BEAD_WARPS);
   } else {
     for (int blk = blockIdx.x - nbead; blk < w.NB; blk += gridDim.x - nbead) {
-      if (w.pbc) gmat_block<MIXED, true>(w, pos, blk, Tm, Te, E, T64);
-      else gmat_block<MIXED, false>(w, pos, blk, Tm, Te, E, T64);
+      if (w.pbc) gmat_block<MODE, true>(w, pos, blk, Tm, Te, E, T63);
+      else gmat_block<MODE, false>(w, pos, blk, Tm, Te, E, T63);
     }
   }
   pdl_trigger();
@@ -367,27 +383,27 @@ __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__
 // Replica batch: bead_tab[k] = (replica, first particle), blk_tab[k] =
 // (replica, block of g); positions and forces of replica r start at element
 // off[r] of the packed arrays.
-template <bool MIXED>
+template <int MODE>
 __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict__ ws,
                                                     const int2 *__restrict__ bead_tab, int nbead,
                                                     const int2 *__restrict__ blk_tab, int nblk,
                                                     const long long *__restrict__ off,
                                                     const double *__restrict__ pos, double *__restrict__ F) {
-  using M_t = typename std::conditional<MIXED, float, double>::type;
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
   __shared__ M_t Tm[TILE * 33];
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
-  __shared__ double T64[64];  // float64 pair factors: 2^(j/64)
-  if (!MIXED) exp2_table_init(T64);  // published by the first barrier of gmat_block
+  __shared__ unsigned long long T63[256];
+  if (MODE != BPIMD_MIXED32) pow2_table_init(T63);
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
     const int2 e = bead_tab[blockIdx.x];
-    bead_pass_body<MIXED>(ws[e.x], pos + off[e.x], F + off[e.x], e.y);
+    bead_pass_body<MODE != BPIMD_FP64>(ws[e.x], pos + off[e.x], F + off[e.x], e.y);
   } else {
     for (int k = blockIdx.x - nbead; k < nblk; k += gridDim.x - nbead) {
       const int2 e = blk_tab[k];
-      if (ws[e.x].pbc) gmat_block<MIXED, true>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T64);
-      else gmat_block<MIXED, false>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T64);
+      if (ws[e.x].pbc) gmat_block<MODE, true>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T63);
+      else gmat_block<MODE, false>(ws[e.x], pos + off[e.x], e.y, Tm, Te, E, T63);
     }
   }
   pdl_trigger();
@@ -513,8 +529,11 @@ cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaSt
   const int nbead = (w.N + BEAD_WARPS - 1) / BEAD_WARPS;
   const int cap = sm_count() * 8;
   const int grid = nbead + (w.NB < cap ? w.NB : cap);
-  return w.mixed ? launch_pdl(prep_kernel<true>, grid, 256, 0, s, w, pos, F, nbead)
-                 : launch_pdl(prep_kernel<false>, grid, 256, 0, s, w, pos, F, nbead);
+  switch (w.mode) {
+    case BPIMD_FP64: return launch_pdl(prep_kernel<BPIMD_FP64>, grid, 256, 0, s, w, pos, F, nbead);
+    case BPIMD_MIXED: return launch_pdl(prep_kernel<BPIMD_MIXED>, grid, 256, 0, s, w, pos, F, nbead);
+    default: return launch_pdl(prep_kernel<BPIMD_MIXED32>, grid, 256, 0, s, w, pos, F, nbead);
+  }
 }
 
 cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s) {
@@ -526,13 +545,20 @@ cudaError_t launch_gmat_padding(const Workspace &w, cudaStream_t s) {
 }
 
 cudaError_t launch_prep_batched(const Workspace *ws, const int2 *bead_tab, int nbead, const int2 *blk_tab,
-                                int nblk, const long long *off, bool mixed, const double *pos, double *F,
+                                int nblk, const long long *off, int mode, const double *pos, double *F,
                                 int blocks_per_sm, cudaStream_t s) {
   if (nbead <= 0 && nblk <= 0) return cudaSuccess;
   const int cap = sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 8);
   const int grid = nbead + (nblk < cap ? nblk : cap);
-  return mixed ? launch_pdl(prep_batched<true>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F)
-               : launch_pdl(prep_batched<false>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
+  switch (mode) {
+    case BPIMD_FP64:
+      return launch_pdl(prep_batched<BPIMD_FP64>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
+    case BPIMD_MIXED:
+      return launch_pdl(prep_batched<BPIMD_MIXED>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos, F);
+    default:
+      return launch_pdl(prep_batched<BPIMD_MIXED32>, grid, 256, 0, s, ws, bead_tab, nbead, blk_tab, nblk, off, pos,
+                        F);
+  }
 }
 
 cudaError_t launch_gmat_padding_batched(const Workspace *ws, const int2 *tab, int ntab, bool mixed,

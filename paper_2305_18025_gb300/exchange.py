@@ -19,7 +19,7 @@ class ExchangeEnergy:
     def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None, box=0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
-        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        prec = _c.PRECISIONS[precision]
         self.N, self.P = int(N), int(P)
         self.m, self.omega_P, self.beta = float(m), float(omega_P), float(beta)
         self.precision = precision
@@ -120,7 +120,7 @@ class RingPolymerMD:
                  seed=0, precision="fp64", device="cuda", stream=None, lennard_jones=None, box=0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
-        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        prec = _c.PRECISIONS[precision]
         self.N, self.P = int(N), int(P)
         self.device = torch.device(device)
         if self.device.index is None:
@@ -173,7 +173,7 @@ class BatchedExchangeEnergy:
     def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
-        prec = {"fp64": _c.BPIMD_FP64, "mixed": _c.BPIMD_MIXED}[precision]
+        prec = _c.PRECISIONS[precision]
         self.N = [int(n) for n in N]
         self.P = [int(p) for p in P]
         self.R = len(self.N)

@@ -40,11 +40,13 @@ def test_roofline_follows_the_dominant_stage(stage_ms, kernel, monkeypatch):
 
 def test_roofline_prep_counts_the_pair_factor_bytes_of_its_precision(monkeypatch):
     monkeypatch.setattr(bench, "load_traffic", lambda k: None)
+    m32 = bench.roofline([1.0, 0.1, 0.1], ARGS, None, PEAKS, "mixed32")
     mixed = bench.roofline([1.0, 0.1, 0.1], ARGS, None, PEAKS, "mixed")
     fp64 = bench.roofline([1.0, 0.1, 0.1], ARGS, None, PEAKS, "fp64")
     pairs = 1024 * 1025 // 2
-    # both copies of g: 4 more mantissa bytes per entry in float64
-    assert (fp64["achieved"] - mixed["achieved"]) * 1e9 * 1e-3 == pytest.approx(2 * pairs * 4, rel=1e-9)
+    # both copies of g: float64 mantissas in float64 and mixed, float32 in mixed32
+    assert (fp64["achieved"] - m32["achieved"]) * 1e9 * 1e-3 == pytest.approx(2 * pairs * 4, rel=1e-9)
+    assert mixed["achieved"] == fp64["achieved"]
 
 
 def test_traffic_figure_only_while_sources_match(tmp_path, monkeypatch):

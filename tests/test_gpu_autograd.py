@@ -68,7 +68,7 @@ def test_gradient_matches_central_differences(beta):
     eng.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5), ("mixed32", 1e-5)])
 def test_gradient_matches_algorithm_1_and_scales(prec, tol):
     N, P, beta = 300, 16, 1.3
     pos = inputs.clustered_chain_positions(N, P, seed=202)

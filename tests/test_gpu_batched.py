@@ -19,7 +19,7 @@ from paper_2305_18025_gb300.exchange import BatchedExchangeEnergy, ExchangeEnerg
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda", 0)
-TOL = {"fp64": dict(v=1e-12, f=1e-10), "mixed": dict(v=1e-6, f=1e-5)}
+TOL = {"fp64": dict(v=1e-12, f=1e-10), "mixed": dict(v=1e-6, f=1e-5), "mixed32": dict(v=1e-6, f=1e-5)}
 
 
 def reference(pos, wP, beta):
@@ -74,7 +74,7 @@ def make(kind, N, P, seed):
     return inputs.coincident_positions(N, P)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_mixed_batch_matches_oracle(prec):
     systems = [(make(k, N, P, 500 + i), b) for i, (N, P, b, k) in enumerate(MIX)]
     V, Fs, eng, _ = run_batch(systems, prec)
@@ -82,7 +82,7 @@ def test_mixed_batch_matches_oracle(prec):
     eng.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_256_replica_workload(prec):
     reps = inputs.batched_replicas(256, seed=11)
     systems = [(rep.positions, rep.beta) for rep in reps]

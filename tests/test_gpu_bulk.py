@@ -40,7 +40,7 @@ def reference(pos, m, wP, beta, L):
     return float(VB), np.asarray(F, dtype=np.float64)
 
 
-@pytest.mark.parametrize("prec,tv,tf", [("fp64", 1e-12, 1e-10), ("mixed", 1e-6, 1e-5)])
+@pytest.mark.parametrize("prec,tv,tf", [("fp64", 1e-12, 1e-10), ("mixed", 1e-6, 1e-5), ("mixed32", 1e-6, 1e-5)])
 @pytest.mark.parametrize("N,P,L,spread", [(20, 4, 3.0, 0.3), (100, 8, 5.0, 0.4), (300, 6, 8.0, 0.5)])
 def test_exchange_in_a_box_matches_oracle(prec, tv, tf, N, P, L, spread):
     beta = 1.0
@@ -63,7 +63,7 @@ def test_exchange_in_a_box_matches_oracle(prec, tv, tf, N, P, L, spread):
     eng.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-5), ("mixed32", 1e-5)])
 @pytest.mark.parametrize("cells", [3, 4])
 def test_helium_md_matches_oracle(prec, tol, cells):
     """cells = 3: 108 atoms, L = 17.0 A < 3 rc (all pairs); cells = 4: 256

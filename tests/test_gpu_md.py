@@ -19,7 +19,7 @@ from paper_2305_18025_gb300.exchange import RingPolymerMD
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-5}
+TOL = {"fp64": 1e-10, "mixed": 1e-5, "mixed32": 1e-5}
 
 
 def _start(N, P, seed):
@@ -44,7 +44,7 @@ def _run_gpu(pos, vel, beta, prec, nsteps, calls=1, stream=None, **kw):
     return out
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("stream", [None, "side"])
 @pytest.mark.parametrize("N,P,beta,pair", [(16, 8, 2.0, True), (5, 4, 1.0, False), (40, 6, 1.5, True)])
 def test_md_trajectory_matches_oracle(prec, stream, N, P, beta, pair):
@@ -85,7 +85,7 @@ def test_md_nve_energy_is_conserved():
     md.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_md_harmonic_closed_form_and_equipartition(prec):
     """N = 4 trapped bosons, P = 8, beta = 2 (beta hbar w0 = 2): <E_prim> equals
     -d ln Z/d beta of the P-bead discretisation (closed form), <KE> = 3NP/(2 beta)."""

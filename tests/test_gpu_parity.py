@@ -23,7 +23,8 @@ from paper_2305_18025_gb300.exchange import ExchangeEnergy
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": dict(v=1e-12, f=1e-10, fmax=1e-10, pot=1e-12, M=1e-10),
-       "mixed": dict(v=1e-6, f=1e-5, fmax=None, pot=1e-6, M=1e-5)}
+       "mixed": dict(v=1e-6, f=1e-5, fmax=None, pot=1e-6, M=1e-5),
+       "mixed32": dict(v=1e-6, f=1e-5, fmax=None, pot=1e-6, M=1e-5)}
 
 
 def gen(kind, N, P, seed):
@@ -100,7 +101,7 @@ def check(pos, beta, prec, want_M=True, m=1.0):
     return gV, gF
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("N,P,kind", [
     (1, 2, "trapped"), (1, 5, "trapped"), (2, 3, "trapped"), (3, 4, "clustered"),
     (5, 2, "clustered"), (16, 8, "trapped"), (31, 8, "clustered"), (32, 8, "trapped"),
@@ -111,7 +112,7 @@ def test_parity_small(prec, N, P, kind):
     check(gen(kind, N, P, seed=1000 + N), beta=1.3, prec=prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("N", [1280, 1281, 1313])
 def test_parity_cluster_size_switch(prec, N):
     """The recursion switches from 8- to 16-CTA clusters above N = 1280 (40
@@ -120,19 +121,19 @@ def test_parity_cluster_size_switch(prec, N):
     check(inputs.trapped_positions(N, 4, seed=N), beta=1.0, prec=prec, want_M=False)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("beta", [0.5, 1.0, 2.0, 4.0])
 def test_parity_beta_sweep(prec, beta):
     check(inputs.trapped_positions(64, 32, seed=7), beta=beta, prec=prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_parity_headline_size(prec):
     """N = 1024, P = 32, beta = 1: the throughput configuration, element by element."""
     check(inputs.trapped_positions(1024, 32, seed=3), beta=1.0, prec=prec, want_M=False)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_parity_large_n(prec):
     """N = 4096, P = 64 (liquid-helium-sized system, trapped inputs)."""
     check(inputs.clustered_chain_positions(4096, 64, seed=5), beta=1.0, prec=prec, want_M=False)
@@ -153,7 +154,7 @@ def load_referee(name):
     return d
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_parity_maximum_size(prec):
     """Largest N the recursion kernel accepts (6912), against sampled outputs of
     the long-double oracle stored by tests/golden/make_referee_samples.py."""
@@ -205,7 +206,7 @@ def test_host_entry_point_matches_device():
     assert torch.equal(Fh, F.cpu())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_entry_point_pinned_and_pageable(prec, pinned):
     """Pinned and pageable host buffers give the device entry point's bits,

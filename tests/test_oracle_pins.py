@@ -390,6 +390,24 @@ def test_harmonic_recursion_matches_cycle_index():
         assert harmonic.mean_energy(N, P, beta) == pytest.approx(fd, rel=1e-7)
 
 
+def test_harmonic_trap_energy_limits():
+    """<U-bar> at P -> infinity is half the energy (virial theorem of the
+    harmonic Hamiltonian, <T> = <U>, which holds for bosons as for any
+    eigenstate mixture); at P = 1 (classical) it is dim N / (2 beta) for N = 1;
+    and it is -(w0/(2 beta)) d ln Z/d w0 by central differences of the
+    unscaled partition function."""
+    for N in (1, 8):
+        for beta in (0.5, 2.0):
+            assert harmonic.mean_trap_energy(N, 200000, beta) == pytest.approx(
+                0.5 * harmonic.mean_energy(N, 200000, beta), rel=1e-7)
+    assert harmonic.mean_trap_energy(1, 1, 1.7) == pytest.approx(1.5 / 1.7, rel=1e-12)
+    P, beta, w0, h = 10, 1.3, 0.8, 1e-6
+    for N in (1, 4):
+        fd = (math.log(harmonic.partition_function(N, P, beta, w0 + h))
+              - math.log(harmonic.partition_function(N, P, beta, w0 - h))) / (2 * h)
+        assert harmonic.mean_trap_energy(N, P, beta, w0) == pytest.approx(-(w0 / (2 * beta)) * fd, rel=1e-7)
+
+
 def test_harmonic_ground_state_limit():
     """beta -> infinity at large P: all bosons in the ground state, 1.5 N w0."""
     assert harmonic.mean_energy(16, 100000, 60.0) == pytest.approx(1.5 * 16, rel=1e-6)

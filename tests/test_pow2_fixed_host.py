@@ -30,7 +30,13 @@ int main() {
   float a;
   while (std::scanf("%%7s", kind) == 1) {
     bpimd::pow2fx::mexp r;
-    if (kind[0] == 'd') {
+    if (kind[0] == 'p') {
+      unsigned long long b1, b2;
+      std::scanf("%%llx %%llx", &b1, &b2);
+      std::memcpy(&x, &b1, 8);
+      std::memcpy(&c, &b2, 8);
+      r = bpimd::pow2fx::pow2neg_dd(x, c, bpimd::pow2fx::T63);
+    } else if (kind[0] == 'd') {
       unsigned long long b;
       std::scanf("%%llx", &b);
       std::memcpy(&x, &b, 8);
@@ -126,3 +132,18 @@ def test_integer_arguments_are_exact_powers(exe):
     got = run(exe, ["d " + dbits(float(k)) for k in range(0, 2000, 7)])
     for k, (m, e) in zip(range(0, 2000, 7), got):
         assert (m, e) == (1.0, -k)
+
+
+def test_double_times_double_is_exact_before_the_power(exe):
+    """x = a * c for two doubles, the 106-bit product truncated to 64 bits on
+    the integer pipe (the float64 path of the pair factors)."""
+    mp.dps = 50
+    rng = np.random.default_rng(2)
+    a = rng.uniform(0, 30, 500) ** 2
+    c = -np.log(rng.uniform(0.01, 1, 500)) * 3.1
+    lines = ["p " + dbits(float(ai)) + " " + dbits(float(ci)) for ai, ci in zip(a, c)]
+    worst = 0.0
+    for ai, ci, (m, e) in zip(a, c, run(exe, lines)):
+        exact = power(2, -(mpf(float(ai)) * mpf(float(ci))))
+        worst = max(worst, float(rel_err(m, e, exact)))
+    assert worst <= 1.2 * 2.0 ** -53, worst

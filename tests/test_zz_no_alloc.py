@@ -17,7 +17,7 @@ from paper_2305_18025_gb300.exchange import ExchangeEnergy
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": (1e-12, 1e-10), "mixed": (1e-6, 1e-5)}
+TOL = {"fp64": (1e-12, 1e-10), "mixed": (1e-6, 1e-5), "mixed32": (1e-6, 1e-5)}
 
 
 def with_context(pos, beta, prec):
@@ -30,7 +30,7 @@ def with_context(pos, beta, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_noalloc_matches_context_entry_point_on_consecutive_calls(prec):
     beta = 1.0
     cases = [(bpimd.BPIMD_NOALLOC_MAX_N, 8, 11), (100, 16, 12)]  # largest size, then a smaller one
@@ -39,7 +39,7 @@ def test_noalloc_matches_context_entry_point_on_consecutive_calls(prec):
         pos = torch.from_numpy(inputs.trapped_positions(N, P, seed)).cuda()
         V_ref, F_ref = with_context(pos, beta, prec)
         cfg = bpimd.make_config(N, P, 1.0, inputs.omega_P(P, beta), beta,
-                                bpimd.BPIMD_FP64 if prec == "fp64" else bpimd.BPIMD_MIXED)
+                                bpimd.PRECISIONS[prec])
         for _ in range(2):  # two calls in a row share the scratch array
             V = torch.full((), float("nan"), dtype=torch.float64, device="cuda:0")
             F = torch.full_like(pos, float("nan"))
@@ -82,7 +82,7 @@ print(dv, df)
 """
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
 def test_noalloc_as_the_first_call_of_a_fresh_process(prec):
     """A caller whose very first library call is the allocation-free entry
     point (no context exists yet, so the scratch address and the recursion
@@ -91,8 +91,7 @@ def test_noalloc_as_the_first_call_of_a_fresh_process(prec):
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    code = FIRST_CALL_SCRIPT.format(root=root, name=prec,
-                                    prec=bpimd.BPIMD_FP64 if prec == "fp64" else bpimd.BPIMD_MIXED)
+    code = FIRST_CALL_SCRIPT.format(root=root, name=prec, prec=bpimd.PRECISIONS[prec])
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     dv, df = (float(x) for x in r.stdout.split()[-2:])

@@ -192,6 +192,77 @@ def roofline(stage_ms_per_eval, args, sm_mhz, peaks, precision="mixed"):
     return obj
 
 
+# Counted per-pair work of the O(N^2) stages (thread-level operations of the
+# kernels as written; the counts are listed with the kernels' rooflines):
+#   probability pass, float64: 13 float64 ops per pair (bead differences,
+#     Pr = alpha mu g, row and column terms) + 20 float64 adds of the column
+#     butterfly (4 sums x 5 levels, every lane) = 33 float64 ops;
+#   probability pass, mixed: 2 64 x 64-bit high products (alpha mu, then g)
+#     = 8 integer 32 x 32 -> 64 multiply-adds per pair;
+#   probability pass, mixed32: float32 only (12 ops per pair + 20 butterfly adds);
+#   pair factors, float64: 6 float64 ops per pair (difference and square);
+#   pair factors, mixed: the 128-bit product and 6 64-bit high products of
+#     the integer power (pow2_fixed.cuh) = 28 integer multiply-adds.
+PROB_F64_OPS, PROB_MIXED_IMADS, PROB_M32_F32OPS = 33, 8, 32
+G_F64_OPS, G_MIXED_IMADS = 6, 28
+
+
+def measure_unit_peaks(dev, stream, iters=2000):
+    """Throughput of the float64 pipe and of 32-bit integer multiply-adds over
+    the whole GPU, by the library's probe kernels (CUDA events, best of 3)."""
+    import torch
+    from paper_2305_18025_gb300 import bpimd
+    sink = torch.empty(8 * 8 * 256, dtype=torch.float64, device=dev)
+    out = {}
+    for kind, name in ((0, "fp64_fma_per_s"), (1, "int_mad_per_s")):
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = bpimd.bpimd_peak_probe(kind, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            rate = ops / (e0.elapsed_time(e1) * 1e-3)
+            best = rate if best is None else max(best, rate)
+        out[name] = best
+    return out
+
+
+def roofline_stages(stage_ms_per_eval, args, sm_mhz, peaks, unit_peaks, precision):
+    """A roofline fraction for each stage of one evaluation: the bead pass
+    with pair factors against HBM (and, in float64, the float64 pipe), the
+    recursions against their dependent-step floor, the probability pass
+    against the unit its per-pair work loads (counts above)."""
+    N = args.N
+    pairs = N * (N + 1) / 2
+    t_prep, t_rec, t_prob = (x * 1e-3 for x in stage_ms_per_eval)
+    prep = roofline([1.0, 0.0, 0.0], args, sm_mhz, peaks, precision)  # HBM bytes of the stage
+    prep["achieved"] = prep["achieved"] * 1e-3 / t_prep  # roofline() was given 1 ms
+    prep["frac"] = prep["achieved"] / prep["peak"]
+    if precision == "fp64":
+        prep["fp64_pipe_frac"] = G_F64_OPS * pairs / t_prep / unit_peaks["fp64_fma_per_s"]
+    elif precision == "mixed":
+        prep["int_pipe_frac"] = G_MIXED_IMADS * pairs / t_prep / unit_peaks["int_mad_per_s"]
+    rec = roofline([0.0, 1.0, 0.0], args, sm_mhz, peaks, precision)
+    rec["achieved"] = N / t_rec
+    rec["frac"] = rec["achieved"] / rec["peak"]
+    if precision == "fp64":
+        prob = {"bound": "fp64", "unit": "float64 ops/s", "achieved": PROB_F64_OPS * pairs / t_prob,
+                "peak": unit_peaks["fp64_fma_per_s"], "peak_source": "library float64 FMA probe (measured)"}
+    elif precision == "mixed":
+        prob = {"bound": "int", "unit": "32-bit integer multiply-adds/s", "achieved": PROB_MIXED_IMADS * pairs / t_prob,
+                "peak": unit_peaks["int_mad_per_s"], "peak_source": "library integer multiply-add probe (measured)"}
+    else:
+        fp32_peak = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6 * 152 * 128
+        prob = {"bound": "fp32", "unit": "float32 ops/s", "achieved": PROB_M32_F32OPS * pairs / t_prob,
+                "peak": fp32_peak, "peak_source": "nominal 128 float32 lanes per SM x 152 SMs x sampled clock"}
+    prob["frac"] = prob["achieved"] / prob["peak"]
+    prob["kernel"] = "prob_forces"
+    for r in (prep, rec):
+        r.pop("traffic", None)
+    return {"prep": prep, "recursions": rec, "prob_forces": prob}
+
+
 # ----------------------------------------------------- replicas across ranks
 def reduce_max(x, dist, device):
     """The largest of every rank's x (the slowest rank's time); x itself on one rank."""
@@ -245,6 +316,7 @@ def run_ours(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     sampler.start()
     results = {}
+    unit_peaks = measure_unit_peaks(dev, torch.cuda.current_stream(dev))
     # the context's own stream (as an application would bind one); the L2
     # flush and the timing events go on the same stream
     stream = torch.cuda.Stream(dev)
@@ -325,12 +397,15 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": results["e2e"],
         "roofline": roof,
+        "unit_peaks": unit_peaks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, pos_np, wP)
         line["cpu_context"] = cpu_context(args)
     line.update({
         "stages_ms": {p: dict(zip(STAGE_NAMES, results[p]["stage_ms"])) for p in ("mixed", "fp64", "mixed32")},
+        "roofline_stages": {p: roofline_stages(results[p]["stage_ms"], args, clocks.get("sm_mhz"), peaks, unit_peaks, p)
+                            for p in ("mixed", "fp64", "mixed32")},
         "V_B": {p: results[p]["V_B"] for p in ("mixed", "fp64", "mixed32")},
         "batched": results["batched"],
         "helium": results["helium"],

@@ -99,6 +99,21 @@ extern "C" {
 #define BPIMD_MIXED 1
 #define BPIMD_MIXED32 2
 
+/* ------------------------------------------------------------ storage */
+/* Largest N a single system accepts. */
+#define BPIMD_MAX_N 16384
+/* Up to this N a context tabulates the pair Boltzmann factors g(u, v) of the
+ * closing springs once per evaluation (two coalesced copies, O(N^2) device
+ * memory: 12 or 16 bytes per pair and copy, ~0.8 GB at N = 8192) and the
+ * probability pass keeps O(N^2 / 32) block partial sums.  Above it -- or at
+ * any N when cfg.flags has BPIMD_FLAG_RECOMPUTE -- nothing O(N^2) is stored:
+ * the recursions and the probability pass recompute each g where they use it
+ * (the same bits), and the probability pass forms every pair twice, once for
+ * its row and once for its column, so that each force sum is completed by one
+ * CTA.  Device memory is then O(N + N P). */
+#define BPIMD_STORE_MAX_N 8192
+#define BPIMD_FLAG_RECOMPUTE 1
+
 /* --------------------------------------------------------- pair potentials */
 #define BPIMD_PAIR_NONE 0
 #define BPIMD_PAIR_GAUSSIAN 1 /* g exp(-r^2 / (2 s^2)) between same-index beads */
@@ -119,7 +134,7 @@ typedef struct {
   double omega_P;
   double beta;
   int32_t precision; /* BPIMD_FP64, BPIMD_MIXED or BPIMD_MIXED32 */
-  int32_t flags;     /* reserved, must be 0 */
+  int32_t flags;     /* 0 or BPIMD_FLAG_RECOMPUTE; other bits must be 0 */
   /* molecular dynamics (bpimd_step) */
   double dt;         /* time step                                   */
   double gamma;      /* Langevin friction (0 = NVE)                  */
@@ -140,8 +155,9 @@ typedef struct {
   uint64_t seed;     /* counter-based RNG key for the thermostat      */
 } bpimd_config;
 
-/* Create a context for one system.  Validates cfg (BPIMD_ERR_ARG), allocates
- * the O(N^2) workspace on the current CUDA device (BPIMD_ERR_NOMEM), binds
+/* Create a context for one system.  Validates cfg (BPIMD_ERR_ARG; 1 <= N <=
+ * BPIMD_MAX_N), allocates the workspace on the current CUDA device
+ * (BPIMD_ERR_NOMEM; O(N^2) up to BPIMD_STORE_MAX_N, else O(N P)), binds
  * `cuda_stream` (a cudaStream_t, NULL = default stream).  On error *out is set
  * to NULL.  Destroy with bpimd_destroy. */
 int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream);
@@ -207,6 +223,13 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M);
  * graph (bound to these position/velocity buffers) and replayed.
  * Lennard-Jones in a box of at least 3 cutoffs per side runs on cell lists
  * (O(N P) per step); otherwise pairs are summed over all partners.
+ * On a replica-batch context (bpimd_create_batched) every replica advances by
+ * the same steps: positions and velocities are the packed arrays of the batch,
+ * dt, gamma, omega0, the Gaussian pair potential and the seed are shared,
+ * each replica is thermostatted at kT = 1/beta_r (or cfg.kT_bead), the
+ * thermostat counter is the element index in the packed array, and energies
+ * (if not NULL) receives 4 float64 per replica in replica order.  Batches
+ * take no Lennard-Jones pairs (they have no periodic box).
  * Errors: BPIMD_ERR_ARG for nsteps < 0, misaligned pointers, dt <= 0,
  * gamma < 0, kT_bead < 0, omega0 < 0, an unknown pair_type, a Gaussian width
  * or Lennard-Jones sigma <= 0, a Lennard-Jones cutoff <= 0 or above box_L/2.
@@ -217,20 +240,25 @@ int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities,
 /* --------------------------------------------------------- replica batches */
 /* Many independent systems ("replicas") of uneven size and temperature
  * evaluated together: the same Algorithm 1 per replica, three kernel launches
- * per batch whatever the number of replicas.  The paper has no batched form;
+ * per batch whatever the number of replicas, plus one recursion launch per
+ * replica with N > 4096 (those take the cluster recursion kernel of single
+ * systems; the other replicas run one CTA per recursion).  The paper has no batched form;
  * it serves workloads such as parallel tempering or many small trapped
  * systems that are too small to fill a GPU one at a time.
  *
- * bpimd_create_batched: cfg supplies m, precision and flags (its N, P,
- * omega_P, beta and MD fields are ignored); host arrays of length R give each
- * replica's N[r] (1..4096), P[r] (>= 2), omega_P[r] and beta[r] (> 0, finite).
+ * bpimd_create_batched: cfg supplies m, precision, flags (0) and the
+ * molecular-dynamics fields (its N, P, omega_P and beta are ignored); host
+ * arrays of length R give each
+ * replica's N[r] (1..BPIMD_STORE_MAX_N), P[r] (>= 2), omega_P[r] and beta[r] (> 0, finite).
  * Packed layout of positions and forces: replica r occupies
  * [N[r]][P[r]][3] float64 starting at element offset
  * off[r] = 3 * sum_{q<r} N[q] P[q] (bpimd_batch_info returns them).
  * Errors: BPIMD_ERR_ARG (sizes, parameters), BPIMD_ERR_NOMEM.  Single-system
  * calls on a batch context (and batch calls on a single-system context)
- * return BPIMD_ERR_STATE; bpimd_sync, bpimd_profile_* and bpimd_destroy work
- * on both. */
+ * return BPIMD_ERR_STATE; bpimd_step (molecular dynamics of every replica),
+ * bpimd_sync, bpimd_profile_* and bpimd_destroy work on both.  cfg's
+ * molecular-dynamics fields (dt, gamma, kT_bead, omega0, the Gaussian pair
+ * potential, seed) are used by bpimd_step. */
 int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R,
                          const int32_t *N, const int32_t *P, const double *omega_P,
                          const double *beta, void *cuda_stream);
@@ -298,6 +326,19 @@ int bpimd_profile_end(bpimd_ctx *ctx, double *stage_ms, int *n_evals);
 #define BPIMD_NOALLOC_MAX_N 256
 int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, const double *positions,
                                          double *V_B, double *forces, void *cuda_stream);
+
+/* --------------------------------------------------- throughput probes */
+/* Measurement utility for roofline figures (no counterpart in the paper):
+ * enqueue one compute-bound kernel on cuda_stream (a cudaStream_t, NULL =
+ * default stream) that keeps every SM busy with independent chains of
+ *   kind 0: float64 fused multiply-adds (the float64 pipe),
+ *   kind 1: 32 x 32 -> 64-bit integer multiply-adds (the integer pipe),
+ * `iters` per chain, and return in *ops (may be NULL) the number of
+ * multiply-adds it performs.  The caller times it (CUDA events on the same
+ * stream) and divides.  sink: a device buffer of at least 8 * 8 * SMs bytes
+ * (8-byte aligned) that the kernel writes only in a case that never occurs.
+ * Asynchronous; BPIMD_ERR_ARG for another kind, iters < 1 or a bad sink. */
+int bpimd_peak_probe(int32_t kind, int64_t iters, void *sink, void *cuda_stream, int64_t *ops);
 
 /* Human-readable text for a status code (static storage). */
 const char *bpimd_status_string(int status);

@@ -81,6 +81,8 @@ class _Oracle:
             lib.ora_thermostat_normals.restype = None
             lib.ora_set_box.argtypes = [self._ctype]
             lib.ora_set_box.restype = None
+            lib.ora_set_noise_offset.argtypes = [ctypes.c_uint64]
+            lib.ora_set_noise_offset.restype = None
             self._lib = lib
         return self._lib
 
@@ -240,12 +242,15 @@ class _Oracle:
         return U[0], F
 
     def md_run(self, pos, vel, m, omega_P, beta, dt, gamma, nsteps, omega0=0.0, pair_type=0,
-               pair_a=0.0, pair_b=1.0, kT=0.0, seed=0, step0=0, pair_rc=0.0, box=0.0):
-        """nsteps BAOAB steps; returns (pos, vel, energies[4]) as new arrays."""
+               pair_a=0.0, pair_b=1.0, kT=0.0, seed=0, step0=0, pair_rc=0.0, box=0.0, elem0=0):
+        """nsteps BAOAB steps; returns (pos, vel, energies[4]) as new arrays.
+        elem0: element offset of the thermostat counters (a replica at that
+        offset of a packed batch; 0 for a single system)."""
         pos = self._pos(pos).copy()
         vel = self._arr(vel).copy()
         N, P, _ = pos.shape
         en = np.zeros(4, dtype=self.dtype)
+        self.lib().ora_set_noise_offset(int(elem0))
         self._check(self.lib().ora_md_run(N, P, m, omega_P, beta, dt, gamma, kT, omega0, pair_type,
                                           pair_a, pair_b, pair_rc, box, seed, step0, nsteps, self._p(pos),
                                           self._p(vel), self._p(en)), "md_run")

@@ -122,6 +122,10 @@ int ora_external_forces(int N, int P, ora_real m, ora_real omega0, int pair_type
                         ora_real pb, ora_real pc, ora_real L, const ora_real *pos, ora_real *F,
                         ora_real *ubar);
 
+/* Element offset of the thermostat counters for the next ora_md_run (a
+ * replica at element offset e0 of a packed batch); reset to 0 by it. */
+void ora_set_noise_offset(uint64_t e0);
+
 /* nsteps BAOAB Langevin steps in place (kT <= 0: 1/beta; L > 0: periodic box
  * for the springs and the pairs); energies (may be NULL): [0] V^{[1,N]},
  * [1] U-bar, [2] kinetic, [3] primitive estimator. */

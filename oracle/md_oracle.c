@@ -69,11 +69,19 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Standard normals for elements 0..n-1 of step `step` (mapping in the header). */
+/* Index of the first element in the counter mapping: 0 for a single system;
+ * a replica of a packed batch takes the counters of its elements' positions
+ * in the packed array (set by ora_set_noise_offset, reset by ora_md_run). */
+static uint64_t ora_noise_e0 = 0;
+void ora_set_noise_offset(uint64_t e0) { ora_noise_e0 = e0; }
+
+/* Standard normals for elements 0..n-1 of step `step` (mapping in the header);
+ * element i takes word (e0 + i) mod 4 of the block with counter (e0 + i) div 4. */
 void ora_thermostat_normals(uint64_t seed, uint64_t step, int64_t n, double *z) {
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   const double two_pi = 6.283185307179586476925286766559;
-  for (int64_t g = 0; 4 * g < n; ++g) {
+  const uint64_t e0 = ora_noise_e0;
+  for (uint64_t g = e0 / 4; 4 * g < e0 + (uint64_t)n; ++g) {
     const uint32_t ctr[4] = {(uint32_t)g, (uint32_t)step, (uint32_t)(step >> 32), 0u};
     uint32_t x[4];
     ora_philox4x32_10(ctr, key, x);
@@ -82,7 +90,10 @@ void ora_thermostat_normals(uint64_t seed, uint64_t step, int64_t n, double *z) 
     const double ra = sqrt(-2.0 * log(u[0])), rb = sqrt(-2.0 * log(u[2]));
     const double zz[4] = {ra * cos(two_pi * u[1]), ra * sin(two_pi * u[1]),
                           rb * cos(two_pi * u[3]), rb * sin(two_pi * u[3])};
-    for (int i = 0; i < 4 && 4 * g + i < n; ++i) z[4 * g + i] = zz[i];
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t e = 4 * g + (uint64_t)i;
+      if (e >= e0 && e < e0 + (uint64_t)n) z[e - e0] = zz[i];
+    }
   }
 }
 
@@ -212,6 +223,7 @@ int ora_md_run(int N, int P, ora_real m, ora_real omega_P, ora_real beta, ora_re
     energies[3] = 3.0 * N * P / (2.0 * beta) - spring + ubar;
   }
   ora_set_box(0.0);
+  ora_noise_e0 = 0;
   free(F);
   free(M);
   free(z);

@@ -25,6 +25,9 @@ BPIMD_FP64 = 0
 BPIMD_MIXED = 1
 BPIMD_MIXED32 = 2
 PRECISIONS = {"fp64": BPIMD_FP64, "mixed": BPIMD_MIXED, "mixed32": BPIMD_MIXED32}
+BPIMD_MAX_N = 16384
+BPIMD_STORE_MAX_N = 8192
+BPIMD_FLAG_RECOMPUTE = 1
 
 BPIMD_PAIR_NONE = 0
 BPIMD_PAIR_GAUSSIAN = 1
@@ -36,7 +39,7 @@ EXPORTED = [
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
     "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
     "bpimd_create_batched", "bpimd_exchange_energy_forces_batched", "bpimd_batch_info",
-    "bpimd_batch_set_tuning",
+    "bpimd_batch_set_tuning", "bpimd_peak_probe",
 ]
 BATCH_MAX_N = 4096
 BPIMD_NUM_STAGES = 3
@@ -99,6 +102,7 @@ def load(build_if_missing=True):
     lib.bpimd_exchange_energy_forces_batched.argtypes = [vp, vp, vp, vp]
     lib.bpimd_batch_info.argtypes = [vp, vp, vp, vp]
     lib.bpimd_batch_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.bpimd_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("bpimd_status_string", "bpimd_version"):
             getattr(lib, name).restype = ip
@@ -249,3 +253,12 @@ def make_config(N, P, m, omega_P, beta, precision=BPIMD_FP64, **md):
     for k, v in md.items():
         setattr(cfg, k, v)
     return cfg
+
+
+def bpimd_peak_probe(kind, iters, sink, stream=None):
+    """Enqueue the throughput probe (kind 0: float64 FMA, 1: integer 32x32->64
+    multiply-add); returns the number of multiply-adds it performs."""
+    ops = ctypes.c_int64(0)
+    _check(load().bpimd_peak_probe(int(kind), int(iters), _ptr(sink), _stream_handle(stream), ctypes.byref(ops)),
+           "bpimd_peak_probe")
+    return ops.value

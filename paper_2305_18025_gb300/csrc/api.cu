@@ -23,7 +23,7 @@ int validate(const bpimd_config *c) {
   if ((long long)c->N * c->P > (1LL << 31) / 3) return BPIMD_ERR_ARG;
   if (!finite_pos(c->m) || !finite_pos(c->omega_P) || !finite_pos(c->beta)) return BPIMD_ERR_ARG;
   if (!valid_precision(c->precision)) return BPIMD_ERR_ARG;
-  if (c->flags != 0) return BPIMD_ERR_ARG;
+  if (c->flags & ~BPIMD_FLAG_RECOMPUTE) return BPIMD_ERR_ARG;
   if (!(c->box_L >= 0.0) || !std::isfinite(c->box_L)) return BPIMD_ERR_ARG;
   return BPIMD_OK;
 }
@@ -69,6 +69,7 @@ namespace bpimd {
 size_t layout_workspace(Workspace &w, char *base) {
   const size_t N = w.N, NB = w.NB, NT = w.NT, gelems = NB * TILE2;
   const size_t gm_bytes = (w.mixed ? sizeof(float) : sizeof(double)) * gelems;
+  const bool tables = !w.recomp;  // recompute mode: nothing O(N^2)
   size_t off = 0;
   auto take = [&](size_t bytes) -> char * {
     char *p = base ? base + off : nullptr;
@@ -86,10 +87,10 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.nexp = (int *)take(sizeof(int) * N);
   w.Ap = (double *)take(sizeof(double) * N);
   w.C = (double *)take(sizeof(double) * (N + 1));
-  w.gm = (void *)take(gm_bytes);
-  w.ge = (int *)take(sizeof(int) * gelems);
-  w.gbm = (void *)take(gm_bytes);
-  w.gbe = (int *)take(sizeof(int) * gelems);
+  w.gm = tables ? (void *)take(gm_bytes) : nullptr;
+  w.ge = tables ? (int *)take(sizeof(int) * gelems) : nullptr;
+  w.gbm = tables ? (void *)take(gm_bytes) : nullptr;
+  w.gbe = tables ? (int *)take(sizeof(int) * gelems) : nullptr;
   w.yfm = (double *)take(sizeof(double) * (N + 1));
   w.yfe = (int *)take(sizeof(int) * (N + 1));
   w.ybm = (double *)take(sizeof(double) * (N + 1));
@@ -98,10 +99,10 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.ale = (int *)take(sizeof(int) * N);
   w.scal = (double *)take(sizeof(double) * 4);
   w.scal_i = (int *)take(sizeof(int) * 4);
-  w.rowpart = (double *)take(sizeof(double) * NB * TILE * 4);
-  w.colpart = (double *)take(sizeof(double) * NB * TILE * 4);
-  w.rowcnt = (int *)take(sizeof(int) * NT);
-  w.colcnt = (int *)take(sizeof(int) * NT);
+  w.rowpart = tables ? (double *)take(sizeof(double) * NB * TILE * 4) : nullptr;
+  w.colpart = tables ? (double *)take(sizeof(double) * NB * TILE * 4) : nullptr;
+  w.rowcnt = tables ? (int *)take(sizeof(int) * NT) : nullptr;
+  w.colcnt = tables ? (int *)take(sizeof(int) * NT) : nullptr;
   w.status = (int *)take(sizeof(int) * 4);
   return off;
 }
@@ -201,6 +202,8 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
+  w.cx = w.beta * w.half_k * LOG2E;
+  w.recomp = (cfg->flags & BPIMD_FLAG_RECOMPUTE) || cfg->N > BPIMD_STORE_MAX_N;
   set_box(w, cfg->box_L);
   const size_t N = w.N;
   // one allocation: the workspace, then the diagnostic potentials
@@ -217,7 +220,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   ctx->d_Vf = (double *)(b + wbytes);
   ctx->d_Vb = (double *)(b + wbytes + align_up(sizeof(double) * (N + 1)));
   if (cudaMemsetAsync(ctx->dev_block, 0, off, ctx->stream) != cudaSuccess ||
-      launch_gmat_padding(w, ctx->stream) != cudaSuccess ||
+      (!w.recomp && launch_gmat_padding(w, ctx->stream) != cudaSuccess) ||
       cudaMallocHost(&ctx->host_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ctx->dev_block);
@@ -317,11 +320,11 @@ int bpimd_connection_probabilities(bpimd_ctx *ctx, double *M) {
 
 int bpimd_step(bpimd_ctx *ctx, double *positions, double *velocities, int32_t nsteps, double *energies) {
   if (!ctx || nsteps < 0) return BPIMD_ERR_ARG;
-  if (ctx->R) return BPIMD_ERR_STATE;
   int rc;
   if ((rc = check_ptr(positions)) || (rc = check_ptr(velocities))) return rc;
   if (energies && (((uintptr_t)energies) & 7)) return BPIMD_ERR_ARG;
-  rc = md_run(ctx, positions, velocities, nsteps, energies);
+  rc = ctx->R ? md_run_batched(ctx, positions, velocities, nsteps, energies)
+              : md_run(ctx, positions, velocities, nsteps, energies);
   if (rc != BPIMD_OK) return rc;
   return read_status(ctx);
 }

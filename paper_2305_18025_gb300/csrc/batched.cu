@@ -1,7 +1,9 @@
 // C ABI of replica batches: many independent systems of uneven N, P, beta
 // (same mass and precision) evaluated together, three launches per batch
 // (bead pass with pair factors, both recursions of every replica,
-// probabilities and forces), whatever the number of replicas.
+// probabilities and forces), whatever the number of replicas -- plus one
+// recursion launch per replica larger than BATCH_MAX_N, which takes the
+// cluster kernel of single systems.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -33,8 +35,14 @@ int evaluate_batched(bpimd_ctx *ctx, const double *pos, double *V_B, double *F) 
                           mode, pos, F, ctx->tune_gmat_bpsm, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(1);
-  if (launch_chains_batched(ctx->d_ws, ctx->d_order, ctx->R, ctx->maxN, mode == BPIMD_MIXED32, V_B, s) !=
-      cudaSuccess)
+  // replicas above BATCH_MAX_N (first in the order) take the cluster recursion
+  // kernel of single systems, one launch each; the rest share one launch
+  for (int k = 0; k < ctx->n_big; ++k) {
+    const int r = ctx->h_order[k];
+    if (launch_chains(ctx->h_ws[r], V_B ? V_B + r : nullptr, s) != cudaSuccess) return BPIMD_ERR_CUDA;
+  }
+  if (launch_chains_batched(ctx->d_ws, ctx->d_order + ctx->n_big, ctx->R - ctx->n_big, ctx->maxN,
+                            mode == BPIMD_MIXED32, V_B, s) != cudaSuccess)
     return BPIMD_ERR_CUDA;
   mark(2);
   if (launch_prob_forces_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, ctx->d_off, mode, pos, F,
@@ -58,7 +66,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
   if (!valid_precision(cfg->precision)) return BPIMD_ERR_ARG;
   long long total = 0;
   for (int r = 0; r < R; ++r) {
-    if (N[r] < 1 || N[r] > BATCH_MAX_N || P[r] < 2 || P[r] > (1 << 16)) return BPIMD_ERR_ARG;
+    if (N[r] < 1 || N[r] > BPIMD_STORE_MAX_N || P[r] < 2 || P[r] > (1 << 16)) return BPIMD_ERR_ARG;
     if (!finite_positive(omega_P[r]) || !finite_positive(beta[r])) return BPIMD_ERR_ARG;
     total += 3LL * N[r] * P[r];
   }
@@ -92,15 +100,19 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
     w.beta = beta[r];
     w.k = cfg->m * omega_P[r] * omega_P[r];
     w.half_k = 0.5 * w.k;
+    w.cx = w.beta * w.half_k * LOG2E;
+  w.cx = w.beta * w.half_k * LOG2E;
     wbytes += align256(layout_workspace(w, nullptr));
     ctx->h_off[r] = off;
     off += 3LL * N[r] * P[r];
     for (int l0 = 0; l0 < N[r]; l0 += BEAD_BLOCK_PARTICLES) bead_tab.push_back(make_int2(r, l0));
     for (int b = 0; b < w.NB; ++b) blk_tab.push_back(make_int2(r, b));
-    ctx->maxN = std::max(ctx->maxN, N[r]);
+    if (N[r] <= BATCH_MAX_N) ctx->maxN = std::max(ctx->maxN, N[r]);
+    else ctx->n_big++;
   }
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return N[a] > N[b]; });
+  ctx->h_order = order;
   ctx->n_bead_tab = (int)bead_tab.size();
   ctx->n_blk_tab = (int)blk_tab.size();
   // one allocation: workspaces, shared status word, tables

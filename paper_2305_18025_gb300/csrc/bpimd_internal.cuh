@@ -39,7 +39,7 @@ constexpr int TILE2 = TILE * TILE;
 constexpr int XZERO_E = -(1 << 29);   // exponent carried by an extended zero
 constexpr int CHAIN_THREADS = 640;     // 20 warps: up to 96 registers per thread
 constexpr int CHAIN_CLUSTER = 8;      // CTAs per recursion (small N): one lead + seven bulk CTAs
-constexpr int CHAIN_MAX_N = 6912;     // largest N the library accepts
+constexpr int CHAIN_MAX_N = BPIMD_MAX_N;  // largest N the library accepts
 constexpr int BATCH_MAX_N = 4096;     // largest replica of a batch (one CTA per recursion)
 constexpr int BEAD_BLOCK_PARTICLES = 8;  // particles per block of the bead pass
 constexpr double LOG2E = 1.4426950408889634074;
@@ -131,6 +131,8 @@ struct Workspace {
   int mixed;            // MIXED32: float32 pair-factor and alpha mantissas, 32-bit recursion chain
   int bead32;           // MIXED and MIXED32: float32 bead differences and spring energies
   double m, omega_P, beta, k, half_k;
+  double cx;            // beta (1/2) k log2(e): g = 2^(-cx d^2)
+  int recomp;           // recompute mode: no O(N^2) table; g is formed where it is used
   // periodic cubic box of side L (0: open boundaries); every spring joins the
   // minimum image of its beads.  MIXED keeps the bead-1/bead-P copies in a box
   // as 32-bit fixed-point fractions of L (R1s/RPs reinterpreted as uint32
@@ -264,6 +266,9 @@ cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F,
 cudaError_t launch_dense_probabilities(const Workspace &w, double *M, cudaStream_t s);
 // per block of g: (1/2) m w_P^2 sum Pr[b -> a] |r_b^P - r_a^1|^2 over a <= b (part[NB])
 cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStream_t s);
+// the same per (replica, block) entry of a batch's block table
+cudaError_t launch_spring_expectation_batched(const Workspace *ws, const int2 *tab, int ntab, double *part,
+                                             cudaStream_t s);
 cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, cudaStream_t s);
 
 // Replica batches: ws[r] is replica r's workspace (device array); block tables

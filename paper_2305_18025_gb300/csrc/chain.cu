@@ -82,6 +82,7 @@ struct LeadSmem {
   int Ye[YRING];
   int Ae[2 * TILE];
   int misci[4];         // 1/(N y_N) exponent
+  unsigned long long T63[256];  // recompute mode: table of the integer-pipe power of two
 };
 
 // Shared memory of a bulk CTA: its rows' partial sums (local tile lt = T / 7),
@@ -100,11 +101,55 @@ __host__ __device__ constexpr int helper_tiles(int NT, int NH) { return (NT + NH
 
 __host__ __device__ constexpr size_t helper_smem_bytes(int NT, int NH) {
   return (size_t)helper_tiles(NT, NH) * TILE * (sizeof(double) + sizeof(int)) * 5 +
-         (size_t)32 * 8 * (sizeof(double) + sizeof(int));
+         (size_t)32 * 8 * (sizeof(double) + sizeof(int)) + 256 * sizeof(unsigned long long);
 }
 
-template <bool MIXED, bool BWD, int NHELP>
+// Staging of the next tile's blocks from the stored factors or, in recompute
+// mode, from the endpoint copies (the box flag is read at run time).
+template <int MODE, bool BWD, bool RC, int NR>
+__device__ __forceinline__ void stage_diag_any(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de,
+                                               const unsigned long long *T63) {
+  if constexpr (!RC) stage_diag<MODE == BPIMD_MIXED32, BWD, NR>(w, tt, i0, dm, de);
+  else if (w.pbc) stage_diag_rc<MODE, BWD, true, NR>(w, tt, i0, dm, de, T63);
+  else stage_diag_rc<MODE, BWD, false, NR>(w, tt, i0, dm, de, T63);
+}
+template <int MODE, bool BWD, bool RC, int NR>
+__device__ __forceinline__ void stage_offdiag_any(const Workspace &w, int tt, int i0, void *dm, int *de,
+                                                  const unsigned long long *T63) {
+  if constexpr (!RC) stage_offdiag<MODE == BPIMD_MIXED32, BWD, NR>(w, tt, i0, dm, de);
+  else if (w.pbc) stage_offdiag_rc<MODE, BWD, true, NR>(w, tt, i0, dm, de, T63);
+  else stage_offdiag_rc<MODE, BWD, false, NR>(w, tt, i0, dm, de, T63);
+}
+
+// Recompute mode: the 8 factors H(sb + i, r) of one bulk task (rows past N
+// get extended zeros).
+template <int MODE, bool BWD, typename M_t>
+__device__ __forceinline__ void bulk_factors_rc(const Workspace &w, int r, int sb, const unsigned long long *T63,
+                                                M_t (&m)[8], int (&e)[8]) {
+  if (r >= w.N) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { m[i] = (M_t)1.0; e[i] = XZERO_E; }
+    return;
+  }
+  if (w.pbc) {
+    RowEnds<MODE, BWD, true> re;
+    re.load(w, r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = re.h(w, sb + i, T63, e[i]);
+  } else {
+    RowEnds<MODE, BWD, false> re;
+    re.load(w, r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = re.h(w, sb + i, T63, e[i]);
+  }
+}
+
+// MODE: precision form (the stored-factor kernels serve BPIMD_MIXED with the
+// BPIMD_FP64 code: the same float64-mantissa layout); RC: recompute mode, H
+// formed from the endpoint copies wherever it is used.
+template <int MODE, bool BWD, int NHELP, bool RC>
 __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V_B) {
+  constexpr bool MIXED = MODE == BPIMD_MIXED32;
   cg::cluster_group cluster = cg::this_cluster();
   const unsigned rank = cluster.block_rank();
   const int N = w.N, NT = w.NT;
@@ -130,8 +175,12 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
     const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
-    if (q >= 0 && q < 8) stage_diag<MIXED, BWD, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde);
-    if (q >= 8 && q < 12) stage_offdiag<MIXED, BWD, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe);
+    if (RC) {
+      pairg::table_init(sm.T63);
+      __syncthreads();
+    }
+    if (q >= 0 && q < 8) stage_diag_any<MODE, BWD, RC, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde, sm.T63);
+    if (q >= 8 && q < 12) stage_offdiag_any<MODE, BWD, RC, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe, sm.T63);
     cluster.sync();
 
     xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
@@ -150,10 +199,13 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
                           sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
                           sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
       } else if (q >= 0 && q < 8) {
-        if (t + 1 < NT) stage_diag<MIXED, BWD, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK);
+        if (t + 1 < NT)
+          stage_diag_any<MODE, BWD, RC, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK,
+                                          sm.T63);
       } else if (q >= 8 && q < 12) {
         if (t + 1 < NT)
-          stage_offdiag<MIXED, BWD, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK, sm.Hoe + (buf ^ 1) * BLK);
+          stage_offdiag_any<MODE, BWD, RC, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK,
+                                             sm.Hoe + (buf ^ 1) * BLK, sm.T63);
       } else if (q == 13) {
         // export Y of tile t-1 from the ring to global memory, off the chain
         // warp (a release barrier after global stores would wait for them)
@@ -206,10 +258,12 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     hs.Yd = (double *)p; p += sizeof(double) * 32 * 8;
     hs.Ae = (int *)p; p += sizeof(int) * lt_max * TILE;
     hs.Pe = (int *)p; p += sizeof(int) * 4 * lt_max * TILE;
-    hs.Yx = (int *)p;
+    hs.Yx = (int *)p; p += sizeof(int) * 32 * 8;
+    unsigned long long *T63 = (unsigned long long *)p;  // recompute mode
     const int h = (int)rank - 1;  // owns row tiles T with T mod NHELP == h
     const int nwarps = (int)(blockDim.x >> 5);
     for (int q = tid; q < lt_max * TILE; q += blockDim.x) { hs.Am[q] = 0.0; hs.Ae[q] = XZERO_E; }
+    if (RC) pairg::table_init(T63);
     cluster.sync();
     for (int t = 0; t < NT; ++t) {
       const int T0 = (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP;  // first owned row tile >= t+1
@@ -234,10 +288,14 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
           if (MIXED) {
             float m[8];
             int e[8];
+            if (RC) {
+              bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              m[i] = __ldg((const float *)gm + gbase + i * 32);
-              e[i] = __ldg(ge + gbase + i * 32);
+              for (int i = 0; i < 8; ++i) {
+                m[i] = __ldg((const float *)gm + gbase + i * 32);
+                e[i] = __ldg(ge + gbase + i * 32);
+              }
             }
             float sacc = 0.0f;
             int E = XZERO_E;
@@ -249,10 +307,16 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
             double m[8];
             int e[8];
             int E = XZERO_E;
+            if (RC) {
+              bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              m[i] = __ldg((const double *)gm + gbase + i * 32);
-              e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
+              for (int i = 0; i < 8; ++i) e[i] += Yx[i];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                m[i] = __ldg((const double *)gm + gbase + i * 32);
+                e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
+              }
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i) E = max(E, e[i]);
@@ -298,12 +362,12 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
 // Cluster size CL (CTAs per recursion) is given at launch; blocks [0, CL) run
 // the forward recursion, [CL, 2 CL) the backward one.
-template <bool MIXED, int CL>
+template <int MODE, int CL, bool RC>
 __global__ void __launch_bounds__(CHAIN_THREADS, 1) chain_kernel(Workspace w, double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
-  if (blockIdx.x < CL) run_chain<MIXED, false, CL - 1>(w, smem_raw, V_B);
-  else run_chain<MIXED, true, CL - 1>(w, smem_raw, V_B);
+  if (blockIdx.x < CL) run_chain<MODE, false, CL - 1, RC>(w, smem_raw, V_B);
+  else run_chain<MODE, true, CL - 1, RC>(w, smem_raw, V_B);
 }
 
 constexpr size_t chain_smem_bytes(int N, int CL) {
@@ -316,7 +380,7 @@ static_assert(chain_smem_bytes(CHAIN_MAX_N, CHAIN_CLUSTER) <= 227 * 1024,
 constexpr int CHAIN_CLUSTER_LARGE = 16;
 constexpr int LARGE_CLUSTER_MIN_NT = 41;  // N > 1280: the bulk work would set the pace with 7 bulk CTAs
 
-template <bool MIXED, int CL>
+template <int MODE, int CL, bool RC>
 cudaError_t launch_chain_cluster(const Workspace &w, double *V_B, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * CL);
@@ -332,7 +396,21 @@ cudaError_t launch_chain_cluster(const Workspace &w, double *V_B, cudaStream_t s
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, chain_kernel<MIXED, CL>, w, V_B);
+  return cudaLaunchKernelEx(&cfg, chain_kernel<MODE, CL, RC>, w, V_B);
+}
+
+// The kernel variant of a workspace: stored factors serve BPIMD_MIXED with the
+// float64-layout code; the recompute mode has one variant per precision form.
+template <int CL>
+cudaError_t launch_chain_variant(const Workspace &w, double *V_B, cudaStream_t s) {
+  if (!w.recomp)
+    return w.mixed ? launch_chain_cluster<BPIMD_MIXED32, CL, false>(w, V_B, s)
+                   : launch_chain_cluster<BPIMD_FP64, CL, false>(w, V_B, s);
+  switch (w.mode) {
+    case BPIMD_FP64: return launch_chain_cluster<BPIMD_FP64, CL, true>(w, V_B, s);
+    case BPIMD_MIXED: return launch_chain_cluster<BPIMD_MIXED, CL, true>(w, V_B, s);
+    default: return launch_chain_cluster<BPIMD_MIXED32, CL, true>(w, V_B, s);
+  }
 }
 static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
               "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
@@ -350,12 +428,22 @@ std::mutex g_chain_mutex;
 bool g_chain_ready[64] = {false};
 bool g_large_cluster[64] = {false};
 
-template <bool MIXED, int CL>
+template <int MODE, int CL, bool RC>
 cudaError_t prepare_chain_kernel() {
   const int bytes = (int)chain_smem_bytes(CHAIN_MAX_N, CL);
-  cudaError_t e = cudaFuncSetAttribute(chain_kernel<MIXED, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(chain_kernel<MODE, CL, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess && CL > 8)
-    e = cudaFuncSetAttribute(chain_kernel<MIXED, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(chain_kernel<MODE, CL, RC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+template <int CL>
+cudaError_t prepare_chain_variants() {
+  cudaError_t e = prepare_chain_kernel<BPIMD_MIXED32, CL, false>();
+  if (e == cudaSuccess) e = prepare_chain_kernel<BPIMD_FP64, CL, false>();
+  if (e == cudaSuccess) e = prepare_chain_kernel<BPIMD_FP64, CL, true>();
+  if (e == cudaSuccess) e = prepare_chain_kernel<BPIMD_MIXED, CL, true>();
+  if (e == cudaSuccess) e = prepare_chain_kernel<BPIMD_MIXED32, CL, true>();
   return e;
 }
 
@@ -373,7 +461,8 @@ bool clusters_fit() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  const bool ok = cudaOccupancyMaxActiveClusters(&n, chain_kernel<true, CL>, &cfg) == cudaSuccess && n >= 2;
+  const bool ok =
+      cudaOccupancyMaxActiveClusters(&n, chain_kernel<BPIMD_MIXED32, CL, false>, &cfg) == cudaSuccess && n >= 2;
   cudaGetLastError();
   return ok;
 }
@@ -386,11 +475,9 @@ cudaError_t prepare_chains() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_chain_mutex);
   if (g_chain_ready[dev]) return cudaSuccess;
-  e = prepare_chain_kernel<true, CHAIN_CLUSTER>();
-  if (e == cudaSuccess) e = prepare_chain_kernel<false, CHAIN_CLUSTER>();
+  e = prepare_chain_variants<CHAIN_CLUSTER>();
   if (e != cudaSuccess) return e;
-  bool large = prepare_chain_kernel<true, CHAIN_CLUSTER_LARGE>() == cudaSuccess &&
-               prepare_chain_kernel<false, CHAIN_CLUSTER_LARGE>() == cudaSuccess;
+  bool large = prepare_chain_variants<CHAIN_CLUSTER_LARGE>() == cudaSuccess;
   cudaGetLastError();
   large = large && clusters_fit<CHAIN_CLUSTER_LARGE>();
   g_large_cluster[dev] = large;
@@ -409,11 +496,7 @@ cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s) {
     large_ok = g_large_cluster[dev];
   }
   const bool large = large_ok && w.NT >= LARGE_CLUSTER_MIN_NT;
-  if (large)
-    return w.mixed ? launch_chain_cluster<true, CHAIN_CLUSTER_LARGE>(w, V_B, s)
-                   : launch_chain_cluster<false, CHAIN_CLUSTER_LARGE>(w, V_B, s);
-  return w.mixed ? launch_chain_cluster<true, CHAIN_CLUSTER>(w, V_B, s)
-                 : launch_chain_cluster<false, CHAIN_CLUSTER>(w, V_B, s);
+  return large ? launch_chain_variant<CHAIN_CLUSTER_LARGE>(w, V_B, s) : launch_chain_variant<CHAIN_CLUSTER>(w, V_B, s);
 }
 
 }  // namespace bpimd

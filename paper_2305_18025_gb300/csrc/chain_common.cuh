@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
+#include "pairg.cuh"
 
 namespace bpimd {
 namespace chain_detail {
@@ -23,21 +24,6 @@ __device__ __forceinline__ double scale_nonpos(double x, int k) {
   const long long b = __double_as_longlong(x);
   const int ex = (int)(b >> 52);  // sign bit is 0
   return (ex + k <= 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
-}
-
-// acc + K * y, branch-free, for the dependency chain.  Operands are extended
-// numbers whose mantissas are normal doubles in [1, 2^60) (an extended zero is
-// carried as mantissa 1 with exponent XZERO_E, i.e. 2^-536870912).  Both
-// operands are scaled by 2^k, k <= 0 clamped at -1000, by adding k to the
-// exponent field of the high word: a clamped operand is below 2^-900 of the
-// other and cannot change the float64 sum.  One float64 FMA, five integer ops.
-__device__ __forceinline__ xd fma_chain(xd acc, double km, int ke, xd y) {
-  const int pe = ke + y.e;
-  const int E = max(acc.e, pe);
-  const int k1 = max(pe - E, -1000), k2 = max(acc.e - E, -1000);
-  const double ks = __hiloint2double(__double2hiint(km) + k1 * (1 << 20), __double2loint(km));
-  const double as = __hiloint2double(__double2hiint(acc.m) + k2 * (1 << 20), __double2loint(acc.m));
-  return xd{fma(ks, y.m, as), E};
 }
 
 // Explicit shared-memory loads (32-bit shared-window addresses).
@@ -146,8 +132,21 @@ __device__ __forceinline__ xi xi_mul(xi a, xd c) {
 // acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64): the step of the
 // dependency chain.  The product kk * y.m / 2^64 lies in [2^61, 2^63), the
 // aligned sum in [2^61, 2^64); a K carrying an extended-zero exponent leaves
-// acc unchanged.  MIXED uses the top 32 bits of kk only (two 32 x 32-bit
-// products, relative error below 2^-30: K = c g carries a float32 g there).
+// acc unchanged.  The 64-bit form truncates at 2^-59 per step (mulhi_3);
+// MIXED uses the top 32 bits of kk only (two 32 x 32-bit products, relative
+// error below 2^-30: K = c g carries a float32 g there).
+// High 64 bits of a 64 x 64-bit product from three 32 x 32-bit products
+// (independent, so they issue back to back: a shorter dependency than the
+// exact __umul64hi).  The low x low product and the carries out of the
+// cross products are dropped: the result is below the exact high word by at
+// most 3, here 2^-59 of a product in [2^61, 2^63); clamped at 2^61 so that
+// the normalisation below sees its range.
+__device__ __forceinline__ unsigned long long mulhi_3(unsigned long long a, unsigned long long b) {
+  const unsigned a1 = (unsigned)(a >> 32), a0 = (unsigned)a, b1 = (unsigned)(b >> 32), b0 = (unsigned)b;
+  const unsigned long long p = (unsigned long long)a1 * b1 + (((unsigned long long)a1 * b0) >> 32) +
+                               (((unsigned long long)a0 * b1) >> 32);
+  return max(p, 1ull << 61);
+}
 template <bool MIXED>
 __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y) {
   unsigned long long p;
@@ -155,7 +154,7 @@ __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y
     const unsigned k1 = (unsigned)(kk >> 32);
     p = (unsigned long long)k1 * (unsigned)(y.m >> 32) + (((unsigned long long)k1 * (unsigned)y.m) >> 32);
   } else {
-    p = __umul64hi(kk, y.m);
+    p = mulhi_3(kk, y.m);
   }
   const int pe = ke + y.e + 1;
   const int E = max(acc.e, pe);
@@ -316,6 +315,64 @@ __device__ __forceinline__ void stage_diag(const Workspace &w, int tt, int i0, u
   }
 }
 
+// ------------------------------------------ recompute mode (no stored g)
+// H(src, row) of a recursion from the bead pass's endpoint copies: forward
+// H(w, r) = g(a = w, b = r); backward H(w, r) = g(a = N-1-r, b = N-1-w), b the
+// bead-P end and a the bead-1 end of the closing spring (the same bits as the
+// tabulated factors, pairg.cuh).  The row's endpoint is loaded once per lane.
+template <int MODE, bool BWD, bool PBC>
+struct RowEnds {
+  pairg::EndPt<MODE != BPIMD_FP64, PBC> row;
+  __device__ __forceinline__ void load(const Workspace &w, int r) {
+    row = pairg::load_end<MODE != BPIMD_FP64, PBC>(w, BWD ? w.N - 1 - r : r, !BWD);
+  }
+  __device__ __forceinline__ typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type
+  h(const Workspace &w, int src, const unsigned long long *T63, int &e) const {
+    const auto s = pairg::load_end<MODE != BPIMD_FP64, PBC>(w, BWD ? w.N - 1 - src : src, BWD);
+    return BWD ? pairg::g_of<MODE, PBC>(w, s, row, w.cx, T63, e) : pairg::g_of<MODE, PBC>(w, row, s, w.cx, T63, e);
+  }
+};
+
+// stage_offdiag / stage_diag with H recomputed (same layouts and zeros).
+template <int MODE, bool BWD, bool PBC, int NR>
+__device__ __forceinline__ void stage_offdiag_rc(const Workspace &w, int tt, int i0, void *dmv, int *de,
+                                                 const unsigned long long *T63) {
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int srcbase = tt * TILE, row = tt * TILE + TILE + lane;
+  M_t *dm = (M_t *)dmv;
+  RowEnds<MODE, BWD, PBC> re;
+  if (row < w.N) re.load(w, row);
+#pragma unroll 2
+  for (int i = i0; i < i0 + NR; ++i) {
+    M_t m = (M_t)1.0;
+    int e = XZERO_E;
+    if (row < w.N) m = re.h(w, srcbase + i, T63, e);
+    dm[i * 33 + lane] = m;
+    de[i * 33 + lane] = e;
+  }
+}
+template <int MODE, bool BWD, bool PBC, int NR>
+__device__ __forceinline__ void stage_diag_rc(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de,
+                                              const unsigned long long *T63) {
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int r0 = tt * TILE, row = r0 + lane;
+  const xd c = (row < w.N) ? xnorm_int(chain_coef<BWD>(w, row)) : xd{1.0, 0};
+  RowEnds<MODE, BWD, PBC> re;
+  if (row < w.N) re.load(w, row);
+#pragma unroll 2
+  for (int i = i0; i < i0 + NR; ++i) {
+    const int src = r0 + i;
+    M_t m = (M_t)1.0;
+    int e = XZERO_E;
+    if (row < w.N && src <= row) m = re.h(w, src, T63, e);
+    const xk k = mul_mant<M_t>(c, m, e);
+    dm[i * 33 + lane] = k.m;
+    de[i * 33 + lane] = k.e;
+  }
+}
+
 // The 32 dependent steps of row tile t, run by one warp.  A is this lane's
 // row sum over sources < 32t except tile t-1 (which is in nxt), crow the row's
 // coefficient.  K (diagonal, c-scaled, integer mantissas) and H (to tile t+1)
@@ -347,6 +404,7 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
     y = xi_from(y0);
   }
   nxt = xd{1.0, XZERO_E};
+  xi nx{1ull << 62, XZERO_E};  // FP64 layout: the next tile's partial sum, integer format
   float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
   int nexp = XZERO_E;
   const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
@@ -374,13 +432,17 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
       fmerge(nsum, nexp, __int_as_float((int)((y.m >> 7) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
     } else {
       acc = xi_fma<false>(acc, km, ke, y);  // the dependency chain
-      nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
+      // next tile's rows, off the chain: the same integer format (a float64
+      // FMA here would make a second dependent chain of ~110 cycles a step)
+      nx = xi_fma<false>(nx, (((unsigned long long)__double_as_longlong(hm) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11,
+                         he, y);
     }
     y.m = __shfl_sync(0xffffffffu, acc.m, i);
     y.e = __shfl_sync(0xffffffffu, acc.e, i);
     km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
   }
   if (MIXED) nxt = xd{f2d_int(nsum), nexp};
+  else nxt = xi_to_xd(nx);
   if (row < N) {  // Y_{row+1} = final accumulator of row `row`
     xd yn;
     if constexpr (MIXED) yn = xs_to_xd(acc);

@@ -40,6 +40,8 @@ struct bpimd_ctx {
   int2 *d_bead_tab, *d_blk_tab;           // (replica, particle block), (replica, g block)
   int n_bead_tab, n_blk_tab;
   int *d_order;                           // replicas by decreasing N
+  std::vector<int> h_order;               // the same order on the host
+  int n_big;                              // replicas above BATCH_MAX_N (first in the order)
   long long *d_off;
   int tune_gmat_bpsm, tune_prob_bpsm;     // grid caps (blocks per SM) of the batched passes
 };

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
+#include "pairg.cuh"
 
 namespace bpimd {
 namespace {
@@ -328,6 +329,50 @@ __device__ __forceinline__ void prob_block(const Workspace &w, int blk, const do
   }
 }
 
+// Exterior-bead forces of one row tile (bead P) or column tile (bead 1) from
+// complete sums fin[j][0..3] + fin[j][4..7] = (sum Pr, sum Pr (r - r')), used
+// by the recompute pass (the same formulas as the tile finalisers above).
+template <bool PBC>
+__device__ void finish_rows(const Workspace &w, int t, const double *__restrict__ pos, double *__restrict__ F,
+                            double (*fin)[9]) {
+  const int p = t * TILE + threadIdx.x;
+  if (threadIdx.x >= TILE || p >= w.N) return;
+  const double *r = w.RP + 4 * (size_t)p, *nbP = pos + ((size_t)p * w.P + (w.P - 2)) * 3;  // bead P-1
+  const double M = (p + 1 < w.N) ? direct_link_fast(w, p) : 0.0;
+  const double *fr = fin[threadIdx.x];
+  const double rs = fr[0] + fr[4] + M;
+  double *fP = F + ((size_t)p * w.P + (w.P - 1)) * 3;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double n1 = (p + 1 < w.N) ? w.R1[4 * (size_t)(p + 1) + c] : 0.0;
+    const double rc = fma(M, img<PBC>(w, r[c] - n1), fr[1 + c] + fr[5 + c]);
+    fP[c] = -w.k * fma(rs, img<PBC>(w, r[c] - nbP[c]), rc);
+    ok &= isfinite(fP[c]);
+  }
+  if (!ok) atomicOr(w.status, ST_NONFINITE);
+}
+template <bool PBC>
+__device__ void finish_cols(const Workspace &w, int s, const double *__restrict__ pos, double *__restrict__ F,
+                            double (*fin)[9]) {
+  const int p = s * TILE + threadIdx.x;
+  if (threadIdx.x >= TILE || p >= w.N) return;
+  const double *r = w.R1 + 4 * (size_t)p, *nb1 = pos + ((size_t)p * w.P + 1) * 3;  // bead 2
+  const double M = (p >= 1) ? direct_link_fast(w, p - 1) : 0.0;
+  const double *fc = fin[threadIdx.x];
+  const double cs = fc[0] + fc[4] + M;
+  double *f1 = F + (size_t)p * w.P * 3;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double pP = (p >= 1) ? w.RP[4 * (size_t)(p - 1) + c] : 0.0;
+    const double cc = fma(M, img<PBC>(w, r[c] - pP), fc[1 + c] + fc[5 + c]);
+    f1[c] = -w.k * fma(cs, img<PBC>(w, r[c] - nb1[c]), cc);
+    ok &= isfinite(f1[c]);
+  }
+  if (!ok) atomicOr(w.status, ST_NONFINITE);
+}
+
 // ----------------------------------------------------------- MIXED (config 3)
 // Unevaluated sums h + l of two float32 numbers (|l| <= ulp(h)/2 after
 // renormalisation): about 46 significant bits on the float32 pipe.
@@ -488,6 +533,136 @@ __global__ void __launch_bounds__(256, 4) prob_force_batched_mixed(const Workspa
   pdl_trigger();
 }
 
+// ------------------------------------------------- recompute mode (no table)
+// Probabilities and exterior forces by whole tiles: work item 2k is row tile
+// NT-1-k (all its source tiles), item 2k+1 column tile k (all its row tiles),
+// so that the items come in decreasing size.  A row item forms Pr[b -> a] for
+// its 32 rows b (lanes) and every source a (8 warps, 4 sources each per 32x32
+// block), with g recomputed from the endpoint copies, and accumulates the row
+// sums in registers; the column items do the same for the 32 columns.  Every
+// pair is formed twice (once per item kind) and nothing O(N^2) is stored; the
+// sums are combined across warps in a fixed order (deterministic).
+// Accumulators: float64 (FP64) or compensated float32 pairs (mixed forms).
+template <int MODE>
+struct PAcc {
+  using T = typename std::conditional<MODE == BPIMD_FP64, double, ff>::type;
+  T s, x, y, z;
+  __device__ __forceinline__ void zero() {
+    if constexpr (MODE == BPIMD_FP64) s = x = y = z = 0.0;
+    else s = x = y = z = ff{0.0f, 0.0f};
+  }
+};
+
+// Pr(a, b) for the recompute items: alpha_a, mu_b and g as extended numbers.
+template <int MODE>
+__device__ __forceinline__ typename PAcc<MODE>::T prob_rc(const Workspace &w, int a, xd mu, double gm, int ge) {
+  if constexpr (MODE == BPIMD_FP64) {
+    return (((const double *)w.alm)[a] * mu.m * gm) * pow2_normal(w.ale[a] + mu.e + ge);
+  } else if constexpr (MODE == BPIMD_MIXED) {
+    const unsigned long long aa =
+        (((unsigned long long)__double_as_longlong(((const double *)w.alm)[a]) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+    const unsigned long long mm = (((unsigned long long)__double_as_longlong(mu.m) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11;
+    unsigned long long am = __umul64hi(aa, mm);
+    const int sh = (int)(am >> 63) ^ 1;
+    am <<= sh;
+    return prob_ff(am, w.ale[a] + mu.e + 1 - sh, gm, ge);
+  } else {
+    const int e = w.ale[a] + mu.e + ge;
+    float M = ((const float *)w.alm)[a] * (float)mu.m * (float)gm;
+    M = (e < -150) ? 0.0f : (e > 0 ? M * (float)(1 << min(e, 2)) : M * pow2f_nonpos(e));
+    return ff{M, 0.0f};
+  }
+}
+
+template <int MODE, typename D3>
+__device__ __forceinline__ void acc_add(PAcc<MODE> &A, typename PAcc<MODE>::T pr, D3 d, float sign) {
+  if constexpr (MODE == BPIMD_FP64) {
+    A.s += pr;
+    A.x = fma(sign * pr, d.x, A.x);
+    A.y = fma(sign * pr, d.y, A.y);
+    A.z = fma(sign * pr, d.z, A.z);
+  } else {
+    A.s = ff_add(A.s, pr);
+    A.x = ff_add(A.x, ff_mul(pr, sign * d.x));
+    A.y = ff_add(A.y, ff_mul(pr, sign * d.y));
+    A.z = ff_add(A.z, ff_mul(pr, sign * d.z));
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ double acc_val(typename PAcc<MODE>::T v) {
+  if constexpr (MODE == BPIMD_FP64) return v;
+  else return (double)v.h + (double)v.l;
+}
+
+// One work item of the recompute pass (all 256 threads).  red: [8][32][4]
+// per-warp sums; fin as in the tile finalisers.
+template <int MODE, bool PBC>
+__device__ void prob_item_rc(const Workspace &w, int item, const double *__restrict__ pos, double *__restrict__ F,
+                             const unsigned long long *T63, double (*red)[32][4], double (*fin)[9]) {
+  using EP = pairg::EndPt<MODE != BPIMD_FP64, PBC>;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool row_item = !(item & 1);
+  const int tile = row_item ? w.NT - 1 - (item >> 1) : (item >> 1);
+  const int me = tile * TILE + lane;  // this lane's particle (row b or column a)
+  PAcc<MODE> A;
+  A.zero();
+  if (me < w.N) {
+    const EP mine = pairg::load_end<MODE != BPIMD_FP64, PBC>(w, me, row_item);  // bead P of b, or bead 1 of a
+    const xd mub = row_item ? mu_of(w, me) : xd{0.0, 0};
+    const int t0 = row_item ? 0 : tile, t1 = row_item ? tile : w.NT - 1;
+    for (int o = t0; o <= t1; ++o) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int other = o * TILE + wp + 8 * kk;  // source a (row item) or row b (column item)
+        const int a = row_item ? other : me, b = row_item ? me : other;
+        if (a <= b && b < w.N) {
+          const EP oth = pairg::load_end<MODE != BPIMD_FP64, PBC>(w, other, !row_item);
+          const EP &eb = row_item ? mine : oth, &ea = row_item ? oth : mine;
+          int ge;
+          const double gm = (double)pairg::g_of<MODE, PBC>(w, eb, ea, w.cx, T63, ge);
+          const auto pr = prob_rc<MODE>(w, a, row_item ? mub : mu_of(w, b), gm, ge);
+          // row b: Pr (r_b^P - r_a^1); column a: Pr (r_a^1 - r_b^P)
+          acc_add<MODE>(A, pr, pairg::diff3(w, eb, ea), row_item ? 1.0f : -1.0f);
+        }
+      }
+    }
+  }
+  red[wp][lane][0] = acc_val<MODE>(A.s);
+  red[wp][lane][1] = acc_val<MODE>(A.x);
+  red[wp][lane][2] = acc_val<MODE>(A.y);
+  red[wp][lane][3] = acc_val<MODE>(A.z);
+  __syncthreads();
+  if (threadIdx.x < 128) {  // fixed-order sum over the 8 warps, into the finalisers' layout
+    const int jj = threadIdx.x >> 2, q = threadIdx.x & 3;
+    double v = 0.0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) v += red[g][jj][q];
+    fin[jj][q] = v;
+    fin[jj][q + 4] = 0.0;
+  }
+  __syncthreads();
+  if (row_item) finish_rows<PBC>(w, tile, pos, F, fin);
+  else finish_cols<PBC>(w, tile, pos, F, fin);
+  __syncthreads();
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) prob_rc_kernel(Workspace w, const double *__restrict__ pos,
+                                                      double *__restrict__ F) {
+  __shared__ double red[8][32][4];
+  __shared__ double fin[32][9];
+  __shared__ unsigned long long T63[256];
+  if (MODE != BPIMD_MIXED32) pairg::table_init(T63);
+  __syncthreads();
+  pdl_wait();
+  for (int item = blockIdx.x; item < 2 * w.NT; item += gridDim.x) {
+    if (w.pbc) prob_item_rc<MODE, true>(w, item, pos, F, T63, red, fin);
+    else prob_item_rc<MODE, false>(w, item, pos, F, T63, red, fin);
+  }
+  pdl_trigger();
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256, 4) prob_force_kernel(Workspace w, const double *__restrict__ pos,
                                                          double *__restrict__ F) {
@@ -527,34 +702,51 @@ __global__ void __launch_bounds__(256, 4) prob_force_batched(const Workspace *__
 // of the lower triangle: (1/2) m w_P^2 sum_{a<=b in block} Pr[b -> a] |r_b^P - r_a^1|^2
 // (the direct links l -> l+1 are added by the caller).  Float64 throughout;
 // run once per molecular-dynamics call, for the primitive energy estimator.
+// All threads of the block call it; thread 0 gets the sum.
+__device__ double spring_block(const Workspace &w, int blk, double *red) {
+  int t, s;
+  block_coords_f(blk, t, s);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+    const int a = s * TILE + (e >> 5), b = t * TILE + (e & 31);
+    if (b < w.N && a <= b) {
+      const size_t gi = (size_t)blk * TILE2 + e;
+      const xd g = w.recomp ? pairg::g_runtime(w, a, b)
+                            : xd{w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi], w.ge[gi]};
+      const xd al = alpha_of(w, a), mu = mu_of(w, b);
+      const double M = xtod(xd{al.m * mu.m * g.m, al.e + mu.e + g.e});
+      const double dx = mimage(w, w.RP[4 * b] - w.R1[4 * a]), dy = mimage(w, w.RP[4 * b + 1] - w.R1[4 * a + 1]),
+                   dz = mimage(w, w.RP[4 * b + 2] - w.R1[4 * a + 2]);
+      acc += M * (dx * dx + dy * dy + dz * dz);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q];
+  __syncthreads();
+  return w.half_k * sum;
+}
+
 __global__ void __launch_bounds__(256) spring_expect_kernel(Workspace w, double *part) {
   __shared__ double red[8];
   for (int blk = blockIdx.x; blk < w.NB; blk += gridDim.x) {
-    int t, s;
-    block_coords_f(blk, t, s);
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
-      const int a = s * TILE + (e >> 5), b = t * TILE + (e & 31);
-      if (b < w.N && a <= b) {
-        const size_t gi = (size_t)blk * TILE2 + e;
-        const double gmd = w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi];
-        const xd al = alpha_of(w, a), mu = mu_of(w, b);
-        const double M = xtod(xd{al.m * mu.m * gmd, al.e + mu.e + w.ge[gi]});
-        const double dx = mimage(w, w.RP[4 * b] - w.R1[4 * a]), dy = mimage(w, w.RP[4 * b + 1] - w.R1[4 * a + 1]),
-                     dz = mimage(w, w.RP[4 * b + 2] - w.R1[4 * a + 2]);
-        acc += M * (dx * dx + dy * dy + dz * dz);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q];
-      part[blk] = w.half_k * sum;
-    }
-    __syncthreads();
+    const double v = spring_block(w, blk, red);
+    if (threadIdx.x == 0) part[blk] = v;
+  }
+}
+
+// Replica batch: entry k of tab is (replica, block); part[k] as above.
+__global__ void __launch_bounds__(256) spring_expect_batched(const Workspace *__restrict__ ws,
+                                                             const int2 *__restrict__ tab, int ntab, double *part) {
+  __shared__ double red[8];
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int2 e = tab[k];
+    const double v = spring_block(ws[e.x], e.y, red);
+    if (threadIdx.x == 0) part[k] = v;
   }
 }
 
@@ -566,9 +758,10 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
     if (a <= b) {
       const int t = b >> 5, s = a >> 5;
       const size_t gi = ((size_t)(t * (t + 1) / 2 + s) << 10) + ((a & 31) << 5) + (b & 31);
-      const double gmd = w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi];
+      const xd g = w.recomp ? pairg::g_runtime(w, a, b)
+                            : xd{w.mixed ? (double)((const float *)w.gm)[gi] : ((const double *)w.gm)[gi], w.ge[gi]};
       const xd al = alpha_of(w, a), mu = mu_of(w, b);
-      v = xtod(xd{al.m * mu.m * gmd, al.e + mu.e + w.ge[gi]});
+      v = xtod(xd{al.m * mu.m * g.m, al.e + mu.e + g.e});
     } else if (a == b + 1) {
       v = direct_link_prob(w, b);
     }
@@ -580,8 +773,18 @@ __global__ void dense_prob_kernel(Workspace w, double *M) {
 
 cudaError_t launch_prob_forces(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   const int sms = sm_count();
-  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   cudaError_t e;
+  if (w.recomp) {
+    const int items = 2 * w.NT, grid_rc = items < sms * 4 ? items : sms * 4;
+    switch (w.mode) {
+      case BPIMD_FP64: e = launch_pdl(prob_rc_kernel<BPIMD_FP64>, grid_rc, 256, 0, s, w, pos, F); break;
+      case BPIMD_MIXED: e = launch_pdl(prob_rc_kernel<BPIMD_MIXED>, grid_rc, 256, 0, s, w, pos, F); break;
+      default: e = launch_pdl(prob_rc_kernel<BPIMD_MIXED32>, grid_rc, 256, 0, s, w, pos, F); break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  const int grid = w.NB < sms * 8 ? w.NB : sms * 8;
   switch (w.mode) {
     case BPIMD_FP64: e = launch_pdl(prob_force_kernel<false>, grid, 256, 0, s, w, pos, F); break;
     case BPIMD_MIXED: e = launch_pdl(prob_force_kernel_mixed, grid, 256, 0, s, w, pos, F); break;
@@ -595,6 +798,15 @@ cudaError_t launch_spring_expectation(const Workspace &w, double *part, cudaStre
   const int sms = sm_count();
   const int grid = w.NB < sms * 4 ? w.NB : sms * 4;
   spring_expect_kernel<<<grid, 256, 0, s>>>(w, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spring_expectation_batched(const Workspace *ws, const int2 *tab, int ntab, double *part,
+                                             cudaStream_t s) {
+  if (ntab <= 0) return cudaSuccess;
+  const int sms = sm_count();
+  const int grid = ntab < sms * 4 ? ntab : sms * 4;
+  spring_expect_batched<<<grid, 256, 0, s>>>(ws, tab, ntab, part);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ def main():
              "#define BPIMD_POW2_T63_INIT \\"]
     for k in range(0, 256, 4):
         chunk = ", ".join(f"0x{v:016X}ull" for v in rows[k:k + 4])
-        lines.append(f"  {chunk}{',' if k + 4 < 256 else ''} \\")
+        lines.append(f"  {chunk}," + " \\" if k + 4 < 256 else f"  {chunk}")
     lines.append("")
     with open(os.path.join(HERE, "pow2_table.h"), "w") as f:
         f.write("\n".join(lines))

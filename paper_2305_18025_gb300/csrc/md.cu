@@ -28,6 +28,7 @@
 // caller's position and velocity buffers and replayed; the step counter lives
 // in device memory and is advanced by the last kernel of the step.
 #include <cmath>
+#include <vector>
 #include <type_traits>
 
 #include "context.cuh"
@@ -143,15 +144,14 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // periodic box (PBC) pair distances by minimum image.  MIXED: pair terms in
 // float32, accumulated per lane in float32 and added to the float64 force.
 template <bool MIXED, bool PBC>
-__global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__restrict__ pos, double *__restrict__ F,
-                                                                int N, int P, PairParams pp, double *ubar_part) {
+__device__ __forceinline__ double ext_force_body(const double *__restrict__ pos, double *__restrict__ F, int N,
+                                                 int P, const PairParams &pp, int lb, int j,
+                                                 typename std::conditional<MIXED, float4, Dbl4>::type *sr,
+                                                 double *red, double *T2) {
   using R = typename std::conditional<MIXED, float, double>::type;
   using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
-  __shared__ R4 sr[EXT_CHUNK];
-  __shared__ double red[EXT_THREADS / 32];
-  __shared__ double T2[64];  // float64: 2^(j/64) for exp2_table
-  const int j = blockIdx.y, sub = threadIdx.x % EXT_SPLIT;
-  const int l = blockIdx.x * EXT_PARTICLES + threadIdx.x / EXT_SPLIT;
+  const int sub = threadIdx.x % EXT_SPLIT;
+  const int l = lb * EXT_PARTICLES + threadIdx.x / EXT_SPLIT;
   const bool valid = l < N;
   double rx = 0, ry = 0, rz = 0;
   if (valid) {
@@ -228,8 +228,124 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
                                                     : 0.5 * (4.0 * pp.eps * (double)u - pp.ushift * nin);
     ul = pp.inv_P * (up + 0.5 * pp.kt * (rx * rx + ry * ry + rz * rz));
   }
-  const double s = block_sum(ul, red);
+  return block_sum(ul, red);
+}
+
+template <bool MIXED, bool PBC>
+__global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__restrict__ pos, double *__restrict__ F,
+                                                                int N, int P, PairParams pp, double *ubar_part) {
+  using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
+  __shared__ R4 sr[EXT_CHUNK];
+  __shared__ double red[EXT_THREADS / 32];
+  __shared__ double T2[64];  // float64: 2^(j/64) for exp2_table
+  const double s = ext_force_body<MIXED, PBC>(pos, F, N, P, pp, blockIdx.x, blockIdx.y, sr, red, T2);
   if (threadIdx.x == 0) ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// ----------------------------------------------------------- replica batches
+// Replica r of a batch occupies elements [off[r], off[r] + 3 N_r P_r) of the
+// packed arrays; the replica of element e by binary search over off.
+__device__ __forceinline__ int replica_of(const long long *__restrict__ off, int R, long long e) {
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// B A O A over every replica of a batch: as md_baoa_kernel, with the
+// thermostat amplitude c2 of each element's replica (its own temperature).
+template <bool MIXED>
+__global__ void __launch_bounds__(MD_THREADS) md_baoa_batched(double *__restrict__ x, double *__restrict__ v,
+                                                              const double *__restrict__ F, long long n,
+                                                              double half_dt_over_m, double half_dt, double c1,
+                                                              const double *__restrict__ c2r,
+                                                              const long long *__restrict__ off, int R, uint32_t k0,
+                                                              uint32_t k1, const unsigned long long *__restrict__ step) {
+  const unsigned long long s = *step;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * g < n;
+       g += (long long)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)g, (uint32_t)s, (uint32_t)(s >> 32), 0u};
+    philox4x32_10(c, k0, k1);
+    double z[4];
+    box_muller<MIXED>(c, z);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long e = 4 * g + i;
+      if (e < n) {
+        const double c2 = __ldg(c2r + replica_of(off, R, e));
+        double vi = v[e] + half_dt_over_m * F[e];  // B
+        double xi = x[e] + half_dt * vi;           // A
+        vi = c1 * vi + c2 * z[i];                  // O
+        x[e] = xi + half_dt * vi;                  // A
+        v[e] = vi;
+      }
+    }
+  }
+}
+
+// Trap and pair forces of every replica: entry k of tab is (replica,
+// particle block, bead index); the trap frequency and pair parameters are
+// shared, 1/P_r is the replica's.
+template <bool MIXED>
+__global__ void __launch_bounds__(EXT_THREADS) ext_force_batched(const double *__restrict__ pos,
+                                                                 double *__restrict__ F,
+                                                                 const Workspace *__restrict__ ws,
+                                                                 const long long *__restrict__ off,
+                                                                 const int4 *__restrict__ tab, int ntab, PairParams pp,
+                                                                 double *ubar_part) {
+  using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
+  __shared__ R4 sr[EXT_CHUNK];
+  __shared__ double red[EXT_THREADS / 32];
+  __shared__ double T2[64];
+  for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
+    const int4 e = tab[k];
+    const int N = ws[e.x].N, P = ws[e.x].P;
+    PairParams q = pp;
+    q.inv_P = 1.0 / P;
+    const double s = ext_force_body<MIXED, false>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T2);
+    if (threadIdx.x == 0) ubar_part[k] = s;
+    __syncthreads();  // sr and T2 are reused by the next entry
+  }
+}
+
+// energies[4 r + 0..3] of replica r (one block each): V_B, U-bar, kinetic,
+// primitive estimator, from the partial sums of the last force pass.
+__global__ void __launch_bounds__(MD_THREADS) energies_batched(const Workspace *__restrict__ ws,
+                                                               const long long *__restrict__ off,
+                                                               const double *__restrict__ VBr,
+                                                               const double *__restrict__ ubar_part,
+                                                               const int *__restrict__ ext_first,
+                                                               const double *__restrict__ spring_part,
+                                                               const int *__restrict__ blk_first,
+                                                               const double *__restrict__ v, double half_m,
+                                                               double *energies) {
+  __shared__ double red[MD_THREADS / 32];
+  const int r = blockIdx.x;
+  const Workspace &w = ws[r];
+  double sp = 0.0, ub = 0.0, ke = 0.0;
+  for (int q = blk_first[r] + threadIdx.x; q < blk_first[r + 1]; q += blockDim.x) sp += spring_part[q];
+  for (int l = threadIdx.x; l < w.N; l += blockDim.x) {
+    sp += w.Eint[l];
+    if (l + 1 < w.N) sp += direct_link_prob(w, l) * w.link[l];
+  }
+  for (int q = ext_first[r] + threadIdx.x; q < ext_first[r + 1]; q += blockDim.x) ub += ubar_part[q];
+  const long long n = 3LL * w.N * w.P;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) ke += v[off[r] + e] * v[off[r] + e];
+  sp = block_sum(sp, red);
+  ub = block_sum(ub, red);
+  ke = block_sum(ke, red);
+  if (threadIdx.x == 0) {
+    double *en = energies + 4 * (size_t)r;
+    en[0] = VBr[r];
+    en[1] = ub;
+    en[2] = half_m * ke;
+    en[3] = 1.5 * (double)w.N * (double)w.P / w.beta - sp + ub;
+    for (int i = 0; i < 4; ++i)
+      if (!isfinite(en[i])) atomicOr(w.status, ST_NONFINITE);
+  }
 }
 
 __global__ void __launch_bounds__(MD_THREADS) ke_kernel(const double *__restrict__ v, long long n, double half_m,
@@ -407,6 +523,11 @@ int md_alloc(bpimd_ctx *ctx, const MDParams &p) {
 void md_init(MDState *md) { *md = MDState{}; }
 
 void md_free(MDState *md) {
+  cudaFree(md->VBr);
+  cudaFree(md->c2r);
+  cudaFree(md->ext_tab);
+  cudaFree(md->ext_first);
+  cudaFree(md->blk_first);
   if (md->exec) cudaGraphExecDestroy(md->exec);
   if (md->graph) cudaGraphDestroy(md->graph);
   cudaFree(md->F);
@@ -464,6 +585,156 @@ int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *ene
     if (rc == BPIMD_OK) {
       energies_kernel<<<1, MD_THREADS, 0, s>>>(ctx->w, md.VB, md.ubar_part, md.ext_blocks, md.ke_part, g1,
                                               md.spring_part, energies);
+      if (cudaGetLastError() != cudaSuccess) rc = BPIMD_ERR_CUDA;
+    }
+  }
+  ctx->prof_on = prof;
+  return rc;
+}
+
+// ----------------------------------------------------------- replica batches
+// bpimd_step on a batch context: every replica advances by the same BAOAB
+// steps (shared dt, gamma, trap, Gaussian pair potential and seed; each
+// replica thermostatted at its own kT = 1/beta_r unless cfg.kT_bead > 0).
+// One step is: the batched B A O A kernel, the three evaluation launches of
+// the batch (plus one per replica above 4096 particles), the batched trap and
+// pair forces, and the closing B -- captured once into a CUDA graph bound to
+// the caller's buffers and replayed.  Thermostat noise: Philox4x32-10 with the
+// element index of the packed arrays as the counter.
+namespace {
+
+int md_alloc_batched(bpimd_ctx *ctx, const MDParams &p) {
+  MDState &md = ctx->md;
+  const int R = ctx->R;
+  const size_t n = (size_t)ctx->total_elems;
+  std::vector<int4> tab;
+  std::vector<int> ext_first(R + 1), blk_first(R + 1);
+  int blk = 0;
+  for (int r = 0; r < R; ++r) {
+    const Workspace &w = ctx->h_ws[r];
+    ext_first[r] = (int)tab.size();
+    for (int j = 0; j < w.P; ++j)
+      for (int lb = 0; lb * EXT_PARTICLES < w.N; ++lb) tab.push_back(make_int4(r, lb, j, 0));
+    blk_first[r] = blk;
+    blk += w.NB;
+  }
+  ext_first[R] = (int)tab.size();
+  blk_first[R] = blk;
+  md.n_ext = (int)tab.size();
+  md.spring_blocks = ctx->n_blk_tab;
+  md.ke_blocks = 0;
+  md.ext_blocks = md.n_ext;
+  std::vector<double> c2(R);
+  for (int r = 0; r < R; ++r) {
+    const double kT = ctx->cfg.kT_bead > 0.0 ? ctx->cfg.kT_bead : 1.0 / ctx->h_ws[r].beta;
+    c2[r] = std::sqrt((1.0 - p.c1 * p.c1) * kT / ctx->cfg.m);
+  }
+  if (cudaMalloc(&md.F, sizeof(double) * n) != cudaSuccess || cudaMalloc(&md.VBr, sizeof(double) * R) != cudaSuccess ||
+      cudaMalloc(&md.c2r, sizeof(double) * R) != cudaSuccess ||
+      cudaMalloc(&md.ext_tab, sizeof(int4) * md.n_ext) != cudaSuccess ||
+      cudaMalloc(&md.ext_first, sizeof(int) * (R + 1)) != cudaSuccess ||
+      cudaMalloc(&md.blk_first, sizeof(int) * (R + 1)) != cudaSuccess ||
+      cudaMalloc(&md.ubar_part, sizeof(double) * md.n_ext) != cudaSuccess ||
+      cudaMalloc(&md.spring_part, sizeof(double) * md.spring_blocks) != cudaSuccess ||
+      cudaMalloc(&md.step, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    md_free(&md);
+    return BPIMD_ERR_NOMEM;
+  }
+  cudaStream_t s = ctx->stream;
+  if (cudaMemcpyAsync(md.c2r, c2.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(md.ext_tab, tab.data(), sizeof(int4) * md.n_ext, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(md.ext_first, ext_first.data(), sizeof(int) * (R + 1), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(md.blk_first, blk_first.data(), sizeof(int) * (R + 1), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(md.step, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)  // the host tables go out of scope
+    return BPIMD_ERR_CUDA;
+  md.ready = true;
+  return BPIMD_OK;
+}
+
+int total_force_batched(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
+  MDState &md = ctx->md;
+  int rc = evaluate_batched(ctx, pos, md.VBr, md.F);
+  if (rc != BPIMD_OK) return rc;
+  const int grid = md.n_ext < sm_count() * 8 ? md.n_ext : sm_count() * 8;
+  if (ctx->w.bead32)
+    ext_force_batched<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->d_ws, ctx->d_off, md.ext_tab,
+                                                                   md.n_ext, p.pp, md.ubar_part);
+  else
+    ext_force_batched<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->d_ws, ctx->d_off, md.ext_tab,
+                                                                    md.n_ext, p.pp, md.ubar_part);
+  return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+}
+
+int enqueue_step_batched(bpimd_ctx *ctx, const MDParams &p, double *pos, double *vel) {
+  MDState &md = ctx->md;
+  cudaStream_t s = ctx->stream;
+  const long long n = ctx->total_elems;
+  const int g4 = grid_for((n + 3) / 4, MD_THREADS), g1 = grid_for(n, MD_THREADS);
+  if (ctx->w.bead32)
+    md_baoa_batched<true><<<g4, MD_THREADS, 0, s>>>(pos, vel, md.F, n, p.half_dt_over_m, p.half_dt, p.c1, md.c2r,
+                                                    ctx->d_off, ctx->R, p.k0, p.k1, md.step);
+  else
+    md_baoa_batched<false><<<g4, MD_THREADS, 0, s>>>(pos, vel, md.F, n, p.half_dt_over_m, p.half_dt, p.c1, md.c2r,
+                                                     ctx->d_off, ctx->R, p.k0, p.k1, md.step);
+  if (cudaGetLastError() != cudaSuccess) return BPIMD_ERR_CUDA;
+  int rc = total_force_batched(ctx, p, pos);
+  if (rc != BPIMD_OK) return rc;
+  md_kick_kernel<<<g1, MD_THREADS, 0, s>>>(vel, md.F, n, p.half_dt_over_m, md.step);
+  return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+}
+
+}  // namespace
+
+int md_run_batched(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies) {
+  bpimd_config c = ctx->cfg;
+  if (c.pair_type == BPIMD_PAIR_LJ) return BPIMD_ERR_ARG;  // batches have no periodic box
+  c.N = 1;
+  c.P = 2;
+  c.beta = 1.0;  // md_params' kT only fills p.c2, which batches replace per replica
+  MDParams p;
+  int rc = md_params(c, p);
+  if (rc != BPIMD_OK) return rc;
+  p.n = ctx->total_elems;
+  MDState &md = ctx->md;
+  if (!md.ready && (rc = md_alloc_batched(ctx, p)) != BPIMD_OK) return rc;
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  rc = total_force_batched(ctx, p, pos);
+  const bool use_graph = ctx->stream != nullptr && nsteps > 1;
+  if (rc == BPIMD_OK && use_graph && (!md.exec || md.g_pos != pos || md.g_vel != vel)) {
+    if (md.exec) { cudaGraphExecDestroy(md.exec); md.exec = nullptr; }
+    if (md.graph) { cudaGraphDestroy(md.graph); md.graph = nullptr; }
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = BPIMD_ERR_CUDA;
+    } else {
+      const int rc_step = enqueue_step_batched(ctx, p, pos, vel);
+      const cudaError_t e = cudaStreamEndCapture(ctx->stream, &md.graph);
+      if (rc_step != BPIMD_OK || e != cudaSuccess || cudaGraphInstantiate(&md.exec, md.graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        rc = BPIMD_ERR_CUDA;
+      } else {
+        md.g_pos = pos;
+        md.g_vel = vel;
+      }
+    }
+  }
+  for (int32_t k = 0; k < nsteps && rc == BPIMD_OK; ++k) {
+    if (use_graph) rc = cudaGraphLaunch(md.exec, ctx->stream) == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+    else rc = enqueue_step_batched(ctx, p, pos, vel);
+  }
+  if (rc == BPIMD_OK) md.steps_taken += (uint64_t)nsteps;
+  if (rc == BPIMD_OK && energies) {
+    cudaStream_t s = ctx->stream;
+    if (launch_spring_expectation_batched(ctx->d_ws, ctx->d_blk_tab, ctx->n_blk_tab, md.spring_part, s) !=
+        cudaSuccess)
+      rc = BPIMD_ERR_CUDA;
+    if (rc == BPIMD_OK) {
+      energies_batched<<<ctx->R, MD_THREADS, 0, s>>>(ctx->d_ws, ctx->d_off, md.VBr, md.ubar_part, md.ext_first,
+                                                     md.spring_part, md.blk_first, vel, 0.5 * ctx->cfg.m, energies);
       if (cudaGetLastError() != cudaSuccess) rc = BPIMD_ERR_CUDA;
     }
   }

@@ -23,9 +23,18 @@ struct MDState {
   void *cell_block;          // cell-list buffers (Lennard-Jones in a box)
   CellList cells;
   bool ready;
+  // replica batches
+  double *VBr;               // [R] V_B of every replica
+  double *c2r;               // [R] thermostat amplitude sqrt((1 - c1^2) kT_r / m)
+  int4 *ext_tab;             // (replica, particle block, bead index) of the pair-force pass
+  int n_ext;
+  int *ext_first;            // [R+1] first ext_tab entry of each replica
+  int *blk_first;            // [R+1] first block-table entry of each replica
 };
 void md_init(MDState *md);
 void md_free(MDState *md);
 int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies);
 int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F);
+int evaluate_batched(bpimd_ctx *ctx, const double *pos, double *V_B, double *F);
+int md_run_batched(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies);
 }  // namespace bpimd

@@ -80,6 +80,7 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   w.beta = cfg->beta;
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
+  w.cx = w.beta * w.half_k * LOG2E;
   if (!(cfg->box_L >= 0.0) || !(cfg->box_L < __builtin_huge_val())) return BPIMD_ERR_ARG;
   set_box(w, cfg->box_L);
   if (layout_workspace(w, nullptr) > NOALLOC_SCRATCH_BYTES) return BPIMD_ERR_SIZE;

@@ -27,7 +27,7 @@
 #include <type_traits>
 
 #include "bpimd_internal.cuh"
-#include "pow2_fixed.cuh"
+#include "pairg.cuh"
 
 namespace bpimd {
 namespace {
@@ -194,11 +194,6 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
 }
 
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // block index -> (t, s) with s <= t, blk = t(t+1)/2 + s
 // (float32 estimate of the triangular root, corrected with integer tests:
@@ -251,52 +246,26 @@ __device__ __forceinline__ void stage_endpoints(const Workspace &w, const double
 
 // g for one pair from the staged bead-P position of b (slot j of side 0) and
 // bead-1 position of a (slot i of side 1): returns the mantissa (float for
-// MIXED32, else double in [1, 2)) and sets the exponent.  cx = beta (1/2) k
-// log2(e) > 0, g = 2^(-cx d^2).
-//  FP64   : float64 difference and square; 2^(-cx d^2) from the exact
-//           53 x 53-bit product on the integer pipe (pow2_fixed.cuh).
-//  MIXED  : float32 difference (high/low parts or fixed point) and square,
-//           the same exact product and integer power: float64-accurate
-//           2^(-x) of the float32 closing-spring energy.
-//  MIXED32: float32 difference and square, hardware ex2.approx.
+// MIXED32, else double in [1, 2)) and sets the exponent (pairg.cuh; the
+// recompute mode forms the same bits from the bead pass's copies).
 template <int MODE, bool PBC>
 __device__ __forceinline__ double pair_factor(const Workspace &w, double cx, const EndTiles &E, int i, int j,
                                               int &e, const unsigned long long *T63) {
-  if (MODE != BPIMD_FP64) {
-    float fx, fy, fz;
-    if (PBC) {  // minimum image from the fixed-point copies
-      const uint4 ub = *(const uint4 *)E.v[0][j], ua = *(const uint4 *)E.v[1][i];
-      fx = fixdiff(ub.x, ua.x, w.Lscale);
-      fy = fixdiff(ub.y, ua.y, w.Lscale);
-      fz = fixdiff(ub.z, ua.z, w.Lscale);
-    } else {
-      const float4 bh = ((const float4 *)E.v[0][j])[0], bl = ((const float4 *)E.v[0][j])[1];
-      const float4 ah = ((const float4 *)E.v[1][i])[0], al = ((const float4 *)E.v[1][i])[1];
-      fx = (bh.x - ah.x) + (bl.x - al.x);
-      fy = (bh.y - ah.y) + (bl.y - al.y);
-      fz = (bh.z - ah.z) + (bl.z - al.z);
-    }
-    const float d2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-    if (MODE == BPIMD_MIXED) {
-      const pow2fx::mexp g = pow2fx::pow2neg_fd(d2, cx, T63);
-      e = g.e;
-      return g.m;
-    }
-    // exponents below -2^28 stand for zero (keeps every exponent sum in int32)
-    const float x = fmaxf(-(float)cx * d2, -268435456.0f);
-    const float n = floorf(x);
-    float mm = ex2_approx(x - n);  // in [1, 2]
-    e = (int)n;
-    if (mm >= 2.0f) { mm *= 0.5f; e += 1; }
-    return mm;
+  using EP = pairg::EndPt<MODE != BPIMD_FP64, PBC>;
+  EP rb, ra;
+  if constexpr (MODE == BPIMD_FP64) {
+    rb = EP{E.v[0][j][0], E.v[0][j][1], E.v[0][j][2]};
+    ra = EP{E.v[1][i][0], E.v[1][i][1], E.v[1][i][2]};
+  } else if constexpr (PBC) {
+    rb.u = *(const uint4 *)E.v[0][j];
+    ra.u = *(const uint4 *)E.v[1][i];
   } else {
-    const double *rb = E.v[0][j], *ra = E.v[1][i];
-    double dx = rb[0] - ra[0], dy = rb[1] - ra[1], dz = rb[2] - ra[2];
-    if (PBC) { dx = mimage(w, dx); dy = mimage(w, dy); dz = mimage(w, dz); }
-    const pow2fx::mexp g = pow2fx::pow2neg_dd(fma(dx, dx, fma(dy, dy, dz * dz)), cx, T63);
-    e = g.e;
-    return g.m;
+    rb.h = ((const float4 *)E.v[0][j])[0];
+    rb.l = ((const float4 *)E.v[0][j])[1];
+    ra.h = ((const float4 *)E.v[1][i])[0];
+    ra.l = ((const float4 *)E.v[1][i])[1];
   }
+  return (double)pairg::g_of<MODE, PBC>(w, rb, ra, cx, T63, e);
 }
 
 // One pass over the forward blocks (a = s*32+i, b = t*32+j): each valid pair
@@ -311,7 +280,7 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__r
                                            typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type *Tm,
                                            int *Te, EndTiles &E, const unsigned long long *T63) {
   using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
-  const double cx = w.beta * w.half_k * LOG2E;
+  const double cx = w.cx;
   const int N = w.N;
   M_t *gm = (M_t *)w.gm, *gbm = (M_t *)w.gbm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -350,12 +319,6 @@ __device__ __forceinline__ void gmat_block(const Workspace &w, const double *__r
   __syncthreads();
 }
 
-// Shared-memory copy of the 256-entry table of 2^(-j/256) (FP64 and MIXED
-// pair factors); published by the first barrier of gmat_block.
-__device__ __forceinline__ void pow2_table_init(unsigned long long *T) {
-  for (int j = threadIdx.x; j < 256; j += blockDim.x) T[j] = pow2fx::T63[j];
-}
-
 // One evaluation's preparation: blocks 0..nbead-1 run the bead pass (8
 // particles each), the others stride over the blocks of g.  MODE is the
 // precision form (BPIMD_FP64, BPIMD_MIXED, BPIMD_MIXED32).
@@ -367,7 +330,7 @@ __global__ void __launch_bounds__(256) prep_kernel(Workspace w, const double *__
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
   __shared__ unsigned long long T63[256];
-  if (MODE != BPIMD_MIXED32) pow2_table_init(T63);
+  if (MODE != BPIMD_MIXED32) pairg::table_init(T63);  // published by gmat_block's first barrier
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
     bead_pass_body<MODE != BPIMD_FP64>(w, pos, F, blockIdx.x * BEAD_WARPS);
@@ -394,7 +357,7 @@ __global__ void __launch_bounds__(256) prep_batched(const Workspace *__restrict_
   __shared__ int Te[TILE * 33];
   __shared__ EndTiles E;
   __shared__ unsigned long long T63[256];
-  if (MODE != BPIMD_MIXED32) pow2_table_init(T63);
+  if (MODE != BPIMD_MIXED32) pairg::table_init(T63);  // published by gmat_block's first barrier
   pdl_wait();
   if ((int)blockIdx.x < nbead) {
     const int2 e = bead_tab[blockIdx.x];
@@ -528,7 +491,7 @@ cudaError_t launch_diag_potentials(const Workspace &w, double *Vf, double *Vb, c
 cudaError_t launch_prep(const Workspace &w, const double *pos, double *F, cudaStream_t s) {
   const int nbead = (w.N + BEAD_WARPS - 1) / BEAD_WARPS;
   const int cap = sm_count() * 8;
-  const int grid = nbead + (w.NB < cap ? w.NB : cap);
+  const int grid = nbead + (w.recomp ? 0 : (w.NB < cap ? w.NB : cap));  // recompute mode: bead pass only
   switch (w.mode) {
     case BPIMD_FP64: return launch_pdl(prep_kernel<BPIMD_FP64>, grid, 256, 0, s, w, pos, F, nbead);
     case BPIMD_MIXED: return launch_pdl(prep_kernel<BPIMD_MIXED>, grid, 256, 0, s, w, pos, F, nbead);

@@ -16,7 +16,10 @@ from . import bpimd as _c
 class ExchangeEnergy:
     """Exchange potential and forces for one system of N particles, P beads."""
 
-    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None, box=0.0):
+    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None, box=0.0,
+                 recompute=False):
+        """recompute=True: no O(N^2) storage at any N (automatic above
+        BPIMD_STORE_MAX_N): the pair factors are recomputed where used."""
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
         prec = _c.PRECISIONS[precision]
@@ -30,7 +33,8 @@ class ExchangeEnergy:
             self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec, box_L=float(box))
+            self.cfg = _c.make_config(self.N, self.P, self.m, self.omega_P, self.beta, prec, box_L=float(box),
+                                      flags=_c.BPIMD_FLAG_RECOMPUTE if recompute else 0)
             self.ctx = _c.bpimd_create(self.cfg, self.stream)
             self._V = torch.empty((), dtype=torch.float64, device=self.device)
 
@@ -117,7 +121,8 @@ class RingPolymerMD:
     """
 
     def __init__(self, N, P, m, omega_P, beta, dt, gamma=1.0, omega0=0.0, gaussian=None, kT=0.0,
-                 seed=0, precision="fp64", device="cuda", stream=None, lennard_jones=None, box=0.0):
+                 seed=0, precision="fp64", device="cuda", stream=None, lennard_jones=None, box=0.0,
+                 recompute=False):
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
         prec = _c.PRECISIONS[precision]
@@ -132,6 +137,7 @@ class RingPolymerMD:
             md.update(pair_type=_c.BPIMD_PAIR_LJ, pair_a=float(lennard_jones[0]), pair_b=float(lennard_jones[1]),
                       pair_rc=float(lennard_jones[2]))
         md["box_L"] = float(box)
+        md["flags"] = _c.BPIMD_FLAG_RECOMPUTE if recompute else 0
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.cfg = _c.make_config(self.N, self.P, float(m), float(omega_P), float(beta), prec, **md)
@@ -167,10 +173,13 @@ class BatchedExchangeEnergy:
     and precision).  Positions and forces are packed: replica r is the
     [N_r][P_r][3] block at element offset ``offsets[r]`` of one flat float64
     tensor (``pack``/``unpack`` convert from/to lists of tensors).  Three kernel
-    launches per evaluation regardless of R.
+    launches per evaluation regardless of R (plus one per replica above 4096
+    particles); ``step`` runs BAOAB molecular dynamics of every replica.
     """
 
-    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None):
+    def __init__(self, N, P, m, omega_P, beta, precision="fp64", device="cuda", stream=None, md=None):
+        """md: optional molecular-dynamics parameters for ``step`` (dt, gamma,
+        omega0, gaussian=(g, s), kT, seed), shared by all replicas."""
         if not torch.cuda.is_available():
             raise RuntimeError("bpimd needs a CUDA device; there is no CPU fallback")
         prec = _c.PRECISIONS[precision]
@@ -183,8 +192,17 @@ class BatchedExchangeEnergy:
             self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            cfg = _c.make_config(0, 0, float(m), 1.0, 1.0, prec)
+            kw = {}
+            if md:
+                kw = dict(dt=float(md.get("dt", 0.0)), gamma=float(md.get("gamma", 1.0)),
+                          kT_bead=float(md.get("kT", 0.0)), omega0=float(md.get("omega0", 0.0)),
+                          seed=int(md.get("seed", 0)))
+                if md.get("gaussian") is not None:
+                    kw.update(pair_type=_c.BPIMD_PAIR_GAUSSIAN, pair_a=float(md["gaussian"][0]),
+                              pair_b=float(md["gaussian"][1]))
+            cfg = _c.make_config(0, 0, float(m), 1.0, 1.0, prec, **kw)
             self.ctx = _c.bpimd_create_batched(cfg, self.N, self.P, omega_P, beta, self.stream)
+            self.energies = torch.zeros((self.R, 4), dtype=torch.float64, device=self.device)
         _, self.elements, self.offsets = _c.bpimd_batch_info(self.ctx)
 
     def close(self):
@@ -224,6 +242,17 @@ class BatchedExchangeEnergy:
 
     def set_tuning(self, pair_blocks_per_sm, prob_blocks_per_sm):
         _c.bpimd_batch_set_tuning(self.ctx, pair_blocks_per_sm, prob_blocks_per_sm)
+
+    def step(self, pos, vel, nsteps=1, energies=True):
+        """Advance every replica by nsteps BAOAB steps (packed pos, vel in
+        place); returns the device tensor [R][4] of (V_B, U-bar, kinetic,
+        primitive estimator) per replica after the last step, or None."""
+        for t in (pos, vel):
+            if t.dtype != torch.float64 or t.device != self.device or t.numel() != self.elements \
+                    or not t.is_contiguous():
+                raise ValueError(f"positions/velocities must be contiguous packed float64 of {self.elements}")
+        _c.bpimd_step(self.ctx, pos, vel, nsteps, self.energies if energies else None)
+        return self.energies if energies else None
 
     def sync(self):
         _c.bpimd_sync(self.ctx)

@@ -23,12 +23,16 @@ from paper_2305_18025_gb300 import inputs  # noqa: E402
 CASES = [
     # name, N, P, beta, generator, seed
     ("referee_N6912_P4_trapped_seed9_beta1.txt", 6912, 4, 1.0, "trapped", 9),
+    # the largest N accepted (recompute mode; the oracle itself needs ~9 GB here)
+    ("referee_N16384_P4_trapped_seed13_beta1.txt", 16384, 4, 1.0, "trapped", 13),
 ]
 SAMPLES = 256
 
 
-def main():
+def main(only=None):
     for name, N, P, beta, gen, seed in CASES:
+        if only and only not in name:
+            continue
         pos = inputs.trapped_positions(N, P, seed)
         wP = inputs.omega_P(P, beta)
         VB, F, V, W, _ = oracle.long_double.fast_pimdb(pos, 1.0, wP, beta, full=True)
@@ -58,4 +62,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1] if len(sys.argv) > 1 else None)

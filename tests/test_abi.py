@@ -61,7 +61,7 @@ def test_config_struct_matches_header_layout():
 
 @pytest.mark.parametrize("field,value", [
     ("N", 0), ("P", 1), ("m", 0.0), ("omega_P", -1.0), ("beta", float("nan")),
-    ("beta", float("inf")), ("precision", 7), ("flags", 1), ("N", 6913),
+    ("beta", float("inf")), ("precision", 7), ("precision", 3), ("flags", 2), ("N", 16385),
     ("box_L", -1.0), ("box_L", float("nan")), ("box_L", float("inf")),
 ])
 def test_create_rejects_invalid_config_without_gpu(lib, field, value):
@@ -109,7 +109,7 @@ def test_create_batched_rejects_invalid_arguments_without_gpu(lib, case):
     elif case == "N0":
         N[1] = 0
     elif case == "Nbig":
-        N[2] = bpimd.BATCH_MAX_N + 1
+        N[2] = bpimd.BPIMD_STORE_MAX_N + 1
     elif case == "P1":
         P[0] = 1
     elif case == "beta0":
@@ -170,3 +170,13 @@ def test_binding_argument_kinds_match_the_header_prototypes():
         got = ["int" if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64) else "ptr"
                for t in argtypes]
         assert got == want, (name, plist, argtypes)
+
+
+def test_header_constants_match_the_binding():
+    """The storage limits and the recompute flag of bpimd.h, as the binding uses them."""
+    text = open(HEADER).read()
+    for name in ("BPIMD_MAX_N", "BPIMD_STORE_MAX_N", "BPIMD_FLAG_RECOMPUTE", "BPIMD_MIXED32",
+                 "BPIMD_NOALLOC_MAX_N"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", text)
+        assert m, name
+        assert int(m.group(1)) == getattr(bpimd, name), name

@@ -147,3 +147,20 @@ def test_cpu_context_reports_every_workload():
     assert set(rows) == {"N16_P32", "N32_P32"}
     assert all(r["algorithm2_ms"] > 0 and r["algorithm1_ms"] > 0 for r in rows.values())
     json.dumps(c)
+
+
+@pytest.mark.parametrize("prec,bound", [("fp64", "fp64"), ("mixed", "int"), ("mixed32", "fp32")])
+def test_every_stage_has_a_roofline_fraction(prec, bound, monkeypatch):
+    monkeypatch.setattr(bench, "load_traffic", lambda k: None)
+    units = {"fp64_fma_per_s": 1e12, "int_mad_per_s": 2e13}
+    st = bench.roofline_stages([0.014, 0.096, 0.019], ARGS, 2070.0, PEAKS, units, prec)
+    assert set(st) == {"prep", "recursions", "prob_forces"}
+    for r in st.values():
+        assert r["frac"] is not None and r["frac"] > 0
+    assert st["prep"]["bound"] == "hbm"
+    assert st["recursions"]["achieved"] == pytest.approx(1024 / 0.096e-3)
+    assert st["prob_forces"]["bound"] == bound
+    pairs = 1024 * 1025 / 2
+    if prec == "fp64":
+        assert st["prob_forces"]["achieved"] == pytest.approx(bench.PROB_F64_OPS * pairs / 0.019e-3)
+        assert st["prep"]["fp64_pipe_frac"] == pytest.approx(bench.G_F64_OPS * pairs / 0.014e-3 / 1e12)

@@ -137,3 +137,14 @@ def test_single_system_calls_rejected_on_batch_context():
         bpimd.bpimd_exchange_energy_forces(eng.ctx, x, None, torch.empty_like(x))
     assert e.value.status == bpimd.BPIMD_ERR_STATE
     eng.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_with_a_replica_above_4096(prec):
+    """A replica larger than the one-CTA recursion holds (N = 5000) runs the
+    cluster recursion kernel inside the batch; every replica matches the oracle."""
+    systems = [(make("trapped", 5000, 2, 811), 1.0), (make("clustered", 40, 8, 812), 0.8),
+               (make("trapped", 300, 4, 813), 2.0)]
+    V, Fs, eng, _ = run_batch(systems, prec)
+    eng.close()
+    check(systems, V, Fs, prec)

@@ -277,3 +277,32 @@ def test_invalid_size_rejected_on_host():
     with pytest.raises(bpimd.BpimdError) as ei:
         ExchangeEnergy(8, 1, 1.0, 2.0, 1.0, device="cuda:0")
     assert ei.value.status == bpimd.BPIMD_ERR_ARG
+
+
+@pytest.fixture(scope="module")
+def condensed_snapshot():
+    """N = 64, P = 32, beta = 0.5 trapped bosons after 4e4 BAOAB steps from a
+    compact start: a configuration from the equilibrium of the sampler, with
+    long exchange cycles (the closed-form energy of this state point is that of
+    a largely condensed system), unlike the seeded test inputs."""
+    from paper_2305_18025_gb300.exchange import RingPolymerMD
+    N, P, beta = 64, 32, 0.5
+    dev = torch.device("cuda", 0)
+    md = RingPolymerMD(N, P, 1.0, inputs.omega_P(P, beta), beta, dt=0.005, gamma=1.0, omega0=1.0, seed=5,
+                       precision="mixed32", stream=torch.cuda.Stream(dev))
+    rng = np.random.default_rng(1)
+    x = torch.tensor(rng.normal(0, 0.5, (N, 1, 3)) + rng.normal(0, 0.05, (N, P, 3)), device=dev)
+    v = torch.zeros_like(x)
+    md.step(x, v, 40000, energies=False)
+    md.close()
+    return x.cpu().numpy(), beta
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
+def test_parity_on_an_equilibrated_condensed_snapshot(prec, condensed_snapshot):
+    pos, beta = condensed_snapshot
+    wP = inputs.omega_P(pos.shape[1], beta)
+    VB, F, Vf, Vb, M = oracle.long_double.fast_pimdb(pos, 1.0, wP, beta, full=True)
+    # the exchange is strong here: most of each row's probability is off the diagonal
+    assert np.mean(np.diag(np.asarray(M, np.float64))) < 0.6
+    check(pos, beta, prec)

@@ -133,3 +133,23 @@ def test_equipartition_and_harmonic_closed_form():
         b = en[:, col].reshape(100, -1).mean(axis=1)
         err = b.std(ddof=1) / np.sqrt(len(b))
         assert abs(b.mean() - exact) < 4 * err + 1e-3 * abs(exact), (col, b.mean(), exact, err)
+
+
+def test_noise_offset_takes_the_counters_of_the_packed_position():
+    """A replica at element offset e0 of a packed batch draws, for its element
+    i, the normal of element e0 + i of one long system: the same Philox stream
+    cut at e0 (offsets that are not a multiple of 4 included)."""
+    o = oracle.float64
+    N, P = 3, 5  # 45 elements
+    pos = np.random.default_rng(4).normal(0, 1, (N, P, 3))
+    c1 = np.exp(-50.0 * 1e-6)
+    for e0 in (0, 6, 45):
+        # dt -> 0, no forces to speak of: after one step v = c2 z, so v / c2 = z
+        _, v, _ = o.md_run(pos, np.zeros((N, P, 3)), 1.0, 1e-9, 1.0, 1e-6, 50.0, 1, seed=9, kT=1.0, elem0=e0)
+        z = v.reshape(-1) / np.sqrt(1 - c1 * c1)
+        # the first e0 + 45 normals of one long system (elements of 3 particles of
+        # P = 5 per 45; the long system has (e0 + 45) / 15 particles of P = 5)
+        M = -(-(e0 + 45) // 15)
+        _, vl, _ = o.md_run(np.zeros((M, 5, 3)), np.zeros((M, 5, 3)), 1.0, 1e-9, 1.0, 1e-6, 50.0, 1, seed=9, kT=1.0)
+        zl = vl.reshape(-1) / np.sqrt(1 - c1 * c1)
+        np.testing.assert_allclose(z, zl[e0:e0 + 45], rtol=0, atol=1e-6)

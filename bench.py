@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--he-cells", type=int, default=10, help="FCC cells per side of the helium box (4 atoms each)")
     ap.add_argument("--he-P", type=int, default=64)
     ap.add_argument("--he-steps", type=int, default=20, help="timed helium MD steps (mixed; float64 a fifth)")
+    ap.add_argument("--only", choices=["all", "headline", "md", "batched", "helium"], default="all",
+                    help="run the headline exchange and only this one of the other workloads (for profiling)")
     return ap.parse_args()
 
 
@@ -374,9 +376,12 @@ def run_ours(args, rank, world, local_rank):
                                   "api": "bpimd_exchange_energy_forces_host (pinned host buffers; the call "
                                          "replays one captured CUDA graph of copies and kernels)"}
             eng.close()
-    results["md"] = md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world)
-    results["batched"] = batched_throughput(args, dev, flush, max_over_ranks, barrier, world)
-    results["helium"] = helium_throughput(args, dev, max_over_ranks, barrier, world)
+    def want(name):
+        return args.only in ("all", name)
+
+    results["md"] = md_throughput(args, pos_np, wP, dev, max_over_ranks, barrier, world) if want("md") else {}
+    results["batched"] = batched_throughput(args, dev, flush, max_over_ranks, barrier, world) if want("batched") else {}
+    results["helium"] = helium_throughput(args, dev, flush, max_over_ranks, barrier, world) if want("helium") else {}
     clocks = sampler.stop()
 
     if rank != 0:
@@ -421,9 +426,13 @@ def run_ours(args, rank, world, local_rank):
     line["summary"] = {
         "evals_per_s": {"mixed": mixed["value"], "fp64": fp64["value"], "mixed32": m32["value"],
                         "e2e_mixed": results["e2e"]["value"]},
-        "md_steps_per_s": {p: results["md"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
-        "batched_evals_per_s": {p: results["batched"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
-        "helium_md_steps_per_s": {p: results["helium"][p]["value"] for p in ("mixed", "fp64", "mixed32")},
+        "md_steps_per_s": {p: results["md"][p]["value"] for p in ("mixed", "fp64", "mixed32") if p in results["md"]},
+        "batched_evals_per_s": {p: results["batched"][p]["value"] for p in ("mixed", "fp64", "mixed32")
+                                if p in results["batched"]},
+        "helium_md_steps_per_s": {p: results["helium"][p]["value"] for p in ("mixed", "fp64", "mixed32")
+                                  if p in results["helium"]},
+        "helium_exchange_evals_per_s": {k: v["value"] for k, v in results["helium"].get("exchange", {}).items()
+                                        if isinstance(v, dict) and "value" in v},
         "recursion_frac": roof["frac"] if roof["kernel"] == "recursions" else None,
     }
     return line
@@ -533,7 +542,7 @@ def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
 HE = dict(m=4.0026, T=1.5, eps=10.22, sigma=2.556, rho=0.0218, hbar=6.9648)  # A, K, amu units
 
 
-def helium_throughput(args, dev, max_over_ranks, barrier, world):
+def helium_throughput(args, dev, flush, max_over_ranks, barrier, world):
     """Bulk liquid helium: FCC start (10^3 cells, 4000 atoms) at 0.0218 A^-3,
     P = 64, T = 1.5 K, Lennard-Jones eps = 10.22 K, sigma = 2.556 A cut and
     shifted at 2.5 sigma (cell lists), periodic box with minimum-image springs,
@@ -573,11 +582,63 @@ def helium_throughput(args, dev, max_over_ranks, barrier, world):
         out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "MD steps/s", "steps": steps,
                      "ms_per_step": ms / steps,
                      "energies_after_K": dict(zip(["V_B", "U_bar", "kinetic", "E_prim"], en))}
+    out["exchange"] = helium_exchange(args, dev, flush, pos, HE["m"], wP, beta, L, max_over_ranks, barrier, world)
     out["config"] = {"workload": f"liquid helium N={N} (FCC {cells}^3 x 4) P={P} T=1.5 K rho=0.0218/A^3 "
                                  f"box {L:.2f} A, Lennard-Jones eps=10.22 K sigma=2.556 A cut+shift 2.5 sigma",
                      "integrator": "BAOAB Langevin dt=1 fs gamma=1 (A, K, amu units), Philox noise",
                      "timing": "CUDA events around one bpimd_step call (one initial force evaluation + graph "
                                "replays); L2 not flushed between MD steps"}
+    return out
+
+
+def helium_exchange(args, dev, flush, pos, m, wP, beta, L, max_over_ranks, barrier, world, steps=10):
+    """Exchange V_B + forces of the helium box alone (mixed form), with the
+    pair factors tabulated (the default below N = 8192) and recomputed where
+    they are used (no O(N^2) storage): evaluations/s, stage times, and the
+    roofline of the recursions in recompute mode, whose DRAM traffic (from the
+    committed ncu summary) is compared with the O(N P) algorithmic bytes
+    (positions in, forces out)."""
+    import torch
+    from paper_2305_18025_gb300 import bpimd
+    from paper_2305_18025_gb300.exchange import ExchangeEnergy
+    N, P = pos.shape[0], pos.shape[1]
+    x = torch.from_numpy(pos).to(dev)
+    out = {}
+    for name, rc in (("mixed_stored", False), ("mixed_recompute", True)):
+        s = torch.cuda.Stream(dev)
+        eng = ExchangeEnergy(N, P, m, wP, beta, precision="mixed", device=dev, stream=s, box=L, recompute=rc)
+        F = torch.empty_like(x)
+        V = torch.empty((), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                flush.fill_(1)
+                eng.forces(x, out=F, V_out=V)
+            eng.sync()
+            bpimd.bpimd_profile_begin(eng.ctx, steps)
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+            barrier()
+            torch.cuda.synchronize(dev)
+            for k in range(steps):
+                flush.fill_(k & 255)
+                starts[k].record(s)
+                eng.forces(x, out=F, V_out=V)
+                ends[k].record(s)
+            torch.cuda.synchronize(dev)
+            barrier()
+            stage_ms, n = bpimd.bpimd_profile_end(eng.ctx)
+            eng.sync()
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)))
+        out[name] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / steps,
+                     "stages_ms": [x_ / max(n, 1) for x_ in stage_ms], "V_B": float(V.item())}
+        eng.close()
+    algo = 48 * N * P  # positions in + forces out
+    rec_t = out["mixed_recompute"]["stages_ms"][1] * 1e-3
+    traffic = load_traffic("recursions_recompute_helium")
+    out["roofline_recompute"] = {"kernel": "recursions (recompute mode)", "bound": "alu",
+                                 "achieved": N / rec_t, "unit": "chain steps/s",
+                                 "traffic": traffic, "algorithmic_bytes_O_NP": algo,
+                                 "traffic_over_algorithmic": (traffic / algo) if traffic else None}
     return out
 
 

@@ -340,6 +340,13 @@ int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, const double *
  * Asynchronous; BPIMD_ERR_ARG for another kind, iters < 1 or a bad sink. */
 int bpimd_peak_probe(int32_t kind, int64_t iters, void *sink, void *cuda_stream, int64_t *ops);
 
+/* Self-test of the device's powers of two (no counterpart in the paper; for
+ * tests): out[i] = 2^x[i] by the float64 table method of the MD pair force
+ * (method 0, x <= 0), or 2^(-x[i]) by the integer-pipe fixed-point method of
+ * the pair factors (method 1, x >= 0; 0 below the float64 normal range).
+ * x, out: device arrays of n float64.  Asynchronous on cuda_stream. */
+int bpimd_pow2_selftest(int32_t method, const double *x, double *out, int32_t n, void *cuda_stream);
+
 /* Human-readable text for a status code (static storage). */
 const char *bpimd_status_string(int status);
 

@@ -39,7 +39,7 @@ EXPORTED = [
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
     "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
     "bpimd_create_batched", "bpimd_exchange_energy_forces_batched", "bpimd_batch_info",
-    "bpimd_batch_set_tuning", "bpimd_peak_probe",
+    "bpimd_batch_set_tuning", "bpimd_peak_probe", "bpimd_pow2_selftest",
 ]
 BATCH_MAX_N = 4096
 BPIMD_NUM_STAGES = 3
@@ -103,6 +103,7 @@ def load(build_if_missing=True):
     lib.bpimd_batch_info.argtypes = [vp, vp, vp, vp]
     lib.bpimd_batch_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     lib.bpimd_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp]
+    lib.bpimd_pow2_selftest.argtypes = [ctypes.c_int32, vp, vp, ctypes.c_int32, vp]
     for name in EXPORTED:
         if name not in ("bpimd_status_string", "bpimd_version"):
             getattr(lib, name).restype = ip
@@ -262,3 +263,10 @@ def bpimd_peak_probe(kind, iters, sink, stream=None):
     _check(load().bpimd_peak_probe(int(kind), int(iters), _ptr(sink), _stream_handle(stream), ctypes.byref(ops)),
            "bpimd_peak_probe")
     return ops.value
+
+
+def bpimd_pow2_selftest(method, x, out, stream=None):
+    """out = 2^x (method 0, float64 table method) or 2^-x (method 1, integer
+    fixed-point method), elementwise on device tensors."""
+    _check(load().bpimd_pow2_selftest(int(method), _ptr(x), _ptr(out), int(x.numel()), _stream_handle(stream)),
+           "bpimd_pow2_selftest")

@@ -26,6 +26,21 @@ __device__ __forceinline__ double scale_nonpos(double x, int k) {
   return (ex + k <= 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
 }
 
+// acc + K * y, branch-free, for the dependency chain.  Operands are extended
+// numbers whose mantissas are normal doubles in [1, 2^60) (an extended zero is
+// carried as mantissa 1 with exponent XZERO_E, i.e. 2^-536870912).  Both
+// operands are scaled by 2^k, k <= 0 clamped at -1000, by adding k to the
+// exponent field of the high word: a clamped operand is below 2^-900 of the
+// other and cannot change the float64 sum.  One float64 FMA, five integer ops.
+__device__ __forceinline__ xd fma_chain(xd acc, double km, int ke, xd y) {
+  const int pe = ke + y.e;
+  const int E = max(acc.e, pe);
+  const int k1 = max(pe - E, -1000), k2 = max(acc.e - E, -1000);
+  const double ks = __hiloint2double(__double2hiint(km) + k1 * (1 << 20), __double2loint(km));
+  const double as = __hiloint2double(__double2hiint(acc.m) + k2 * (1 << 20), __double2loint(acc.m));
+  return xd{fma(ks, y.m, as), E};
+}
+
 // Explicit shared-memory loads (32-bit shared-window addresses).
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ double lds_f64(unsigned a) {
@@ -132,21 +147,8 @@ __device__ __forceinline__ xi xi_mul(xi a, xd c) {
 // acc + K * y with K = kk 2^(ke - 63), kk in [2^63, 2^64): the step of the
 // dependency chain.  The product kk * y.m / 2^64 lies in [2^61, 2^63), the
 // aligned sum in [2^61, 2^64); a K carrying an extended-zero exponent leaves
-// acc unchanged.  The 64-bit form truncates at 2^-59 per step (mulhi_3);
-// MIXED uses the top 32 bits of kk only (two 32 x 32-bit products, relative
-// error below 2^-30: K = c g carries a float32 g there).
-// High 64 bits of a 64 x 64-bit product from three 32 x 32-bit products
-// (independent, so they issue back to back: a shorter dependency than the
-// exact __umul64hi).  The low x low product and the carries out of the
-// cross products are dropped: the result is below the exact high word by at
-// most 3, here 2^-59 of a product in [2^61, 2^63); clamped at 2^61 so that
-// the normalisation below sees its range.
-__device__ __forceinline__ unsigned long long mulhi_3(unsigned long long a, unsigned long long b) {
-  const unsigned a1 = (unsigned)(a >> 32), a0 = (unsigned)a, b1 = (unsigned)(b >> 32), b0 = (unsigned)b;
-  const unsigned long long p = (unsigned long long)a1 * b1 + (((unsigned long long)a1 * b0) >> 32) +
-                               (((unsigned long long)a0 * b1) >> 32);
-  return max(p, 1ull << 61);
-}
+// acc unchanged.  MIXED uses the top 32 bits of kk only (two 32 x 32-bit
+// products, relative error below 2^-30: K = c g carries a float32 g there).
 template <bool MIXED>
 __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y) {
   unsigned long long p;
@@ -154,7 +156,7 @@ __device__ __forceinline__ xi xi_fma(xi acc, unsigned long long kk, int ke, xi y
     const unsigned k1 = (unsigned)(kk >> 32);
     p = (unsigned long long)k1 * (unsigned)(y.m >> 32) + (((unsigned long long)k1 * (unsigned)y.m) >> 32);
   } else {
-    p = mulhi_3(kk, y.m);
+    p = __umul64hi(kk, y.m);
   }
   const int pe = ke + y.e + 1;
   const int E = max(acc.e, pe);
@@ -404,7 +406,6 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
     y = xi_from(y0);
   }
   nxt = xd{1.0, XZERO_E};
-  xi nx{1ull << 62, XZERO_E};  // FP64 layout: the next tile's partial sum, integer format
   float nsum = 0.0f;  // MIXED: the next tile's partial sum in float32
   int nexp = XZERO_E;
   const unsigned aKm = smem_addr(Kdm + lane), aKe = smem_addr(Kde + lane), aHe = smem_addr(Hoe + lane);
@@ -432,17 +433,14 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
       fmerge(nsum, nexp, __int_as_float((int)((y.m >> 7) & 0x7FFFFFu) | 0x3F800000) * hf, he + y.e);
     } else {
       acc = xi_fma<false>(acc, km, ke, y);  // the dependency chain
-      // next tile's rows, off the chain: the same integer format (a float64
-      // FMA here would make a second dependent chain of ~110 cycles a step)
-      nx = xi_fma<false>(nx, (((unsigned long long)__double_as_longlong(hm) & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11,
-                         he, y);
+      nxt = fma_chain(nxt, hm, he, xi_to_xd(y));
     }
     y.m = __shfl_sync(0xffffffffu, acc.m, i);
     y.e = __shfl_sync(0xffffffffu, acc.e, i);
     km = km1; hm = hm1; hf = hf1; ke = ke1; he = he1;
   }
   if (MIXED) nxt = xd{f2d_int(nsum), nexp};
-  else nxt = xi_to_xd(nx);
+
   if (row < N) {  // Y_{row+1} = final accumulator of row `row`
     xd yn;
     if constexpr (MIXED) yn = xs_to_xd(acc);

@@ -53,3 +53,39 @@ extern "C" int bpimd_peak_probe(int32_t kind, int64_t iters, void *sink, void *c
   if (ops) *ops = (int64_t)blocks * PEAK_THREADS * 8 * iters;
   return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
 }
+
+// ------------------------------------------------ powers-of-two self-test
+// The device's own powers of two on caller-given arguments, for tests that
+// compare them with a reference exp2: method 0 = the float64 table method of
+// the MD pair force (exp2_table.cuh), 2^y for y <= 0; method 1 = the
+// integer-pipe fixed-point method of the pair factors (pow2_fixed.cuh),
+// 2^(-x) for x >= 0 (the result as a double, 0 below the normal range).
+#include "exp2_table.cuh"
+#include "pow2_fixed.cuh"
+
+namespace bpimd {
+namespace {
+__global__ void pow2_selftest_kernel(int method, const double *__restrict__ x, double *__restrict__ out, int n) {
+  __shared__ double T64[64];
+  exp2_table_init(T64);
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (method == 0) {
+      out[i] = exp2_table(x[i], T64);
+    } else {
+      const pow2fx::mexp g = pow2fx::pow2neg(x[i], pow2fx::T63);
+      out[i] = g.e < -1022 ? 0.0 : g.m * __longlong_as_double((long long)(g.e + 1023) << 52);
+    }
+  }
+}
+}  // namespace
+}  // namespace bpimd
+
+extern "C" int bpimd_pow2_selftest(int32_t method, const double *x, double *out, int32_t n, void *cuda_stream) {
+  using namespace bpimd;
+  if ((method != 0 && method != 1) || n < 0 || (n > 0 && (!x || !out))) return BPIMD_ERR_ARG;
+  if (n == 0) return BPIMD_OK;
+  pow2_selftest_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, (cudaStream_t)cuda_stream>>>(
+      method, x, out, n);
+  return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
+}

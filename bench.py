@@ -632,13 +632,20 @@ def helium_exchange(args, dev, flush, pos, m, wP, beta, L, max_over_ranks, barri
         out[name] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "evals/s", "ms_per_step": ms / steps,
                      "stages_ms": [x_ / max(n, 1) for x_ in stage_ms], "V_B": float(V.item())}
         eng.close()
-    algo = 48 * N * P  # positions in + forces out
+    # O(N) algorithmic bytes of the two recursions in recompute mode: per
+    # particle and recursion both float32 endpoint copies of the periodic
+    # box (2 x 16 bytes), the coefficient c (12) and Y written (12); the
+    # forward one also reads Ap, n (12) and writes C' (8).  The evaluation
+    # as a whole moves O(N P): positions in, forces out (48 N P).
+    algo_rec = N * (2 * (2 * 16 + 12 + 12) + 20)
     rec_t = out["mixed_recompute"]["stages_ms"][1] * 1e-3
     traffic = load_traffic("recursions_recompute_helium")
     out["roofline_recompute"] = {"kernel": "recursions (recompute mode)", "bound": "alu",
                                  "achieved": N / rec_t, "unit": "chain steps/s",
-                                 "traffic": traffic, "algorithmic_bytes_O_NP": algo,
-                                 "traffic_over_algorithmic": (traffic / algo) if traffic else None}
+                                 "traffic": traffic, "algorithmic_bytes_O_N": algo_rec,
+                                 "traffic_over_algorithmic": (traffic / algo_rec) if traffic else None,
+                                 "stored_tables_bytes": 2 * (N * (N + 1) // 2) * 12,
+                                 "eval_algorithmic_bytes_O_NP": 48 * N * P}
     return out
 
 

@@ -104,6 +104,8 @@ size_t layout_workspace(Workspace &w, char *base) {
   w.rowcnt = tables ? (int *)take(sizeof(int) * NT) : nullptr;
   w.colcnt = tables ? (int *)take(sizeof(int) * NT) : nullptr;
   w.status = (int *)take(sizeof(int) * 4);
+  w.bk = w.blocks ? (unsigned long long *)take(sizeof(unsigned long long) * 4 * NT * TILE2) : nullptr;
+  w.be = w.blocks ? (int *)take(sizeof(int) * 4 * NT * TILE2) : nullptr;
   return off;
 }
 
@@ -204,6 +206,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.half_k = 0.5 * w.k;
   w.cx = w.beta * w.half_k * LOG2E;
   w.recomp = (cfg->flags & BPIMD_FLAG_RECOMPUTE) || cfg->N > BPIMD_STORE_MAX_N;
+  w.blocks = 1;
   set_box(w, cfg->box_L);
   const size_t N = w.N;
   // one allocation: the workspace, then the diagnostic potentials

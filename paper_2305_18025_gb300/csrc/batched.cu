@@ -101,6 +101,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
     w.k = cfg->m * omega_P[r] * omega_P[r];
     w.half_k = 0.5 * w.k;
     w.cx = w.beta * w.half_k * LOG2E;
+    w.blocks = N[r] > BATCH_MAX_N;  // those take the cluster recursion
     wbytes += align256(layout_workspace(w, nullptr));
     ctx->h_off[r] = off;
     off += 3LL * N[r] * P[r];

@@ -174,6 +174,13 @@ struct Workspace {
   // (the last block of a tile forms its forces and resets the count to 0)
   int *rowcnt, *colcnt;
   int *status;          // device status word
+  // blocked recursions (cluster kernel): per recursion and row tile, the
+  // c-scaled coupling block Dc to the previous tile's unknowns and the tile
+  // inverse M = (I - L)^{-1}, as 64-bit integer mantissas in [2^63, 2^64) and
+  // exponents, [recursion][tile][Dc, M][row][source]
+  int blocks;           // 1: bk/be present (single systems; batch replicas above BATCH_MAX_N)
+  unsigned long long *bk;
+  int *be;
 };
 
 // Precision form of a workspace (the three BPIMD_* precision values).

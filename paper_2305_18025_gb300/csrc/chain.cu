@@ -1,5 +1,7 @@
-// Forward and backward potential recursions, one thread-block cluster each
-// (the two clusters run concurrently).
+// Forward and backward potential recursions as blocked triangular solves: one
+// kernel forms the inverses of the diagonal tiles, then one thread-block
+// cluster per recursion runs the row tiles in order (the two clusters run
+// concurrently).
 //
 // Forward  (Eq. our-forward-potential-recurrence, linear-space form):
 //   y_0 = 1,  y_{r+1} = c_{r+1} * S_r,  S_r = sum_{w<=r} y_w g(w+1, r+1)
@@ -7,50 +9,49 @@
 // r = N-1-a and sources w = N-1-b so that it has the same lower-triangular
 // shape:  Y_0 = mu_N = 1, S_r = B_{a+1} = sum_{w<=r} Y_w g(a+1, b+1),
 //   Y_{r+1} = mu_a = c_a * S_r   (c_0 := 1 for the last row, Y_N = B_1).
-// Both are lower-triangular solves with the matrix H of pair factors g, and
-// with K(w, r) = c_r H(w, r) each is  Y_{r+1} = sum_{w<=r} K(w, r) Y_w.
+// Both read  Y_{r+1} = c_r sum_{w<=r} H(w, r) Y_w  with the pair factors H of
+// the recursion's own coordinates and c_r its row coefficient.
 //
-// GB300 facts behind the schedule (measured): a float64 FMA has a 64-cycle
-// latency (plus ~40 before a shuffle can read it), while the integer form of
-// the step below takes ~100 cycles including its shuffle with 64-bit
-// mantissas and ~80 with the 32-bit words of MIXED; a release/acquire
-// hand-off between warps inside a step costs far more than the step itself;
-// a cluster barrier costs ~360 cycles and a distributed shared-memory access
-// ~215.  So the rows are processed in tiles of 32 and
-//   * all intra-tile work stays in one warp of the lead CTA (cluster rank 0):
-//     warp 0 runs the 32 dependent steps of row tile t.  Lane j holds
-//     c_r * (partial row sum) of row 32t+j and the partial sum of row
-//     32(t+1)+j.  A step is one integer extended multiply-add on the current
-//     row (the dependency chain: acc_j += K(i, j) y_i with integer
-//     mantissas, 32-bit words in MIXED and 64-bit in FP64, chain_common.cuh),
-//     one term of the next tile's row (off the chain), and a shuffle that
-//     broadcasts the new Y;
-//   * twelve other lead warps (none on warp 0's sub-partition) stage, for
-//     tile t+1, the block of H from source tile t+1 to the rows of tile t+2
-//     and the diagonal block pre-scaled by c; one more lead warp of the
-//     forward cluster forms the prefix sums C, one tile of 32 per period;
-//   * the O(N^2) bulk runs on the other CTAs of the cluster (seven, or
+// Blocked form.  Row tile t (rows r = 32t + j) has the unknowns
+// X^t_j = Y_{32t+1+j}; the previous tile's unknowns X^{t-1} are the sources
+// 32t-31 .. 32t (X^{-1} = (0, ..., 0, Y_0)).  Then
+//   X^t = b^t + L^t X^t,      L^t(j, i) = c_r H(32t+1+i, r)  for i < j,
+//   b^t_j = c_r A^t_j + sum_i Dc^t(j, i) X^{t-1}_i,   Dc^t(j, i) = c_r H(32t-31+i, r),
+// where A^t_j sums the sources before X^{t-1} (w <= 32t-32).  Hence
+//   X^t = M^t b^t,   M^t = (I - L^t)^{-1} = sum_{k<32} (L^t)^k,
+// a unit lower-triangular matrix with nonnegative entries (L^t is strictly
+// lower triangular and nonnegative), so every sum below adds nonnegative
+// terms: no cancellation anywhere.  M^t and Dc^t depend on the positions only;
+// tile_inverse_kernel forms them for every tile at once, spread over the GPU,
+// and the sequential part of a recursion is two 32 x 32 matrix-vector
+// products per tile instead of 32 dependent steps.
+//
+// Cluster schedule.  GB300 facts behind it (measured): a cluster barrier costs
+// ~360 cycles and a distributed shared-memory access ~215; a float64 FMA has a
+// 64-cycle latency and the SM's float64 pipe retires ~1.7 lanes per clock,
+// against ~19 for a 32 x 32 -> 64-bit integer multiply-add.
+//   * The lead CTA (cluster rank 0) runs tile t in period t with eight warps,
+//     four rows each; a row's 32 sources are split over eight lanes (four
+//     products per lane) and reduced by three shuffle levels.  Phase 1 forms
+//     b^t = c A^t + Dc^t X^{t-1}, phase 2 X^t = M^t b^t; both use 64-bit
+//     integer mantissas (the xi format of chain_common.cuh): no float64
+//     instruction on the sequential path.  The warps prefetch the next tile's
+//     rows of Dc and M into registers during the current period.  One more
+//     warp copies each finished tile of Y to global memory one period later,
+//     another forms the prefix sums C' (forward recursion).
+//   * The O(N^2) bulk runs on the other CTAs of the cluster (seven, or
 //     fifteen in the 16-CTA form used above N = 1280): row tile T belongs to
-//     CTA 1 + T mod NH, which keeps its rows' partial sums in its own shared
-//     memory.  In period t each of them adds source tile t-1 to
-//     every row tile T >= t+1 it owns: one warp per (row tile, quarter of 8
-//     sources), each reading its 8 values of Y from the lead's shared memory
-//     and issuing its 16 loads at once; the quarters are then combined in a
-//     fixed order, and the owner of tile t+1 writes that tile's finished
-//     sums into the lead.
-// The float64 pipe of an SM is shared by all its warps and is slow on GB300
-// (a warp-wide float64 instruction occupies it for about 64 cycles), so
-// outside the dependency chain the kernel uses integer and float32 work:
-// staging converts and scales mantissas with integer arithmetic, and MIXED
-// sums the next tile's rows in float32.
+//     CTA 1 + T mod NH, which keeps its rows' sums A in its own shared memory.
+//     In period t each adds X^{t-1} to every row tile T >= t+1 it owns: one
+//     warp per (row tile, quarter of 8 sources), 64-bit integer products of
+//     the float64 factors (float32 products of BPIMD_MIXED32's float32
+//     factors); the quarters are combined in a fixed order, and the owner of
+//     tile t+1 hands c A^{t+1} to the lead.
 // Periods are separated by one cluster barrier (release/acquire), which also
-// orders every distributed shared-memory access; nothing spins.
-// Each recursion reads H from a copy of the pair factors laid out in its own
-// (row, source) coordinates, so all block loads are coalesced.
-// Every value is an extended number m * 2^e (int32 exponent), so no exp/log
-// sits on the dependency chain.  MIXED: the bulk products are summed in
-// float32 per 32-source tile and added to the float64 row accumulator; the
-// tile hand-offs stay float64 and the dependent steps use the integer format.
+// orders every distributed shared-memory access; nothing spins.  Every value
+// is an extended number m * 2^e (int32 exponent), so no exp or log is
+// evaluated in the recursions; each recursion reads its own copy of the pair
+// factors, laid out in its (source, row) coordinates, with coalesced loads.
 #include <cooperative_groups.h>
 #include <mutex>
 #include <type_traits>
@@ -64,65 +65,199 @@ namespace {
 
 using namespace chain_detail;
 
-// Bulk CTAs per recursion (NH): 7 in an 8-CTA cluster; 15 in a 16-CTA
-// cluster (a non-portable size that GB300 grants on request) once N is large
-// enough for the bulk work, rather than the chain, to set the pace.
-constexpr int YRING = 128;                // Y values kept in the lead (4 tiles)
+constexpr int YRING = 128;       // Y values kept in the lead (4 tiles)
+constexpr int LEAD_WARPS = 8;    // warps of the two phases
+constexpr int EXPORT_WARP = 8;   // copies finished tiles of Y to global memory
+constexpr int PREFIX_WARP = 9;   // prefix sums C' (forward recursion)
+constexpr int TINV_THREADS = 1024;
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  unsigned long long Kdm[2 * BLK];  // c-scaled diagonal blocks (double buffer)
-  double Hom[2 * BLK];  // H(source of tile t, row of tile t+1) (double buffer; MIXED: floats)
-  double Ym[YRING];     // Y_v at v mod YRING
-  double Am[2 * TILE];  // bulk row sums of the next tile, written by its owner
-  double misc[4];       // end of the forward recursion: C'[N], 1/(N y_N) mantissa
-  long long nsum;       // sum of the exponent parts n carried by y_N
-  int Kde[2 * BLK];
-  int Hoe[2 * BLK];
+  // Dc and M of the current and the next tile (bulk copies, double buffer)
+  unsigned long long Bk[2][2 * TILE2];
+  int Be[2][2 * TILE2];
+  unsigned long long mbar[2];      // completion of the copies into Bk/Be[b]
+  unsigned long long Ym[YRING];    // Y_v at v mod YRING (xi mantissas)
+  unsigned long long cAm[2 * TILE];  // c A of the coming tile, written by its owner (double buffer)
+  unsigned long long bm[TILE];     // b of the current tile (phase 1 -> phase 2)
+  double misc[4];                  // end of the forward recursion: C'[N], 1/(N y_N) mantissa
+  long long nsum;                  // sum of the exponent parts n carried by y_N
   int Ye[YRING];
-  int Ae[2 * TILE];
-  int misci[4];         // 1/(N y_N) exponent
-  unsigned long long T63[256];  // recompute mode: table of the integer-pipe power of two
+  int cAe[2 * TILE];
+  int be[TILE];
+  int misci[4];                    // 1/(N y_N) exponent
 };
 
-// Shared memory of a bulk CTA: its rows' partial sums (local tile lt = T / 7),
-// one slot of 8 Y values per warp, and the partial sums of the current period
-// (4 quarter-tiles of 8 sources per owned row tile).
+// Shared memory of a bulk CTA: the last two tiles of X written by the lead
+// (at offset 0, where the lead addresses them), its rows' sums (local tile
+// lt = T / NH) and the partial sums of the current period (4 quarter-tiles of
+// 8 sources per owned row tile), all in the xi format, and (stored factors)
+// one staging slot per warp for the factors of its next task.
 struct HelperSmem {
-  double *Am;   // [ltiles][32]
-  int *Ae;      // [ltiles][32]
-  double *Pm;   // [4 * ltiles][32] partial sums of the period (MIXED: floats)
-  int *Pe;      // [4 * ltiles][32]
-  double *Yd;   // [32 warps][8] Y mantissas (MIXED: floats)
-  int *Yx;      // [32 warps][8] exponents
+  unsigned long long *Xm;  // [2][32] X^t in slot t & 1
+  int *Xe;
+  unsigned long long *mbar;  // [32 warps] staging completion
+  unsigned long long *Am;  // [ltiles][32]
+  int *Ae;
+  unsigned long long *Pm;  // [4 * ltiles][32]
+  int *Pe;
+  unsigned long long *Sm;  // [32 warps][8 sources][32 lanes] factor mantissas (float: low half used)
+  int *Se;
+  double *Cm;              // [ltiles][32] row coefficients c of the owned rows
+  int *Ce;
 };
 
 __host__ __device__ constexpr int helper_tiles(int NT, int NH) { return (NT + NH - 1) / NH; }
 
-__host__ __device__ constexpr size_t helper_smem_bytes(int NT, int NH) {
-  return (size_t)helper_tiles(NT, NH) * TILE * (sizeof(double) + sizeof(int)) * 5 +
-         (size_t)32 * 8 * (sizeof(double) + sizeof(int)) + 256 * sizeof(unsigned long long);
+__host__ __device__ constexpr size_t helper_smem_bytes(int NT, int NH, bool RC) {
+  return (size_t)helper_tiles(NT, NH) * TILE * (sizeof(unsigned long long) + sizeof(int)) * 6 +
+         (size_t)2 * TILE * (sizeof(unsigned long long) + sizeof(int)) + 32 * sizeof(unsigned long long) +
+         256 * sizeof(unsigned long long) +
+         (RC ? 0 : (size_t)(CHAIN_THREADS / 32) * 8 * TILE * (sizeof(unsigned long long) + sizeof(int)));
 }
 
-// Staging of the next tile's blocks from the stored factors or, in recompute
-// mode, from the endpoint copies (the box flag is read at run time).
-template <int MODE, bool BWD, bool RC, int NR>
-__device__ __forceinline__ void stage_diag_any(const Workspace &w, int tt, int i0, unsigned long long *dm, int *de,
-                                               const unsigned long long *T63) {
-  if constexpr (!RC) stage_diag<MODE == BPIMD_MIXED32, BWD, NR>(w, tt, i0, dm, de);
-  else if (w.pbc) stage_diag_rc<MODE, BWD, true, NR>(w, tt, i0, dm, de, T63);
-  else stage_diag_rc<MODE, BWD, false, NR>(w, tt, i0, dm, de, T63);
+// Row r's pair factors H(src, r) as stored, or recomputed from the endpoint
+// copies (bit-identical), as c_r H in the K format.
+template <int MODE, bool BWD, bool RC, bool PBC>
+struct RowFactors {
+  using M_t = typename std::conditional<MODE == BPIMD_MIXED32, float, double>::type;
+  RowEnds<MODE, BWD, PBC> re;
+  int r;
+  __device__ __forceinline__ void load(const Workspace &w, int row) {
+    r = row;
+    if (RC) re.load(w, row);
+  }
+  __device__ __forceinline__ void h(const Workspace &w, int src, const unsigned long long *T63, M_t &m,
+                                    int &e) const {
+    if constexpr (RC) {
+      m = re.h(w, src, T63, e);
+    } else {
+      const size_t gi = hidx(src, r);
+      m = __ldg((const M_t *)chain_gm<BWD>(w) + gi);
+      e = __ldg(chain_ge<BWD>(w) + gi);
+    }
+  }
+  __device__ __forceinline__ xk k(const Workspace &w, xd c, int src, const unsigned long long *T63) const {
+    M_t m;
+    int e;
+    h(w, src, T63, m, e);
+    return mul_mant<M_t>(c, m, e);
+  }
+};
+
+// Base of tile t's blocks of one recursion: Dc at +0, M at +TILE2.
+__device__ __forceinline__ size_t tile_block_base(const Workspace &w, bool bwd, int t) {
+  return (size_t)((bwd ? w.NT : 0) + t) * 2 * TILE2;
 }
-template <int MODE, bool BWD, bool RC, int NR>
-__device__ __forceinline__ void stage_offdiag_any(const Workspace &w, int tt, int i0, void *dm, int *de,
-                                                  const unsigned long long *T63) {
-  if constexpr (!RC) stage_offdiag<MODE == BPIMD_MIXED32, BWD, NR>(w, tt, i0, dm, de);
-  else if (w.pbc) stage_offdiag_rc<MODE, BWD, true, NR>(w, tt, i0, dm, de, T63);
-  else stage_offdiag_rc<MODE, BWD, false, NR>(w, tt, i0, dm, de, T63);
+// Layout of a 32 x 32 tile block, in the order the lead's phase warps read it:
+// warp w (rows 4w .. 4w+3) lane l = 8 (j & 3) + g holds sources 4g .. 4g+3 of
+// row j; a warp's mantissas are two planes of 16-byte pairs (sources 4g, 4g+1
+// and 4g+2, 4g+3), its exponents one plane of 16-byte quads, so each read is
+// one conflict-free 16-byte load per lane.  Entry (j, i) sits at mantissa
+// index 2 (32 (2 (j/4) + (i/2)%2) + 8 (j%4) + i/4) + i%2 and exponent index
+// 4 (32 (j/4) + 8 (j%4) + i/4) + i%4; blk_jk / blk_je give (j, i) of an index.
+__device__ __forceinline__ int2 blk_jk(int x) {  // (j, i) of mantissa index x
+  const int l = (x >> 1) & 31, z = x >> 6;
+  return make_int2((z >> 1) * 4 + (l >> 3), (l & 7) * 4 + (z & 1) * 2 + (x & 1));
+}
+__device__ __forceinline__ int2 blk_je(int x) {  // (j, i) of exponent index x
+  const int l = (x >> 2) & 31;
+  return make_int2((x >> 7) * 4 + (l >> 3), (l & 7) * 4 + (x & 3));
+}
+
+// ---------------------------------------------------------- tile inverses
+// One CTA per (tile, recursion), one warp per source column: thread (i, j)
+// forms L(j, i) and Dc(j, i) of row j; then warp k forms column k of M by
+// forward substitution, M(:, k) = e_k + L M(:, k): lane j holds M(j, k),
+// and step s adds L(j, s) M(s, k) once M(s, k) is final (s >= k).
+template <int MODE, bool BWD, bool RC, bool PBC>
+__device__ void tile_inverse_body(const Workspace &w, int t, const unsigned long long *T63,
+                                  unsigned long long (*Lk)[TILE + 1], int (*Le)[TILE + 1],
+                                  unsigned long long (*Ok)[TILE + 1], int (*Oe)[TILE + 1]) {
+  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
+  const int r0 = t * TILE, row = r0 + lane;
+  xk L{1ull << 63, XZERO_E}, D{1ull << 63, XZERO_E};
+  if (row < w.N) {
+    const xd c = xnorm_int(chain_coef<BWD>(w, row));
+    RowFactors<MODE, BWD, RC, PBC> f;
+    f.load(w, row);
+    if (i < lane) L = f.k(w, c, r0 + 1 + i, T63);
+    if (r0 - 31 + i >= 0) D = f.k(w, c, r0 - 31 + i, T63);
+  }
+  Lk[i][lane] = L.m;
+  Le[i][lane] = L.e;
+  Ok[lane][i] = D.m;
+  Oe[lane][i] = D.e;
+  __syncthreads();
+  const size_t base = tile_block_base(w, BWD, t);
+  const int x = threadIdx.x;
+  const int2 pk = blk_jk(x), pe = blk_je(x);
+  w.bk[base + x] = Ok[pk.x][pk.y];  // Dc
+  w.be[base + x] = Oe[pe.x][pe.y];
+  __syncthreads();
+  const int k = i;
+  xi acc{1ull << 62, lane == k ? 0 : XZERO_E};
+  for (int s = k; s < TILE - 1; ++s) {
+    xi y;
+    y.m = __shfl_sync(0xffffffffu, acc.m, s);
+    y.e = __shfl_sync(0xffffffffu, acc.e, s);
+    acc = xi_fma<false>(acc, Lk[s][lane], Le[s][lane], y);
+  }
+  Ok[lane][k] = acc.m << 1;  // the K format: the same value
+  Oe[lane][k] = acc.e;
+  __syncthreads();
+  w.bk[base + TILE2 + x] = Ok[pk.x][pk.y];  // M
+  w.be[base + TILE2 + x] = Oe[pe.x][pe.y];
+}
+
+template <int MODE, bool RC>
+__global__ void __launch_bounds__(TINV_THREADS) tile_inverse_kernel(Workspace w) {
+  __shared__ unsigned long long Lk[TILE][TILE + 1], Ok[TILE][TILE + 1];
+  __shared__ int Le[TILE][TILE + 1], Oe[TILE][TILE + 1];
+  __shared__ unsigned long long T63[256];
+  if (RC) {
+    pairg::table_init(T63);
+    __syncthreads();
+  }
+  pdl_wait();
+  pdl_trigger();  // the recursions wait for this grid's completion
+  const int t = blockIdx.x;
+  const bool bwd = blockIdx.y != 0;
+  if (w.pbc) {
+    if (bwd) tile_inverse_body<MODE, true, RC, true>(w, t, T63, Lk, Le, Ok, Oe);
+    else tile_inverse_body<MODE, false, RC, true>(w, t, T63, Lk, Le, Ok, Oe);
+  } else {
+    if (bwd) tile_inverse_body<MODE, true, RC, false>(w, t, T63, Lk, Le, Ok, Oe);
+    else tile_inverse_body<MODE, false, RC, false>(w, t, T63, Lk, Le, Ok, Oe);
+  }
+}
+
+// ------------------------------------------------------------ recursions
+// This lane's four entries (row 4 wid + lane/8, sources 4 (lane%8) .. +3) of
+// a tile block in shared memory (the blk_k / blk_e layout).
+__device__ __forceinline__ void load_row4(const unsigned long long *bk, const int *be, int wid, int lane,
+                                          unsigned long long (&k)[4], int (&e)[4]) {
+  const ulonglong2 a = *(const ulonglong2 *)(bk + (((wid * 2 + 0) * 32 + lane) << 1));
+  const ulonglong2 b = *(const ulonglong2 *)(bk + (((wid * 2 + 1) * 32 + lane) << 1));
+  const int4 q = *(const int4 *)(be + ((wid * 32 + lane) << 2));
+  k[0] = a.x; k[1] = a.y; k[2] = b.x; k[3] = b.y;
+  e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
+}
+
+// Reduce an xsum over the eight lanes of a row (lane bits 0..2).
+__device__ __forceinline__ xsum row_reduce(xsum s) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    xsum u;
+    u.s = __shfl_xor_sync(0xffffffffu, s.s, o);
+    u.E = __shfl_xor_sync(0xffffffffu, s.E, o);
+    s = xsum_add(s, u);
+  }
+  return s;
 }
 
 // Recompute mode: the 8 factors H(sb + i, r) of one bulk task (rows past N
-// get extended zeros).
+// get extended zeros; sources below 0 meet X^{-1}'s zeros and read H(0, r)).
 template <int MODE, bool BWD, typename M_t>
 __device__ __forceinline__ void bulk_factors_rc(const Workspace &w, int r, int sb, const unsigned long long *T63,
                                                 M_t (&m)[8], int (&e)[8]) {
@@ -135,12 +270,12 @@ __device__ __forceinline__ void bulk_factors_rc(const Workspace &w, int r, int s
     RowEnds<MODE, BWD, true> re;
     re.load(w, r);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) m[i] = re.h(w, sb + i, T63, e[i]);
+    for (int i = 0; i < 8; ++i) m[i] = re.h(w, max(sb + i, 0), T63, e[i]);
   } else {
     RowEnds<MODE, BWD, false> re;
     re.load(w, r);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) m[i] = re.h(w, sb + i, T63, e[i]);
+    for (int i = 0; i < 8; ++i) m[i] = re.h(w, max(sb + i, 0), T63, e[i]);
   }
 }
 
@@ -149,15 +284,14 @@ __device__ __forceinline__ void bulk_factors_rc(const Workspace &w, int r, int s
 // formed from the endpoint copies wherever it is used.
 template <int MODE, bool BWD, int NHELP, bool RC>
 __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V_B) {
-  constexpr bool MIXED = MODE == BPIMD_MIXED32;
+  constexpr bool MIXED = MODE == BPIMD_MIXED32;  // float32 factors and bulk products
   cg::cluster_group cluster = cg::this_cluster();
   const unsigned rank = cluster.block_rank();
   const int N = w.N, NT = w.NT;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // H(src, row) in this recursion's own coordinates (both copies share the layout)
   using M_t = typename std::conditional<MIXED, float, double>::type;
-  const void *gm = BWD ? w.gbm : w.gm;
-  const int *ge = BWD ? w.gbe : w.ge;
+  const M_t *gm = (const M_t *)chain_gm<BWD>(w);
+  const int *ge = chain_ge<BWD>(w);
   double *gYm = BWD ? w.ybm : w.yfm;
   int *gYe = BWD ? w.ybe : w.yfe;
   LeadSmem *lead_local = (LeadSmem *)smem_raw;
@@ -166,68 +300,110 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 
   if (rank == 0) {
     LeadSmem &sm = *lead_local;
-    // Staging warps are the lead's warps off warp 0's sub-partition (warp id
-    // not a multiple of 4), numbered q = 0, 1, ...: q < 8 stage four rows each
-    // of the diagonal block, 8 <= q < 12 eight rows each of the off-diagonal
-    // block, q == 12 forms the prefix sums (forward recursion), q == 13
-    // copies each finished tile of Y to global memory one period later.
-    if (tid < 2 * TILE) { sm.Am[tid] = 0.0; sm.Ae[tid] = XZERO_E; }
-    if (tid == 0) { sm.Ym[0] = 1.0; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
+    for (int v = tid; v < YRING; v += blockDim.x) { sm.Ym[v] = 1ull << 62; sm.Ye[v] = XZERO_E; }
+    if (tid < 2 * TILE) { sm.cAm[tid] = 1ull << 62; sm.cAe[tid] = XZERO_E; }
+    __syncthreads();
+    if (tid == 0) { sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
     if (!BWD && tid == 0) w.C[0] = 0.0;
-    const int q = (wid & 3) ? wid - (wid >> 2) - 1 : -1;  // staging index (-1: SMSP of warp 0)
-    if (RC) {
-      pairg::table_init(sm.T63);
-      __syncthreads();
+    // tile t's Dc and M arrive by bulk copy in buffer t & 1, issued one period ahead
+    const unsigned mb0 = smem_addr(&sm.mbar[0]);
+    auto issue_tile = [&](int tt) {
+      const int b = tt & 1;
+      const size_t base = tile_block_base(w, BWD, tt);
+      fence_proxy_async();
+      mbar_expect_tx(mb0 + 8 * b, 2 * TILE2 * (sizeof(unsigned long long) + sizeof(int)));
+      bulk_g2s(smem_addr(sm.Bk[b]), w.bk + base, 2 * TILE2 * sizeof(unsigned long long), mb0 + 8 * b);
+      bulk_g2s(smem_addr(sm.Be[b]), w.be + base, 2 * TILE2 * sizeof(int), mb0 + 8 * b);
+    };
+    if (tid == 0) {
+      mbar_init(mb0, 1);
+      mbar_init(mb0 + 8, 1);
+      mbar_fence_init();
+      issue_tile(0);
     }
-    if (q >= 0 && q < 8) stage_diag_any<MODE, BWD, RC, 4>(w, 0, 4 * q, sm.Kdm, sm.Kde, sm.T63);
-    if (q >= 8 && q < 12) stage_offdiag_any<MODE, BWD, RC, 8>(w, 0, 8 * (q - 8), sm.Hom, sm.Hoe, sm.T63);
+    // phase warps: rows j = 4 wid + (lane >> 3), sources 4g .. 4g+3 (g = lane & 7)
+    const int g = lane & 7, jrow = 4 * wid + (lane >> 3);
     cluster.sync();
 
-    xd nxt{1.0, XZERO_E};  // warp 0: partial sum of row 32(t+1)+lane over source tile t
-    xd cnext{1.0, 0};      // warp 0: coefficient of its row in the coming tile
-    if (wid == 0 && lane < N) cnext = chain_coef<BWD>(w, lane);
     double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
     long long ncarry = 0;  // and the running sum of the exponent parts n
     for (int t = 0; t < NT; ++t) {
       const int buf = t & 1;
-      if (wid == 0) {
-        // ---------------------------------------------- dependent steps of tile t
-        const int row = t * TILE + lane;
-        const xd crow = cnext;
-        if (row + TILE < N) cnext = chain_coef<BWD>(w, row + TILE);  // prefetch for tile t+1
-        chain_tile<MIXED>(N, t, xd{sm.Am[buf * TILE + lane], sm.Ae[buf * TILE + lane]}, crow, nxt,
-                          sm.Kdm + buf * BLK, sm.Kde + buf * BLK, sm.Hom + buf * BLK, sm.Hoe + buf * BLK,
-                          sm.Ym, sm.Ye, YRING - 1, nullptr, nullptr);
-      } else if (q >= 0 && q < 8) {
-        if (t + 1 < NT)
-          stage_diag_any<MODE, BWD, RC, 4>(w, t + 1, 4 * q, sm.Kdm + (buf ^ 1) * BLK, sm.Kde + (buf ^ 1) * BLK,
-                                          sm.T63);
-      } else if (q >= 8 && q < 12) {
-        if (t + 1 < NT)
-          stage_offdiag_any<MODE, BWD, RC, 8>(w, t + 1, 8 * (q - 8), sm.Hom + (buf ^ 1) * BLK,
-                                             sm.Hoe + (buf ^ 1) * BLK, sm.T63);
-      } else if (q == 13) {
-        // export Y of tile t-1 from the ring to global memory, off the chain
-        // warp (a release barrier after global stores would wait for them)
+      if (wid < LEAD_WARPS) {
+        mbar_wait(mb0 + 8 * buf, (t >> 1) & 1, w.status);
+        unsigned long long Dk[4], Mk[4];
+        int De[4], Me[4];
+        load_row4(sm.Bk[buf], sm.Be[buf], wid, lane, Dk, De);
+        load_row4(sm.Bk[buf] + TILE2, sm.Be[buf] + TILE2, wid, lane, Mk, Me);
+        // phase 1: b_j = c_j A_j + sum_i Dc(j, i) X^{t-1}_i   (33 terms: S = 6)
+        xi X[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int v = (t * TILE - 31 + 4 * g + q) & (YRING - 1);
+          X[q] = xi{sm.Ym[v], sm.Ye[v]};
+        }
+        unsigned long long p0 = 0;
+        int pe0 = 2 * XZERO_E;
+        if (g == 0) { p0 = sm.cAm[buf * TILE + jrow]; pe0 = sm.cAe[buf * TILE + jrow]; }
+        const xsum s1 = row_reduce(xsum_dot<6, 4>(Dk, De, X, p0, pe0));
+        if (g == 0) {
+          const xi b = xsum_fin<6>(s1);
+          sm.bm[jrow] = b.m;
+          sm.be[jrow] = b.e;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(LEAD_WARPS * 32) : "memory");
+        // the next tile's blocks (buffer (t+1)&1 was last read in period t-1),
+        // issued once this tile's blocks have been read so that the copy does
+        // not compete with those reads
+        if (tid == 0 && t + 1 < NT) issue_tile(t + 1);
+        // phase 2: X^t_j = sum_{i <= j} M(j, i) b_i   (32 terms: S = 5)
+        xi B[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) B[q] = xi{sm.bm[4 * g + q], sm.be[4 * g + q]};
+        const xsum s2 = row_reduce(xsum_dot<5, 4>(Mk, Me, B, 0, 2 * XZERO_E));
+        // every lane of the row holds the same sum (the butterfly pairs the
+        // same partial sums in every lane): lane g == 0 keeps X^t_j in the
+        // ring, lane g writes it into bulk CTAs g+1, g+9 (slot t & 1)
+        const xi x = xsum_fin<5>(s2);
+        if (g == 0) {
+          const int v = (t * TILE + 1 + jrow) & (YRING - 1);
+          sm.Ym[v] = x.m;
+          sm.Ye[v] = x.e;
+        }
+        for (int hh = g + 1; hh <= NHELP; hh += 8) {
+          unsigned long long *hx = (unsigned long long *)cluster.map_shared_rank((void *)smem_raw, hh);
+          hx[(t & 1) * TILE + jrow] = x.m;
+          ((int *)(hx + 2 * TILE))[(t & 1) * TILE + jrow] = x.e;
+        }
+      } else if (wid == EXPORT_WARP) {
+        // Y of tile t-1 from the ring to global memory, off the phase warps
         if (t >= 1) {
           const int v = (t - 1) * TILE + lane + 1;
-          if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
+          if (v <= N) {
+            const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
+            gYm[v] = y.m;
+            gYe[v] = y.e;
+          }
         }
-      } else if (!BWD && q == 12) {
+      } else if (!BWD && wid == PREFIX_WARP) {
         prefix_tile(w, t, carry, ncarry);
       }
       cluster.sync();
     }
     pdl_trigger();  // the probability pass may launch during the epilogue
-    if (q == 13) {  // the last tile's Y
+    if (wid == EXPORT_WARP) {  // the last tile's Y
       const int v = (NT - 1) * TILE + lane + 1;
-      if (v <= N) { gYm[v] = sm.Ym[v & (YRING - 1)]; gYe[v] = sm.Ye[v & (YRING - 1)]; }
+      if (v <= N) {
+        const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
+        gYm[v] = y.m;
+        gYe[v] = y.e;
+      }
     }
     if (!BWD) {
       // V^{[1,N]} = C'[N] - (ln(y_N) - n ln 2)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
-      if (q == 12 && lane == 0) { sm.misc[0] = carry; sm.nsum = ncarry; }
+      if (wid == PREFIX_WARP && lane == 0) { sm.misc[0] = carry; sm.nsum = ncarry; }
       __syncthreads();
-      const xd yN{sm.Ym[N & (YRING - 1)], sm.Ye[N & (YRING - 1)]};
+      const xd yN = xi_to_xd(xi{sm.Ym[N & (YRING - 1)], sm.Ye[N & (YRING - 1)]});
       if (tid == 0) {  // the normaliser first: the alpha values wait for it
         const xd inv = xnorm(1.0 / (yN.m * (double)N), -yN.e);
         w.scal[1] = inv.m;
@@ -253,105 +429,154 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     HelperSmem hs;
     unsigned char *p = smem_raw;
     const int lt_max = helper_tiles(NT, NHELP);
-    hs.Am = (double *)p; p += sizeof(double) * lt_max * TILE;
-    hs.Pm = (double *)p; p += sizeof(double) * 4 * lt_max * TILE;
-    hs.Yd = (double *)p; p += sizeof(double) * 32 * 8;
+    const int nwarps = (int)(blockDim.x >> 5);
+    hs.Xm = (unsigned long long *)p; p += sizeof(unsigned long long) * 2 * TILE;  // offset 0: the lead writes here
+    hs.Xe = (int *)p; p += sizeof(int) * 2 * TILE;
+    hs.mbar = (unsigned long long *)p; p += sizeof(unsigned long long) * 32;
+    hs.Am = (unsigned long long *)p; p += sizeof(unsigned long long) * lt_max * TILE;
+    hs.Pm = (unsigned long long *)p; p += sizeof(unsigned long long) * 4 * lt_max * TILE;
+    hs.Sm = (unsigned long long *)p; p += RC ? 0 : sizeof(unsigned long long) * nwarps * 8 * TILE;
+    hs.Cm = (double *)p; p += sizeof(double) * lt_max * TILE;
     hs.Ae = (int *)p; p += sizeof(int) * lt_max * TILE;
     hs.Pe = (int *)p; p += sizeof(int) * 4 * lt_max * TILE;
-    hs.Yx = (int *)p; p += sizeof(int) * 32 * 8;
+    hs.Se = (int *)p; p += RC ? 0 : sizeof(int) * nwarps * 8 * TILE;
+    hs.Ce = (int *)p; p += sizeof(int) * lt_max * TILE;
     unsigned long long *T63 = (unsigned long long *)p;  // recompute mode
     const int h = (int)rank - 1;  // owns row tiles T with T mod NHELP == h
-    const int nwarps = (int)(blockDim.x >> 5);
-    for (int q = tid; q < lt_max * TILE; q += blockDim.x) { hs.Am[q] = 0.0; hs.Ae[q] = XZERO_E; }
+    // first owned row tile >= t+1 and the number of owned row tiles from it
+    auto first_tile = [&](int t) { return (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP; };
+    auto units = [&](int t) {
+      const int T0 = first_tile(t);
+      return T0 < NT ? (NT - 1 - T0) / NHELP + 1 : 0;
+    };
+    // this warp's tasks in order: period t, task k (row tile first_tile(t) +
+    // (k/4) NHELP, sources 32t-31 + 8 (k%4) .. +7), k = wid, wid + nwarps, ...
+    // (units never grow with t: a warp without a task in period t has none later)
+    auto advance = [&](int &t, int &k) {
+      while (t < NT && k >= 4 * units(t)) {
+        ++t;
+        k = wid;
+        if (t < NT && wid >= 4 * units(t)) t = NT;
+      }
+    };
+    // Stored factors: lane 0 stages a task's 8 x 32 factors into the warp's
+    // slot by bulk copies, one task ahead of their use (tasks of period 0,
+    // whose sources start below 0, load theirs directly).  Sources 8q+1 ..
+    // 8q+8 of tile t-1 are contiguous in the tile-packed table for q < 3; for
+    // q = 3 the last one is row 0 of the next source tile.
+    M_t *Sm = (M_t *)(hs.Sm + (RC ? 0 : wid * 8 * TILE));
+    int *Se = hs.Se + (RC ? 0 : wid * 8 * TILE);
+    const unsigned mb = smem_addr(hs.mbar + wid);
+    auto stage = [&](int t, int k) {
+      const int T = first_tile(t) + (k >> 2) * NHELP, q = k & 3;
+      const int sb = t * TILE - 31 + 8 * q;  // >= 1
+      const int n1 = q == 3 ? 7 : 8;
+      const size_t g0 = hidx(sb, T * TILE);
+      fence_proxy_async();  // the slot's previous contents were read by this warp
+      mbar_expect_tx(mb, 8 * TILE * (sizeof(M_t) + sizeof(int)));
+      bulk_g2s(smem_addr(Sm), gm + g0, n1 * TILE * sizeof(M_t), mb);
+      bulk_g2s(smem_addr(Se), ge + g0, n1 * TILE * sizeof(int), mb);
+      if (q == 3) {
+        const size_t g1 = hidx(t * TILE, T * TILE);
+        bulk_g2s(smem_addr(Sm + 7 * TILE), gm + g1, TILE * sizeof(M_t), mb);
+        bulk_g2s(smem_addr(Se + 7 * TILE), ge + g1, TILE * sizeof(int), mb);
+      }
+    };
+    for (int q = tid; q < lt_max * TILE; q += blockDim.x) {
+      hs.Am[q] = 1ull << 62;
+      hs.Ae[q] = XZERO_E;
+      const int r = ((q >> 5) * NHELP + h) * TILE + (q & 31);  // owned row of local tile q/32
+      const xd c = r < N ? chain_coef<BWD>(w, r) : xd{1.0, XZERO_E};
+      hs.Cm[q] = c.m;
+      hs.Ce[q] = c.e;
+    }
+    if (tid < TILE) {  // X^{-1} = (0, ..., 0, Y_0) in slot 1
+      hs.Xm[TILE + tid] = 1ull << 62;
+      hs.Xe[TILE + tid] = tid == TILE - 1 ? 0 : XZERO_E;
+    }
     if (RC) pairg::table_init(T63);
+    int nt = 0, nk = wid;  // this warp's next task to stage
+    unsigned phase = 0;    // completed stagings of this warp's slot
+    advance(nt, nk);
+    if (!RC && lane == 0) {
+      mbar_init(mb, 1);
+      mbar_fence_init();
+      if (nt >= 1 && nt < NT) stage(nt, nk);
+    }
     cluster.sync();
     for (int t = 0; t < NT; ++t) {
-      const int T0 = (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP;  // first owned row tile >= t+1
-      const int nunits = (t >= 1 && T0 < NT) ? (NT - 1 - T0) / NHELP + 1 : 0;
+      const int T0 = first_tile(t);
+      const int nunits = units(t);
       if (nunits > 0) {
-        const int srcbase = (t - 1) * TILE;
-        // task k: row tile T0 + (k/4)*7, sources srcbase + 8(k%4) .. +7 (source tile t-1)
+        const int srcbase = t * TILE - 31;  // X^{t-1}
+        const unsigned long long *Xm = hs.Xm + ((t - 1) & 1) * TILE;
+        const int *Xe = hs.Xe + ((t - 1) & 1) * TILE;
         for (int k = wid; k < 4 * nunits; k += nwarps) {
           const int u = k >> 2, q = k & 3;
           const int r = (T0 + u * NHELP) * TILE + lane;
           const int sb = srcbase + 8 * q;
-          M_t *Ym = (M_t *)hs.Yd + wid * 8;
-          int *Yx = hs.Yx + wid * 8;
-          if (lane < 8) {  // this warp's 8 values of Y, from the lead
-            const int v = sb + lane;
-            const double ym = lead->Ym[v & (YRING - 1)];
-            Ym[lane] = MIXED ? (M_t)mant_to_float(ym) : (M_t)ym;
-            Yx[lane] = lead->Ye[v & (YRING - 1)];
-          }
-          __syncwarp();
-          const size_t gbase = hidx(sb, r);  // + i * 32 for source sb + i
-          if (MIXED) {
-            float m[8];
-            int e[8];
-            if (RC) {
-              bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
+          M_t m[8];
+          int e[8];
+          if (RC) {
+            bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
+          } else {
+            if (t >= 1) {
+              mbar_wait(mb, phase & 1, w.status);
+              ++phase;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                m[i] = Sm[i * TILE + lane];
+                e[i] = Se[i * TILE + lane];
+              }
             } else {
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                m[i] = __ldg((const float *)gm + gbase + i * 32);
-                e[i] = __ldg(ge + gbase + i * 32);
+                const size_t gi = hidx(max(sb + i, 0), r);  // rows past N hold extended zeros
+                m[i] = __ldg(gm + gi);
+                e[i] = __ldg(ge + gi);
               }
             }
+            __syncwarp();  // the slot is free: stage the next task while this one computes
+            nk += nwarps;
+            advance(nt, nk);
+            if (lane == 0 && nt >= 1 && nt < NT) stage(nt, nk);  // period 0 loads directly
+          }
+          xi y[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) y[i] = xi{Xm[8 * q + i], Xe[8 * q + i]};
+          xi part;
+          if constexpr (MIXED) {
             float sacc = 0.0f;
             int E = XZERO_E;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fmerge(sacc, E, (float)Ym[i] * m[i], e[i] + Yx[i]);
-            ((float *)hs.Pm)[k * TILE + lane] = sacc;
-            hs.Pe[k * TILE + lane] = E;
+            for (int i = 0; i < 8; ++i) fmerge(sacc, E, xi_mant_float(y[i]) * m[i], e[i] + y[i].e);
+            part = xi_from_float(sacc, E);
           } else {
-            double m[8];
-            int e[8];
-            int E = XZERO_E;
-            if (RC) {
-              bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
+            unsigned long long kk[8];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) e[i] += Yx[i];
-            } else {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                m[i] = __ldg((const double *)gm + gbase + i * 32);
-                e[i] = __ldg(ge + gbase + i * 32) + Yx[i];
-              }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) E = max(E, e[i]);
-            double sacc = 0.0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sacc = fma(scale_nonpos(m[i], e[i] - E), (double)Ym[i], sacc);
-            hs.Pm[k * TILE + lane] = sacc;
-            hs.Pe[k * TILE + lane] = E;
+            for (int i = 0; i < 8; ++i) kk[i] = mant53(m[i]) << 11;
+            part = xsum_fin<3>(xsum_dot<3, 8>(kk, e, y, 0, 2 * XZERO_E));
           }
-          __syncwarp();
+          hs.Pm[k * TILE + lane] = part.m;
+          hs.Pe[k * TILE + lane] = part.e;
         }
         __syncthreads();
         // combine the four quarters of each owned row tile in a fixed order
         for (int u = wid; u < nunits; u += nwarps) {
           const int T = T0 + u * NHELP, lt = T / NHELP;
-          xd acc{hs.Am[lt * TILE + lane], hs.Ae[lt * TILE + lane]};
-          if (MIXED) {
-            float sacc = 0.0f;
-            int E = XZERO_E;
+          xi acc{hs.Am[lt * TILE + lane], hs.Ae[lt * TILE + lane]};
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              fmerge(sacc, E, ((const float *)hs.Pm)[(4 * u + q) * TILE + lane], hs.Pe[(4 * u + q) * TILE + lane]);
-            acc = xadd_int(acc, xd{f2d_int(sacc), E});
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              acc = xadd_int(acc, xnorm_int(xd{hs.Pm[(4 * u + q) * TILE + lane], hs.Pe[(4 * u + q) * TILE + lane]}));
-          }
-          acc = xnorm_int(acc);
+          for (int q = 0; q < 4; ++q)
+            acc = xi_add(acc, xi{hs.Pm[(4 * u + q) * TILE + lane], hs.Pe[(4 * u + q) * TILE + lane]});
           hs.Am[lt * TILE + lane] = acc.m;
           hs.Ae[lt * TILE + lane] = acc.e;
-          if (T == t + 1) {  // finished: hand the tile's sums to the lead
+          if (T == t + 1) {  // finished: hand c A of the tile to the lead
+            const int r = T * TILE + lane;
+            const xi ca = (r < N) ? xi_mul(acc, xd{hs.Cm[lt * TILE + lane], hs.Ce[lt * TILE + lane]})
+                                  : xi{1ull << 62, XZERO_E};
             const int slot = ((t + 1) & 1) * TILE + lane;
-            lead->Am[slot] = acc.m;
-            lead->Ae[slot] = acc.e;
+            lead->cAm[slot] = ca.m;
+            lead->cAe[slot] = ca.e;
           }
         }
       }
@@ -370,22 +595,42 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 1) chain_kernel(Workspace w, do
   else run_chain<MODE, true, CL - 1, RC>(w, smem_raw, V_B);
 }
 
-constexpr size_t chain_smem_bytes(int N, int CL) {
+constexpr size_t chain_smem_bytes(int N, int CL, bool RC) {
   const size_t lead = sizeof(LeadSmem);
-  const size_t help = helper_smem_bytes((N + TILE - 1) / TILE, CL - 1);
+  const size_t help = helper_smem_bytes((N + TILE - 1) / TILE, CL - 1, RC);
   return lead > help ? lead : help;
 }
-static_assert(chain_smem_bytes(CHAIN_MAX_N, CHAIN_CLUSTER) <= 227 * 1024,
+// the largest N of each mode: stored factors up to BPIMD_STORE_MAX_N
+constexpr int chain_max_n(bool RC) { return RC ? CHAIN_MAX_N : BPIMD_STORE_MAX_N; }
+static_assert(chain_smem_bytes(chain_max_n(true), CHAIN_CLUSTER, true) <= 227 * 1024 &&
+                  chain_smem_bytes(chain_max_n(false), CHAIN_CLUSTER, false) <= 227 * 1024,
               "recursion state for the largest N must fit in shared memory");
 constexpr int CHAIN_CLUSTER_LARGE = 16;
 constexpr int LARGE_CLUSTER_MIN_NT = 41;  // N > 1280: the bulk work would set the pace with 7 bulk CTAs
 
+template <int MODE, bool RC>
+cudaError_t launch_tile_inverse(const Workspace &w, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(w.NT, 2);
+  cfg.blockDim = dim3(TINV_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tile_inverse_kernel<MODE, RC>, w);
+}
+
 template <int MODE, int CL, bool RC>
 cudaError_t launch_chain_cluster(const Workspace &w, double *V_B, cudaStream_t s) {
+  cudaError_t e = launch_tile_inverse<MODE, RC>(w, s);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * CL);
   cfg.blockDim = dim3(CHAIN_THREADS);
-  cfg.dynamicSmemBytes = chain_smem_bytes(w.N, CL);
+  cfg.dynamicSmemBytes = chain_smem_bytes(w.N, CL, RC);
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -412,8 +657,8 @@ cudaError_t launch_chain_variant(const Workspace &w, double *V_B, cudaStream_t s
     default: return launch_chain_cluster<BPIMD_MIXED32, CL, true>(w, V_B, s);
   }
 }
-static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 >= 19 && CHAIN_THREADS / 32 <= 32,
-              "the lead needs 14 warps off warp 0's sub-partition (staging, prefix sums, Y export); a bulk CTA has at most 32 Y slots");
+static_assert(CHAIN_THREADS % 32 == 0 && CHAIN_THREADS / 32 > PREFIX_WARP && CHAIN_THREADS / 32 <= 32,
+              "the lead needs its phase, export and prefix warps; a bulk CTA has at most 32 Y slots");
 
 }  // namespace
 
@@ -430,7 +675,7 @@ bool g_large_cluster[64] = {false};
 
 template <int MODE, int CL, bool RC>
 cudaError_t prepare_chain_kernel() {
-  const int bytes = (int)chain_smem_bytes(CHAIN_MAX_N, CL);
+  const int bytes = (int)chain_smem_bytes(chain_max_n(RC), CL, RC);
   cudaError_t e =
       cudaFuncSetAttribute(chain_kernel<MODE, CL, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess && CL > 8)
@@ -452,7 +697,7 @@ bool clusters_fit() {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * CL);
   cfg.blockDim = dim3(CHAIN_THREADS);
-  cfg.dynamicSmemBytes = chain_smem_bytes(CHAIN_MAX_N, CL);
+  cfg.dynamicSmemBytes = chain_smem_bytes(chain_max_n(false), CL, false);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
@@ -486,6 +731,7 @@ cudaError_t prepare_chains() {
 }
 
 cudaError_t launch_chains(const Workspace &w, double *V_B, cudaStream_t s) {
+  if (!w.blocks) return cudaErrorInvalidValue;  // no tile-inverse storage in this workspace
   cudaError_t e = prepare_chains();
   if (e != cudaSuccess) return e;
   int dev = 0;

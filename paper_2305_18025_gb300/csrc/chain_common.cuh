@@ -455,6 +455,107 @@ __device__ __forceinline__ void chain_tile(int N, int t, xd A, xd crow, xd &nxt,
   nxt = xnorm_int(nxt);
 }
 
+// ------------------------------------------------ asynchronous copies
+// Bulk copies (TMA) into this CTA's shared memory signal an mbarrier with
+// their byte count; per-thread cp.async copies complete by commit groups.
+// Neither is waited for by the CTA or cluster barriers in between, so a copy
+// issued in one period of a recursion lands during the next.
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+// generic-proxy accesses of a buffer before the bulk copy that overwrites it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+// Wait for the mbarrier phase of the given parity, bounded (about a second):
+// on expiry the status word records ST_TIMEOUT and the caller goes on (the
+// evaluation's results are then invalid; the host reports BPIMD_ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, int *status) {
+  for (unsigned i = 0; i < (1u << 25); ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i >= 64) __nanosleep(32);
+  }
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+__device__ __forceinline__ void cp_async8(unsigned dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ------------------------------------------------ the blocked recursion
+// Sums of products in the chain's integer format.  A term K y (K = kk
+// 2^(ke - 63) with kk in [2^63, 2^64), y an xi) is the high product
+// p = kk y.m / 2^64 in [2^61, 2^63), of value p 2^(pe - 62), pe = ke + y.e + 1;
+// an xi itself is the term (y.m, y.e).  A sum of at most 2^S terms is aligned
+// to the largest exponent E with S bits of headroom: s = sum_i p_i >>
+// (E - pe_i + S) < 2^63, of value s 2^(E + S - 62); each shift truncates below
+// 2^-(61 - S) of the largest term.  Partial sums of one S combine by xsum_add.
+struct xsum {
+  unsigned long long s;
+  int E;
+};
+__device__ __forceinline__ xsum xsum_add(xsum a, xsum b) {
+  const int E = max(a.E, b.E);
+  return xsum{(a.s >> min(E - a.E, 63)) + (b.s >> min(E - b.E, 63)), E};
+}
+// sum over K products kk[i] y[i] plus the term (p0, pe0) (p0 = 0: none)
+template <int S, int K>
+__device__ __forceinline__ xsum xsum_dot(const unsigned long long *kk, const int *ke, const xi *y,
+                                         unsigned long long p0, int pe0) {
+  unsigned long long p[K];
+  int pe[K];
+  int E = pe0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    p[i] = __umul64hi(kk[i], y[i].m);
+    pe[i] = ke[i] + y[i].e + 1;
+    E = max(E, pe[i]);
+  }
+  unsigned long long s = p0 >> min(E - pe0 + S, 63);
+#pragma unroll
+  for (int i = 0; i < K; ++i) s += p[i] >> min(E - pe[i] + S, 63);
+  return xsum{s, E};
+}
+// The sum as an xi (s > 0: every term has a normalised mantissa).  Results
+// below the extended zero's exponent become the extended zero, so exponents
+// stay far from int32 overflow however many zeros a value has met.
+template <int S>
+__device__ __forceinline__ xi xsum_fin(xsum a) {
+  const int lz = __clzll((long long)a.s);  // 1 <= lz <= S + 2
+  const int e = a.E + S - (lz - 1);
+  if (e < XZERO_E) return xi{1ull << 62, XZERO_E};
+  return xi{a.s << (lz - 1), e};
+}
+// A float partial sum x 2^E (x >= 0) as an xi.
+__device__ __forceinline__ xi xi_from_float(float x, int E) {
+  const unsigned b = (unsigned)__float_as_int(x);
+  if (b < 0x00800000u) return xi{1ull << 62, XZERO_E};
+  return xi{(unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << 39, E + (int)(b >> 23) - 127};
+}
+// The top 24 bits of an xi mantissa as a float in [1, 2) (exponent y.e).
+__device__ __forceinline__ float xi_mant_float(xi y) {
+  return __int_as_float((int)((unsigned)(y.m >> 39) & 0x7FFFFFu) | 0x3F800000);
+}
+
 // Reduced prefix sums C'[i+1] = sum_{q<=i} Ap[q] of tile t (one warp), and the
 // running total of the integer exponent parts n_q that the recursion carries
 // in its exponents (ncarry, exact in 64 bits).

@@ -24,7 +24,7 @@
 namespace bpimd {
 namespace {
 
-constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)1 << 20;  // 1 MiB per device
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)2 << 20;  // 2 MiB per device
 static_assert(BPIMD_NOALLOC_MAX_N >= 1, "maximum size must be positive");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -81,6 +81,7 @@ extern "C" int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, con
   w.k = cfg->m * cfg->omega_P * cfg->omega_P;
   w.half_k = 0.5 * w.k;
   w.cx = w.beta * w.half_k * LOG2E;
+  w.blocks = 1;
   if (!(cfg->box_L >= 0.0) || !(cfg->box_L < __builtin_huge_val())) return BPIMD_ERR_ARG;
   set_box(w, cfg->box_L);
   if (layout_workspace(w, nullptr) > NOALLOC_SCRATCH_BYTES) return BPIMD_ERR_SIZE;

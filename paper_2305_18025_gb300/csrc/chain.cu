@@ -70,50 +70,54 @@ constexpr int LEAD_WARPS = 8;    // warps of the two phases
 constexpr int EXPORT_WARP = 8;   // copies finished tiles of Y to global memory
 constexpr int PREFIX_WARP = 9;   // prefix sums C' (forward recursion)
 constexpr int TINV_THREADS = 1024;
+constexpr int OPBUF = 3;         // tiles of lead operands in shared memory: the current one and two ahead
+constexpr int XRING = 16;        // tiles of X held by a bulk CTA: more than the 15 bulk CTAs of a cluster
+constexpr int BAR_PHASE = 1;     // named barrier of the phase warps (phase 1 -> phase 2)
+constexpr int BAR_TILE = 2;      // named barrier of the phase warps and the export warp (tile done)
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  // Dc and M of the current and the next tile (bulk copies, double buffer)
-  unsigned long long Bk[2][2 * TILE2];
-  int Be[2][2 * TILE2];
-  unsigned long long mbar[2];      // completion of the copies into Bk/Be[b]
-  unsigned long long Ym[YRING];    // Y_v at v mod YRING (xi mantissas)
-  unsigned long long cAm[2 * TILE];  // c A of the coming tile, written by its owner (double buffer)
-  unsigned long long bm[TILE];     // b of the current tile (phase 1 -> phase 2)
-  double misc[4];                  // end of the forward recursion: C'[N], 1/(N y_N) mantissa
-  long long nsum;                  // sum of the exponent parts n carried by y_N
-  int Ye[YRING];
+  // Dc and M of tile t in buffer t % OPBUF (each lane copies its own entries)
+  unsigned long long Bk[OPBUF][2 * TILE2];
+  int Be[OPBUF][2 * TILE2];
+  unsigned long long cAm[2 * TILE];  // c A of tile t in slot t & 1, handed in by the tile's owner
+  unsigned long long cabar[2];       // completion of those hand-offs
+  unsigned long long Ym[YRING];      // Y_v at v mod YRING (xi mantissas)
+  unsigned long long bm[TILE];       // b of the current tile (phase 1 -> phase 2)
+  double misc[4];                    // end of the forward recursion: C'[N], 1/(N y_N) mantissa
+  long long nsum;                    // sum of the exponent parts n carried by y_N
   int cAe[2 * TILE];
+  int Ye[YRING];
   int be[TILE];
-  int misci[4];                    // 1/(N y_N) exponent
+  int misci[4];                      // 1/(N y_N) exponent
+  int aborted;                       // a hand-off wait of this CTA expired
 };
 
-// Shared memory of a bulk CTA: the last two tiles of X written by the lead
-// (at offset 0, where the lead addresses them), its rows' sums (local tile
-// lt = T / NH) and the partial sums of the current period (4 quarter-tiles of
-// 8 sources per owned row tile), all in the xi format, and (stored factors)
-// one staging slot per warp for the factors of its next task.
-struct HelperSmem {
-  unsigned long long *Xm;  // [2][32] X^t in slot t & 1
-  int *Xe;
-  unsigned long long *mbar;  // [32 warps] staging completion
-  unsigned long long *Am;  // [ltiles][32]
-  int *Ae;
-  unsigned long long *Pm;  // [4 * ltiles][32]
-  int *Pe;
-  unsigned long long *Sm;  // [32 warps][8 sources][32 lanes] factor mantissas (float: low half used)
-  int *Se;
-  double *Cm;              // [ltiles][32] row coefficients c of the owned rows
-  int *Ce;
+// Start of a bulk CTA's shared memory (the lead hands X^t in at these
+// offsets): X^t in slot t mod XRING, X^{-1} = (0, ..., 0, Y_0) in slot XRING,
+// and one mbarrier per ring slot.  The rows' sums A (local tile lt = T / NH),
+// the quarter-tile partial sums of the current period and the rows'
+// coefficients c follow.
+struct HelperHead {
+  unsigned long long Xm[XRING + 1][TILE];
+  int Xe[XRING + 1][TILE];
+  unsigned long long xbar[XRING];
+  int aborted;
+  int pad[3];
 };
 
 __host__ __device__ constexpr int helper_tiles(int NT, int NH) { return (NT + NH - 1) / NH; }
 
 __host__ __device__ constexpr size_t helper_smem_bytes(int NT, int NH, bool RC) {
-  return (size_t)helper_tiles(NT, NH) * TILE * (sizeof(unsigned long long) + sizeof(int)) * 6 +
-         (size_t)2 * TILE * (sizeof(unsigned long long) + sizeof(int)) + 32 * sizeof(unsigned long long) +
-         256 * sizeof(unsigned long long) +
-         (RC ? 0 : (size_t)(CHAIN_THREADS / 32) * 8 * TILE * (sizeof(unsigned long long) + sizeof(int)));
+  return sizeof(HelperHead) +
+         (size_t)helper_tiles(NT, NH) * TILE * (sizeof(unsigned long long) + sizeof(int)) * 6 +
+         256 * sizeof(unsigned long long);
+}
+
+// First row tile >= t + 1 owned by bulk CTA h (tiles T with T mod NH == h);
+// the CTA has work in period t while it is below NT.
+__host__ __device__ constexpr int bulk_first_tile(int t, int h, int NH) {
+  return (t + 1) + ((h - (t + 1) % NH) + NH) % NH;
 }
 
 // Row r's pair factors H(src, r) as stored, or recomputed from the endpoint
@@ -294,68 +298,76 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
   const int *ge = chain_ge<BWD>(w);
   double *gYm = BWD ? w.ybm : w.yfm;
   int *gYe = BWD ? w.ybe : w.yfe;
-  LeadSmem *lead_local = (LeadSmem *)smem_raw;
-  // the lead's shared memory as seen from this CTA (distributed shared memory)
-  LeadSmem *lead = cluster.map_shared_rank(lead_local, 0);
 
   if (rank == 0) {
-    LeadSmem &sm = *lead_local;
+    LeadSmem &sm = *(LeadSmem *)smem_raw;
     for (int v = tid; v < YRING; v += blockDim.x) { sm.Ym[v] = 1ull << 62; sm.Ye[v] = XZERO_E; }
     if (tid < 2 * TILE) { sm.cAm[tid] = 1ull << 62; sm.cAe[tid] = XZERO_E; }
-    __syncthreads();
-    if (tid == 0) { sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0; }
-    if (!BWD && tid == 0) w.C[0] = 0.0;
-    // tile t's Dc and M arrive by bulk copy in buffer t & 1, issued one period ahead
-    const unsigned mb0 = smem_addr(&sm.mbar[0]);
-    auto issue_tile = [&](int tt) {
-      const int b = tt & 1;
-      const size_t base = tile_block_base(w, BWD, tt);
-      fence_proxy_async();
-      mbar_expect_tx(mb0 + 8 * b, 2 * TILE2 * (sizeof(unsigned long long) + sizeof(int)));
-      bulk_g2s(smem_addr(sm.Bk[b]), w.bk + base, 2 * TILE2 * sizeof(unsigned long long), mb0 + 8 * b);
-      bulk_g2s(smem_addr(sm.Be[b]), w.be + base, 2 * TILE2 * sizeof(int), mb0 + 8 * b);
-    };
-    if (tid == 0) {
-      mbar_init(mb0, 1);
-      mbar_init(mb0 + 8, 1);
+    if (tid < 2) {
+      mbar_init(smem_addr(&sm.cabar[tid]), 1);
       mbar_fence_init();
-      issue_tile(0);
+    }
+    if (tid == 0) {
+      sm.aborted = 0;
+      sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0;
+      if (!BWD) w.C[0] = 0.0;
     }
     // phase warps: rows j = 4 wid + (lane >> 3), sources 4g .. 4g+3 (g = lane & 7)
     const int g = lane & 7, jrow = 4 * wid + (lane >> 3);
-    cluster.sync();
+    // this lane's entries of tile tt's Dc and M (the load_row4 layout) into buffer tt % OPBUF
+    auto prefetch_tile = [&](int tt) {
+      if (tt < NT) {
+        const int b = tt % OPBUF;
+        const size_t base = tile_block_base(w, BWD, tt);
+        const int m0 = ((wid * 2 + 0) * 32 + lane) << 1, m1 = ((wid * 2 + 1) * 32 + lane) << 1,
+                  e0 = (wid * 32 + lane) << 2;
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk) {
+          const size_t o = base + blk * TILE2;
+          cp_async16(smem_addr(sm.Bk[b] + blk * TILE2 + m0), w.bk + o + m0);
+          cp_async16(smem_addr(sm.Bk[b] + blk * TILE2 + m1), w.bk + o + m1);
+          cp_async16(smem_addr(sm.Be[b] + blk * TILE2 + e0), w.be + o + e0);
+        }
+      }
+      cp_async_commit();  // one group per tile (empty past the last) keeps the wait count fixed
+    };
+    if (wid < LEAD_WARPS) {
+      prefetch_tile(0);
+      prefetch_tile(1);
+    }
+    cluster.sync();  // every mbarrier of the cluster is initialised
 
     double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
     long long ncarry = 0;  // and the running sum of the exponent parts n
-    for (int t = 0; t < NT; ++t) {
-      const int buf = t & 1;
-      if (wid < LEAD_WARPS) {
-        mbar_wait(mb0 + 8 * buf, (t >> 1) & 1, w.status);
+    if (wid < LEAD_WARPS) {
+      const HelperHead *hh0 = (const HelperHead *)smem_raw;  // offsets of the bulk CTAs' X slots
+      for (int t = 0; t < NT; ++t) {
+        prefetch_tile(t + 2);
+        cp_async_wait<2>();  // this lane's entries of tile t have landed
+        const int buf = t % OPBUF;
         unsigned long long Dk[4], Mk[4];
         int De[4], Me[4];
         load_row4(sm.Bk[buf], sm.Be[buf], wid, lane, Dk, De);
         load_row4(sm.Bk[buf] + TILE2, sm.Be[buf] + TILE2, wid, lane, Mk, Me);
-        // phase 1: b_j = c_j A_j + sum_i Dc(j, i) X^{t-1}_i   (33 terms: S = 6)
         xi X[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int v = (t * TILE - 31 + 4 * g + q) & (YRING - 1);
           X[q] = xi{sm.Ym[v], sm.Ye[v]};
         }
+        // c A^t from the tile's owner (tile 0 has none)
+        if (t >= 1) handoff_wait(smem_addr(&sm.cabar[t & 1]), ((t - 1) >> 1) & 1, w.status, (volatile int *)&sm.aborted);
         unsigned long long p0 = 0;
         int pe0 = 2 * XZERO_E;
-        if (g == 0) { p0 = sm.cAm[buf * TILE + jrow]; pe0 = sm.cAe[buf * TILE + jrow]; }
+        if (g == 0) { p0 = sm.cAm[(t & 1) * TILE + jrow]; pe0 = sm.cAe[(t & 1) * TILE + jrow]; }
+        // phase 1: b_j = c_j A_j + sum_i Dc(j, i) X^{t-1}_i   (33 terms: S = 6)
         const xsum s1 = row_reduce(xsum_dot<6, 4>(Dk, De, X, p0, pe0));
         if (g == 0) {
           const xi b = xsum_fin<6>(s1);
           sm.bm[jrow] = b.m;
           sm.be[jrow] = b.e;
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(LEAD_WARPS * 32) : "memory");
-        // the next tile's blocks (buffer (t+1)&1 was last read in period t-1),
-        // issued once this tile's blocks have been read so that the copy does
-        // not compete with those reads
-        if (tid == 0 && t + 1 < NT) issue_tile(t + 1);
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_PHASE), "n"(LEAD_WARPS * 32) : "memory");
         // phase 2: X^t_j = sum_{i <= j} M(j, i) b_i   (32 terms: S = 5)
         xi B[4];
 #pragma unroll
@@ -363,42 +375,45 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         const xsum s2 = row_reduce(xsum_dot<5, 4>(Mk, Me, B, 0, 2 * XZERO_E));
         // every lane of the row holds the same sum (the butterfly pairs the
         // same partial sums in every lane): lane g == 0 keeps X^t_j in the
-        // ring, lane g writes it into bulk CTAs g+1, g+9 (slot t & 1)
+        // ring, lane g hands it to bulk CTAs g+1 and g+9 if they still have
+        // work in period t+1 (slot t mod XRING; row 0 adds the expected bytes)
         const xi x = xsum_fin<5>(s2);
         if (g == 0) {
           const int v = (t * TILE + 1 + jrow) & (YRING - 1);
           sm.Ym[v] = x.m;
           sm.Ye[v] = x.e;
         }
-        for (int hh = g + 1; hh <= NHELP; hh += 8) {
-          unsigned long long *hx = (unsigned long long *)cluster.map_shared_rank((void *)smem_raw, hh);
-          hx[(t & 1) * TILE + jrow] = x.m;
-          ((int *)(hx + 2 * TILE))[(t & 1) * TILE + jrow] = x.e;
-        }
-      } else if (wid == EXPORT_WARP) {
-        // Y of tile t-1 from the ring to global memory, off the phase warps
-        if (t >= 1) {
-          const int v = (t - 1) * TILE + lane + 1;
-          if (v <= N) {
-            const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
-            gYm[v] = y.m;
-            gYe[v] = y.e;
+        if (!*(volatile int *)&sm.aborted) {
+          const int slot = t % XRING;
+          const unsigned lm = smem_addr(&hh0->Xm[slot][jrow]), le = smem_addr(&hh0->Xe[slot][jrow]),
+                         lb = smem_addr(&hh0->xbar[slot]);
+          for (int hh = g + 1; hh <= NHELP; hh += 8) {
+            if (bulk_first_tile(t + 1, hh - 1, NHELP) >= NT) continue;
+            const unsigned rb = cluster_addr(lb, hh);
+            st_async_u64(cluster_addr(lm, hh), x.m, rb);
+            st_async_u32(cluster_addr(le, hh), (unsigned)x.e, rb);
+            if (jrow == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
           }
         }
-      } else if (!BWD && wid == PREFIX_WARP) {
-        prefix_tile(w, t, carry, ncarry);
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"((LEAD_WARPS + 1) * 32) : "memory");
       }
-      cluster.sync();
+    } else if (wid == EXPORT_WARP) {
+      // Y of each finished tile from the ring to global memory, off the phase warps
+      for (int t = 0; t < NT; ++t) {
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"((LEAD_WARPS + 1) * 32) : "memory");
+        const int v = t * TILE + lane + 1;
+        if (v <= N) {
+          const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
+          gYm[v] = y.m;
+          gYe[v] = y.e;
+        }
+      }
+    } else if (!BWD && wid == PREFIX_WARP) {
+      for (int t = 0; t < NT; ++t) prefix_tile(w, t, carry, ncarry);
     }
+    // every hand-off this CTA takes part in is complete: release the bulk CTAs
+    cluster_arrive();
     pdl_trigger();  // the probability pass may launch during the epilogue
-    if (wid == EXPORT_WARP) {  // the last tile's Y
-      const int v = (NT - 1) * TILE + lane + 1;
-      if (v <= N) {
-        const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
-        gYm[v] = y.m;
-        gYe[v] = y.e;
-      }
-    }
     if (!BWD) {
       // V^{[1,N]} = C'[N] - (ln(y_N) - n ln 2)/beta, normaliser 1/(N y_N), alpha_a = y_a/(N y_N)
       if (wid == PREFIX_WARP && lane == 0) { sm.misc[0] = carry; sm.nsum = ncarry; }
@@ -426,25 +441,19 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     }
   } else {
     // ------------------------------------------------------------ bulk CTA
-    HelperSmem hs;
-    unsigned char *p = smem_raw;
+    HelperHead &hd = *(HelperHead *)smem_raw;
+    unsigned char *p = smem_raw + sizeof(HelperHead);
     const int lt_max = helper_tiles(NT, NHELP);
     const int nwarps = (int)(blockDim.x >> 5);
-    hs.Xm = (unsigned long long *)p; p += sizeof(unsigned long long) * 2 * TILE;  // offset 0: the lead writes here
-    hs.Xe = (int *)p; p += sizeof(int) * 2 * TILE;
-    hs.mbar = (unsigned long long *)p; p += sizeof(unsigned long long) * 32;
-    hs.Am = (unsigned long long *)p; p += sizeof(unsigned long long) * lt_max * TILE;
-    hs.Pm = (unsigned long long *)p; p += sizeof(unsigned long long) * 4 * lt_max * TILE;
-    hs.Sm = (unsigned long long *)p; p += RC ? 0 : sizeof(unsigned long long) * nwarps * 8 * TILE;
-    hs.Cm = (double *)p; p += sizeof(double) * lt_max * TILE;
-    hs.Ae = (int *)p; p += sizeof(int) * lt_max * TILE;
-    hs.Pe = (int *)p; p += sizeof(int) * 4 * lt_max * TILE;
-    hs.Se = (int *)p; p += RC ? 0 : sizeof(int) * nwarps * 8 * TILE;
-    hs.Ce = (int *)p; p += sizeof(int) * lt_max * TILE;
+    unsigned long long *Am = (unsigned long long *)p; p += sizeof(unsigned long long) * lt_max * TILE;
+    unsigned long long *Pm = (unsigned long long *)p; p += sizeof(unsigned long long) * 4 * lt_max * TILE;
+    double *Cm = (double *)p; p += sizeof(double) * lt_max * TILE;
+    int *Ae = (int *)p; p += sizeof(int) * lt_max * TILE;
+    int *Pe = (int *)p; p += sizeof(int) * 4 * lt_max * TILE;
+    int *Ce = (int *)p; p += sizeof(int) * lt_max * TILE;
     unsigned long long *T63 = (unsigned long long *)p;  // recompute mode
     const int h = (int)rank - 1;  // owns row tiles T with T mod NHELP == h
-    // first owned row tile >= t+1 and the number of owned row tiles from it
-    auto first_tile = [&](int t) { return (t + 1) + ((h - (t + 1) % NHELP) + NHELP) % NHELP; };
+    auto first_tile = [&](int t) { return bulk_first_tile(t, h, NHELP); };
     auto units = [&](int t) {
       const int T0 = first_tile(t);
       return T0 < NT ? (NT - 1 - T0) / NHELP + 1 : 0;
@@ -459,130 +468,116 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         if (t < NT && wid >= 4 * units(t)) t = NT;
       }
     };
-    // Stored factors: lane 0 stages a task's 8 x 32 factors into the warp's
-    // slot by bulk copies, one task ahead of their use (tasks of period 0,
-    // whose sources start below 0, load theirs directly).  Sources 8q+1 ..
-    // 8q+8 of tile t-1 are contiguous in the tile-packed table for q < 3; for
-    // q = 3 the last one is row 0 of the next source tile.
-    M_t *Sm = (M_t *)(hs.Sm + (RC ? 0 : wid * 8 * TILE));
-    int *Se = hs.Se + (RC ? 0 : wid * 8 * TILE);
-    const unsigned mb = smem_addr(hs.mbar + wid);
-    auto stage = [&](int t, int k) {
-      const int T = first_tile(t) + (k >> 2) * NHELP, q = k & 3;
-      const int sb = t * TILE - 31 + 8 * q;  // >= 1
-      const int n1 = q == 3 ? 7 : 8;
-      const size_t g0 = hidx(sb, T * TILE);
-      fence_proxy_async();  // the slot's previous contents were read by this warp
-      mbar_expect_tx(mb, 8 * TILE * (sizeof(M_t) + sizeof(int)));
-      bulk_g2s(smem_addr(Sm), gm + g0, n1 * TILE * sizeof(M_t), mb);
-      bulk_g2s(smem_addr(Se), ge + g0, n1 * TILE * sizeof(int), mb);
-      if (q == 3) {
-        const size_t g1 = hidx(t * TILE, T * TILE);
-        bulk_g2s(smem_addr(Sm + 7 * TILE), gm + g1, TILE * sizeof(M_t), mb);
-        bulk_g2s(smem_addr(Se + 7 * TILE), ge + g1, TILE * sizeof(int), mb);
+    // stored factors of task (t, k): rows past N hold extended zeros; sources
+    // below 0 meet X^{-1}'s zeros and read H(0, r)
+    auto load_factors = [&](int t, int k, M_t(&m)[8], int(&e)[8]) {
+      const int r = (first_tile(t) + (k >> 2) * NHELP) * TILE + lane;
+      const int sb = t * TILE - 31 + 8 * (k & 3);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const size_t gi = hidx(max(sb + i, 0), r);
+        m[i] = __ldg(gm + gi);
+        e[i] = __ldg(ge + gi);
       }
     };
     for (int q = tid; q < lt_max * TILE; q += blockDim.x) {
-      hs.Am[q] = 1ull << 62;
-      hs.Ae[q] = XZERO_E;
+      Am[q] = 1ull << 62;
+      Ae[q] = XZERO_E;
       const int r = ((q >> 5) * NHELP + h) * TILE + (q & 31);  // owned row of local tile q/32
       const xd c = r < N ? chain_coef<BWD>(w, r) : xd{1.0, XZERO_E};
-      hs.Cm[q] = c.m;
-      hs.Ce[q] = c.e;
+      Cm[q] = c.m;
+      Ce[q] = c.e;
     }
-    if (tid < TILE) {  // X^{-1} = (0, ..., 0, Y_0) in slot 1
-      hs.Xm[TILE + tid] = 1ull << 62;
-      hs.Xe[TILE + tid] = tid == TILE - 1 ? 0 : XZERO_E;
+    if (tid < TILE) {  // X^{-1} = (0, ..., 0, Y_0)
+      hd.Xm[XRING][tid] = 1ull << 62;
+      hd.Xe[XRING][tid] = tid == TILE - 1 ? 0 : XZERO_E;
     }
-    if (RC) pairg::table_init(T63);
-    int nt = 0, nk = wid;  // this warp's next task to stage
-    unsigned phase = 0;    // completed stagings of this warp's slot
-    advance(nt, nk);
-    if (!RC && lane == 0) {
-      mbar_init(mb, 1);
+    if (tid < XRING) {
+      mbar_init(smem_addr(&hd.xbar[tid]), 1);
       mbar_fence_init();
-      if (nt >= 1 && nt < NT) stage(nt, nk);
     }
-    cluster.sync();
+    if (tid == 0) hd.aborted = 0;
+    if (RC) pairg::table_init(T63);
+    int nt = 0, nk = wid;  // this warp's next task
+    advance(nt, nk);
+    M_t fm[8];             // its factors, loaded one task ahead (stored mode)
+    int fe[8];
+    if (!RC && nt < NT) load_factors(nt, nk, fm, fe);
+    cluster.sync();  // every mbarrier of the cluster is initialised
+    const LeadSmem *L0 = (const LeadSmem *)smem_raw;  // offsets of the lead's hand-off slots
     for (int t = 0; t < NT; ++t) {
-      const int T0 = first_tile(t);
       const int nunits = units(t);
-      if (nunits > 0) {
-        const int srcbase = t * TILE - 31;  // X^{t-1}
-        const unsigned long long *Xm = hs.Xm + ((t - 1) & 1) * TILE;
-        const int *Xe = hs.Xe + ((t - 1) & 1) * TILE;
-        for (int k = wid; k < 4 * nunits; k += nwarps) {
-          const int u = k >> 2, q = k & 3;
-          const int r = (T0 + u * NHELP) * TILE + lane;
-          const int sb = srcbase + 8 * q;
-          M_t m[8];
-          int e[8];
-          if (RC) {
-            bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
-          } else {
-            if (t >= 1) {
-              mbar_wait(mb, phase & 1, w.status);
-              ++phase;
+      if (nunits == 0) break;  // and none later
+      const int T0 = first_tile(t);
+      const int xs = t == 0 ? XRING : (t - 1) % XRING;  // X^{t-1}
+      if (t >= 1) handoff_wait(smem_addr(&hd.xbar[xs]), ((t - 1) / XRING) & 1, w.status, (volatile int *)&hd.aborted);
+      const unsigned long long *Xm = hd.Xm[xs];
+      const int *Xe = hd.Xe[xs];
+      for (int k = wid; k < 4 * nunits; k += nwarps) {
+        const int u = k >> 2, q = k & 3;
+        const int r = (T0 + u * NHELP) * TILE + lane;
+        const int sb = t * TILE - 31 + 8 * q;
+        M_t m[8];
+        int e[8];
+        if (RC) {
+          bulk_factors_rc<MODE, BWD>(w, r, sb, T63, m, e);
+        } else {
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                m[i] = Sm[i * TILE + lane];
-                e[i] = Se[i * TILE + lane];
-              }
-            } else {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const size_t gi = hidx(max(sb + i, 0), r);  // rows past N hold extended zeros
-                m[i] = __ldg(gm + gi);
-                e[i] = __ldg(ge + gi);
-              }
-            }
-            __syncwarp();  // the slot is free: stage the next task while this one computes
-            nk += nwarps;
-            advance(nt, nk);
-            if (lane == 0 && nt >= 1 && nt < NT) stage(nt, nk);  // period 0 loads directly
-          }
-          xi y[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) y[i] = xi{Xm[8 * q + i], Xe[8 * q + i]};
-          xi part;
-          if constexpr (MIXED) {
-            float sacc = 0.0f;
-            int E = XZERO_E;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) fmerge(sacc, E, xi_mant_float(y[i]) * m[i], e[i] + y[i].e);
-            part = xi_from_float(sacc, E);
-          } else {
-            unsigned long long kk[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) kk[i] = mant53(m[i]) << 11;
-            part = xsum_fin<3>(xsum_dot<3, 8>(kk, e, y, 0, 2 * XZERO_E));
-          }
-          hs.Pm[k * TILE + lane] = part.m;
-          hs.Pe[k * TILE + lane] = part.e;
+          for (int i = 0; i < 8; ++i) { m[i] = fm[i]; e[i] = fe[i]; }
+          nk += nwarps;
+          advance(nt, nk);
+          if (nt < NT) load_factors(nt, nk, fm, fe);
         }
-        __syncthreads();
-        // combine the four quarters of each owned row tile in a fixed order
-        for (int u = wid; u < nunits; u += nwarps) {
-          const int T = T0 + u * NHELP, lt = T / NHELP;
-          xi acc{hs.Am[lt * TILE + lane], hs.Ae[lt * TILE + lane]};
+        xi y[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            acc = xi_add(acc, xi{hs.Pm[(4 * u + q) * TILE + lane], hs.Pe[(4 * u + q) * TILE + lane]});
-          hs.Am[lt * TILE + lane] = acc.m;
-          hs.Ae[lt * TILE + lane] = acc.e;
-          if (T == t + 1) {  // finished: hand c A of the tile to the lead
-            const int r = T * TILE + lane;
-            const xi ca = (r < N) ? xi_mul(acc, xd{hs.Cm[lt * TILE + lane], hs.Ce[lt * TILE + lane]})
-                                  : xi{1ull << 62, XZERO_E};
-            const int slot = ((t + 1) & 1) * TILE + lane;
-            lead->cAm[slot] = ca.m;
-            lead->cAe[slot] = ca.e;
-          }
+        for (int i = 0; i < 8; ++i) y[i] = xi{Xm[8 * q + i], Xe[8 * q + i]};
+        xi part;
+        if constexpr (MIXED) {
+          float sacc = 0.0f;
+          int E = XZERO_E;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) fmerge(sacc, E, xi_mant_float(y[i]) * m[i], e[i] + y[i].e);
+          part = xi_from_float(sacc, E);
+        } else {
+          unsigned long long kk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) kk[i] = mant53(m[i]) << 11;
+          part = xsum_fin<3>(xsum_dot<3, 8>(kk, e, y, 0, 2 * XZERO_E));
+        }
+        Pm[k * TILE + lane] = part.m;
+        Pe[k * TILE + lane] = part.e;
+      }
+      __syncthreads();
+      // combine the four quarters of each owned row tile in a fixed order;
+      // the owner of tile t+1 hands c A of the finished tile to the lead
+      for (int u = wid; u < nunits; u += nwarps) {
+        const int T = T0 + u * NHELP, lt = T / NHELP;
+        xi acc{Am[lt * TILE + lane], Ae[lt * TILE + lane]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc = xi_add(acc, xi{Pm[(4 * u + q) * TILE + lane], Pe[(4 * u + q) * TILE + lane]});
+        Am[lt * TILE + lane] = acc.m;
+        Ae[lt * TILE + lane] = acc.e;
+        if (T == t + 1 && !*(volatile int *)&hd.aborted) {
+          const int r = T * TILE + lane;
+          const xi ca = (r < N) ? xi_mul(acc, xd{Cm[lt * TILE + lane], Ce[lt * TILE + lane]})
+                                : xi{1ull << 62, XZERO_E};
+          const int slot = (t + 1) & 1;
+          const unsigned rb = cluster_addr(smem_addr(&L0->cabar[slot]), 0);
+          st_async_u64(cluster_addr(smem_addr(&L0->cAm[slot * TILE + lane]), 0), ca.m, rb);
+          st_async_u32(cluster_addr(smem_addr(&L0->cAe[slot * TILE + lane]), 0), (unsigned)ca.e, rb);
+          if (lane == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
         }
       }
-      cluster.sync();
+      __syncthreads();  // the partial sums are read: the next period may overwrite them
     }
+    cluster_arrive();
   }
+  // No CTA leaves while a hand-off into its shared memory may be in flight:
+  // each arrived above once its own waits were over.  After an expired wait
+  // a hand-off may still be on its way: give it time to land.
+  cluster_wait();
+  if (*(volatile int *)w.status & ST_TIMEOUT)
+    for (int i = 0; i < 200; ++i) __nanosleep(1000);
 }
 
 // Cluster size CL (CTAs per recursion) is given at launch; blocks [0, CL) run

@@ -492,6 +492,77 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, int *s
   atomicOr(status, ST_TIMEOUT);
   return false;
 }
+// ------------------------------------------ hand-offs between CTAs of a cluster
+// A producer stores into another CTA's shared memory with st.async, each store
+// completing its byte count on an mbarrier of the receiving CTA; one producer
+// thread adds the single expected arrival with the total byte count.  The
+// consumer waits for the phase (acquire at cluster scope).  No cluster barrier
+// is involved, so producer and consumer run decoupled.
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // bound of every hand-off wait (1 s)
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_u64(unsigned raddr, unsigned long long v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr), "l"(v),
+               "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_u32(unsigned raddr, unsigned v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr), "r"(v),
+               "r"(rbar)
+               : "memory");
+}
+// the one expected arrival of a hand-off, with its byte count, on a remote mbarrier
+__device__ __forceinline__ void mbar_arrive_expect_remote(unsigned rbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.relaxed.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(rbar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test_cluster(unsigned addr, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for a hand-off, bounded by WAIT_LIMIT_NS of the global timer.  Once a
+// wait of this CTA has expired (*aborted set), later waits return at once and
+// the caller stops handing off: the status word records ST_TIMEOUT and the
+// evaluation's results are invalid, but every thread still reaches the end.
+__device__ __forceinline__ bool handoff_wait(unsigned addr, unsigned parity, int *status, volatile int *aborted) {
+  if (*aborted) return false;
+  if (mbar_test_cluster(addr, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test_cluster(addr, parity)) {
+    if (*aborted || global_ns() - t0 > WAIT_LIMIT_NS) {
+      *aborted = 1;
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+// split cluster barrier: arrive (release) once this thread's part is done, wait later
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void cp_async8(unsigned dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }

@@ -26,32 +26,41 @@
 // and the sequential part of a recursion is two 32 x 32 matrix-vector
 // products per tile instead of 32 dependent steps.
 //
-// Cluster schedule.  GB300 facts behind it (measured): a cluster barrier costs
-// ~360 cycles and a distributed shared-memory access ~215; a float64 FMA has a
-// 64-cycle latency and the SM's float64 pipe retires ~1.7 lanes per clock,
-// against ~19 for a 32 x 32 -> 64-bit integer multiply-add.
-//   * The lead CTA (cluster rank 0) runs tile t in period t with eight warps,
-//     four rows each; a row's 32 sources are split over eight lanes (four
-//     products per lane) and reduced by three shuffle levels.  Phase 1 forms
-//     b^t = c A^t + Dc^t X^{t-1}, phase 2 X^t = M^t b^t; both use 64-bit
+// Cluster schedule.  GB300 facts behind it (measured): a cluster barrier, and
+// a bulk copy in flight anywhere in the cluster, hold a period for ~2000
+// cycles; a float64 FMA has a 64-cycle latency and the SM's float64 pipe
+// retires ~1.7 lanes per clock, against ~19 for a 32 x 32 -> 64-bit integer
+// multiply-add.  So nothing in the loop is a cluster barrier or a bulk copy:
+//   * The lead CTA (cluster rank 0) runs tile t in period t with eight phase
+//     warps, four rows each; a row's 32 sources are split over eight lanes
+//     (four products per lane) and reduced by three shuffle levels.  Phase 1
+//     forms b^t = c A^t + Dc^t X^{t-1}, phase 2 X^t = M^t b^t; both use 64-bit
 //     integer mantissas (the xi format of chain_common.cuh): no float64
-//     instruction on the sequential path.  The warps prefetch the next tile's
-//     rows of Dc and M into registers during the current period.  One more
-//     warp copies each finished tile of Y to global memory one period later,
-//     another forms the prefix sums C' (forward recursion).
+//     instruction on the sequential path.  A loader warp copies tile t+3's Dc
+//     and M into shared memory once tile t is done (cp.async, counted on an
+//     mbarrier); the export warp writes each finished tile of Y to global
+//     memory and hands X^t to the bulk CTAs; another warp forms the prefix
+//     sums C' (forward recursion).
 //   * The O(N^2) bulk runs on the other CTAs of the cluster (seven, or
-//     fifteen in the 16-CTA form used above N = 1280): row tile T belongs to
+//     fifteen in the 16-CTA form used above N = 256): row tile T belongs to
 //     CTA 1 + T mod NH, which keeps its rows' sums A in its own shared memory.
 //     In period t each adds X^{t-1} to every row tile T >= t+1 it owns: one
 //     warp per (row tile, quarter of 8 sources), 64-bit integer products of
 //     the float64 factors (float32 products of BPIMD_MIXED32's float32
-//     factors); the quarters are combined in a fixed order, and the owner of
-//     tile t+1 hands c A^{t+1} to the lead.
-// Periods are separated by one cluster barrier (release/acquire), which also
-// orders every distributed shared-memory access; nothing spins.  Every value
-// is an extended number m * 2^e (int32 exponent), so no exp or log is
-// evaluated in the recursions; each recursion reads its own copy of the pair
-// factors, laid out in its (source, row) coordinates, with coalesced loads.
+//     factors); the quarters are combined in a fixed order.  The owner of
+//     tile t+1 takes that tile's quarters first and hands c A^{t+1} to the
+//     lead as soon as they are done.
+//   * Hand-offs are st.async stores into the receiving CTA's shared memory,
+//     completed on its mbarriers (X^t in slot t mod XRING of each bulk CTA,
+//     c A^t in slot t mod 2 of the lead); every wait is bounded.  Slot reuse
+//     is safe without back-pressure: the lead reaches period t only after
+//     c A of the last tile <= t of every bulk CTA, so a bulk CTA is at most NH
+//     periods behind the X it is sent (XRING > NH), and c A^{t+2} needs X^t,
+//     which the lead hands off after reading c A^t.
+// Every value is an extended number m * 2^e (int32 exponent), so no exp or
+// log is evaluated in the recursions; each recursion reads its own copy of
+// the pair factors, laid out in its (source, row) coordinates, with coalesced
+// loads.
 #include <cooperative_groups.h>
 #include <mutex>
 #include <type_traits>
@@ -69,17 +78,22 @@ constexpr int YRING = 128;       // Y values kept in the lead (4 tiles)
 constexpr int LEAD_WARPS = 8;    // warps of the two phases
 constexpr int EXPORT_WARP = 8;   // copies finished tiles of Y to global memory
 constexpr int PREFIX_WARP = 9;   // prefix sums C' (forward recursion)
+constexpr int LOADER_WARP = 10;  // copies the phase warps' operands of coming tiles
 constexpr int TINV_THREADS = 1024;
 constexpr int OPBUF = 3;         // tiles of lead operands in shared memory: the current one and two ahead
 constexpr int XRING = 16;        // tiles of X held by a bulk CTA: more than the 15 bulk CTAs of a cluster
 constexpr int BAR_PHASE = 1;     // named barrier of the phase warps (phase 1 -> phase 2)
-constexpr int BAR_TILE = 2;      // named barrier of the phase warps and the export warp (tile done)
+constexpr int BAR_TILE = 2;      // named barrier of the phase, export and loader warps (tile done)
+constexpr int BAR_TILE_THREADS = (LEAD_WARPS + 2) * 32;
+constexpr int BAR_CRIT = 3;      // named barrier of the four warps of a bulk CTA's critical row tile
 
 // Shared memory of the lead CTA.
 struct LeadSmem {
-  // Dc and M of tile t in buffer t % OPBUF (each lane copies its own entries)
+  // Dc and M of tile t in buffer t % OPBUF, copied by the loader warp; opbar[b]
+  // completes when its copies into buffer b have landed
   unsigned long long Bk[OPBUF][2 * TILE2];
   int Be[OPBUF][2 * TILE2];
+  unsigned long long opbar[OPBUF];
   unsigned long long cAm[2 * TILE];  // c A of tile t in slot t & 1, handed in by the tile's owner
   unsigned long long cabar[2];       // completion of those hand-offs
   unsigned long long Ym[YRING];      // Y_v at v mod YRING (xi mantissas)
@@ -307,6 +321,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       mbar_init(smem_addr(&sm.cabar[tid]), 1);
       mbar_fence_init();
     }
+    if (tid >= 32 && tid < 32 + OPBUF) mbar_init(smem_addr(&sm.opbar[tid - 32]), 32);  // one per loader lane
     if (tid == 0) {
       sm.aborted = 0;
       sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0;
@@ -314,37 +329,26 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     }
     // phase warps: rows j = 4 wid + (lane >> 3), sources 4g .. 4g+3 (g = lane & 7)
     const int g = lane & 7, jrow = 4 * wid + (lane >> 3);
-    // this lane's entries of tile tt's Dc and M (the load_row4 layout) into buffer tt % OPBUF
-    auto prefetch_tile = [&](int tt) {
-      if (tt < NT) {
-        const int b = tt % OPBUF;
-        const size_t base = tile_block_base(w, BWD, tt);
-        const int m0 = ((wid * 2 + 0) * 32 + lane) << 1, m1 = ((wid * 2 + 1) * 32 + lane) << 1,
-                  e0 = (wid * 32 + lane) << 2;
-#pragma unroll
-        for (int blk = 0; blk < 2; ++blk) {
-          const size_t o = base + blk * TILE2;
-          cp_async16(smem_addr(sm.Bk[b] + blk * TILE2 + m0), w.bk + o + m0);
-          cp_async16(smem_addr(sm.Bk[b] + blk * TILE2 + m1), w.bk + o + m1);
-          cp_async16(smem_addr(sm.Be[b] + blk * TILE2 + e0), w.be + o + e0);
-        }
-      }
-      cp_async_commit();  // one group per tile (empty past the last) keeps the wait count fixed
+    // loader warp: tile tt's Dc and M (24 KB, contiguous in both places) into
+    // buffer tt % OPBUF, 16-byte copies, completion counted on opbar
+    auto copy_tile = [&](int tt) {
+      const int b = tt % OPBUF;
+      const size_t base = tile_block_base(w, BWD, tt);
+      for (int i = lane; i < TILE2; i += 32) cp_async16(smem_addr(sm.Bk[b] + 2 * i), w.bk + base + 2 * i);
+      for (int i = lane; i < TILE2 / 2; i += 32) cp_async16(smem_addr(sm.Be[b] + 4 * i), w.be + base + 4 * i);
+      cp_async_arrive(smem_addr(&sm.opbar[b]));
     };
-    if (wid < LEAD_WARPS) {
-      prefetch_tile(0);
-      prefetch_tile(1);
-    }
+    __syncthreads();  // the operand mbarriers are initialised
+    if (wid == LOADER_WARP)
+      for (int tt = 0; tt < OPBUF && tt < NT; ++tt) copy_tile(tt);
     cluster.sync();  // every mbarrier of the cluster is initialised
 
     double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
     long long ncarry = 0;  // and the running sum of the exponent parts n
     if (wid < LEAD_WARPS) {
-      const HelperHead *hh0 = (const HelperHead *)smem_raw;  // offsets of the bulk CTAs' X slots
       for (int t = 0; t < NT; ++t) {
-        prefetch_tile(t + 2);
-        cp_async_wait<2>();  // this lane's entries of tile t have landed
         const int buf = t % OPBUF;
+        handoff_wait(smem_addr(&sm.opbar[buf]), (t / OPBUF) & 1, w.status, (volatile int *)&sm.aborted);
         unsigned long long Dk[4], Mk[4];
         int De[4], Me[4];
         load_row4(sm.Bk[buf], sm.Be[buf], wid, lane, Dk, De);
@@ -374,39 +378,47 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         for (int q = 0; q < 4; ++q) B[q] = xi{sm.bm[4 * g + q], sm.be[4 * g + q]};
         const xsum s2 = row_reduce(xsum_dot<5, 4>(Mk, Me, B, 0, 2 * XZERO_E));
         // every lane of the row holds the same sum (the butterfly pairs the
-        // same partial sums in every lane): lane g == 0 keeps X^t_j in the
-        // ring, lane g hands it to bulk CTAs g+1 and g+9 if they still have
-        // work in period t+1 (slot t mod XRING; row 0 adds the expected bytes)
+        // same partial sums in every lane): lane g == 0 keeps X^t_j in the ring
         const xi x = xsum_fin<5>(s2);
         if (g == 0) {
           const int v = (t * TILE + 1 + jrow) & (YRING - 1);
           sm.Ym[v] = x.m;
           sm.Ye[v] = x.e;
         }
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"(BAR_TILE_THREADS) : "memory");
+      }
+    } else if (wid == EXPORT_WARP) {
+      // off the phase warps, lane j takes row j of each finished tile t: Y to
+      // global memory, and X^t to every bulk CTA that still has work in
+      // period t+1 (slot t mod XRING; lane 0 adds the expected bytes)
+      const HelperHead *hh0 = (const HelperHead *)smem_raw;  // offsets of the bulk CTAs' X slots
+      for (int t = 0; t < NT; ++t) {
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"(BAR_TILE_THREADS) : "memory");
+        const int v = t * TILE + lane + 1;
+        const xi x{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]};
         if (!*(volatile int *)&sm.aborted) {
           const int slot = t % XRING;
-          const unsigned lm = smem_addr(&hh0->Xm[slot][jrow]), le = smem_addr(&hh0->Xe[slot][jrow]),
+          const unsigned lm = smem_addr(&hh0->Xm[slot][lane]), le = smem_addr(&hh0->Xe[slot][lane]),
                          lb = smem_addr(&hh0->xbar[slot]);
-          for (int hh = g + 1; hh <= NHELP; hh += 8) {
-            if (bulk_first_tile(t + 1, hh - 1, NHELP) >= NT) continue;
+          for (int hh = 1; hh <= NHELP; ++hh) {
+            if (bulk_first_tile(t + 1, hh - 1, NHELP) >= NT) continue;  // warp-uniform
             const unsigned rb = cluster_addr(lb, hh);
             st_async_u64(cluster_addr(lm, hh), x.m, rb);
             st_async_u32(cluster_addr(le, hh), (unsigned)x.e, rb);
-            if (jrow == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
+            if (lane == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
           }
         }
-        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"((LEAD_WARPS + 1) * 32) : "memory");
-      }
-    } else if (wid == EXPORT_WARP) {
-      // Y of each finished tile from the ring to global memory, off the phase warps
-      for (int t = 0; t < NT; ++t) {
-        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"((LEAD_WARPS + 1) * 32) : "memory");
-        const int v = t * TILE + lane + 1;
         if (v <= N) {
-          const xd y = xi_to_xd(xi{sm.Ym[v & (YRING - 1)], sm.Ye[v & (YRING - 1)]});
+          const xd y = xi_to_xd(x);
           gYm[v] = y.m;
           gYe[v] = y.e;
         }
+      }
+    } else if (wid == LOADER_WARP) {
+      // buffer t % OPBUF is free once tile t is done: copy tile t + OPBUF into it
+      for (int t = 0; t < NT; ++t) {
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR_TILE), "n"(BAR_TILE_THREADS) : "memory");
+        if (t + OPBUF < NT) copy_tile(t + OPBUF);
       }
     } else if (!BWD && wid == PREFIX_WARP) {
       for (int t = 0; t < NT; ++t) prefix_tile(w, t, carry, ncarry);
@@ -505,12 +517,32 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     if (!RC && nt < NT) load_factors(nt, nk, fm, fe);
     cluster.sync();  // every mbarrier of the cluster is initialised
     const LeadSmem *L0 = (const LeadSmem *)smem_raw;  // offsets of the lead's hand-off slots
+    // unit u of period t: add the four quarter partials to the rows' sums A; the
+    // owner of tile t+1 hands c A of the finished tile to the lead (one warp)
+    auto combine = [&](int t, int T0, int u) {
+      const int T = T0 + u * NHELP, lt = T / NHELP;
+      xi acc{Am[lt * TILE + lane], Ae[lt * TILE + lane]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc = xi_add(acc, xi{Pm[(4 * u + q) * TILE + lane], Pe[(4 * u + q) * TILE + lane]});
+      Am[lt * TILE + lane] = acc.m;
+      Ae[lt * TILE + lane] = acc.e;
+      if (T == t + 1 && !*(volatile int *)&hd.aborted) {
+        const int r = T * TILE + lane;
+        const xi ca = (r < N) ? xi_mul(acc, xd{Cm[lt * TILE + lane], Ce[lt * TILE + lane]}) : xi{1ull << 62, XZERO_E};
+        const int slot = (t + 1) & 1;
+        const unsigned rb = cluster_addr(smem_addr(&L0->cabar[slot]), 0);
+        st_async_u64(cluster_addr(smem_addr(&L0->cAm[slot * TILE + lane]), 0), ca.m, rb);
+        st_async_u32(cluster_addr(smem_addr(&L0->cAe[slot * TILE + lane]), 0), (unsigned)ca.e, rb);
+        if (lane == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
+      }
+    };
     for (int t = 0; t < NT; ++t) {
       const int nunits = units(t);
       if (nunits == 0) break;  // and none later
       const int T0 = first_tile(t);
       const int xs = t == 0 ? XRING : (t - 1) % XRING;  // X^{t-1}
       if (t >= 1) handoff_wait(smem_addr(&hd.xbar[xs]), ((t - 1) / XRING) & 1, w.status, (volatile int *)&hd.aborted);
+      const bool crit = T0 == t + 1;  // this CTA owns the tile the lead needs next
       const unsigned long long *Xm = hd.Xm[xs];
       const int *Xe = hd.Xe[xs];
       for (int k = wid; k < 4 * nunits; k += nwarps) {
@@ -546,28 +578,16 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         }
         Pm[k * TILE + lane] = part.m;
         Pe[k * TILE + lane] = part.e;
-      }
-      __syncthreads();
-      // combine the four quarters of each owned row tile in a fixed order;
-      // the owner of tile t+1 hands c A of the finished tile to the lead
-      for (int u = wid; u < nunits; u += nwarps) {
-        const int T = T0 + u * NHELP, lt = T / NHELP;
-        xi acc{Am[lt * TILE + lane], Ae[lt * TILE + lane]};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc = xi_add(acc, xi{Pm[(4 * u + q) * TILE + lane], Pe[(4 * u + q) * TILE + lane]});
-        Am[lt * TILE + lane] = acc.m;
-        Ae[lt * TILE + lane] = acc.e;
-        if (T == t + 1 && !*(volatile int *)&hd.aborted) {
-          const int r = T * TILE + lane;
-          const xi ca = (r < N) ? xi_mul(acc, xd{Cm[lt * TILE + lane], Ce[lt * TILE + lane]})
-                                : xi{1ull << 62, XZERO_E};
-          const int slot = (t + 1) & 1;
-          const unsigned rb = cluster_addr(smem_addr(&L0->cabar[slot]), 0);
-          st_async_u64(cluster_addr(smem_addr(&L0->cAm[slot * TILE + lane]), 0), ca.m, rb);
-          st_async_u32(cluster_addr(smem_addr(&L0->cAe[slot * TILE + lane]), 0), (unsigned)ca.e, rb);
-          if (lane == 0) mbar_arrive_expect_remote(rb, TILE * (sizeof(unsigned long long) + sizeof(int)));
+        if (crit && k < 4) {
+          // the four quarters of the critical tile t+1 (tasks 0..3, the first
+          // task of warps 0..3) are done: hand it off before the other tasks
+          asm volatile("bar.sync %0, %1;" ::"n"(BAR_CRIT), "n"(4 * 32) : "memory");
+          if (wid == 0) combine(t, T0, 0);
         }
       }
+      __syncthreads();
+      // combine the four quarters of each other owned row tile in a fixed order
+      for (int u = wid + (crit ? 1 : 0); u < nunits; u += nwarps) combine(t, T0, u);
       __syncthreads();  // the partial sums are read: the next period may overwrite them
     }
     cluster_arrive();
@@ -601,7 +621,7 @@ static_assert(chain_smem_bytes(chain_max_n(true), CHAIN_CLUSTER, true) <= 227 * 
                   chain_smem_bytes(chain_max_n(false), CHAIN_CLUSTER, false) <= 227 * 1024,
               "recursion state for the largest N must fit in shared memory");
 constexpr int CHAIN_CLUSTER_LARGE = 16;
-constexpr int LARGE_CLUSTER_MIN_NT = 41;  // N > 1280: the bulk work would set the pace with 7 bulk CTAs
+constexpr int LARGE_CLUSTER_MIN_NT = 9;  // N > 256: the bulk work would set the pace with 7 bulk CTAs
 
 template <int MODE, bool RC>
 cudaError_t launch_tile_inverse(const Workspace &w, cudaStream_t s) {

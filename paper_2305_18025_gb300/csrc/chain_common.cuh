@@ -496,7 +496,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, int *s
 // A producer stores into another CTA's shared memory with st.async, each store
 // completing its byte count on an mbarrier of the receiving CTA; one producer
 // thread adds the single expected arrival with the total byte count.  The
-// consumer waits for the phase (acquire at cluster scope).  No cluster barrier
+// consumer waits for the phase (its transaction count covers the stores).  No cluster barrier
 // is involved, so producer and consumer run decoupled.
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // bound of every hand-off wait (1 s)
 
@@ -529,7 +529,7 @@ __device__ __forceinline__ void mbar_arrive_expect_remote(unsigned rbar, unsigne
 __device__ __forceinline__ bool mbar_test_cluster(unsigned addr, unsigned parity) {
   unsigned done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(done)
       : "r"(addr), "r"(parity)
       : "memory");
@@ -557,6 +557,11 @@ __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// one arrival on a CTA-local mbarrier once this thread's cp.async copies so far
+// have landed (the barrier counts one arrival per copying thread)
+__device__ __forceinline__ void cp_async_arrive(unsigned mbar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {

@@ -113,11 +113,12 @@ def test_parity_small(prec, N, P, kind):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed32"])
-@pytest.mark.parametrize("N", [1280, 1281, 1313])
+@pytest.mark.parametrize("N", [256, 257, 289, 1313])
 def test_parity_cluster_size_switch(prec, N):
-    """The recursion switches from 8- to 16-CTA clusters above N = 1280 (40
-    row tiles): the last 8-CTA size, the first 16-CTA size (a one-row ragged
-    tail) and a tile count that is not a multiple of the 15 bulk CTAs."""
+    """The recursion switches from 8- to 16-CTA clusters above N = 256 (8 row
+    tiles): the last 8-CTA size, the first 16-CTA size (a one-row ragged
+    tail), fewer row tiles than bulk CTAs, and a tile count that is not a
+    multiple of the 15 bulk CTAs."""
     check(inputs.trapped_positions(N, 4, seed=N), beta=1.0, prec=prec, want_M=False)
 
 

@@ -39,7 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exchange V_B+force evals/s at N=1024,P=32 (mixed vs FP64 GPU); MD steps/s"
 N_DEF, P_DEF, BETA_DEF, SEED_DEF = 1024, 32, 1.0, 3
-LAUNCHES_PER_EVAL = 3          # bead pass + pair factors, recursions (2 clusters), probabilities + forces
+LAUNCHES_PER_EVAL = 4          # bead pass + pair factors, tile inverses, recursions (2 clusters), probabilities + forces
+BATCH_LAUNCHES_PER_EVAL = 3    # replica batch: bead pass + pair factors, recursions, probabilities + forces
+BATCH_MD = dict(dt=0.01, gamma=1.0, omega0=1.0, gaussian=(1.0, 0.5), seed=77)  # 256-replica workload
 DFMA_LATENCY_CYCLES = 64       # measured on GB300: dependent float64 FMA latency
 FLUSH_BYTES = 256 << 20        # > 129 MB L2
 
@@ -429,6 +431,8 @@ def run_ours(args, rank, world, local_rank):
         "md_steps_per_s": {p: results["md"][p]["value"] for p in ("mixed", "fp64", "mixed32") if p in results["md"]},
         "batched_evals_per_s": {p: results["batched"][p]["value"] for p in ("mixed", "fp64", "mixed32")
                                 if p in results["batched"]},
+        "batched_md_steps_per_s": {p: v["value"] for p, v in results["batched"].get("md", {}).items()
+                                   if p in ("mixed", "fp64")},
         "helium_md_steps_per_s": {p: results["helium"][p]["value"] for p in ("mixed", "fp64", "mixed32")
                                   if p in results["helium"]},
         "helium_exchange_evals_per_s": {k: v["value"] for k, v in results["helium"].get("exchange", {}).items()
@@ -528,14 +532,56 @@ def batched_throughput(args, dev, flush, max_over_ranks, barrier, world):
         ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
         out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "batch evals/s",
                      "replica_evals_per_s": aggregate_rate(world, steps * eng.R, ms * 1e-3),
-                     "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": LAUNCHES_PER_EVAL * steps,
+                     "ms_per_batch": ms / steps, "steps": steps, "gpu_launches": BATCH_LAUNCHES_PER_EVAL * steps,
                      "tuning": {"choice": list(tuned["choice"]), "cached": tuned["cached"]}}
         eng.close()
+    out["md"] = batched_md_throughput(args, dev, reps, wPs, max_over_ranks, barrier, world)
     out["config"] = {"workload": f"{args.batch_replicas} independent trapped replicas, N~U[16,512], "
                                  "P in {16,32,64}, beta~U[0.5,4], seed 11 (exchange V_B + all bead forces of each)",
                      "sum_N": int(sum(Ns)), "sum_NP": int(sum(n * p for n, p in zip(Ns, Ps))),
                      "sum_pairs": int(sum(n * (n + 1) // 2 for n in Ns)),
                      "l2": "flushed between timed batches (256 MiB device write, untimed)"}
+    return out
+
+
+def batched_md_throughput(args, dev, reps, wPs, max_over_ranks, barrier, world):
+    """BAOAB molecular dynamics of the whole replica batch: harmonic trap w0 = 1
+    and Gaussian repulsion g = 1, s = 0.5 between equal-index beads, each
+    replica thermostatted at its own beta; the steps are CUDA-graph replays on
+    a dedicated stream (batch evaluation, pair forces, integrator: 6 launches
+    per step).  Back to back as in a trajectory, so the L2 is not flushed."""
+    import numpy as np
+    import torch
+    from paper_2305_18025_gb300.exchange import BatchedExchangeEnergy
+    Ns, Ps, betas = [r.N for r in reps], [r.P for r in reps], [r.beta for r in reps]
+    out = {}
+    for prec, steps in (("mixed", max(4, args.batch_steps)), ("fp64", max(4, args.batch_steps // 4))):
+        side = torch.cuda.Stream(dev)
+        eng = BatchedExchangeEnergy(Ns, Ps, 1.0, wPs, betas, precision=prec, device=dev, stream=side, md=BATCH_MD)
+        rng = np.random.default_rng(12)
+        x = eng.pack([torch.from_numpy(r.positions) for r in reps])
+        v = eng.pack([torch.from_numpy(rng.normal(0.0, 1.0 / np.sqrt(r.beta), r.positions.shape)) for r in reps])
+        eng.step(x, v, max(2, args.warmup), energies=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(side)
+        eng.step(x, v, steps, energies=False)
+        e1.record(side)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        en = eng.step(x, v, 1).cpu().numpy()
+        eng.close()
+        out[prec] = {"value": aggregate_rate(world, steps, ms * 1e-3), "unit": "batch MD steps/s", "steps": steps,
+                     "replica_steps_per_s": aggregate_rate(world, steps * len(reps), ms * 1e-3),
+                     "ms_per_step": ms / steps, "gpu_launches": (BATCH_LAUNCHES_PER_EVAL + 3) * steps,
+                     "finite": bool(np.isfinite(en).all()),
+                     "mean_E_prim_per_bead": float(np.mean(en[:, 3] / np.array([n * p for n, p in zip(Ns, Ps)])))}
+    out["config"] = {"workload": "the same 256 replicas, harmonic trap w0=1 and Gaussian repulsion g=1 s=0.5 "
+                                 "between equal-index beads",
+                     "integrator": "BAOAB Langevin, dt=0.01, gamma=1, kT=1/beta of each replica, Philox4x32-10 noise",
+                     "timing": "CUDA events around one bpimd_step call on a dedicated stream (CUDA-graph replays)"}
     return out
 
 

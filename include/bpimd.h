@@ -41,9 +41,13 @@
  *   (BPIMD_ERR_ARG).  Device-side conditions (non-finite positions or results)
  *   are recorded in a device status word; they surface as BPIMD_ERR_NONFINITE
  *   from the next call that synchronises (the _host calls, bpimd_sync,
- *   bpimd_step).  No kernel of this version spins on a flag or barrier that
- *   another block sets (the recursions meet at hardware cluster barriers), so
- *   BPIMD_ERR_TIMEOUT is reserved: no current call returns it.
+ *   bpimd_step).  The CTAs of a recursion cluster hand their results to one
+ *   another through shared-memory mbarriers; each such wait is bounded (one
+ *   second of the GPU's global timer).  A wait that expires records
+ *   BPIMD_ERR_TIMEOUT: the CTAs then stop waiting and handing off, every
+ *   kernel runs to its end (the evaluation's outputs are invalid), and the
+ *   context and the CUDA context stay usable.  BPIMD_FLAG_TEST_TIMEOUT makes
+ *   this happen on purpose, for tests of the error path.
  */
 #ifndef BPIMD_H
 #define BPIMD_H
@@ -60,7 +64,7 @@ extern "C" {
 #define BPIMD_ERR_ARG (-1)       /* invalid size, parameter or null pointer      */
 #define BPIMD_ERR_NONFINITE (-2) /* NaN/Inf in positions or in a result          */
 #define BPIMD_ERR_CUDA (-3)      /* a CUDA runtime call failed                  */
-#define BPIMD_ERR_TIMEOUT (-4)   /* reserved: a bounded device-side wait expired */
+#define BPIMD_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired           */
 #define BPIMD_ERR_NOMEM (-5)     /* device or host allocation failed            */
 #define BPIMD_ERR_STATE (-6)     /* call not valid for this context's state     */
 #define BPIMD_ERR_SIZE (-7)      /* problem larger than a fixed-size buffer      */
@@ -113,6 +117,12 @@ extern "C" {
  * CTA.  Device memory is then O(N + N P). */
 #define BPIMD_STORE_MAX_N 8192
 #define BPIMD_FLAG_RECOMPUTE 1
+/* Test hook of the error path (bpimd_create only): the forward recursion's
+ * first hand-off wait waits for a hand-off that is never made, so every
+ * evaluation of the context ends with BPIMD_ERR_TIMEOUT after about one
+ * second, with invalid outputs.  No GPU fault is involved: the wait gives up,
+ * and the kernels finish. */
+#define BPIMD_FLAG_TEST_TIMEOUT 2
 
 /* --------------------------------------------------------- pair potentials */
 #define BPIMD_PAIR_NONE 0
@@ -134,7 +144,7 @@ typedef struct {
   double omega_P;
   double beta;
   int32_t precision; /* BPIMD_FP64, BPIMD_MIXED or BPIMD_MIXED32 */
-  int32_t flags;     /* 0 or BPIMD_FLAG_RECOMPUTE; other bits must be 0 */
+  int32_t flags;     /* 0, BPIMD_FLAG_RECOMPUTE, BPIMD_FLAG_TEST_TIMEOUT; other bits must be 0 */
   /* molecular dynamics (bpimd_step) */
   double dt;         /* time step                                   */
   double gamma;      /* Langevin friction (0 = NVE)                  */

@@ -28,6 +28,7 @@ PRECISIONS = {"fp64": BPIMD_FP64, "mixed": BPIMD_MIXED, "mixed32": BPIMD_MIXED32
 BPIMD_MAX_N = 16384
 BPIMD_STORE_MAX_N = 8192
 BPIMD_FLAG_RECOMPUTE = 1
+BPIMD_FLAG_TEST_TIMEOUT = 2
 
 BPIMD_PAIR_NONE = 0
 BPIMD_PAIR_GAUSSIAN = 1

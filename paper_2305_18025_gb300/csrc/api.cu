@@ -23,7 +23,7 @@ int validate(const bpimd_config *c) {
   if ((long long)c->N * c->P > (1LL << 31) / 3) return BPIMD_ERR_ARG;
   if (!finite_pos(c->m) || !finite_pos(c->omega_P) || !finite_pos(c->beta)) return BPIMD_ERR_ARG;
   if (!valid_precision(c->precision)) return BPIMD_ERR_ARG;
-  if (c->flags & ~BPIMD_FLAG_RECOMPUTE) return BPIMD_ERR_ARG;
+  if (c->flags & ~(BPIMD_FLAG_RECOMPUTE | BPIMD_FLAG_TEST_TIMEOUT)) return BPIMD_ERR_ARG;
   if (!(c->box_L >= 0.0) || !std::isfinite(c->box_L)) return BPIMD_ERR_ARG;
   return BPIMD_OK;
 }
@@ -206,6 +206,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   w.half_k = 0.5 * w.k;
   w.cx = w.beta * w.half_k * LOG2E;
   w.recomp = (cfg->flags & BPIMD_FLAG_RECOMPUTE) || cfg->N > BPIMD_STORE_MAX_N;
+  w.test_timeout = (cfg->flags & BPIMD_FLAG_TEST_TIMEOUT) != 0;
   w.blocks = 1;
   set_box(w, cfg->box_L);
   const size_t N = w.N;

@@ -133,6 +133,7 @@ struct Workspace {
   double m, omega_P, beta, k, half_k;
   double cx;            // beta (1/2) k log2(e): g = 2^(-cx d^2)
   int recomp;           // recompute mode: no O(N^2) table; g is formed where it is used
+  int test_timeout;     // BPIMD_FLAG_TEST_TIMEOUT: the forward lead waits for a hand-off never made
   // periodic cubic box of side L (0: open boundaries); every spring joins the
   // minimum image of its beads.  MIXED keeps the bead-1/bead-P copies in a box
   // as 32-bit fixed-point fractions of L (R1s/RPs reinterpreted as uint32

@@ -96,6 +96,7 @@ struct LeadSmem {
   unsigned long long opbar[OPBUF];
   unsigned long long cAm[2 * TILE];  // c A of tile t in slot t & 1, handed in by the tile's owner
   unsigned long long cabar[2];       // completion of those hand-offs
+  unsigned long long never;          // an mbarrier nothing arrives on (BPIMD_FLAG_TEST_TIMEOUT)
   unsigned long long Ym[YRING];      // Y_v at v mod YRING (xi mantissas)
   unsigned long long bm[TILE];       // b of the current tile (phase 1 -> phase 2)
   double misc[4];                    // end of the forward recursion: C'[N], 1/(N y_N) mantissa
@@ -322,6 +323,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       mbar_fence_init();
     }
     if (tid >= 32 && tid < 32 + OPBUF) mbar_init(smem_addr(&sm.opbar[tid - 32]), 32);  // one per loader lane
+    if (tid == 64) mbar_init(smem_addr(&sm.never), 1);
     if (tid == 0) {
       sm.aborted = 0;
       sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0;
@@ -346,6 +348,8 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
     long long ncarry = 0;  // and the running sum of the exponent parts n
     if (wid < LEAD_WARPS) {
+      // the error-path test: a wait that expires before the first tile
+      if (!BWD && w.test_timeout) handoff_wait(smem_addr(&sm.never), 0, w.status, (volatile int *)&sm.aborted);
       for (int t = 0; t < NT; ++t) {
         const int buf = t % OPBUF;
         handoff_wait(smem_addr(&sm.opbar[buf]), (t / OPBUF) & 1, w.status, (volatile int *)&sm.aborted);

@@ -40,29 +40,45 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
 }
 
-// Phase 1 of the bead pass for one particle (one warp): lane j of each chunk
-// of 32 beads forms the spring vector d_j = r^{j+1} - r^j (minimum image in a
-// box) once; the interior force on bead j is k (d_j - d_{j-1}), with d_{j-1}
-// taken from the neighbouring lane (lane 0 from lane 31 of the previous chunk).
-// Adds sum |d_j|^2 to s32 (MIXED) or s64 (FP64).
+// Phase 1 of the bead pass for one particle (one warp).  The particle's
+// [P][3] row is contiguous: each chunk of 32 beads (and the first bead of the
+// next chunk) is staged into the warp's shared buffer with coalesced 16-byte
+// loads (8-byte loads where the row is not 16-byte aligned, i.e. odd P and odd
+// particle index).  Lane j then forms the spring vector d_j = r^{j+1} - r^j
+// (minimum image in a box) once; the interior force on bead j is
+// k (d_j - d_{j-1}), with d_{j-1} taken from the neighbouring lane (lane 0
+// from lane 31 of the previous chunk).  Adds sum |d_j|^2 to s32 (MIXED) or s64
+// (FP64).
+constexpr int STAGE_DOUBLES = 3 * 33 + 1;  // 33 beads, padded to a 16-byte multiple
 template <bool MIXED, bool PBC>
 __device__ __forceinline__ void bead_springs(const Workspace &w, const double *__restrict__ p,
                                              double *__restrict__ f, int lane, bool &finite, float &s32,
-                                             double &s64) {
+                                             double &s64, double *__restrict__ stage) {
   using D_t = typename std::conditional<MIXED, float, double>::type;
   const int P = w.P;
   const D_t kk = (D_t)w.k;
   D_t cx = 0, cy = 0, cz = 0;  // d_{j0-1} carried from the previous chunk
+  const bool aligned = (((uintptr_t)p) & 15) == 0;  // warp-uniform
   for (int j0 = 0; j0 < P; j0 += 32) {
+    const int nd = 3 * min(33, P - j0);  // doubles of beads j0 .. j0+32 that exist
+    const double *src = p + 3 * j0;      // 16-byte aligned with p (3 * 32 doubles per chunk)
+    __syncwarp();                        // the previous chunk's reads of the buffer are done
+    if (aligned) {
+      for (int i = lane; i < nd / 2; i += 32) ((double2 *)stage)[i] = __ldg((const double2 *)src + i);
+      if ((nd & 1) && lane == 0) stage[nd - 1] = __ldg(src + nd - 1);
+    } else {
+      for (int i = lane; i < nd; i += 32) stage[i] = __ldg(src + i);
+    }
+    __syncwarp();
     const int j = j0 + lane;
     double dx = 0.0, dy = 0.0, dz = 0.0;
     if (j < P) {
-      const double x = p[3 * j], y = p[3 * j + 1], z = p[3 * j + 2];
+      const double x = stage[3 * lane], y = stage[3 * lane + 1], z = stage[3 * lane + 2];
       finite &= finite_bits(x) && finite_bits(y) && finite_bits(z);
       if (j + 1 < P) {
-        dx = p[3 * j + 3] - x;
-        dy = p[3 * j + 4] - y;
-        dz = p[3 * j + 5] - z;
+        dx = stage[3 * lane + 3] - x;
+        dy = stage[3 * lane + 4] - y;
+        dz = stage[3 * lane + 5] - z;
         if (PBC) { dx = mimage(w, dx); dy = mimage(w, dy); dz = mimage(w, dz); }
       }
     }
@@ -90,6 +106,7 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
                                                double *__restrict__ F, int l0) {
   __shared__ double eint_s[BEAD_WARPS];
   __shared__ int finite_s[BEAD_WARPS];
+  __shared__ __align__(16) double stage_s[BEAD_WARPS][STAGE_DOUBLES];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int P = w.P;
   // phase 1: one warp per particle -- interior springs and interior forces
@@ -101,8 +118,8 @@ __device__ __forceinline__ void bead_pass_body(const Workspace &w, const double 
     if (l < w.N) {  // warp-uniform
       const double *p = pos + (size_t)l * P * 3;
       double *f = F + (size_t)l * P * 3;
-      if (w.pbc) bead_springs<MIXED, true>(w, p, f, lane, finite, s32, s64);
-      else bead_springs<MIXED, false>(w, p, f, lane, finite, s32, s64);
+      if (w.pbc) bead_springs<MIXED, true>(w, p, f, lane, finite, s32, s64, stage_s[wp]);
+      else bead_springs<MIXED, false>(w, p, f, lane, finite, s32, s64, stage_s[wp]);
     }
     if (MIXED) {
 #pragma unroll

@@ -61,7 +61,7 @@ def test_config_struct_matches_header_layout():
 
 @pytest.mark.parametrize("field,value", [
     ("N", 0), ("P", 1), ("m", 0.0), ("omega_P", -1.0), ("beta", float("nan")),
-    ("beta", float("inf")), ("precision", 7), ("precision", 3), ("flags", 2), ("N", 16385),
+    ("beta", float("inf")), ("precision", 7), ("precision", 3), ("flags", 4), ("flags", 8), ("N", 16385),
     ("box_L", -1.0), ("box_L", float("nan")), ("box_L", float("inf")),
 ])
 def test_create_rejects_invalid_config_without_gpu(lib, field, value):

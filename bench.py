@@ -445,11 +445,11 @@ def run_ours(args, rank, world, local_rank):
 # arithmetic of each precision form (what the path computes in)
 DTYPES = {
     "mixed": "f32+f64+u64 (float32 bead differences and spring energies; float64-accurate pair factors, "
-             "64-bit integer recursion steps, float64 bulk sums, integer-mantissa probabilities, "
+             "64-bit integer recursions, integer-mantissa probabilities, "
              "compensated float32-pair force sums)",
-    "fp64": "f64+u64 (float64, with 64-bit integer recursion steps and integer-pipe pair factors)",
-    "mixed32": "f32+u32+f64 (float32 pair factors and sums, 32-bit integer recursion steps, "
-               "float64 prefix sums, hand-offs and outputs)",
+    "fp64": "f64+u64 (float64, with 64-bit integer recursions and integer-pipe pair factors)",
+    "mixed32": "f32+u64+f64 (float32 pair factors, recursion bulk sums and probabilities; 64-bit integer "
+               "tile products; float64 prefix sums and outputs)",
 }
 
 

@@ -77,26 +77,31 @@ extern "C" {
  * BPIMD_FP64: float64 bead differences, spring energies, closing-spring
  *   distances and forces; pair Boltzmann factors g = 2^(-x) of the exact
  *   float64 product x by a 64-bit fixed-point table method (integer pipe,
- *   2^-60 relative before the final float64 rounding); recursion steps with
- *   64-bit integer mantissas (truncation 2^-61 per operation); float64 bulk
- *   sums of the recursions, probabilities and force sums.
+ *   2^-60 relative before the final float64 rounding); the blocked recursions
+ *   (tile inverses, the lead's tile products and the bulk sums) on 64-bit
+ *   integer mantissas with int32 exponents (truncation 2^-61 per operation);
+ *   float64 probabilities and force sums.
  * BPIMD_MIXED: float32 bead differences, per-particle spring energies (float32
  *   warp sums) and closing-spring distances; everything after them at float64
  *   accuracy or better: the link coefficients and the prefix sums of spring
  *   energies in float64, g = 2^(-x) of the exact product of the float32
  *   closing-spring term and the float64 constant beta k/2 log2(e) by the same
- *   integer table method, recursion steps with 64-bit integer mantissas and
- *   float64 bulk sums, probabilities Pr = alpha mu g from 64-bit integer
+ *   integer table method, the recursions on 64-bit integer mantissas as in
+ *   BPIMD_FP64, probabilities Pr = alpha mu g from 64-bit integer
  *   mantissa products, and the probability and force sums as unevaluated
  *   sums of two float32 numbers (compensated: 2^-46 relative) over float32
  *   bead differences.
  * BPIMD_MIXED32: the fastest form: float32 bead differences and spring
- *   energies, g from the float32 hardware exponential (ex2.approx), recursion
- *   steps on 32-bit integer mantissas (31 bits, multiplied by the top 32 bits
- *   of K = c g: truncation 2^-30 per step), float32 bulk and next-tile sums,
+ *   energies, g from the float32 hardware exponential (ex2.approx), the
+ *   recursions' bulk sums as float32 products over 8 sources, the tile
+ *   inverses and the lead's tile products on 64-bit integer mantissas,
  *   float32 probabilities and block-local force sums (combined across blocks
  *   with float32 TwoSum compensation); float64 prefix sums, link coefficients,
- *   tile hand-offs and outputs.
+ *   and outputs.
+ * Replica batches (bpimd_create_batched) run each recursion of a replica of
+ * up to 4096 particles on one CTA as 32 dependent steps per tile, in the same
+ * formats, except that BPIMD_MIXED32 multiplies there by the top 32 bits of
+ * the 64-bit factor mantissa (truncation 2^-30 per step).
  * All three meet the mixed tolerances (1e-6 relative on V_B, 1e-5 RMS on
  * forces); BPIMD_FP64 meets 1e-12 / 1e-10. */
 #define BPIMD_FP64 0

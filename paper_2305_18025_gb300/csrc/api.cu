@@ -196,6 +196,7 @@ int bpimd_create(bpimd_ctx **out, const bpimd_config *cfg, void *cuda_stream) {
   Workspace &w = ctx->w;
   w.N = cfg->N;
   w.P = cfg->P;
+  w.inv_P = 1.0 / cfg->P;
   w.NT = (w.N + TILE - 1) / TILE;
   w.NB = w.NT * (w.NT + 1) / 2;
   set_precision(w, cfg->precision);

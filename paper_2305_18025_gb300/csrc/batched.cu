@@ -92,6 +92,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
     Workspace &w = ctx->h_ws[r];
     w.N = N[r];
     w.P = P[r];
+    w.inv_P = 1.0 / P[r];
     w.NT = (w.N + TILE - 1) / TILE;
     w.NB = w.NT * (w.NT + 1) / 2;
     set_precision(w, cfg->precision);

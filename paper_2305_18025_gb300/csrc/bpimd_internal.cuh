@@ -131,6 +131,7 @@ struct Workspace {
   int mixed;            // MIXED32: float32 pair-factor and alpha mantissas, 32-bit recursion chain
   int bead32;           // MIXED and MIXED32: float32 bead differences and spring energies
   double m, omega_P, beta, k, half_k;
+  double inv_P;         // 1/P (kernels take it from here: a float64 division costs a GB300 SM ~20 warp-cycles per lane)
   double cx;            // beta (1/2) k log2(e): g = 2^(-cx d^2)
   int recomp;           // recompute mode: no O(N^2) table; g is formed where it is used
   int test_timeout;     // BPIMD_FLAG_TEST_TIMEOUT: the forward lead waits for a hand-off never made

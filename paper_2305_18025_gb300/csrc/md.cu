@@ -122,6 +122,46 @@ __global__ void __launch_bounds__(MD_THREADS) md_kick_kernel(double *__restrict_
 }
 
 // Deterministic block sum (fixed shuffle tree, then warps in order); thread 0 gets it.
+// float64 -> float32, round to nearest even, on the integer pipe (a
+// conversion instruction runs on GB300's narrow float64 pipe); results below
+// the float32 normal range flush to a signed zero, so the value must be
+// finite and below 2^128 in magnitude.  Bit-identical to __double2float_rn
+// for every normal float32 result.
+__device__ __forceinline__ float f32_of_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned r = (unsigned)(m >> 29);
+  const unsigned long long rem = m & ((1ull << 29) - 1);
+  r += (rem > (1ull << 28)) || (rem == (1ull << 28) && (r & 1u));
+  return ex <= 0 ? __uint_as_float(sign) : __uint_as_float(sign | (((unsigned)ex << 23) + r));
+}
+
+// float32 -> float64 on the integer pipe (exact; zero and subnormal inputs give
+// a signed zero; the value must be finite)
+__device__ __forceinline__ double f64_of_f32(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned ex = (b >> 23) & 0xffu;
+  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)s);
+  return __longlong_as_double(
+      (long long)(s | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// block-wide sum of a float32 per thread: float32 warp sums, float64 across warps
+__device__ __forceinline__ double block_sum_f(float v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f64_of_f32(v);
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -158,12 +198,19 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
     const double *r = pos + ((size_t)l * P + j) * 3;
     rx = r[0]; ry = r[1]; rz = r[2];
   }
-  const R px = (R)rx, py = (R)ry, pz = (R)rz;
-  const R a = (R)(-0.5 * pp.inv_s2);
-  const double a2 = -0.5 * pp.inv_s2 * 1.4426950408889634;  // float64: the exponent in base 2 (times log2 e)
+  // mixed: float32 positions and constants from integer-pipe conversions
+  // and host-formed copies, so that no per-thread float64 work remains but the
+  // three force accumulations
+  R px, py, pz, a, L, invL, sig2, rc2;
+  if constexpr (MIXED) {
+    px = f32_of_f64(rx); py = f32_of_f64(ry); pz = f32_of_f64(rz);
+    a = pp.fa; L = pp.fL; invL = pp.finvL; sig2 = pp.fsig2; rc2 = pp.frc2;
+  } else {
+    px = rx; py = ry; pz = rz;
+    a = -0.5 * pp.inv_s2; L = pp.L; invL = pp.invL; sig2 = pp.sig2; rc2 = pp.rc2;
+  }
+  const double a2 = MIXED ? 0.0 : -0.5 * pp.inv_s2 * 1.4426950408889634;  // float64: the exponent in base 2
   if (!MIXED) exp2_table_init(T2);
-  const R L = (R)pp.L, invL = (R)pp.invL;
-  const R sig2 = (R)pp.sig2, rc2 = (R)pp.rc2;
   auto img = [&](R d) -> R {
     if constexpr (PBC) return d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL)));
     else return d;
@@ -177,7 +224,9 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
       for (int q = threadIdx.x; q < cnt; q += EXT_THREADS) {
         const double *r = pos + ((size_t)(base + q) * P + j) * 3;
         R4 t;
-        t.x = (R)r[0]; t.y = (R)r[1]; t.z = (R)r[2]; t.w = (R)0;
+        if constexpr (MIXED) { t.x = f32_of_f64(r[0]); t.y = f32_of_f64(r[1]); t.z = f32_of_f64(r[2]); }
+        else { t.x = r[0]; t.y = r[1]; t.z = r[2]; }
+        t.w = (R)0;
         sr[q] = t;
       }
       __syncthreads();
@@ -215,6 +264,19 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
     fz += __shfl_xor_sync(0xffffffffu, fz, o);
     u += __shfl_xor_sync(0xffffffffu, u, o);
     nin += __shfl_xor_sync(0xffffffffu, nin, o);
+  }
+  if constexpr (MIXED) {
+    float ulf = 0.0f;
+    if (valid && sub == 0) {
+      if (pp.pair == BPIMD_PAIR_GAUSSIAN) u -= 1.0f;  // the self term (d = 0, e = 1) carries no force
+      double *f = F + ((size_t)l * P + j) * 3;
+      f[0] += f64_of_f32(pp.finv_P * (pp.ffs * fx - pp.fkt * px));
+      f[1] += f64_of_f32(pp.finv_P * (pp.ffs * fy - pp.fkt * py));
+      f[2] += f64_of_f32(pp.finv_P * (pp.ffs * fz - pp.fkt * pz));
+      const float up = pp.pair == BPIMD_PAIR_GAUSSIAN ? pp.fup * u : pp.fup * u - pp.fush * (float)nin;
+      ulf = pp.finv_P * (up + 0.5f * pp.fkt * (px * px + py * py + pz * pz));
+    }
+    return block_sum_f(ulf, red);
   }
   double ul = 0.0;
   if (valid && sub == 0) {
@@ -304,7 +366,8 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_batched(const double *_
     const int4 e = tab[k];
     const int N = ws[e.x].N, P = ws[e.x].P;
     PairParams q = pp;
-    q.inv_P = 1.0 / P;
+    q.inv_P = ws[e.x].inv_P;
+    q.finv_P = f32_of_f64(q.inv_P);
     const double s = ext_force_body<MIXED, false>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T2);
     if (threadIdx.x == 0) ubar_part[k] = s;
     __syncthreads();  // sr and T2 are reused by the next entry
@@ -434,6 +497,16 @@ int md_params(const bpimd_config &c, MDParams &p) {
   q.invL = L > 0.0 ? 1.0 / L : 0.0;
   q.Lscale = (float)(q.L / 4294967296.0);
   q.pbc = L > 0.0 ? 1 : 0;
+  q.fa = (float)(-0.5 * q.inv_s2);
+  q.ffs = (float)(c.pair_type == BPIMD_PAIR_GAUSSIAN ? q.ga * q.inv_s2 : 24.0 * q.eps);
+  q.fup = (float)(c.pair_type == BPIMD_PAIR_GAUSSIAN ? 0.5 * q.ga : 2.0 * q.eps);
+  q.fkt = (float)q.kt;
+  q.fL = (float)q.L;
+  q.finvL = (float)q.invL;
+  q.fsig2 = (float)q.sig2;
+  q.frc2 = (float)q.rc2;
+  q.fush = (float)(0.5 * q.ushift);
+  q.finv_P = (float)q.inv_P;
   p.cell_nc = 0;
   if (c.pair_type == BPIMD_PAIR_LJ && L > 0.0) {
     const int nc = (int)std::floor(L / c.pair_rc);

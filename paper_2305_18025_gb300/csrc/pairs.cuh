@@ -15,6 +15,11 @@ struct PairParams {
   double L, invL;        // periodic box (L = 0: open)
   float Lscale;          // L / 2^32 (fixed-point differences)
   int pbc;               // L > 0 (integer test; float64 compares use the slow float64 pipe)
+  // float32 copies for the mixed forms, formed on the host (a conversion in a
+  // kernel runs on the narrow float64 pipe): -1/(2 s^2), the force factor
+  // (g/s^2 or 24 eps), the energy factor (g/2 or 2 eps), kt, L, 1/L, sigma^2, rc^2
+  float fa, ffs, fup, fkt, fL, finvL, fsig2, frc2;
+  float fush, finv_P;    // ushift / 2, 1/P
 };
 
 // Cell lists per bead index: nc^3 cells of side L/nc >= rc in a periodic box.

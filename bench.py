@@ -549,9 +549,12 @@ def batched_md_throughput(args, dev, reps, wPs, max_over_ranks, barrier, world):
     and Gaussian repulsion g = 1, s = 0.5 between equal-index beads, each
     replica thermostatted at its own beta; the steps are CUDA-graph replays on
     a dedicated stream (batch evaluation, pair forces, integrator: 6 launches
-    per step).  Back to back as in a trajectory, so the L2 is not flushed."""
+    per step), with the pair tile (lanes per particle) picked by the
+    autotuner on scratch copies first.  Back to back as in a trajectory, so
+    the L2 is not flushed."""
     import numpy as np
     import torch
+    from paper_2305_18025_gb300 import autotune
     from paper_2305_18025_gb300.exchange import BatchedExchangeEnergy
     Ns, Ps, betas = [r.N for r in reps], [r.P for r in reps], [r.beta for r in reps]
     out = {}
@@ -561,6 +564,7 @@ def batched_md_throughput(args, dev, reps, wPs, max_over_ranks, barrier, world):
         rng = np.random.default_rng(12)
         x = eng.pack([torch.from_numpy(r.positions) for r in reps])
         v = eng.pack([torch.from_numpy(rng.normal(0.0, 1.0 / np.sqrt(r.beta), r.positions.shape)) for r in reps])
+        tuned = autotune.tune_pair_tile(eng, x, v, steps=2, reps=2)
         eng.step(x, v, max(2, args.warmup), energies=False)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
@@ -577,6 +581,8 @@ def batched_md_throughput(args, dev, reps, wPs, max_over_ranks, barrier, world):
                      "replica_steps_per_s": aggregate_rate(world, steps * len(reps), ms * 1e-3),
                      "ms_per_step": ms / steps, "gpu_launches": (BATCH_LAUNCHES_PER_EVAL + 3) * steps,
                      "finite": bool(np.isfinite(en).all()),
+                     "tuning": {"pair_tile_lanes": int(tuned["choice"]), "cached": tuned["cached"],
+                                "timings_ms": tuned["timings_ms"]},
                      "mean_E_prim_per_bead": float(np.mean(en[:, 3] / np.array([n * p for n, p in zip(Ns, Ps)])))}
     out["config"] = {"workload": "the same 256 replicas, harmonic trap w0=1 and Gaussian repulsion g=1 s=0.5 "
                                  "between equal-index beads",

@@ -295,6 +295,19 @@ int bpimd_batch_info(bpimd_ctx *ctx, int32_t *R, int64_t *elements, int64_t *off
  * autotuner (paper_2305_18025_gb300/autotune.py); results do not depend on it. */
 int bpimd_batch_set_tuning(bpimd_ctx *ctx, int32_t pair_blocks_per_sm, int32_t prob_blocks_per_sm);
 
+/* Pair tile of the batch's molecular dynamics (bpimd_step): the trap and pair
+ * forces between beads of equal index (the potential U of Eq.
+ * int-of-sum-all-permutations) run one 256-thread block per (replica, block
+ * of particles, bead index), lanes_per_particle lanes sharing each particle's
+ * partners (2, 4 or 8: 128, 64 or 32 particles per block; default 4).  Few
+ * lanes suit large replicas, many lanes small ones.  Set by the autotuner.
+ * The per-lane partner order changes with the tile, so forces differ by
+ * float rounding (within the precision form's tolerance).  Any time: a tile
+ * changed after MD steps drops the captured step, which the next bpimd_step
+ * recaptures; positions, velocities and the thermostat counter are kept.
+ * BPIMD_ERR_STATE for a single-system context, BPIMD_ERR_ARG for other values. */
+int bpimd_batch_set_pair_tile(bpimd_ctx *ctx, int32_t lanes_per_particle);
+
 /* ------------------------------------------------------------- profiling */
 /* Stage timing with CUDA events recorded on the context stream around each
  * kernel of an evaluation.  Stage order:

@@ -1,4 +1,8 @@
-"""Autotuner of the batched launch shape (bpimd_batch_set_tuning).
+"""Autotuner of the batched launch shapes.
+
+``tune`` picks the grid caps of the batched exchange passes
+(bpimd_batch_set_tuning); ``tune_pair_tile`` picks the tile of the batch's MD
+pair forces, lanes per particle (bpimd_batch_set_pair_tile).
 
 The batched pair-factor and probability passes run a grid-stride loop over
 (replica, block) tables; how many CTAs per SM they launch trades occupancy
@@ -83,5 +87,50 @@ def tune(engine, positions, reps=5, candidates=CANDIDATES, use_cache=True):
     if use_cache:
         table = _load(path)
         table[key] = {"choice": list(best), "timings_ms": timings}
+        _save(path, table)
+    return {"choice": best, "timings_ms": timings, "cached": False, "key": key}
+
+
+PAIR_TILES = (2, 4, 8)  # lanes per particle of the batched MD pair forces
+
+
+def tune_pair_tile(engine, positions, velocities, steps=3, reps=3, candidates=PAIR_TILES, use_cache=True):
+    """Pick the pair tile (lanes per particle) of a BatchedExchangeEnergy's MD.
+
+    Each candidate runs ``steps`` BAOAB steps of scratch copies of the given
+    positions and velocities (the caller's tensors are not touched), timed
+    with CUDA events on the engine's stream; the fastest median wins.  The
+    thermostat counter advances during the trials.  Cached like ``tune``
+    (GPU, precision, batch signature, plus an ``md-pair-tile`` tag)."""
+    path = cache_path()
+    key = batch_key(engine) + "|md-pair-tile"
+    table = _load(path) if use_cache else {}
+    if key in table:
+        choice = int(table[key]["choice"])
+        engine.set_pair_tile(choice)
+        return {"choice": choice, "timings_ms": {}, "cached": True, "key": key}
+    x = positions.clone()
+    v = velocities.clone()
+    stream = engine.stream
+    timings = {}
+    for cand in candidates:
+        engine.set_pair_tile(cand)
+        engine.step(x, v, steps, energies=False)  # warm-up (and the graph capture)
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            engine.step(x, v, steps, energies=False)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        timings[str(cand)] = statistics.median(ms)
+    best = min(candidates, key=lambda c: timings[str(c)])
+    engine.set_pair_tile(best)
+    engine.sync()
+    if use_cache:
+        table = _load(path)
+        table[key] = {"choice": best, "timings_ms": timings}
         _save(path, table)
     return {"choice": best, "timings_ms": timings, "cached": False, "key": key}

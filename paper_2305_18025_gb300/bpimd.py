@@ -40,7 +40,7 @@ EXPORTED = [
     "bpimd_connection_probabilities", "bpimd_step", "bpimd_status_string", "bpimd_version",
     "bpimd_profile_begin", "bpimd_profile_end", "bpimd_exchange_energy_forces_noalloc",
     "bpimd_create_batched", "bpimd_exchange_energy_forces_batched", "bpimd_batch_info",
-    "bpimd_batch_set_tuning", "bpimd_peak_probe", "bpimd_pow2_selftest",
+    "bpimd_batch_set_tuning", "bpimd_batch_set_pair_tile", "bpimd_peak_probe", "bpimd_pow2_selftest",
 ]
 BATCH_MAX_N = 4096
 BPIMD_NUM_STAGES = 3
@@ -103,6 +103,7 @@ def load(build_if_missing=True):
     lib.bpimd_exchange_energy_forces_batched.argtypes = [vp, vp, vp, vp]
     lib.bpimd_batch_info.argtypes = [vp, vp, vp, vp]
     lib.bpimd_batch_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.bpimd_batch_set_pair_tile.argtypes = [vp, ctypes.c_int32]
     lib.bpimd_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp]
     lib.bpimd_pow2_selftest.argtypes = [ctypes.c_int32, vp, vp, ctypes.c_int32, vp]
     for name in EXPORTED:
@@ -241,6 +242,10 @@ def bpimd_batch_info(ctx):
     off = np.zeros(R.value, dtype=np.int64)
     _check(load().bpimd_batch_info(ctx, None, None, off.ctypes.data), "bpimd_batch_info")
     return R.value, n.value, off
+
+
+def bpimd_batch_set_pair_tile(ctx, lanes_per_particle):
+    _check(load().bpimd_batch_set_pair_tile(ctx, int(lanes_per_particle)), "bpimd_batch_set_pair_tile")
 
 
 def bpimd_batch_set_tuning(ctx, pair_blocks_per_sm, prob_blocks_per_sm):

@@ -80,6 +80,7 @@ int bpimd_create_batched(bpimd_ctx **out, const bpimd_config *cfg, int32_t R, co
   ctx->R = R;
   ctx->total_elems = total;
   ctx->tune_gmat_bpsm = 8;
+  ctx->pair_lanes = 4;
   ctx->tune_prob_bpsm = 8;
   ctx->h_ws.resize(R);
   ctx->h_off.resize(R);
@@ -198,6 +199,14 @@ int bpimd_batch_set_tuning(bpimd_ctx *ctx, int32_t pair_blocks_per_sm, int32_t p
   ctx->tune_gmat_bpsm = pair_blocks_per_sm;
   ctx->tune_prob_bpsm = prob_blocks_per_sm;
   return BPIMD_OK;
+}
+
+// Pair tile of the batched MD pair forces (lanes per particle).
+int bpimd_batch_set_pair_tile(bpimd_ctx *ctx, int32_t lanes_per_particle) {
+  if (!ctx) return BPIMD_ERR_ARG;
+  if (ctx->R == 0) return BPIMD_ERR_STATE;
+  if (lanes_per_particle != 2 && lanes_per_particle != 4 && lanes_per_particle != 8) return BPIMD_ERR_ARG;
+  return md_set_pair_tile(ctx, lanes_per_particle);
 }
 
 }  // extern "C"

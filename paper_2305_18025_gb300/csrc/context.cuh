@@ -44,4 +44,5 @@ struct bpimd_ctx {
   int n_big;                              // replicas above BATCH_MAX_N (first in the order)
   long long *d_off;
   int tune_gmat_bpsm, tune_prob_bpsm;     // grid caps (blocks per SM) of the batched passes
+  int pair_lanes;                         // lanes per particle of the batched pair forces (2, 4 or 8)
 };

@@ -175,23 +175,24 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // -grad U-bar added to F, per bead index j = blockIdx.y and particle
-// l = blockIdx.x * EXT_PARTICLES + thread / EXT_SPLIT (all pairs).  The
-// EXT_SPLIT lanes of one particle take the partners q = sub, sub + EXT_SPLIT, ...
+// l = blockIdx.x * (256 / SPLIT) + thread / SPLIT (all pairs).  The SPLIT
+// lanes of one particle take the partners q = sub, sub + SPLIT, ...
 // of each staged chunk and combine their sums by a fixed shuffle butterfly;
 // U-bar partial sum per block.  The positions of bead j of all particles pass
 // through shared memory in chunks.  Pairs: Gaussian g exp(-r^2/(2 s^2)), or
 // Lennard-Jones 4 eps ((sig/r)^12 - (sig/r)^6) truncated and shifted at rc; in a
 // periodic box (PBC) pair distances by minimum image.  MIXED: pair terms in
 // float32, accumulated per lane in float32 and added to the float64 force.
-template <bool MIXED, bool PBC>
+template <bool MIXED, bool PBC, int SPLIT>
 __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos, double *__restrict__ F, int N,
                                                  int P, const PairParams &pp, int lb, int j,
                                                  typename std::conditional<MIXED, float4, Dbl4>::type *sr,
                                                  double *red, double *T2) {
   using R = typename std::conditional<MIXED, float, double>::type;
   using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
-  const int sub = threadIdx.x % EXT_SPLIT;
-  const int l = lb * EXT_PARTICLES + threadIdx.x / EXT_SPLIT;
+  constexpr int PARTICLES = EXT_THREADS / SPLIT;
+  const int sub = threadIdx.x % SPLIT;
+  const int l = lb * PARTICLES + threadIdx.x / SPLIT;
   const bool valid = l < N;
   double rx = 0, ry = 0, rz = 0;
   if (valid) {
@@ -232,7 +233,7 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
       __syncthreads();
       if (valid && pp.pair == BPIMD_PAIR_GAUSSIAN) {
 #pragma unroll 4
-        for (int q = sub; q < cnt; q += EXT_SPLIT) {
+        for (int q = sub; q < cnt; q += SPLIT) {
           const R4 t = sr[q];
           const R dx = img(px - t.x), dy = img(py - t.y), dz = img(pz - t.z);
           const R d2 = dx * dx + dy * dy + dz * dz;
@@ -242,7 +243,7 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
         }
       } else if (valid) {  // Lennard-Jones: force over 24 eps, energy over 4 eps
 #pragma unroll 4
-        for (int q = sub; q < cnt; q += EXT_SPLIT) {
+        for (int q = sub; q < cnt; q += SPLIT) {
           const R4 t = sr[q];
           const R dx = img(px - t.x), dy = img(py - t.y), dz = img(pz - t.z);
           const R r2 = dx * dx + dy * dy + dz * dz;
@@ -258,7 +259,7 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
     }
   }
 #pragma unroll
-  for (int o = 1; o < EXT_SPLIT; o <<= 1) {
+  for (int o = 1; o < SPLIT; o <<= 1) {
     fx += __shfl_xor_sync(0xffffffffu, fx, o);
     fy += __shfl_xor_sync(0xffffffffu, fy, o);
     fz += __shfl_xor_sync(0xffffffffu, fz, o);
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
   __shared__ R4 sr[EXT_CHUNK];
   __shared__ double red[EXT_THREADS / 32];
   __shared__ double T2[64];  // float64: 2^(j/64) for exp2_table
-  const double s = ext_force_body<MIXED, PBC>(pos, F, N, P, pp, blockIdx.x, blockIdx.y, sr, red, T2);
+  const double s = ext_force_body<MIXED, PBC, EXT_SPLIT>(pos, F, N, P, pp, blockIdx.x, blockIdx.y, sr, red, T2);
   if (threadIdx.x == 0) ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -350,8 +351,9 @@ __global__ void __launch_bounds__(MD_THREADS) md_baoa_batched(double *__restrict
 
 // Trap and pair forces of every replica: entry k of tab is (replica,
 // particle block, bead index); the trap frequency and pair parameters are
-// shared, 1/P_r is the replica's.
-template <bool MIXED>
+// shared, 1/P_r is the replica's.  SPLIT lanes per particle, 256 / SPLIT
+// particles per block (the batch's pair tile, bpimd_batch_set_pair_tile).
+template <bool MIXED, int SPLIT>
 __global__ void __launch_bounds__(EXT_THREADS) ext_force_batched(const double *__restrict__ pos,
                                                                  double *__restrict__ F,
                                                                  const Workspace *__restrict__ ws,
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_batched(const double *_
     PairParams q = pp;
     q.inv_P = ws[e.x].inv_P;
     q.finv_P = f32_of_f64(q.inv_P);
-    const double s = ext_force_body<MIXED, false>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T2);
+    const double s = ext_force_body<MIXED, false, SPLIT>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T2);
     if (threadIdx.x == 0) ubar_part[k] = s;
     __syncthreads();  // sr and T2 are reused by the next entry
   }
@@ -676,22 +678,35 @@ int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *ene
 // element index of the packed arrays as the counter.
 namespace {
 
+// (replica, particle block, bead index) table of the batched pair forces for
+// `lanes` lanes per particle (256 / lanes particles per block)
+void pair_table(const bpimd_ctx *ctx, int lanes, std::vector<int4> &tab, std::vector<int> &ext_first) {
+  const int R = ctx->R, pb = EXT_THREADS / lanes;
+  tab.clear();
+  ext_first.assign(R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    const Workspace &w = ctx->h_ws[r];
+    ext_first[r] = (int)tab.size();
+    for (int j = 0; j < w.P; ++j)
+      for (int lb = 0; lb * pb < w.N; ++lb) tab.push_back(make_int4(r, lb, j, 0));
+  }
+  ext_first[R] = (int)tab.size();
+}
+
 int md_alloc_batched(bpimd_ctx *ctx, const MDParams &p) {
   MDState &md = ctx->md;
   const int R = ctx->R;
   const size_t n = (size_t)ctx->total_elems;
   std::vector<int4> tab;
-  std::vector<int> ext_first(R + 1), blk_first(R + 1);
+  std::vector<int> ext_first, blk_first(R + 1);
+  pair_table(ctx, 8, tab, ext_first);  // the largest table: its size is the capacity
+  md.ext_cap = (int)tab.size();
+  pair_table(ctx, ctx->pair_lanes, tab, ext_first);
   int blk = 0;
   for (int r = 0; r < R; ++r) {
-    const Workspace &w = ctx->h_ws[r];
-    ext_first[r] = (int)tab.size();
-    for (int j = 0; j < w.P; ++j)
-      for (int lb = 0; lb * EXT_PARTICLES < w.N; ++lb) tab.push_back(make_int4(r, lb, j, 0));
     blk_first[r] = blk;
-    blk += w.NB;
+    blk += ctx->h_ws[r].NB;
   }
-  ext_first[R] = (int)tab.size();
   blk_first[R] = blk;
   md.n_ext = (int)tab.size();
   md.spring_blocks = ctx->n_blk_tab;
@@ -704,10 +719,10 @@ int md_alloc_batched(bpimd_ctx *ctx, const MDParams &p) {
   }
   if (cudaMalloc(&md.F, sizeof(double) * n) != cudaSuccess || cudaMalloc(&md.VBr, sizeof(double) * R) != cudaSuccess ||
       cudaMalloc(&md.c2r, sizeof(double) * R) != cudaSuccess ||
-      cudaMalloc(&md.ext_tab, sizeof(int4) * md.n_ext) != cudaSuccess ||
+      cudaMalloc(&md.ext_tab, sizeof(int4) * md.ext_cap) != cudaSuccess ||
       cudaMalloc(&md.ext_first, sizeof(int) * (R + 1)) != cudaSuccess ||
       cudaMalloc(&md.blk_first, sizeof(int) * (R + 1)) != cudaSuccess ||
-      cudaMalloc(&md.ubar_part, sizeof(double) * md.n_ext) != cudaSuccess ||
+      cudaMalloc(&md.ubar_part, sizeof(double) * md.ext_cap) != cudaSuccess ||
       cudaMalloc(&md.spring_part, sizeof(double) * md.spring_blocks) != cudaSuccess ||
       cudaMalloc(&md.step, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
@@ -733,12 +748,16 @@ int total_force_batched(bpimd_ctx *ctx, const MDParams &p, const double *pos) {
   int rc = evaluate_batched(ctx, pos, md.VBr, md.F);
   if (rc != BPIMD_OK) return rc;
   const int grid = md.n_ext < sm_count() * 8 ? md.n_ext : sm_count() * 8;
-  if (ctx->w.bead32)
-    ext_force_batched<true><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->d_ws, ctx->d_off, md.ext_tab,
-                                                                   md.n_ext, p.pp, md.ubar_part);
-  else
-    ext_force_batched<false><<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->d_ws, ctx->d_off, md.ext_tab,
-                                                                    md.n_ext, p.pp, md.ubar_part);
+  auto go = [&](auto kernel) {
+    kernel<<<grid, EXT_THREADS, 0, ctx->stream>>>(pos, md.F, ctx->d_ws, ctx->d_off, md.ext_tab, md.n_ext, p.pp,
+                                                  md.ubar_part);
+  };
+  const bool m = ctx->w.bead32;
+  switch (ctx->pair_lanes) {
+    case 2: m ? go(ext_force_batched<true, 2>) : go(ext_force_batched<false, 2>); break;
+    case 8: m ? go(ext_force_batched<true, 8>) : go(ext_force_batched<false, 8>); break;
+    default: m ? go(ext_force_batched<true, 4>) : go(ext_force_batched<false, 4>); break;
+  }
   return cudaGetLastError() == cudaSuccess ? BPIMD_OK : BPIMD_ERR_CUDA;
 }
 
@@ -761,6 +780,34 @@ int enqueue_step_batched(bpimd_ctx *ctx, const MDParams &p, double *pos, double 
 }
 
 }  // namespace
+
+// A new pair tile for a batch: with MD state allocated, rebuild the pair-force
+// table (within the capacity of the 8-lane table) and drop the captured step,
+// which is recaptured by the next bpimd_step; forces, velocities and the
+// thermostat counter are kept, so a trajectory goes on unchanged.
+int md_set_pair_tile(bpimd_ctx *ctx, int lanes) {
+  MDState &md = ctx->md;
+  if (md.ready && lanes != ctx->pair_lanes) {
+    std::vector<int4> tab;
+    std::vector<int> ext_first;
+    pair_table(ctx, lanes, tab, ext_first);
+    if ((int)tab.size() > md.ext_cap) return BPIMD_ERR_STATE;
+    cudaStream_t s = ctx->stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpyAsync(md.ext_tab, tab.data(), sizeof(int4) * tab.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(md.ext_first, ext_first.data(), sizeof(int) * ext_first.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)  // the host tables go out of scope
+      return BPIMD_ERR_CUDA;
+    md.n_ext = (int)tab.size();
+    md.ext_blocks = md.n_ext;
+    if (md.exec) { cudaGraphExecDestroy(md.exec); md.exec = nullptr; }
+    if (md.graph) { cudaGraphDestroy(md.graph); md.graph = nullptr; }
+    md.g_pos = md.g_vel = nullptr;
+  }
+  ctx->pair_lanes = lanes;
+  return BPIMD_OK;
+}
 
 int md_run_batched(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies) {
   bpimd_config c = ctx->cfg;

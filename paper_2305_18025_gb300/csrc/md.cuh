@@ -28,6 +28,7 @@ struct MDState {
   double *c2r;               // [R] thermostat amplitude sqrt((1 - c1^2) kT_r / m)
   int4 *ext_tab;             // (replica, particle block, bead index) of the pair-force pass
   int n_ext;
+  int ext_cap;               // entries allocated for ext_tab and ubar_part (the 8-lane table)
   int *ext_first;            // [R+1] first ext_tab entry of each replica
   int *blk_first;            // [R+1] first block-table entry of each replica
 };
@@ -37,4 +38,5 @@ int md_run(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *ene
 int evaluate(bpimd_ctx *ctx, const double *pos, double *V_B, double *F);
 int evaluate_batched(bpimd_ctx *ctx, const double *pos, double *V_B, double *F);
 int md_run_batched(bpimd_ctx *ctx, double *pos, double *vel, int32_t nsteps, double *energies);
+int md_set_pair_tile(bpimd_ctx *ctx, int lanes);
 }  // namespace bpimd

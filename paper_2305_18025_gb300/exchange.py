@@ -243,6 +243,10 @@ class BatchedExchangeEnergy:
     def set_tuning(self, pair_blocks_per_sm, prob_blocks_per_sm):
         _c.bpimd_batch_set_tuning(self.ctx, pair_blocks_per_sm, prob_blocks_per_sm)
 
+    def set_pair_tile(self, lanes_per_particle):
+        """Pair tile of ``step``'s trap and pair forces: 2, 4 or 8 lanes per particle."""
+        _c.bpimd_batch_set_pair_tile(self.ctx, lanes_per_particle)
+
     def step(self, pos, vel, nsteps=1, energies=True):
         """Advance every replica by nsteps BAOAB steps (packed pos, vel in
         place); returns the device tensor [R][4] of (V_B, U-bar, kinetic,

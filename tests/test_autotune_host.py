@@ -124,3 +124,44 @@ def test_use_cache_false_times_again_and_writes_nothing(fake_cuda):
     res = autotune.tune(eng, x, reps=1, use_cache=False)
     assert res["choice"] == (4, 8) and not res["cached"]
     assert not os.path.exists(autotune.cache_path())
+
+
+class FakeMDEngine(FakeEngine):
+    """Adds the MD pair tile: each step costs the fake clock by the current tile."""
+
+    def __init__(self, N, P, precision="mixed", step_cost=None):
+        super().__init__(N, P, precision)
+        self.tile, self.steps, self.tiles_applied = 4, 0, []
+        self.step_cost = step_cost or {}
+
+    def set_pair_tile(self, lanes):
+        self.tile = lanes
+        self.tiles_applied.append(lanes)
+
+    def step(self, pos, vel, nsteps=1, energies=True):
+        pos += 1.0  # the tuner must hand in scratch copies
+        self.steps += nsteps
+        self.clock += nsteps * self.step_cost.get(self.tile, 2.0)
+
+
+def test_pair_tile_picks_the_fastest_on_scratch_copies_and_caches_apart(fake_cuda):
+    eng = FakeMDEngine([300, 20], [32, 16], step_cost={2: 3.0, 4: 2.0, 8: 1.5})
+    fake_cuda.append(eng)
+    n = 3 * sum(a * b for a, b in zip(eng.N, eng.P))
+    x, v = torch.zeros(n, dtype=torch.float64), torch.zeros(n, dtype=torch.float64)
+    res = autotune.tune_pair_tile(eng, x, v, steps=2, reps=3)
+    assert res["choice"] == 8 and eng.tile == 8 and not res["cached"]
+    assert set(res["timings_ms"]) == {"2", "4", "8"}
+    assert res["timings_ms"]["8"] == pytest.approx(2 * 1.5)
+    assert eng.steps == len(autotune.PAIR_TILES) * 2 * (1 + 3)
+    assert float(x.abs().max()) == 0.0 and float(v.abs().max()) == 0.0  # the caller's tensors untouched
+    assert res["key"].endswith("|md-pair-tile")
+    # the exchange tuning of the same batch is a different entry
+    res_x = autotune.tune(eng, x, reps=1)
+    table = json.load(open(autotune.cache_path()))
+    assert set(table) == {res["key"], res_x["key"]} and table[res["key"]]["choice"] == 8
+
+    again = FakeMDEngine([300, 20], [32, 16])
+    fake_cuda.append(again)
+    res2 = autotune.tune_pair_tile(again, x, v)
+    assert res2["cached"] and res2["choice"] == 8 and again.steps == 0 and again.tiles_applied == [8]

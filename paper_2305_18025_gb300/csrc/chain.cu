@@ -80,6 +80,11 @@ constexpr int EXPORT_WARP = 8;   // copies finished tiles of Y to global memory
 constexpr int PREFIX_WARP = 9;   // prefix sums C' (forward recursion)
 constexpr int LOADER_WARP = 10;  // copies the phase warps' operands of coming tiles
 constexpr int TINV_THREADS = 1024;
+// Dynamic shared memory the tile-inverse kernel asks for and does not use: more
+// than half an SM's, so that no SM holds two of its CTAs.  Each CTA is
+// issue-bound (32 substitution chains); two on one SM took twice as long
+// (ncu: 15.2k against a 6.2k-cycle mean).
+constexpr int TINV_PAD_SMEM = 120 * 1024;
 constexpr int OPBUF = 3;         // tiles of lead operands in shared memory: the current one and two ahead
 constexpr int XRING = 16;        // tiles of X held by a bulk CTA: more than the 15 bulk CTAs of a cluster
 constexpr int BAR_PHASE = 1;     // named barrier of the phase warps (phase 1 -> phase 2)
@@ -632,7 +637,7 @@ cudaError_t launch_tile_inverse(const Workspace &w, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(w.NT, 2);
   cfg.blockDim = dim3(TINV_THREADS);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = TINV_PAD_SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -697,6 +702,9 @@ cudaError_t prepare_chain_kernel() {
   const int bytes = (int)chain_smem_bytes(chain_max_n(RC), CL, RC);
   cudaError_t e =
       cudaFuncSetAttribute(chain_kernel<MODE, CL, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tile_inverse_kernel<MODE, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TINV_PAD_SMEM);
   if (e == cudaSuccess && CL > 8)
     e = cudaFuncSetAttribute(chain_kernel<MODE, CL, RC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;

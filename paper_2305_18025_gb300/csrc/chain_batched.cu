@@ -178,7 +178,9 @@ __device__ void run_single(const Workspace &w, unsigned char *smem_raw, double *
 
 // CTA 2k + d runs recursion d (0 forward, 1 backward) of replica order[k].
 template <bool MIXED>
-__global__ void __launch_bounds__(BATCH_THREADS, 1) chain_batched_kernel(const Workspace *__restrict__ ws,
+// Two CTAs per SM (64 registers a thread, no spills): each CTA's chain is
+// latency-bound on one warp, so two replicas' recursions share an SM.
+__global__ void __launch_bounds__(BATCH_THREADS, 2) chain_batched_kernel(const Workspace *__restrict__ ws,
                                                                          const int *__restrict__ order,
                                                                          double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

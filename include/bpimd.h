@@ -369,9 +369,10 @@ int bpimd_exchange_energy_forces_noalloc(const bpimd_config *cfg, const double *
 int bpimd_peak_probe(int32_t kind, int64_t iters, void *sink, void *cuda_stream, int64_t *ops);
 
 /* Self-test of the device's powers of two (no counterpart in the paper; for
- * tests): out[i] = 2^x[i] by the float64 table method of the MD pair force
- * (method 0, x <= 0), or 2^(-x[i]) by the integer-pipe fixed-point method of
- * the pair factors (method 1, x >= 0; 0 below the float64 normal range).
+ * tests), both by the integer-pipe fixed-point method, x >= 0, 0 below the
+ * float64 normal range: out[i] = 2^(-x[i]/2) with the exact double x double
+ * argument product of the float64 Gaussian pair force (method 0, factor 1/2),
+ * or 2^(-x[i]) as for the float64 pair factors (method 1).
  * x, out: device arrays of n float64.  Asynchronous on cuda_stream. */
 int bpimd_pow2_selftest(int32_t method, const double *x, double *out, int32_t n, void *cuda_stream);
 

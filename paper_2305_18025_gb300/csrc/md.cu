@@ -32,7 +32,7 @@
 #include <type_traits>
 
 #include "context.cuh"
-#include "exp2_table.cuh"
+#include "pairg.cuh"
 #include "pairs.cuh"
 
 namespace bpimd {
@@ -122,6 +122,13 @@ __global__ void __launch_bounds__(MD_THREADS) md_kick_kernel(double *__restrict_
 }
 
 // Deterministic block sum (fixed shuffle tree, then warps in order); thread 0 gets it.
+// m 2^e of the integer-pipe power of two as a double (e <= 0; the exponent is
+// added with integer instructions; results below the normal range give 0)
+__device__ __forceinline__ double pow2_value(pow2fx::mexp r) {
+  const long long b = __double_as_longlong(r.m);
+  return ((int)(b >> 52) + r.e <= 0) ? 0.0 : __longlong_as_double(b + ((long long)r.e << 52));
+}
+
 // float64 -> float32, round to nearest even, on the integer pipe (a
 // conversion instruction runs on GB300's narrow float64 pipe); results below
 // the float32 normal range flush to a signed zero, so the value must be
@@ -187,7 +194,7 @@ template <bool MIXED, bool PBC, int SPLIT>
 __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos, double *__restrict__ F, int N,
                                                  int P, const PairParams &pp, int lb, int j,
                                                  typename std::conditional<MIXED, float4, Dbl4>::type *sr,
-                                                 double *red, double *T2) {
+                                                 double *red, unsigned long long *T63s) {
   using R = typename std::conditional<MIXED, float, double>::type;
   using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
   constexpr int PARTICLES = EXT_THREADS / SPLIT;
@@ -210,8 +217,7 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
     px = rx; py = ry; pz = rz;
     a = -0.5 * pp.inv_s2; L = pp.L; invL = pp.invL; sig2 = pp.sig2; rc2 = pp.rc2;
   }
-  const double a2 = MIXED ? 0.0 : -0.5 * pp.inv_s2 * 1.4426950408889634;  // float64: the exponent in base 2
-  if (!MIXED) exp2_table_init(T2);
+  if (!MIXED) pairg::table_init(T63s);  // float64: the integer-pipe power of two (read after the first barrier)
   auto img = [&](R d) -> R {
     if constexpr (PBC) return d - L * (MIXED ? (R)rintf((float)(d * invL)) : (R)rint((double)(d * invL)));
     else return d;
@@ -237,7 +243,9 @@ __device__ __forceinline__ double ext_force_body(const double *__restrict__ pos,
           const R4 t = sr[q];
           const R dx = img(px - t.x), dy = img(py - t.y), dz = img(pz - t.z);
           const R d2 = dx * dx + dy * dy + dz * dz;
-          const R e = MIXED ? (R)__expf((float)(a * d2)) : (R)exp2_table(a2 * (double)d2, T2);
+          R e;
+          if constexpr (MIXED) e = __expf(a * d2);
+          else e = pow2_value(pow2fx::pow2neg_dd((double)d2, pp.g2c, T63s));  // exactly 1 at d = 0
           fx += e * dx; fy += e * dy; fz += e * dz;
           u += e;
         }
@@ -300,8 +308,8 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_kernel(const double *__
   using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
   __shared__ R4 sr[EXT_CHUNK];
   __shared__ double red[EXT_THREADS / 32];
-  __shared__ double T2[64];  // float64: 2^(j/64) for exp2_table
-  const double s = ext_force_body<MIXED, PBC, EXT_SPLIT>(pos, F, N, P, pp, blockIdx.x, blockIdx.y, sr, red, T2);
+  __shared__ unsigned long long T63s[256];  // float64: the table of the integer-pipe power of two
+  const double s = ext_force_body<MIXED, PBC, EXT_SPLIT>(pos, F, N, P, pp, blockIdx.x, blockIdx.y, sr, red, T63s);
   if (threadIdx.x == 0) ubar_part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -363,16 +371,16 @@ __global__ void __launch_bounds__(EXT_THREADS) ext_force_batched(const double *_
   using R4 = typename std::conditional<MIXED, float4, Dbl4>::type;
   __shared__ R4 sr[EXT_CHUNK];
   __shared__ double red[EXT_THREADS / 32];
-  __shared__ double T2[64];
+  __shared__ unsigned long long T63s[256];
   for (int k = blockIdx.x; k < ntab; k += gridDim.x) {
     const int4 e = tab[k];
     const int N = ws[e.x].N, P = ws[e.x].P;
     PairParams q = pp;
     q.inv_P = ws[e.x].inv_P;
     q.finv_P = f32_of_f64(q.inv_P);
-    const double s = ext_force_body<MIXED, false, SPLIT>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T2);
+    const double s = ext_force_body<MIXED, false, SPLIT>(pos + off[e.x], F + off[e.x], N, P, q, e.y, e.z, sr, red, T63s);
     if (threadIdx.x == 0) ubar_part[k] = s;
-    __syncthreads();  // sr and T2 are reused by the next entry
+    __syncthreads();  // sr is reused by the next entry
   }
 }
 
@@ -487,6 +495,7 @@ int md_params(const bpimd_config &c, MDParams &p) {
   if (c.pair_type == BPIMD_PAIR_GAUSSIAN) {
     q.ga = c.pair_a;
     q.inv_s2 = 1.0 / (c.pair_b * c.pair_b);
+    q.g2c = 0.5 * q.inv_s2 * 1.4426950408889634;  // log2(e) / (2 s^2)
   }
   if (c.pair_type == BPIMD_PAIR_LJ) {
     q.eps = c.pair_a;

@@ -10,6 +10,7 @@ struct PairParams {
   int pair;              // BPIMD_PAIR_NONE / GAUSSIAN / LJ
   double inv_P, kt;      // 1/P, m w0^2 (trap)
   double ga, inv_s2;     // Gaussian g, 1/s^2
+  double g2c;            // log2(e) / (2 s^2): the Gaussian is 2^(-g2c d^2)
   double eps, sig2, rc2; // Lennard-Jones eps, sigma^2, cutoff^2
   double ushift;         // LJ energy at the cutoff (subtracted per pair inside it)
   double L, invL;        // periodic box (L = 0: open)

@@ -56,26 +56,20 @@ extern "C" int bpimd_peak_probe(int32_t kind, int64_t iters, void *sink, void *c
 
 // ------------------------------------------------ powers-of-two self-test
 // The device's own powers of two on caller-given arguments, for tests that
-// compare them with a reference exp2: method 0 = the float64 table method of
-// the MD pair force (exp2_table.cuh), 2^y for y <= 0; method 1 = the
-// integer-pipe fixed-point method of the pair factors (pow2_fixed.cuh),
-// 2^(-x) for x >= 0 (the result as a double, 0 below the normal range).
-#include "exp2_table.cuh"
+// compare them with a reference exp2, both by the integer-pipe fixed-point
+// method (pow2_fixed.cuh), x >= 0, the result as a double (0 below the normal
+// range): method 0 = 2^(-x c) with the exact double x double product of the
+// float64 MD Gaussian (pow2neg_dd, c = 1/2, so that the reference argument is
+// exact too); method 1 = 2^(-x) as for the float64 pair factors (pow2neg).
 #include "pow2_fixed.cuh"
 
 namespace bpimd {
 namespace {
 __global__ void pow2_selftest_kernel(int method, const double *__restrict__ x, double *__restrict__ out, int n) {
-  __shared__ double T64[64];
-  exp2_table_init(T64);
-  __syncthreads();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (method == 0) {
-      out[i] = exp2_table(x[i], T64);
-    } else {
-      const pow2fx::mexp g = pow2fx::pow2neg(x[i], pow2fx::T63);
-      out[i] = g.e < -1022 ? 0.0 : g.m * __longlong_as_double((long long)(g.e + 1023) << 52);
-    }
+    const pow2fx::mexp g =
+        method == 0 ? pow2fx::pow2neg_dd(x[i], 0.5, pow2fx::T63) : pow2fx::pow2neg(x[i], pow2fx::T63);
+    out[i] = g.e < -1022 ? 0.0 : g.m * __longlong_as_double((long long)(g.e + 1023) << 52);
   }
 }
 }  // namespace

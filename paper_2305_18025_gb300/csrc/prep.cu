@@ -19,10 +19,11 @@
 // u <= v -- the closing-spring factor of the cycle energy E^{[u,v]} (Eq.
 // e-recurrence-step, last term) -- stored once per evaluation as an extended
 // number 2^x = mantissa(2^frac(x)) * 2^floor(x), x = -beta (1/2)k |d|^2 log2(e).
-// FP64: float64 difference and square; 2^frac(x) by the table method of
-// exp2_table.cuh (10 float64 instructions).  MIXED: difference of the
-// float32 high/low parts (or fixed-point copies) of the positions, float32
-// square, hardware ex2.approx.  The potentials V^{[1,v]}, V^{[u,N]} for
+// FP64: float64 difference and square; 2^x by the integer-pipe fixed-point
+// method of pow2_fixed.cuh on the exact product of the square and the
+// constant.  MIXED: difference of the float32 high/low parts (or fixed-point
+// copies) of the positions, float32 square, the same integer method on the
+// exact float32 x float64 product (MIXED32: hardware ex2.approx).  The potentials V^{[1,v]}, V^{[u,N]} for
 // diagnostics are computed on demand by diag_potentials_kernel.
 #include <type_traits>
 

@@ -1,11 +1,14 @@
 """The device's powers of two against numpy's float64 exp2 (correctly rounded
 to within an ulp on these arguments) and against the exact values of the
-integer-argument cases:
-  * the float64 table method of the MD pair force (exp2_table.cuh, Tang's
-    method, truncation below 3.6e-17) over y in [-1000, 0], including values at
-    and next to the k/64 table boundaries: within 4 ulp;
-  * the integer-pipe fixed-point method of the pair factors (pow2_fixed.cuh)
-    over x in [0, 1000]: within 2 ulp, exact on integers.
+integer-argument cases, both by the integer-pipe fixed-point method
+(pow2_fixed.cuh):
+  * 2^(-x/2) with the exact double x double product of the float64 Gaussian
+    pair force (pow2neg_dd with c = 1/2, an exact factor, so that numpy's
+    argument is exact too) over x in [0, 2000], including the arguments at and
+    next to multiples of 1/128: within 2 ulp, exactly 1 at x = 0 (the Gaussian
+    self term relies on it);
+  * 2^(-x) as for the float64 pair factors over x in [0, 1000]: within 2 ulp,
+    exact on integers.
 """
 import numpy as np
 import pytest
@@ -37,11 +40,11 @@ def arguments(sign):
     return x if sign < 0 else -x
 
 
-def test_float64_table_method_within_a_few_ulp():
-    y = arguments(-1)
-    got = run(0, y)
-    want = np.exp2(y)
-    assert ulps(got, want).max() <= 4.0
+def test_exact_product_method_of_the_gaussian_within_two_ulp():
+    x = 2.0 * arguments(+1)
+    got = run(0, x)
+    want = np.exp2(-0.5 * x)
+    assert ulps(got, want).max() <= 2.0
     assert run(0, np.array([0.0]))[0] == 1.0  # exact at 0 (the Gaussian self term relies on it)
 
 

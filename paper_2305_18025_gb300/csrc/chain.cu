@@ -81,9 +81,10 @@ constexpr int PREFIX_WARP = 9;   // prefix sums C' (forward recursion)
 constexpr int LOADER_WARP = 10;  // copies the phase warps' operands of coming tiles
 constexpr int TINV_THREADS = 1024;
 // Dynamic shared memory the tile-inverse kernel asks for and does not use: more
-// than half an SM's, so that no SM holds two of its CTAs.  Each CTA is
-// issue-bound (32 substitution chains); two on one SM took twice as long
-// (ncu: 15.2k against a 6.2k-cycle mean).
+// than half an SM's, so that no SM holds two of its issue-bound CTAs (32
+// substitution chains each).  Measured: the recursions stage (tile inverses
+// and clusters) fell from 63.0 to 61.2 us at N = 1024; the longest CTA is
+// still ~2.5x the mean under ncu's cold caches.
 constexpr int TINV_PAD_SMEM = 120 * 1024;
 constexpr int OPBUF = 3;         // tiles of lead operands in shared memory: the current one and two ahead
 constexpr int XRING = 16;        // tiles of X held by a bulk CTA: more than the 15 bulk CTAs of a cluster

@@ -332,8 +332,7 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
     if (tid == 64) mbar_init(smem_addr(&sm.never), 1);
     if (tid == 0) {
       sm.aborted = 0;
-      sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0; gYm[0] = 1.0; gYe[0] = 0;
-      if (!BWD) w.C[0] = 0.0;
+      sm.Ym[0] = 1ull << 62; sm.Ye[0] = 0;
     }
     // phase warps: rows j = 4 wid + (lane >> 3), sources 4g .. 4g+3 (g = lane & 7)
     const int g = lane & 7, jrow = 4 * wid + (lane >> 3);
@@ -347,9 +346,18 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       cp_async_arrive(smem_addr(&sm.opbar[b]));
     };
     __syncthreads();  // the operand mbarriers are initialised
+    // Everything above touches shared memory only, so it runs, and the cluster
+    // barrier starts, while the tile inverses are still being formed; global
+    // memory is accessed only after the wait for that grid.
+    cluster_arrive();
+    pdl_wait();
+    if (tid == 0) {
+      gYm[0] = 1.0; gYe[0] = 0;
+      if (!BWD) w.C[0] = 0.0;
+    }
     if (wid == LOADER_WARP)
       for (int tt = 0; tt < OPBUF && tt < NT; ++tt) copy_tile(tt);
-    cluster.sync();  // every mbarrier of the cluster is initialised
+    cluster_wait();  // every mbarrier of the cluster is initialised
 
     double carry = 0.0;    // prefix-sum warp (forward): running reduced prefix sum C'
     long long ncarry = 0;  // and the running sum of the exponent parts n
@@ -369,15 +377,16 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
           const int v = (t * TILE - 31 + 4 * g + q) & (YRING - 1);
           X[q] = xi{sm.Ym[v], sm.Ye[v]};
         }
-        // c A^t from the tile's owner (tile 0 has none)
+        // phase 1: b_j = c_j A_j + sum_i Dc(j, i) X^{t-1}_i   (33 terms: S = 6).
+        // The 32 Dc terms are summed and reduced while c A^t may still be on its
+        // way from the tile's owner; c A^t (tile 0 has none: an extended zero)
+        // joins the row sum after the reduction, so only one addition follows
+        // its arrival.
+        const xsum sd = row_reduce(xsum_dot<6, 4>(Dk, De, X, 0, 2 * XZERO_E));
         if (t >= 1) handoff_wait(smem_addr(&sm.cabar[t & 1]), ((t - 1) >> 1) & 1, w.status, (volatile int *)&sm.aborted);
-        unsigned long long p0 = 0;
-        int pe0 = 2 * XZERO_E;
-        if (g == 0) { p0 = sm.cAm[(t & 1) * TILE + jrow]; pe0 = sm.cAe[(t & 1) * TILE + jrow]; }
-        // phase 1: b_j = c_j A_j + sum_i Dc(j, i) X^{t-1}_i   (33 terms: S = 6)
-        const xsum s1 = row_reduce(xsum_dot<6, 4>(Dk, De, X, p0, pe0));
         if (g == 0) {
-          const xi b = xsum_fin<6>(s1);
+          const xsum ca{sm.cAm[(t & 1) * TILE + jrow] >> 6, sm.cAe[(t & 1) * TILE + jrow]};
+          const xi b = xsum_fin<6>(xsum_add(sd, ca));
           sm.bm[jrow] = b.m;
           sm.be[jrow] = b.e;
         }
@@ -502,14 +511,6 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
         e[i] = __ldg(ge + gi);
       }
     };
-    for (int q = tid; q < lt_max * TILE; q += blockDim.x) {
-      Am[q] = 1ull << 62;
-      Ae[q] = XZERO_E;
-      const int r = ((q >> 5) * NHELP + h) * TILE + (q & 31);  // owned row of local tile q/32
-      const xd c = r < N ? chain_coef<BWD>(w, r) : xd{1.0, XZERO_E};
-      Cm[q] = c.m;
-      Ce[q] = c.e;
-    }
     if (tid < TILE) {  // X^{-1} = (0, ..., 0, Y_0)
       hd.Xm[XRING][tid] = 1ull << 62;
       hd.Xe[XRING][tid] = tid == TILE - 1 ? 0 : XZERO_E;
@@ -519,13 +520,26 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
       mbar_fence_init();
     }
     if (tid == 0) hd.aborted = 0;
-    if (RC) pairg::table_init(T63);
+    if (RC) pairg::table_init(T63);  // from constant memory
+    // as in the lead: the barrier starts before the wait for the tile inverses,
+    // and global memory is read only after it
+    cluster_arrive();
+    pdl_wait();
+    for (int q = tid; q < lt_max * TILE; q += blockDim.x) {
+      Am[q] = 1ull << 62;
+      Ae[q] = XZERO_E;
+      const int r = ((q >> 5) * NHELP + h) * TILE + (q & 31);  // owned row of local tile q/32
+      const xd c = r < N ? chain_coef<BWD>(w, r) : xd{1.0, XZERO_E};
+      Cm[q] = c.m;
+      Ce[q] = c.e;
+    }
     int nt = 0, nk = wid;  // this warp's next task
     advance(nt, nk);
     M_t fm[8];             // its factors, loaded one task ahead (stored mode)
     int fe[8];
     if (!RC && nt < NT) load_factors(nt, nk, fm, fe);
-    cluster.sync();  // every mbarrier of the cluster is initialised
+    __syncthreads();  // the rows' sums and coefficients are initialised
+    cluster_wait();   // every mbarrier of the cluster is initialised
     const LeadSmem *L0 = (const LeadSmem *)smem_raw;  // offsets of the lead's hand-off slots
     // unit u of period t: add the four quarter partials to the rows' sums A; the
     // owner of tile t+1 hands c A of the finished tile to the lead (one warp)
@@ -615,7 +629,8 @@ __device__ void run_chain(const Workspace &w, unsigned char *smem_raw, double *V
 template <int MODE, int CL, bool RC>
 __global__ void __launch_bounds__(CHAIN_THREADS, 1) chain_kernel(Workspace w, double *V_B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_wait();
+  // run_chain waits for the preceding grid (griddepcontrol.wait) once its
+  // shared-memory set-up is done, before its first global-memory access
   if (blockIdx.x < CL) run_chain<MODE, false, CL - 1, RC>(w, smem_raw, V_B);
   else run_chain<MODE, true, CL - 1, RC>(w, smem_raw, V_B);
 }

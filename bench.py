@@ -156,6 +156,14 @@ def load_traffic(kernel):
     return ent.get("dram_bytes_per_launch")
 
 
+def step_latency(t, N, clock):
+    """Per-step latency of the recursions: the stage time t (s) spread over
+    its N dependent steps, in ns and in SM cycles at the sampled clock (Hz),
+    beside the reference floor of one dependent float64 FMA."""
+    return {"ns_per_step": t / N * 1e9, "cycles_per_step": t / N * clock,
+            "floor_cycles_per_step": DFMA_LATENCY_CYCLES}
+
+
 def roofline(stage_ms_per_eval, args, sm_mhz, peaks, precision="mixed"):
     """Roofline object for the dominant stage."""
     import numpy as np
@@ -177,6 +185,7 @@ def roofline(stage_ms_per_eval, args, sm_mhz, peaks, precision="mixed"):
                "achieved": achieved, "peak": peak, "unit": "chain steps/s",
                "frac": achieved / peak,
                "peak_source": f"measured DFMA latency {DFMA_LATENCY_CYCLES} cycles at the sampled SM clock"}
+        obj.update(step_latency(t, N, clock))
     elif name == "prep":
         # positions read once, interior forces written, the per-particle
         # state, and both copies of g (mantissa + int exponent per pair)
@@ -250,6 +259,7 @@ def roofline_stages(stage_ms_per_eval, args, sm_mhz, peaks, unit_peaks, precisio
     rec = roofline([0.0, 1.0, 0.0], args, sm_mhz, peaks, precision)
     rec["achieved"] = N / t_rec
     rec["frac"] = rec["achieved"] / rec["peak"]
+    rec.update(step_latency(t_rec, N, (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6))
     if precision == "fp64":
         prob = {"bound": "fp64", "unit": "float64 ops/s", "achieved": PROB_F64_OPS * pairs / t_prob,
                 "peak": unit_peaks["fp64_fma_per_s"], "peak_source": "library float64 FMA probe (measured)"}
@@ -438,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
         "helium_exchange_evals_per_s": {k: v["value"] for k, v in results["helium"].get("exchange", {}).items()
                                         if isinstance(v, dict) and "value" in v},
         "recursion_frac": roof["frac"] if roof["kernel"] == "recursions" else None,
+        "recursion_cycles_per_step": roof.get("cycles_per_step"),
     }
     return line
 

@@ -33,6 +33,11 @@ def test_roofline_follows_the_dominant_stage(stage_ms, kernel, monkeypatch):
         assert r["achieved"] == pytest.approx(1024 / 0.067e-3)
         assert r["peak"] == pytest.approx(2070e6 / bench.DFMA_LATENCY_CYCLES)
         assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+        # per-step latency: 67 us over 1024 steps at 2070 MHz
+        assert r["ns_per_step"] == pytest.approx(0.067e-3 / 1024 * 1e9)
+        assert r["cycles_per_step"] == pytest.approx(0.067e-3 / 1024 * 2070e6)
+        assert r["floor_cycles_per_step"] == bench.DFMA_LATENCY_CYCLES
+        assert r["frac"] == pytest.approx(r["floor_cycles_per_step"] / r["cycles_per_step"])
     elif kernel == "prep":
         assert r["bound"] == "hbm" and r["unit"] == "GB/s"
         assert r["frac"] == pytest.approx(r["achieved"] / PEAKS["hbm_gbs"])
@@ -159,6 +164,7 @@ def test_every_stage_has_a_roofline_fraction(prec, bound, monkeypatch):
         assert r["frac"] is not None and r["frac"] > 0
     assert st["prep"]["bound"] == "hbm"
     assert st["recursions"]["achieved"] == pytest.approx(1024 / 0.096e-3)
+    assert st["recursions"]["cycles_per_step"] == pytest.approx(0.096e-3 / 1024 * 2070e6)
     assert st["prob_forces"]["bound"] == bound
     pairs = 1024 * 1025 / 2
     if prec == "fp64":
